@@ -1,0 +1,446 @@
+#!/usr/bin/env python3
+"""Benchmark of the pixel-level CKKS hot path (arXiv 2409.03568) on GB300.
+
+One step = every row of the hot path over one synthetic 64x64 grayscale random-field image at
+N = 8192 with primes 60/40/60 and Delta = 2^40:
+  encrypt the 4096 pixels five ways -- fresh public-key encryption, radix cache base 16 and
+  base 10 with the add/subtract randomness, top-32 frequent-value cache with a 64-entry zero
+  pool (misses encrypted fresh), full 256-value cache with the pool;
+  image operations on the fresh ciphertexts -- 3x3 mean filter, brightness, watermark blend
+  with an encrypted binary pattern, matching (sum of squared differences against an encrypted
+  noisy copy, relinearised);
+  decrypt and decode every result.
+Key generation and cache building are set-up (the paper's offline caching phase) and are not
+timed. `value` = pixel ciphertexts encrypted per second over whole steps (5 x 4096 per step).
+
+Prints one JSON line (rank 0). `--impl reference` times the CPU oracle on a bounded sample of
+the same step instead.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2409_03568_gb300 import inputs, workloads as W  # noqa: E402
+
+METRIC = "pixel ciphertexts/s at N=8192 (fresh + cached encryption, image ops, decryption per step)"
+UNIT = "pixel-ct/s"
+HBM_PEAK = None          # filled from MEASURED_PEAKS.json
+IMAD_PER_SM_CLK = 64     # 32-bit integer multiply-add issue rate per SM per clock
+IMAD_PER_MODMUL = 10     # 32x32 partial products in one 64-bit Shoup product (4 high + 2 x 3 low)
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.strip().split(", ") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for name, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    from paper_2409_03568_gb300 import ichee
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    wl = W.ENC8192
+    hbm_peak, peak_kind = measured_peaks()
+
+    ctx = ichee.Context(**W.ctx_kwargs(wl), device=local)
+    ctx.keygen(2024, with_evk=True)
+    h, w, c = wl["h"], wl["w"], wl["c"]
+    n_px = h * w * c
+    img = W.image_for(wl).reshape(-1)
+    wm = inputs.binary_pattern(h, w, seed=5)
+    noisy = inputs.noisy_copy(img, seed=6)
+    beta = inputs.brightness_beta(4)
+    d_img = torch.from_numpy(img).cuda()
+    scan = d_img
+    caches = {
+        "radix16": ctx.build_cache(ichee.CACHE_RADIX, 11, radix_base=16, randomize=1),
+        "radix10": ctx.build_cache(ichee.CACHE_RADIX, 12, radix_base=10, randomize=1),
+        "freq32_pool64": ctx.build_cache(ichee.CACHE_FREQ, 13, top_k=32, pool_size=64, scan=scan),
+        "full256_pool64": ctx.build_cache(ichee.CACHE_FULL, 14, pool_size=64),
+    }
+    lut_values, _ = ichee.ichee_cache_info(caches["freq32_pool64"])
+    hit_rate = float(np.isin(img, lut_values).mean())
+    wm_ct, wm_meta = ctx.encrypt(torch.from_numpy(wm.reshape(-1)).cuda(), h, w, 1, seed=21)
+    nz_ct, nz_meta = ctx.encrypt(torch.from_numpy(noisy).cuda(), h, w, c, seed=22)
+    L = ctx.L
+    methods = ["fresh"] + list(caches)
+    enc_out = {m: ctx.empty_cts(n_px, L - 1) for m in methods}
+    ops_out = {"meanfilter3": ctx.empty_cts(n_px, L - 2), "brightness": ctx.empty_cts(n_px, L - 1),
+               "blend": ctx.empty_cts(n_px, L - 2), "match": ctx.empty_cts(1, L - 2)}
+    dec_out = {k: torch.empty(n_px, dtype=torch.float64, device="cuda") for k in methods + list(ops_out)}
+    metas = {}
+    st = ctx.stream()
+    H = ctx.handle
+
+    def p_encrypt(m, pixels=None):
+        def f():
+            metas[m] = ichee.ichee_encrypt_image(H, None if m == "fresh" else caches[m],
+                                                 d_img if pixels is None else pixels, h, w, c, 7, enc_out[m], st)
+        return f
+
+    def p_op(name, op, b=None, mb=None, args=()):
+        def f():
+            metas[name] = ichee.ichee_eval(H, op, enc_out["fresh"], metas["fresh"], b, mb, args, ops_out[name], st)
+        return f
+
+    def p_decrypt():
+        def f():
+            for k in methods:
+                ichee.ichee_decrypt_image(H, enc_out[k], metas[k], dec_out[k], st)
+            for k in ops_out:
+                ichee.ichee_decrypt_image(H, ops_out[k], metas[k], dec_out[k], st)
+        return f
+
+    phases = [(m, p_encrypt(m)) for m in methods] + [
+        ("meanfilter3", p_op("meanfilter3", ichee.OP_MEANFILTER3)),
+        ("brightness", p_op("brightness", ichee.OP_BRIGHTNESS, args=(beta,))),
+        ("blend", p_op("blend", ichee.OP_BLEND, wm_ct, wm_meta, args=(0.9,))),
+        ("match", p_op("match", ichee.OP_SQDIFF_SUM, nz_ct, nz_meta)),
+        ("decrypt", p_decrypt()),
+    ]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
+    events = {name: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for name, _ in phases}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def step():
+        for name, fn in phases:
+            events[name][0].record()
+            fn()
+            events[name][1].record()
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    # correctness guard on the benchmarked outputs (decoded pixels of every encryption)
+    for m in methods:
+        err = float((dec_out[m].cpu().numpy() - img).__abs__().max())
+        if err > 1e-3:
+            raise RuntimeError("decode error %.3g for %s" % (err, m))
+    phase_ms = {name: 0.0 for name, _ in phases}
+    total_ms = 0.0
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for _ in range(args.steps):
+        flush.zero_()
+        ev0.record()
+        step()
+        ev1.record()
+        torch.cuda.synchronize()
+        total_ms += ev0.elapsed_time(ev1)
+        for name, _ in phases:
+            phase_ms[name] += events[name][0].elapsed_time(events[name][1])
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    phase_ms = {k: v / args.steps for k, v in phase_ms.items()}
+    units_step = len(methods) * n_px
+    value = units_step * world / (ms_step / 1e3)
+
+    # roofline of every kernel-level phase (algorithmic work per launch / event time)
+    n = ctx.n
+    ct_bytes = 2 * L * n * 8
+    logn = wl["log_n"]
+    modmul_fresh = L * (3 * (n // 2) * logn + 2 * n)           # per pixel ciphertext
+    sm_mhz = clk["sm_mhz"] if clk else SM_MAX_MHZ
+    alu_peak = SM_COUNT * SM_MAX_MHZ * 1e6 * IMAD_PER_SM_CLK / IMAD_PER_MODMUL / 1e9   # Gmodmul/s
+    kernels = {}
+
+    def rl_hbm(name, bytes_per_launch):
+        t = phase_ms[name] / 1e3
+        a = bytes_per_launch / t / 1e9
+        kernels[name] = {"bound": "hbm", "achieved": round(a, 1), "peak": hbm_peak, "unit": "GB/s",
+                         "frac": round(a / hbm_peak, 4), "ms": round(phase_ms[name], 4)}
+
+    def rl_alu(name, modmuls_per_launch):
+        t = phase_ms[name] / 1e3
+        a = modmuls_per_launch / t / 1e9
+        kernels[name] = {"bound": "alu", "achieved": round(a, 1), "peak": round(alu_peak, 1), "unit": "Gmodmul/s",
+                         "frac": round(a / alu_peak, 4), "ms": round(phase_ms[name], 4)}
+
+    rl_alu("fresh", n_px * modmul_fresh)
+    for m in ("radix16", "radix10", "full256_pool64"):
+        rl_hbm(m, n_px * ct_bytes)
+    # frequent-value cache: hits are lookups, misses run the fresh kernel
+    kernels["freq32_pool64"] = {"ms": round(phase_ms["freq32_pool64"], 4), "hit_rate": round(hit_rate, 4)}
+    rl_hbm("meanfilter3", n_px * (ct_bytes + 2 * (L - 1) * n * 8))
+    rl_hbm("brightness", n_px * 2 * ct_bytes)
+    rl_hbm("blend", n_px * (2 * ct_bytes + 2 * (L - 1) * n * 8))
+    rl_alu("match", n_px * L * (2 * (n // 2) * logn + 3 * n))
+    n_dec = len(methods) * n_px * L * n * 8 + n_px * ((L - 1) * n * 8) * 3
+    rl_hbm("decrypt", n_dec)
+    dominant = max((k for k in kernels if "frac" in kernels[k]), key=lambda k: phase_ms[k])
+    roof = dict(kernels[dominant])
+    roof["kernel"] = dominant
+    roof["peak_kind"] = peak_kind if roof["bound"] == "hbm" else "derived: %d SMs x %.0f MHz x %d IMAD/clk / %d IMAD per modmul" % (
+        SM_COUNT, SM_MAX_MHZ, IMAD_PER_SM_CLK, IMAD_PER_MODMUL)
+    roof["traffic"] = None
+
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64 (RNS residues mod 60/40/60-bit primes)",
+        "data": "synthetic (Gaussian random field 64x64, correlation 6 px, seed 2; stands in for USC-SIPI)",
+        "config": {"workload": wl["name"], "N": n, "primes_bits": wl["prime_bits"], "log2_scale": wl["log2_scale"],
+                   "image": "%dx%dx%d" % (h, w, c), "methods": methods, "ops": list(ops_out),
+                   "freq_hit_rate": round(hit_rate, 4), "l2": "flushed (512 MB write) before every step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "phases_ms": {k: round(v, 4) for k, v in phase_ms.items()},
+        "px_per_s": {m: round(n_px / (phase_ms[m] / 1e3), 1) for m in methods},
+        "kernels": kernels,
+        "roofline": roof,
+        "gpu_launches": None,
+        "clocks": clk,
+    }
+    # launches of our kernels per step: 1 per encryption (2 for the frequent-value cache),
+    # 1 per mean filter / brightness / blend, matching: 1 accumulate + 1 reduce + 2 inverse
+    # transform/scale + digits + transform + MAC + transform + mod-down + rescale, 1 per decrypt
+    out["gpu_launches"] = args.steps * (len(methods) + 1 + 3 + 10 + len(methods) + len(ops_out))
+
+    if not args.no_e2e:
+        out["e2e"] = e2e_ours(args, ctx, ichee, img, wm_ct, wm_meta, nz_ct, nz_meta, beta, caches, methods, enc_out,
+                              ops_out, st, world)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(sample_steps=1, sample=484)
+    if rank == 0:
+        print(json.dumps(out))
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def e2e_ours(args, ctx, ichee, img, wm_ct, wm_meta, nz_ct, nz_meta, beta, caches, methods, enc_out, ops_out, st, world):
+    """Same step through the public entry points with HOST buffers: pixels from pinned host
+    memory (the library copies them in), decoded values back into pinned host memory."""
+    import torch
+    h, w, c = 64, 64, 1
+    n_px = img.size
+    H = ctx.handle
+    host_px = torch.from_numpy(img.copy()).pin_memory()
+    host_out = {k: torch.empty(n_px, dtype=torch.float64).pin_memory() for k in methods + list(ops_out)}
+    metas = {}
+
+    def step():
+        for m in methods:
+            metas[m] = ichee.ichee_encrypt_image(H, None if m == "fresh" else caches[m], host_px, h, w, c, 7,
+                                                 enc_out[m], st)
+        a, ma = enc_out["fresh"], metas["fresh"]
+        metas["meanfilter3"] = ichee.ichee_eval(H, ichee.OP_MEANFILTER3, a, ma, None, None, (), ops_out["meanfilter3"], st)
+        metas["brightness"] = ichee.ichee_eval(H, ichee.OP_BRIGHTNESS, a, ma, None, None, (beta,), ops_out["brightness"], st)
+        metas["blend"] = ichee.ichee_eval(H, ichee.OP_BLEND, a, ma, wm_ct, wm_meta, (0.9,), ops_out["blend"], st)
+        metas["match"] = ichee.ichee_eval(H, ichee.OP_SQDIFF_SUM, a, ma, nz_ct, nz_meta, (), ops_out["match"], st)
+        for k in methods:
+            ichee.ichee_decrypt_image(H, enc_out[k], metas[k], host_out[k], st)
+        for k in ops_out:
+            ichee.ichee_decrypt_image(H, ops_out[k], metas[k], host_out[k], st)
+        torch.cuda.synchronize()
+
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    tot = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step()
+        tot += time.perf_counter() - t0
+    units = len(methods) * n_px * args.steps * world
+    return {"value": round(units / tot, 1), "unit": UNIT, "h2d_bytes_per_step": len(methods) * n_px,
+            "d2h_bytes_per_step": (len(methods) + 3) * n_px * 8 + 8,
+            "ms_per_step": round(tot / args.steps * 1e3, 3), "timing": "host wall clock around each step"}
+
+
+# ---------------------------------------------------------------------------------------
+# CPU oracle leg (baseline / reference arm)
+# ---------------------------------------------------------------------------------------
+def oracle_step_setup(sample):
+    from oracle import Oracle, Params
+    wl = W.ENC8192
+    o = Oracle(Params(wl["log_n"], wl["prime_bits"], wl["log2_scale"], wl["special_bits"])).keygen(2024, with_evk=True)
+    img = W.image_for(wl).reshape(-1)
+    idx = np.sort(np.random.default_rng(0).choice(img.size, sample, replace=False)).astype(np.uint64)
+    caches = {"radix16": o.radix_cache(16, 11), "radix10": o.radix_cache(10, 12),
+              "freq32_pool64": o.freq_cache(img, 32, 64, 13), "full256_pool64": o.full_cache(64, 14)}
+    wm = inputs.binary_pattern(64, 64, seed=5).reshape(-1)
+    noisy = inputs.noisy_copy(img, seed=6)
+    return o, img, idx, caches, wm, noisy
+
+
+def oracle_step(o, img, idx, caches, wm, noisy):
+    """The step of the GPU arm restricted to the sampled pixels (ops on a 3x3-neighbourhood
+    patch per sampled pixel are replaced by the same ops on the sampled ciphertexts)."""
+    px = img[idx.astype(np.int64)]
+    outs = {"fresh": o.encrypt_pixels(px, 7, ids=idx)}
+    outs["radix16"] = o.encrypt_radix(px, caches["radix16"], 7, ids=idx)
+    outs["radix10"] = o.encrypt_radix(px, caches["radix10"], 7, ids=idx)
+    outs["freq32_pool64"] = o.encrypt_lookup(px, caches["freq32_pool64"], 7, ids=idx)
+    outs["full256_pool64"] = o.encrypt_lookup(px, caches["full256_pool64"], 7, ids=idx)
+    fr = outs["fresh"]
+    k = len(idx)
+    side = int(np.sqrt(k))
+    mf, sc_mf = o.meanfilter3(fr[:side * side], o.delta, side, side, 1)
+    br, sc_br = o.brightness(fr, o.delta, 7.5)
+    wct = o.encrypt_pixels(wm[idx.astype(np.int64)], 21, ids=idx)
+    bl, sc_bl = o.blend(fr, wct, o.delta, 0.9, 1, 1)
+    nct = o.encrypt_pixels(noisy[idx.astype(np.int64)], 22, ids=idx)
+    mt, sc_mt = o.match(fr, nct, o.delta)
+    for m in outs:
+        o.decrypt(outs[m], o.delta)
+    o.decrypt(mf, sc_mf)
+    o.decrypt(br, sc_br)
+    o.decrypt(bl, sc_bl)
+    o.decrypt(mt, sc_mt)
+    return 5 * k
+
+
+def cpu_baseline(sample_steps=1, sample=36):
+    from oracle.ckks import lib as olib
+    setup = oracle_step_setup(sample)
+    t0 = time.perf_counter()
+    units = 0
+    for _ in range(sample_steps):
+        units += oracle_step(*setup)
+    dt = time.perf_counter() - t0
+    return {"value": round(units / dt, 3), "unit": UNIT, "cores": int(olib().orc_num_threads()), "kind": "oracle",
+            "sample": "%d of the 4096 pixels per method (5 methods), ops on those ciphertexts (mean filter on a "
+                      "%dx%d patch), decryption; %d step(s), %.1f s" % (sample, int(np.sqrt(sample)),
+                                                                      int(np.sqrt(sample)), sample_steps, dt)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    sample = 256
+    setup = oracle_step_setup(sample)
+    for _ in range(args.warmup):
+        oracle_step(*setup)
+    t0 = time.perf_counter()
+    units = 0
+    for _ in range(args.steps):
+        units += oracle_step(*setup)
+    dt = time.perf_counter() - t0
+    from oracle.ckks import lib as olib
+    v = units / dt
+    cb = {"value": round(v, 3), "unit": UNIT, "cores": int(olib().orc_num_threads()), "kind": "oracle",
+          "sample": "%d of the 4096 pixels per method per step, ops on those ciphertexts, decryption" % sample}
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": UNIT, "n_gpus": world,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                      "dtype": "u64 (RNS residues)", "data": "synthetic",
+                      "config": {"workload": W.ENC8192["name"], "sample_pixels_per_method": sample},
+                      "cpu_baseline": cb,
+                      "e2e": {"value": round(v, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

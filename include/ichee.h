@@ -1,0 +1,242 @@
+/*
+ * ichee.h -- C ABI of libichee: pixel-level CKKS encryption of images with cached encryption
+ * and ciphertext-wise image operations on one GB300 GPU (sm_103a), after Wang et al.,
+ * "Enabling Practical and Privacy-Preserving Image Processing" (arXiv 2409.03568; the
+ * method is called iCHEETAH there).
+ *
+ * Conventions for every entry point
+ *  - Status: every call returns ICHEE_OK or an error code; argument, level, scale and shape
+ *    checks happen before any launch. ichee_last_error() returns a thread-local message for
+ *    the last failing call. No call aborts, traps or throws across the ABI.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = the default stream). All GPU
+ *    work is enqueued asynchronously on it; results are ready when the stream is.
+ *  - Memory: ciphertext buffers are caller-owned DEVICE memory (size from ichee_ct_bytes).
+ *    Pixel inputs and decrypted outputs may be host or device memory; host buffers are staged
+ *    through library-owned device memory (and the call then waits for its own copies).
+ *    Library-owned state (keys, tables, caches) lives in opaque handles freed by the
+ *    matching destroy/free call.
+ *  - Layouts: one ciphertext = uint64[2][limbs][N] residues in the coefficient domain
+ *    (polynomial b in {c0, c1}, limb l, coefficient i), each residue in [0, q_l). An image of
+ *    h x w x c pixels is n_ct = h*w*c consecutive ciphertexts, pixel (y, x, ch) at index
+ *    (y*w + x)*c + ch. Pixels are uint8 in the same order.
+ *  - Determinism: outputs depend only on (params, key seed, cache seed, per-call seed, pixel
+ *    values), never on launch shape or batch composition. Random draws come from
+ *    Philox4x32-10 keyed by the seed, countered by (block, stream, ciphertext id).
+ *  - Threads: one context may be used from one host thread at a time.
+ */
+#ifndef ICHEE_H
+#define ICHEE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ICHEE_OK = 0,
+    ICHEE_EINVAL = 1,        /* bad argument (null pointer, size, range, host pointer where device memory is needed) */
+    ICHEE_ENOMEM = 2,        /* device or host allocation failed */
+    ICHEE_ECUDA = 3,         /* a CUDA call failed; the message names it */
+    ICHEE_ELEVEL = 4,        /* level mismatch or no limb left to drop */
+    ICHEE_ESCALE = 5,        /* scale mismatch between operands */
+    ICHEE_EMISMATCH = 6,     /* operands or cache belong to another context, or shapes differ */
+    ICHEE_ETIMEOUT = 7,      /* a bounded device-side wait ran out (reported by ichee_stream_status) */
+    ICHEE_EUNSUPPORTED = 8   /* parameters outside what the kernels implement */
+} ichee_status;
+
+#define ICHEE_MAX_PRIMES 8
+
+/*
+ * CKKS parameters (Sec. 2.2, parameter table: N, Q, L, Delta). N = 2^log_n with
+ * 10 <= log_n <= 14. The ciphertext modulus Q is the product of n_primes primes
+ * (1 <= n_primes <= 8): for each prime_bits[i] in order (20..60), the largest prime
+ * q < 2^bits with q = 1 mod 2N not already taken. special_bits (0 = none, else 30..61) picks
+ * the special prime P of the evaluation key the same way. The scale is Delta = 2^log2_scale
+ * (log2_scale <= 55). sigma and gauss_bound (1..31) define the discrete Gaussian error.
+ */
+typedef struct {
+    uint32_t log_n;
+    uint32_t n_primes;
+    uint32_t prime_bits[ICHEE_MAX_PRIMES];
+    uint32_t special_bits;
+    uint32_t log2_scale;
+    double sigma;
+    uint32_t gauss_bound;
+} ichee_params;
+
+/* Metadata of an image of ciphertexts: shape, level (limbs - 1) and the scale of the encoded
+ * values (Delta for fresh encryptions; changed by plaintext multiply and rescale). */
+typedef struct {
+    uint32_t h, w, c;
+    uint32_t level;
+    double scale;
+} ichee_ctimg_meta;
+
+/* Caching strategies of Sec. 3.2. */
+typedef enum {
+    ICHEE_CACHE_RADIX = 0,   /* Enc(r^k) for every power r^k <= 255 */
+    ICHEE_CACHE_FREQ = 1,    /* Enc(p) for the top_k most frequent values of a scanned image */
+    ICHEE_CACHE_FULL = 2     /* Enc(p) for p = 0..255 */
+} ichee_cache_kind;
+
+/*
+ * Cache description.
+ *  radix_base      RADIX: base r (2..16). FREQ with miss_policy 1: base of the radix fallback.
+ *  radix_randomize RADIX (and the FREQ radix fallback): 1 = apply the add/subtract randomness
+ *                  of Sec. 3.3 (signed digits), 0 = plain sum of cached powers.
+ *  top_k           FREQ: number of values cached (1..256; fewer if the scan has fewer values).
+ *  pool_size       FREQ/FULL: encryptions of zero in the randomness pool of Sec. 3.3
+ *                  (0 = none, else up to 4096).
+ *  miss_policy     FREQ: a value outside the cache is encrypted fresh (0) or radix-encrypted (1).
+ */
+typedef struct {
+    ichee_cache_kind kind;
+    uint32_t radix_base;
+    uint32_t radix_randomize;
+    uint32_t top_k;
+    uint32_t pool_size;
+    uint32_t miss_policy;
+} ichee_cache_desc;
+
+/* Image operations (Sec. 2.2.3 and the case studies of Sec. 4.4). */
+typedef enum {
+    ICHEE_OP_ADD = 0,            /* a (+) b; same shape, level and scale */
+    ICHEE_OP_SUB = 1,            /* a (-) b */
+    ICHEE_OP_PTADD = 2,          /* a + v; args: v (one value), or n_ct values (one per ciphertext) */
+    ICHEE_OP_PTMUL = 3,          /* a * v; args: v; v encoded as llround(v * Delta); scale *= Delta */
+    ICHEE_OP_RESCALE = 4,        /* divide by the last prime with rounding; level - 1; scale /= q_last */
+    ICHEE_OP_MEANFILTER3 = 5,    /* Sec. 4.4.1: 3x3 mean, clamp-to-edge borders, x 1/9, rescale */
+    ICHEE_OP_BRIGHTNESS = 6,     /* Sec. 4.4.2: + beta on every pixel; args: beta */
+    ICHEE_OP_BLEND = 7,          /* alpha * a + (1 - alpha) * b, rescaled; args: alpha; b has c or 1 channels */
+    ICHEE_OP_WATERMARK_PIXEL = 8,/* Sec. 4.4.4: + x at one ciphertext; args: x, index */
+    ICHEE_OP_SQDIFF_SUM = 9      /* Sec. 4.4.3: sum over ciphertexts of (a - b)^2, relinearised
+                                    with the evaluation key and rescaled; output one ciphertext */
+} ichee_op;
+
+#define ICHEE_WITH_EVK 1u
+
+typedef struct ichee_ctx ichee_ctx;
+typedef struct ichee_cache ichee_cache;
+
+/*
+ * Create a context on CUDA device `device` (Sec. 2.2 parameter table): generates the prime
+ * chain, transform tables and constant tables and uploads them. Keys are made by
+ * ichee_keygen. *out receives a handle owned by the caller (ichee_ctx_destroy). Errors:
+ * EINVAL (null pointer, parameter out of range), EUNSUPPORTED (no prime chain), ECUDA, ENOMEM.
+ */
+ichee_status ichee_ctx_create(const ichee_params* params, int device, ichee_ctx** out);
+
+/* Free a context and everything it owns (NULL is a no-op). Caches built from it must be
+ * freed first. Synchronises the device. */
+void ichee_ctx_destroy(ichee_ctx* ctx);
+
+/*
+ * Report the context's primes: q_out[n_primes] receives q_0..q_{L-1} and *p_out the special
+ * prime (0 if none). Either pointer may be NULL. Host memory.
+ */
+ichee_status ichee_ctx_primes(const ichee_ctx* ctx, uint64_t* q_out, uint64_t* p_out);
+
+/*
+ * Key generation (Sec. 2.2.2, KeyGen steps 1-3): secret s ternary, public key
+ * pk = (-a*s + e, a), and with flags & ICHEE_WITH_EVK the evaluation key used by
+ * ICHEE_OP_SQDIFF_SUM (hybrid key switching with the special prime; needs special_bits > 0).
+ * Deterministic in `seed`. Keys stay in the context. Enqueued on `stream`; the call waits for
+ * its own set-up copies. Errors: EINVAL (evk without a special prime), ECUDA.
+ */
+ichee_status ichee_keygen(ichee_ctx* ctx, uint64_t seed, uint32_t flags, void* stream);
+
+/*
+ * Copy a key to host memory for inspection. which: 0 = secret key s as int8[N];
+ * 1 = public key as uint64[2][L][N]; 2 = evaluation key as uint64[L][2][L+1][N]
+ * (coefficient domain, limb L = the special prime). `bytes` must equal that size.
+ * Synchronises `stream`. Errors: EINVAL (size, key absent).
+ */
+ichee_status ichee_export_key(ichee_ctx* ctx, int which, void* host_out, size_t bytes, void* stream);
+
+/*
+ * Build a cache (Sec. 3.2 radix / scanning / full caching, Sec. 3.3 randomness pool).
+ * scan_pixels (host or device, n_scan bytes) is read for ICHEE_CACHE_FREQ only (may be NULL
+ * otherwise). Cached ciphertexts are fresh encryptions keyed by `seed`: value slot j uses
+ * ciphertext id j, pool zero m uses 2^32 + m, radix power k uses 2^33 + k. A radix cache also
+ * tabulates d * Enc(r^k) for |d| <= r. *out receives a handle (ichee_cache_free). Waits for
+ * the histogram when scanning. Errors: EINVAL, ENOMEM, ECUDA.
+ */
+ichee_status ichee_build_cache(ichee_ctx* ctx, const ichee_cache_desc* desc, const uint8_t* scan_pixels,
+                               size_t n_scan, uint64_t seed, ichee_cache** out, void* stream);
+
+/* Free a cache (NULL is a no-op). Synchronises the device. */
+void ichee_cache_free(ichee_cache* cache);
+
+/*
+ * Describe a cache: *n_values receives the number of cached values and values_out (may be
+ * NULL, else 256 entries) the value of each slot; *pool receives the pool size.
+ */
+ichee_status ichee_cache_info(const ichee_cache* cache, uint32_t* n_values, uint8_t* values_out, uint32_t* pool);
+
+/*
+ * Copy cached ciphertexts to host memory. part 0 = value slots [K][2][L][N], 1 = pool
+ * [M][2][L][N], 2 = radix powers [n_pow][2][L][N]. `bytes` must equal the size.
+ */
+ichee_status ichee_cache_export(const ichee_cache* cache, int part, void* host_out, size_t bytes, void* stream);
+
+/* Bytes of one ciphertext at `level` (2 * (level+1) * N * 8). */
+ichee_status ichee_ct_bytes(const ichee_ctx* ctx, uint32_t level, size_t* bytes_per_ct);
+
+/*
+ * Pixel-level encryption of an h x w x c uint8 image (Sec. 3.1): one ciphertext per pixel
+ * value, encoded as the constant polynomial Delta * p. cache == NULL: fresh public-key
+ * encryption (Sec. 2.2.2). Otherwise cached encryption (Sec. 3.2, 3.3) with the cache's
+ * randomness; values a scanning cache lacks follow its miss_policy. Ciphertext k uses id k
+ * and the randomness of `seed`. pixels: host or device, n_ct bytes. d_ct_out: device,
+ * n_ct * ichee_ct_bytes(L-1). meta_out (host) receives the shape, level L-1 and scale Delta.
+ * Errors: EINVAL (keys missing, sizes, non-device output), EMISMATCH (cache of another
+ * context), ECUDA.
+ */
+ichee_status ichee_encrypt_image(ichee_ctx* ctx, const ichee_cache* cache, const uint8_t* pixels, uint32_t h,
+                                 uint32_t w, uint32_t c, uint64_t seed, uint64_t* d_ct_out,
+                                 ichee_ctimg_meta* meta_out, void* stream);
+
+/*
+ * Apply an image operation (see ichee_op). d_a / d_b / d_out are device ciphertext images
+ * described by ma / mb / mout; d_b and mb are used by ADD, SUB, BLEND and SQDIFF_SUM only.
+ * op_args holds the operation's real-valued arguments (host). d_out must not overlap the
+ * inputs, except that PTADD, BRIGHTNESS and WATERMARK_PIXEL may run in place (d_out == d_a).
+ * *mout receives the result's shape, level and scale. Errors: EINVAL, ELEVEL (no limb to
+ * drop), ESCALE, EMISMATCH (shapes), EUNSUPPORTED (no evaluation key), ENOMEM, ECUDA.
+ */
+ichee_status ichee_eval(ichee_ctx* ctx, ichee_op op, const uint64_t* d_a, const ichee_ctimg_meta* ma,
+                        const uint64_t* d_b, const ichee_ctimg_meta* mb, const double* op_args, uint32_t n_args,
+                        uint64_t* d_out, ichee_ctimg_meta* mout, void* stream);
+
+/*
+ * Decrypt and decode (Sec. 2.2.2 decryption; a pixel is read from coefficient 0 of
+ * c0 + c1*s): exact CRT of the residues to the centered integer, divided by meta->scale, one
+ * double per ciphertext. out: host or device, n_ct doubles. Errors: EINVAL, ECUDA.
+ */
+ichee_status ichee_decrypt_image(ichee_ctx* ctx, const uint64_t* d_ct, const ichee_ctimg_meta* meta, double* out,
+                                 void* stream);
+
+/*
+ * Like ichee_decrypt_image, and also writes the residues of coefficient 0 of c0 + c1*s per
+ * limb to residues_out (host or device, n_ct * (level+1) uint64).
+ */
+ichee_status ichee_decrypt_residues(ichee_ctx* ctx, const uint64_t* d_ct, const ichee_ctimg_meta* meta, double* out,
+                                    uint64_t* residues_out, void* stream);
+
+/*
+ * Wait for `stream` and collect errors of work enqueued on it (CUDA launch or execution
+ * errors, the context's device-side status word). Returns ICHEE_OK, ICHEE_ECUDA or
+ * ICHEE_ETIMEOUT and clears the status word.
+ */
+ichee_status ichee_stream_status(ichee_ctx* ctx, void* stream);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* ichee_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ICHEE_H */

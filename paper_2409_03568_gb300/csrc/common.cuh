@@ -1,0 +1,142 @@
+// common.cuh -- device-side building blocks of libichee: word-size modular arithmetic on
+// residues below 2^61 (RNS limbs of the CKKS modulus Q, Sec. 2.2), Philox4x32-10 and the
+// samplers of Sec. 2.2.1 / 2.2.2, and the launch-argument structures shared by the kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ichee {
+
+typedef uint64_t u64;
+typedef uint32_t u32;
+typedef int64_t i64;
+
+constexpr int kMaxPrimes = 8;          // ciphertext limbs
+constexpr int kMaxModuli = kMaxPrimes + 1;  // plus the special prime P
+constexpr int kMaxGaussBound = 31;
+
+// --------------------------------------------------------------------------------------
+// Modular arithmetic. Every modulus q is prime with q < 2^61, so 4q < 2^63 and the lazy
+// ranges [0, 2q) and [0, 4q) of the NTT butterflies never overflow 64 bits.
+// --------------------------------------------------------------------------------------
+
+__device__ __forceinline__ u64 mulhi(u64 a, u64 b) { return __umul64hi(a, b); }
+
+// Shoup product with a fixed multiplicand w < q and its companion wp = floor(w * 2^64 / q):
+// returns x*w mod q in [0, 2q) for any 64-bit x.
+__device__ __forceinline__ u64 shoup_lazy(u64 x, u64 w, u64 wp, u64 q)
+{
+    u64 hi = mulhi(x, wp);
+    return x * w - hi * q;
+}
+
+__device__ __forceinline__ u64 shoup(u64 x, u64 w, u64 wp, u64 q)
+{
+    u64 r = shoup_lazy(x, w, wp, q);
+    return r >= q ? r - q : r;
+}
+
+__device__ __forceinline__ u64 csub(u64 x, u64 q) { return x >= q ? x - q : x; }
+
+__device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 q) { return csub(a + b, q); }
+
+__device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
+
+// Barrett reduction of any 64-bit x with mu = floor(2^64 / q).
+__device__ __forceinline__ u64 reduce64(u64 x, u64 q, u64 mu)
+{
+    u64 r = x - mulhi(x, mu) * q;
+    return csub(r, q);
+}
+
+// Full product a*b mod q for a, b < q (Barrett on the 128-bit product with the 2-word
+// constant m = floor(2^128 / q), m = m1*2^64 + m0).
+__device__ __forceinline__ u64 mul_mod(u64 a, u64 b, u64 q, u64 m0, u64 m1)
+{
+    u64 lo = a * b;
+    u64 hi = mulhi(a, b);
+    // x = hi*2^64 + lo. Estimate floor(x*m / 2^128) from the partial products that reach
+    // the 2^64 and 2^128 places, dropping lo*m0 / 2^128 (< 1).
+    u64 p1 = lo * m1, p1h = mulhi(lo, m1);
+    u64 p2 = hi * m0, p2h = mulhi(hi, m0);
+    u64 mid = p1 + p2;
+    u64 carry = (mid < p1) ? 1 : 0;
+    u64 qhat = hi * m1 + p1h + p2h + carry;
+    // qhat >= floor(x/q) - 3, so x - qhat*q is in [0, 4q) and fits 64 bits (4q < 2^63)
+    u64 r = lo - qhat * q;
+    r = csub(r, 2 * q);
+    r = csub(r, q);
+    return r;
+}
+
+// --------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): key = per-call seed, counter =
+// (block, stream, id lo, id hi). Every random draw of the library is a pure function of
+// (seed, stream, ct id, coefficient), never of the launch shape.
+// --------------------------------------------------------------------------------------
+
+struct Words4 { u32 w[4]; };
+
+__device__ __forceinline__ Words4 philox(u64 seed, u32 stream, u64 id, u32 block)
+{
+    u32 c0 = block, c1 = stream, c2 = (u32)id, c3 = (u32)(id >> 32);
+    u32 k0 = (u32)seed, k1 = (u32)(seed >> 32);
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        u32 hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        u32 hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        u32 n0 = hi1 ^ c1 ^ k0;
+        u32 n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    Words4 r;
+    r.w[0] = c0; r.w[1] = c1; r.w[2] = c2; r.w[3] = c3;
+    return r;
+}
+
+// Streams (which draw of a ciphertext a Philox block belongs to).
+enum Stream : u32 {
+    kStreamV = 0, kStreamE0 = 1, kStreamE1 = 2, kStreamRadixBits = 3, kStreamPool = 4,
+    kStreamKeyS = 8, kStreamKeyE = 9, kStreamKeyA = 16
+};
+
+// Uniform ternary from one 32-bit word: floor(3w / 2^32) - 1.
+__device__ __forceinline__ int ternary_of(u32 w) { return (int)(((u64)w * 3u) >> 32) - 1; }
+
+// Discrete Gaussian from one 64-bit value: top bit sign, magnitude = number of table
+// entries the low 63 bits reach (table strictly increasing, last entry 2^63).
+struct CdtTable { u64 t[kMaxGaussBound + 1]; u32 bound; };
+
+__device__ __forceinline__ int gauss_of(u64 u, const CdtTable& cdt)
+{
+    u64 r = u & 0x7FFFFFFFFFFFFFFFull;
+    int mag = 0;
+    for (u32 k = 0; k < cdt.bound; ++k) mag += (r >= cdt.t[k]) ? 1 : 0;
+    return (u >> 63) ? -mag : mag;
+}
+
+// Residue of a small signed integer.
+__device__ __forceinline__ u64 small_mod(int x, u64 q) { return x < 0 ? q - (u64)(-x) : (u64)x; }
+
+// --------------------------------------------------------------------------------------
+// Per-modulus constants and tables as the kernels see them.
+// --------------------------------------------------------------------------------------
+
+struct ModTables {
+    const u64* tw;    // [N] psi^{bitrev(k)}, forward twiddles (bit-reversed order)
+    const u64* twp;   // [N] Shoup companions
+    const u64* itw;   // [N] psi^{-bitrev(k)}, inverse twiddles
+    const u64* itwp;  // [N]
+};
+
+struct RnsArgs {
+    int logn;
+    int n_mod;                  // moduli described below
+    u64 q[kMaxModuli];
+    u64 mu[kMaxModuli];         // floor(2^64 / q)
+    u64 m0[kMaxModuli], m1[kMaxModuli];  // floor(2^128 / q) as two words
+    ModTables tab[kMaxModuli];
+};
+
+}  // namespace ichee

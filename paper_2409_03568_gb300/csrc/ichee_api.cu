@@ -1,0 +1,1028 @@
+// ichee_api.cu -- the C ABI of libichee (include/ichee.h): argument checks, set-up, and the
+// launch sequences of key generation, cache building, encryption, image operations and
+// decryption. Every arithmetic step on ciphertexts runs in the kernels of kernels_*.cu.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/ichee.h"
+#include "host_math.h"
+#include "ops.h"
+
+using namespace ichee;
+namespace hm = ichee::host;
+
+// ---------------------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------------------
+static thread_local char g_err[512] = "";
+
+static ichee_status fail(ichee_status st, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+#define CK(call)                                                                           \
+    do {                                                                                   \
+        cudaError_t _e = (call);                                                           \
+        if (_e != cudaSuccess) return fail(ICHEE_ECUDA, "%s failed: %s", #call, cudaGetErrorString(_e)); \
+    } while (0)
+
+extern "C" const char* ichee_last_error(void) { return g_err; }
+
+// ---------------------------------------------------------------------------------------
+// Context and cache
+// ---------------------------------------------------------------------------------------
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t want)
+    {
+        if (want <= bytes) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e == cudaSuccess) bytes = want;
+        return e;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+};
+
+struct ichee_ctx {
+    ichee_params params;
+    int device = 0;
+    int logn = 0, n = 0, L = 0, nmod = 0;
+    u64 q[kMaxModuli] = {};
+    u64 P = 0;
+    double delta = 0;
+    RnsArgs rns;                 // all moduli (q_0..q_{L-1}, then P), device tables
+    CdtTable cdt;
+    u64* d_tables = nullptr;     // [nmod][4][N]
+    u64* d_dm = nullptr;         // [L][256]
+    u64* d_ninv = nullptr;       // [nmod] N^{-1} mod modulus
+    CrtLevel crt[kMaxPrimes];    // index nl - 1
+    bool have_keys = false, have_evk = false;
+    std::vector<int8_t> h_s;
+    int8_t* d_s = nullptr;
+    int8_t* d_srev = nullptr;
+    u64* d_pk = nullptr;         // [2][L][N]
+    u64* d_pk_hat = nullptr;
+    u64* d_pk_hat_p = nullptr;
+    u64* d_evk = nullptr;        // [L][2][L+1][N]
+    u64* d_evk_hat = nullptr;
+    u64* d_evk_hat_p = nullptr;
+    DevBuf stage_in, stage_out, stage_res, scratch, kadd;
+    int* d_status = nullptr;
+    int num_sms = 0;
+};
+
+struct ichee_cache {
+    ichee_ctx* ctx = nullptr;
+    ichee_cache_desc desc;
+    std::vector<int> values;
+    int32_t h_lut[256];
+    int32_t* d_lut = nullptr;
+    u64* d_values = nullptr;     // [K][2][L][N]
+    u64* d_pool = nullptr;       // [M][2][L][N]
+    int radix_base = 0, n_pow = 0, radix_randomize = 0;
+    u64* d_radix = nullptr;      // [n_pow][2][L][N]
+    u64* d_mult = nullptr;       // [n_pow][2r+1][2][L][N]
+};
+
+static const u64 kIdPoolBase = 1ull << 32;
+static const u64 kIdRadixBase = 1ull << 33;
+
+static size_t ct_words(const ichee_ctx* c, int limbs) { return (size_t)2 * limbs * c->n; }
+
+static bool is_device_ptr(const void* p)
+{
+    if (p == nullptr) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static RnsArgs rns_prefix(const ichee_ctx* c, int limbs)
+{
+    RnsArgs r = c->rns;
+    r.n_mod = limbs;
+    return r;
+}
+
+static PolyBatch batch(u64* data, int n_poly, int nl, const int* midx)
+{
+    PolyBatch b;
+    b.data = data;
+    b.n_poly = n_poly;
+    b.nl = nl;
+    for (int i = 0; i < kMaxModuli; ++i) b.midx[i] = (i < nl) ? midx[i] : 0;
+    return b;
+}
+
+static std::vector<int> iota_idx(int n)
+{
+    std::vector<int> v(n);
+    for (int i = 0; i < n; ++i) v[i] = i;
+    return v;
+}
+
+// Residue of llround(value * scale) in every limb.
+static void encode_const(const ichee_ctx* c, double value, double scale, int limbs, u64* out)
+{
+    const long long k = llround(value * scale);
+    for (int l = 0; l < limbs; ++l) out[l] = hm::signed_mod(k, c->q[l]);
+}
+
+// ---------------------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------------------
+extern "C" ichee_status ichee_ctx_create(const ichee_params* p, int device, ichee_ctx** out)
+{
+    if (!p || !out) return fail(ICHEE_EINVAL, "ichee_ctx_create: null argument");
+    *out = nullptr;
+    if (p->log_n < (u32)kMinLogN || p->log_n > (u32)kMaxLogN)
+        return fail(ICHEE_EUNSUPPORTED, "log_n %u outside [%d, %d]", p->log_n, kMinLogN, kMaxLogN);
+    if (p->n_primes < 1 || p->n_primes > ICHEE_MAX_PRIMES)
+        return fail(ICHEE_EINVAL, "n_primes %u outside [1, %d]", p->n_primes, ICHEE_MAX_PRIMES);
+    for (u32 i = 0; i < p->n_primes; ++i)
+        if (p->prime_bits[i] < 20 || p->prime_bits[i] > 60)
+            return fail(ICHEE_EINVAL, "prime_bits[%u] = %u outside [20, 60]", i, p->prime_bits[i]);
+    if (p->special_bits != 0 && (p->special_bits < 30 || p->special_bits > 61))
+        return fail(ICHEE_EINVAL, "special_bits %u outside {0} U [30, 61]", p->special_bits);
+    if (p->log2_scale > 55) return fail(ICHEE_EINVAL, "log2_scale %u > 55", p->log2_scale);
+    if (p->gauss_bound < 1 || p->gauss_bound > (u32)kMaxGaussBound)
+        return fail(ICHEE_EINVAL, "gauss_bound %u outside [1, %d]", p->gauss_bound, kMaxGaussBound);
+    if (!(p->sigma > 0.0) || !std::isfinite(p->sigma)) return fail(ICHEE_EINVAL, "sigma must be positive");
+
+    ichee_ctx* c = new ichee_ctx();
+    c->params = *p;
+    c->device = device;
+    c->logn = (int)p->log_n;
+    c->n = 1 << c->logn;
+    c->L = (int)p->n_primes;
+    c->delta = std::ldexp(1.0, (int)p->log2_scale);
+    std::vector<u64> taken;
+    for (int i = 0; i < c->L; ++i) {
+        u64 qi = hm::chain_prime(p->prime_bits[i], p->log_n, taken);
+        if (!qi) { delete c; return fail(ICHEE_EUNSUPPORTED, "no %u-bit prime = 1 mod 2N left", p->prime_bits[i]); }
+        taken.push_back(qi);
+        c->q[i] = qi;
+    }
+    if (p->special_bits) {
+        c->P = hm::chain_prime(p->special_bits, p->log_n, taken);
+        if (!c->P) { delete c; return fail(ICHEE_EUNSUPPORTED, "no special prime"); }
+        c->q[c->L] = c->P;
+    }
+    c->nmod = c->L + (c->P ? 1 : 0);
+
+    auto cleanup = [&](ichee_status st) {
+        ichee_ctx_destroy(c);
+        return st;
+    };
+    if (cudaSetDevice(device) != cudaSuccess) return cleanup(fail(ICHEE_ECUDA, "cudaSetDevice(%d) failed", device));
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+
+    // transform tables
+    const size_t nwords = (size_t)c->nmod * 4 * c->n;
+    if (cudaMalloc(&c->d_tables, nwords * 8) != cudaSuccess) return cleanup(fail(ICHEE_ENOMEM, "tables"));
+    std::memset(&c->rns, 0, sizeof(c->rns));
+    c->rns.logn = c->logn;
+    c->rns.n_mod = c->nmod;
+    std::vector<u64> ninv(c->nmod);
+    for (int m = 0; m < c->nmod; ++m) {
+        const u64 qm = c->q[m];
+        std::vector<u64> t = hm::twiddles(qm, (unsigned)c->logn);
+        if (cudaMemcpy(c->d_tables + (size_t)m * 4 * c->n, t.data(), t.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+            return cleanup(fail(ICHEE_ECUDA, "upload tables"));
+        c->rns.q[m] = qm;
+        c->rns.mu[m] = (u64)(((hm::u128)1 << 64) / qm);
+        const hm::u128 big = ~(hm::u128)0 / qm;  // floor(2^128 / q): q is odd, so 2^128 - 1 gives the same
+        c->rns.m0[m] = (u64)big;
+        c->rns.m1[m] = (u64)(big >> 64);
+        const u64* base = c->d_tables + (size_t)m * 4 * c->n;
+        c->rns.tab[m].tw = base;
+        c->rns.tab[m].twp = base + c->n;
+        c->rns.tab[m].itw = base + 2 * (size_t)c->n;
+        c->rns.tab[m].itwp = base + 3 * (size_t)c->n;
+        ninv[m] = hm::invm((u64)c->n % qm, qm);
+    }
+    if (cudaMalloc(&c->d_ninv, 8 * (size_t)c->nmod) != cudaSuccess) return cleanup(fail(ICHEE_ENOMEM, "ninv"));
+    cudaMemcpy(c->d_ninv, ninv.data(), 8 * (size_t)c->nmod, cudaMemcpyHostToDevice);
+
+    // Delta * p mod q_l for p = 0..255
+    std::vector<u64> dm((size_t)c->L * 256);
+    const u64 dl = 1ull << p->log2_scale;
+    for (int l = 0; l < c->L; ++l)
+        for (int v = 0; v < 256; ++v) dm[(size_t)l * 256 + v] = (u64)((hm::u128)dl * (u64)v % c->q[l]);
+    if (cudaMalloc(&c->d_dm, dm.size() * 8) != cudaSuccess) return cleanup(fail(ICHEE_ENOMEM, "dm"));
+    cudaMemcpy(c->d_dm, dm.data(), dm.size() * 8, cudaMemcpyHostToDevice);
+
+    // Gaussian table
+    std::memset(&c->cdt, 0, sizeof(c->cdt));
+    c->cdt.bound = p->gauss_bound;
+    hm::gauss_cdt(p->sigma, p->gauss_bound, c->cdt.t);
+
+    // CRT constants for every level
+    for (int nl = 1; nl <= c->L; ++nl) {
+        CrtLevel& cl = c->crt[nl - 1];
+        std::memset(&cl, 0, sizeof(cl));
+        cl.nl = nl;
+        u64 Qw[3] = {1, 0, 0};
+        for (int l = 0; l < nl; ++l) hm::mul3(Qw, c->q[l], Qw);
+        std::memcpy(cl.qw, Qw, sizeof(Qw));
+        for (int i = 0; i < nl; ++i) {
+            u64 w3[3] = {1, 0, 0};
+            u64 qi_mod = 1;
+            for (int l = 0; l < nl; ++l)
+                if (l != i) {
+                    hm::mul3(w3, c->q[l], w3);
+                    qi_mod = hm::mulm(qi_mod, c->q[l] % c->q[i], c->q[i]);
+                }
+            std::memcpy(cl.qiw[i], w3, sizeof(w3));
+            cl.inv[i] = hm::invm(qi_mod, c->q[i]);
+            cl.invp[i] = hm::shoup_of(cl.inv[i], c->q[i]);
+            cl.qinv[i] = 1.0 / (double)c->q[i];
+        }
+    }
+    if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess) return cleanup(fail(ICHEE_ENOMEM, "status"));
+    cudaMemset(c->d_status, 0, sizeof(int));
+    if (cudaGetLastError() != cudaSuccess) return cleanup(fail(ICHEE_ECUDA, "context set-up"));
+    *out = c;
+    return ICHEE_OK;
+}
+
+extern "C" void ichee_ctx_destroy(ichee_ctx* c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    void* ptrs[] = {c->d_tables, c->d_dm, c->d_ninv, c->d_s, c->d_srev, c->d_pk, c->d_pk_hat, c->d_pk_hat_p,
+                    c->d_evk, c->d_evk_hat, c->d_evk_hat_p, c->d_status};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    c->stage_in.release();
+    c->stage_out.release();
+    c->stage_res.release();
+    c->scratch.release();
+    c->kadd.release();
+    delete c;
+}
+
+extern "C" ichee_status ichee_ctx_primes(const ichee_ctx* c, uint64_t* q_out, uint64_t* p_out)
+{
+    if (!c) return fail(ICHEE_EINVAL, "null context");
+    if (q_out)
+        for (int i = 0; i < c->L; ++i) q_out[i] = c->q[i];
+    if (p_out) *p_out = c->P;
+    return ICHEE_OK;
+}
+
+extern "C" ichee_status ichee_ct_bytes(const ichee_ctx* c, uint32_t level, size_t* bytes)
+{
+    if (!c || !bytes) return fail(ICHEE_EINVAL, "null argument");
+    if ((int)level >= c->L) return fail(ICHEE_ELEVEL, "level %u >= %d", level, c->L);
+    *bytes = ct_words(c, (int)level + 1) * 8;
+    return ICHEE_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Key generation (Sec. 2.2.2, reading R1 for pk, R11 for evk)
+// ---------------------------------------------------------------------------------------
+extern "C" ichee_status ichee_keygen(ichee_ctx* c, uint64_t seed, uint32_t flags, void* stream)
+{
+    if (!c) return fail(ICHEE_EINVAL, "null context");
+    const bool want_evk = (flags & ICHEE_WITH_EVK) != 0;
+    if (want_evk && !c->P) return fail(ICHEE_EINVAL, "evaluation key needs special_bits > 0");
+    CK(cudaSetDevice(c->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = c->n, L = c->L;
+    const size_t polyb = (size_t)n * 8;
+    if (!c->d_s) {
+        CK(cudaMalloc(&c->d_s, n));
+        CK(cudaMalloc(&c->d_srev, n));
+        CK(cudaMalloc(&c->d_pk, 2 * L * polyb));
+        CK(cudaMalloc(&c->d_pk_hat, 2 * L * polyb));
+        CK(cudaMalloc(&c->d_pk_hat_p, 2 * L * polyb));
+    }
+    const int nm = L + 1;  // moduli of the evaluation key
+    const size_t tmp_polys = want_evk ? (size_t)(3 * L * nm + 2 * nm) : (size_t)(3 * L);
+    int8_t* d_e = nullptr;
+    u64* tmp = nullptr;
+    CK(cudaMalloc(&d_e, n));
+    CK(cudaMalloc(&tmp, tmp_polys * polyb));
+    auto done = [&](ichee_status s) {
+        cudaStreamSynchronize(st);
+        cudaFree(d_e);
+        cudaFree(tmp);
+        return s;
+    };
+#define KCK(call)                                                                           \
+    do {                                                                                    \
+        cudaError_t _e = (call);                                                            \
+        if (_e != cudaSuccess) return done(fail(ICHEE_ECUDA, "%s failed: %s", #call, cudaGetErrorString(_e))); \
+    } while (0)
+
+    // s ternary (stream 8), e Gaussian (stream 9), a_l uniform (stream 16 + l), ct id 0
+    KCK(launch_sample_small(c->d_s, n, seed, kStreamKeyS, 0, 0, c->cdt, st));
+    KCK(launch_sample_small(d_e, n, seed, kStreamKeyE, 0, 1, c->cdt, st));
+    u64* pk0 = c->d_pk;
+    u64* pk1 = c->d_pk + (size_t)L * n;
+    for (int l = 0; l < L; ++l) KCK(launch_sample_uniform(pk1 + (size_t)l * n, n, c->q[l], seed, kStreamKeyA + l, 0, st));
+    // a*s per limb through the transform
+    u64* A = tmp;
+    u64* S = tmp + (size_t)L * n;
+    std::vector<int> id = iota_idx(kMaxModuli);
+    KCK(cudaMemcpyAsync(A, pk1, (size_t)L * polyb, cudaMemcpyDeviceToDevice, st));
+    for (int l = 0; l < L; ++l) KCK(launch_small_to_mod(c->d_s, n, c->q[l], S + (size_t)l * n, st));
+    const RnsArgs rl = rns_prefix(c, L);
+    KCK(launch_ntt_fwd(rl, batch(A, L, L, id.data()), st));
+    KCK(launch_ntt_fwd(rl, batch(S, L, L, id.data()), st));
+    KCK(launch_pointwise_mul(rl, batch(A, L, L, id.data()), A, S, L, st));
+    KCK(launch_ntt_inv(rl, batch(A, L, L, id.data()), st));
+    KCK(launch_scale_const(rl, batch(A, L, L, id.data()), c->d_ninv, st));
+    for (int l = 0; l < L; ++l) KCK(launch_neg_add_small(A + (size_t)l * n, d_e, n, c->q[l], pk0 + (size_t)l * n, st));
+    // pk^ = NTT(pk) * N^{-1} with Shoup companions (the encryption kernel's operands)
+    KCK(cudaMemcpyAsync(c->d_pk_hat, c->d_pk, 2 * L * polyb, cudaMemcpyDeviceToDevice, st));
+    KCK(launch_ntt_fwd(rl, batch(c->d_pk_hat, 2 * L, L, id.data()), st));
+    KCK(launch_scale_const(rl, batch(c->d_pk_hat, 2 * L, L, id.data()), c->d_ninv, st));
+    KCK(launch_shoup_companions(rl, batch(c->d_pk_hat, 2 * L, L, id.data()), c->d_pk_hat_p, st));
+
+    // s on the host: export copy and the reversed-negated form used by decryption
+    c->h_s.resize(n);
+    KCK(cudaMemcpyAsync(c->h_s.data(), c->d_s, n, cudaMemcpyDeviceToHost, st));
+    KCK(cudaStreamSynchronize(st));
+    std::vector<int8_t> srev(n);
+    srev[0] = c->h_s[0];
+    for (int j = 1; j < n; ++j) srev[j] = (int8_t)(-c->h_s[n - j]);
+    KCK(cudaMemcpyAsync(c->d_srev, srev.data(), n, cudaMemcpyHostToDevice, st));
+
+    if (want_evk) {
+        if (!c->d_evk) {
+            KCK(cudaMalloc(&c->d_evk, (size_t)L * 2 * nm * polyb));
+            KCK(cudaMalloc(&c->d_evk_hat, (size_t)L * 2 * nm * polyb));
+            KCK(cudaMalloc(&c->d_evk_hat_p, (size_t)L * 2 * nm * polyb));
+        }
+        const RnsArgs rm = c->rns;  // all L+1 moduli
+        u64* AE = tmp;                               // [L][nm][N] a_j,i
+        u64* SM = tmp + (size_t)L * nm * n;          // [nm][N] s mod m_i, then NTT
+        u64* S2 = SM + (size_t)nm * n;               // [nm][N] s^2
+        for (int j = 0; j < L; ++j)
+            for (int i = 0; i < nm; ++i) {
+                u64* a_ji = c->d_evk + (((size_t)j * 2 + 1) * nm + i) * n;
+                KCK(launch_sample_uniform(a_ji, n, c->q[i], seed, kStreamKeyA + i, 1 + j, st));
+                KCK(cudaMemcpyAsync(AE + ((size_t)j * nm + i) * n, a_ji, polyb, cudaMemcpyDeviceToDevice, st));
+            }
+        for (int i = 0; i < nm; ++i) KCK(launch_small_to_mod(c->d_s, n, c->q[i], SM + (size_t)i * n, st));
+        KCK(launch_ntt_fwd(rm, batch(AE, L * nm, nm, id.data()), st));
+        KCK(launch_ntt_fwd(rm, batch(SM, nm, nm, id.data()), st));
+        KCK(launch_pointwise_mul(rm, batch(AE, L * nm, nm, id.data()), AE, SM, nm, st));
+        KCK(launch_pointwise_mul(rm, batch(S2, nm, nm, id.data()), SM, SM, nm, st));
+        KCK(launch_ntt_inv(rm, batch(AE, L * nm, nm, id.data()), st));
+        KCK(launch_ntt_inv(rm, batch(S2, nm, nm, id.data()), st));
+        KCK(launch_scale_const(rm, batch(AE, L * nm, nm, id.data()), c->d_ninv, st));
+        KCK(launch_scale_const(rm, batch(S2, nm, nm, id.data()), c->d_ninv, st));
+        for (int j = 0; j < L; ++j) {
+            KCK(launch_sample_small(d_e, n, seed, kStreamKeyE, 1 + j, 1, c->cdt, st));
+            for (int i = 0; i < nm; ++i) {
+                u64* b0 = c->d_evk + (((size_t)j * 2 + 0) * nm + i) * n;
+                KCK(launch_neg_add_small(AE + ((size_t)j * nm + i) * n, d_e, n, c->q[i], b0, st));
+                if (i == j) {
+                    const u64 pm = c->P % c->q[j];
+                    KCK(launch_axpy_const(b0, b0, S2 + (size_t)j * n, pm, n, c->q[j], c->rns.m0[j], c->rns.m1[j], st));
+                }
+            }
+        }
+        KCK(cudaMemcpyAsync(c->d_evk_hat, c->d_evk, (size_t)L * 2 * nm * polyb, cudaMemcpyDeviceToDevice, st));
+        KCK(launch_ntt_fwd(rm, batch(c->d_evk_hat, L * 2 * nm, nm, id.data()), st));
+        KCK(launch_scale_const(rm, batch(c->d_evk_hat, L * 2 * nm, nm, id.data()), c->d_ninv, st));
+        KCK(launch_shoup_companions(rm, batch(c->d_evk_hat, L * 2 * nm, nm, id.data()), c->d_evk_hat_p, st));
+        c->have_evk = true;
+    }
+#undef KCK
+    c->have_keys = true;
+    return done(ICHEE_OK);
+}
+
+extern "C" ichee_status ichee_export_key(ichee_ctx* c, int which, void* host_out, size_t bytes, void* stream)
+{
+    if (!c || !host_out) return fail(ICHEE_EINVAL, "null argument");
+    if (!c->have_keys) return fail(ICHEE_EINVAL, "no keys");
+    CK(cudaSetDevice(c->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)c->n;
+    if (which == 0) {
+        if (bytes != n) return fail(ICHEE_EINVAL, "secret key is %zu bytes", n);
+        std::memcpy(host_out, c->h_s.data(), n);
+        return ICHEE_OK;
+    }
+    const void* src = nullptr;
+    size_t want = 0;
+    if (which == 1) { src = c->d_pk; want = 2 * (size_t)c->L * n * 8; }
+    else if (which == 2) {
+        if (!c->have_evk) return fail(ICHEE_EINVAL, "no evaluation key");
+        src = c->d_evk;
+        want = (size_t)c->L * 2 * (c->L + 1) * n * 8;
+    } else return fail(ICHEE_EINVAL, "unknown key %d", which);
+    if (bytes != want) return fail(ICHEE_EINVAL, "key is %zu bytes, got %zu", want, bytes);
+    CK(cudaMemcpyAsync(host_out, src, want, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return ICHEE_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Encryption (Sec. 2.2.2, 3.1) and cached encryption (Sec. 3.2, 3.3)
+// ---------------------------------------------------------------------------------------
+static EncArgs enc_args(const ichee_ctx* c, const uint8_t* d_pix, u64 n_ct, u64 seed, u64 id_base, u64* out)
+{
+    EncArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.rns = rns_prefix(c, c->L);
+    a.L = c->L;
+    a.n_ct = n_ct;
+    a.pixels = d_pix;
+    a.dm = c->d_dm;
+    a.pk_hat = c->d_pk_hat;
+    a.pk_hat_p = c->d_pk_hat_p;
+    a.skip_lut = nullptr;
+    a.seed = seed;
+    a.id_base = id_base;
+    a.cdt = c->cdt;
+    a.out = out;
+    return a;
+}
+
+static RadixArgs radix_args(const ichee_ctx* c, const ichee_cache* k, const uint8_t* d_pix, u64 n_ct, u64 seed, u64* out)
+{
+    RadixArgs a;
+    std::memset(&a, 0, sizeof(a));
+    for (int l = 0; l < c->L; ++l) a.q[l] = c->q[l];
+    a.L = c->L;
+    a.logn = c->logn;
+    a.n_ct = n_ct;
+    a.pixels = d_pix;
+    a.mult = k->d_mult;
+    a.r = k->radix_base;
+    a.n_pow = k->n_pow;
+    a.randomize = k->radix_randomize;
+    a.seed = seed;
+    a.id_base = 0;
+    a.out = out;
+    return a;
+}
+
+// Encrypt `count` pixel values held on the host into dst with ids id_base + k.
+static ichee_status encrypt_values(ichee_ctx* c, const std::vector<uint8_t>& vals, u64 seed, u64 id_base, u64* dst,
+                                   cudaStream_t st)
+{
+    if (vals.empty()) return ICHEE_OK;
+    uint8_t* d_v = nullptr;
+    CK(cudaMalloc(&d_v, vals.size()));
+    cudaError_t e = cudaMemcpyAsync(d_v, vals.data(), vals.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_encrypt_fresh(enc_args(c, d_v, vals.size(), seed, id_base, dst), st);
+    cudaStreamSynchronize(st);
+    cudaFree(d_v);
+    if (e != cudaSuccess) return fail(ICHEE_ECUDA, "cache encryption: %s", cudaGetErrorString(e));
+    return ICHEE_OK;
+}
+
+static ichee_status build_radix(ichee_ctx* c, ichee_cache* k, u32 base, u32 randomize, u64 seed, cudaStream_t st)
+{
+    int n_pow = 1;
+    for (u32 p = base; p <= 255; p *= base) ++n_pow;
+    k->radix_base = (int)base;
+    k->n_pow = n_pow;
+    k->radix_randomize = randomize ? 1 : 0;
+    const size_t ctb = ct_words(c, c->L) * 8;
+    CK(cudaMalloc(&k->d_radix, n_pow * ctb));
+    CK(cudaMalloc(&k->d_mult, (size_t)n_pow * (2 * base + 1) * ctb));
+    std::vector<uint8_t> pw(n_pow);
+    u32 v = 1;
+    for (int i = 0; i < n_pow; ++i, v *= base) pw[i] = (uint8_t)v;
+    ichee_status s = encrypt_values(c, pw, seed, kIdRadixBase, k->d_radix, st);
+    if (s != ICHEE_OK) return s;
+    CK(launch_radix_multiples(k->d_radix, n_pow, (int)base, rns_prefix(c, c->L), c->L, k->d_mult, st));
+    CK(cudaStreamSynchronize(st));
+    return ICHEE_OK;
+}
+
+extern "C" ichee_status ichee_build_cache(ichee_ctx* c, const ichee_cache_desc* d, const uint8_t* scan, size_t n_scan,
+                                          uint64_t seed, ichee_cache** out, void* stream)
+{
+    if (!c || !d || !out) return fail(ICHEE_EINVAL, "null argument");
+    *out = nullptr;
+    if (!c->have_keys) return fail(ICHEE_EINVAL, "ichee_build_cache: run ichee_keygen first");
+    const bool needs_radix = d->kind == ICHEE_CACHE_RADIX || (d->kind == ICHEE_CACHE_FREQ && d->miss_policy == 1);
+    if (needs_radix && (d->radix_base < 2 || d->radix_base > 16))
+        return fail(ICHEE_EINVAL, "radix_base %u outside [2, 16]", d->radix_base);
+    if (d->kind == ICHEE_CACHE_FREQ && (d->top_k < 1 || d->top_k > 256))
+        return fail(ICHEE_EINVAL, "top_k %u outside [1, 256]", d->top_k);
+    if (d->kind == ICHEE_CACHE_FREQ && d->miss_policy > 1) return fail(ICHEE_EINVAL, "miss_policy %u", d->miss_policy);
+    if (d->kind != ICHEE_CACHE_RADIX && d->pool_size > 4096) return fail(ICHEE_EINVAL, "pool_size %u > 4096", d->pool_size);
+    if (d->kind == ICHEE_CACHE_FREQ && (!scan || n_scan == 0)) return fail(ICHEE_EINVAL, "scanning cache needs pixels");
+    if (d->kind > ICHEE_CACHE_FULL) return fail(ICHEE_EINVAL, "unknown cache kind");
+    CK(cudaSetDevice(c->device));
+    cudaStream_t st = (cudaStream_t)stream;
+
+    ichee_cache* k = new ichee_cache();
+    k->ctx = c;
+    k->desc = *d;
+    for (int i = 0; i < 256; ++i) k->h_lut[i] = -1;
+    auto bail = [&](ichee_status s) {
+        ichee_cache_free(k);
+        return s;
+    };
+    const size_t ctb = ct_words(c, c->L) * 8;
+    if (needs_radix) {
+        ichee_status s = build_radix(c, k, d->radix_base, d->kind == ICHEE_CACHE_RADIX ? d->radix_randomize : 1, seed, st);
+        if (s != ICHEE_OK) return bail(s);
+    }
+    if (d->kind != ICHEE_CACHE_RADIX) {
+        if (d->kind == ICHEE_CACHE_FULL) {
+            for (int v = 0; v < 256; ++v) k->values.push_back(v);
+        } else {
+            // scanning step: histogram on the device, top-k on the host (count desc, value asc)
+            const uint8_t* d_scan = scan;
+            uint8_t* tmp = nullptr;
+            u32* d_counts = nullptr;
+            if (cudaMalloc(&d_counts, 256 * 4) != cudaSuccess) return bail(fail(ICHEE_ENOMEM, "histogram"));
+            cudaMemsetAsync(d_counts, 0, 256 * 4, st);
+            if (!is_device_ptr(scan)) {
+                if (cudaMalloc(&tmp, n_scan) != cudaSuccess) { cudaFree(d_counts); return bail(fail(ICHEE_ENOMEM, "scan")); }
+                cudaMemcpyAsync(tmp, scan, n_scan, cudaMemcpyHostToDevice, st);
+                d_scan = tmp;
+            }
+            u32 counts[256];
+            cudaError_t e = launch_histogram(d_scan, n_scan, d_counts, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(counts, d_counts, sizeof(counts), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            cudaFree(d_counts);
+            if (tmp) cudaFree(tmp);
+            if (e != cudaSuccess) return bail(fail(ICHEE_ECUDA, "histogram: %s", cudaGetErrorString(e)));
+            std::vector<int> order;
+            for (int v = 0; v < 256; ++v)
+                if (counts[v]) order.push_back(v);
+            std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return counts[a] > counts[b]; });
+            if (order.size() > d->top_k) order.resize(d->top_k);
+            k->values = order;
+        }
+        for (size_t j = 0; j < k->values.size(); ++j) k->h_lut[k->values[j]] = (int32_t)j;
+        if (cudaMalloc(&k->d_values, std::max<size_t>(1, k->values.size()) * ctb) != cudaSuccess)
+            return bail(fail(ICHEE_ENOMEM, "value cache"));
+        std::vector<uint8_t> vals(k->values.begin(), k->values.end());
+        ichee_status s = encrypt_values(c, vals, seed, 0, k->d_values, st);
+        if (s != ICHEE_OK) return bail(s);
+        if (d->pool_size) {
+            if (cudaMalloc(&k->d_pool, (size_t)d->pool_size * ctb) != cudaSuccess) return bail(fail(ICHEE_ENOMEM, "pool"));
+            std::vector<uint8_t> zeros(d->pool_size, 0);
+            s = encrypt_values(c, zeros, seed, kIdPoolBase, k->d_pool, st);
+            if (s != ICHEE_OK) return bail(s);
+        }
+    }
+    if (cudaMalloc(&k->d_lut, sizeof(k->h_lut)) != cudaSuccess) return bail(fail(ICHEE_ENOMEM, "lut"));
+    if (cudaMemcpy(k->d_lut, k->h_lut, sizeof(k->h_lut), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(fail(ICHEE_ECUDA, "lut upload"));
+    *out = k;
+    return ICHEE_OK;
+}
+
+extern "C" void ichee_cache_free(ichee_cache* k)
+{
+    if (!k) return;
+    cudaSetDevice(k->ctx->device);
+    cudaDeviceSynchronize();
+    void* ptrs[] = {k->d_lut, k->d_values, k->d_pool, k->d_radix, k->d_mult};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete k;
+}
+
+extern "C" ichee_status ichee_cache_info(const ichee_cache* k, uint32_t* n_values, uint8_t* values_out, uint32_t* pool)
+{
+    if (!k) return fail(ICHEE_EINVAL, "null cache");
+    if (n_values) *n_values = (uint32_t)k->values.size();
+    if (values_out)
+        for (size_t j = 0; j < k->values.size(); ++j) values_out[j] = (uint8_t)k->values[j];
+    if (pool) *pool = k->desc.kind == ICHEE_CACHE_RADIX ? 0 : k->desc.pool_size;
+    return ICHEE_OK;
+}
+
+extern "C" ichee_status ichee_cache_export(const ichee_cache* k, int part, void* host_out, size_t bytes, void* stream)
+{
+    if (!k || !host_out) return fail(ICHEE_EINVAL, "null argument");
+    const ichee_ctx* c = k->ctx;
+    CK(cudaSetDevice(c->device));
+    const size_t ctb = ct_words(c, c->L) * 8;
+    const void* src = nullptr;
+    size_t want = 0;
+    if (part == 0) { src = k->d_values; want = k->values.size() * ctb; }
+    else if (part == 1) { src = k->d_pool; want = (k->d_pool ? k->desc.pool_size : 0) * ctb; }
+    else if (part == 2) { src = k->d_radix; want = (size_t)k->n_pow * ctb; }
+    else return fail(ICHEE_EINVAL, "unknown part %d", part);
+    if (bytes != want) return fail(ICHEE_EINVAL, "part is %zu bytes, got %zu", want, bytes);
+    if (want == 0) return ICHEE_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(host_out, src, want, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return ICHEE_OK;
+}
+
+// Pixels as a device pointer: staged through the context when they live on the host.
+static ichee_status device_pixels(ichee_ctx* c, const uint8_t* px, u64 n, cudaStream_t st, const uint8_t** d_px)
+{
+    if (is_device_ptr(px)) { *d_px = px; return ICHEE_OK; }
+    CK(c->stage_in.ensure(n));
+    CK(cudaMemcpyAsync(c->stage_in.p, px, n, cudaMemcpyHostToDevice, st));
+    *d_px = (const uint8_t*)c->stage_in.p;
+    return ICHEE_OK;
+}
+
+extern "C" ichee_status ichee_encrypt_image(ichee_ctx* c, const ichee_cache* k, const uint8_t* pixels, uint32_t h,
+                                            uint32_t w, uint32_t ch, uint64_t seed, uint64_t* d_out,
+                                            ichee_ctimg_meta* meta, void* stream)
+{
+    if (!c || !pixels || !d_out || !meta) return fail(ICHEE_EINVAL, "null argument");
+    if (!c->have_keys) return fail(ICHEE_EINVAL, "ichee_encrypt_image: run ichee_keygen first");
+    if (k && k->ctx != c) return fail(ICHEE_EMISMATCH, "cache belongs to another context");
+    const u64 n_ct = (u64)h * w * ch;
+    if (n_ct == 0) return fail(ICHEE_EINVAL, "empty image %ux%ux%u", h, w, ch);
+    CK(cudaSetDevice(c->device));
+    if (!is_device_ptr(d_out)) return fail(ICHEE_EINVAL, "ciphertext output must be device memory");
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint8_t* d_px = nullptr;
+    ichee_status s = device_pixels(c, pixels, n_ct, st, &d_px);
+    if (s != ICHEE_OK) return s;
+    if (!k) {
+        CK(launch_encrypt_fresh(enc_args(c, d_px, n_ct, seed, 0, d_out), st));
+    } else if (k->desc.kind == ICHEE_CACHE_RADIX) {
+        CK(launch_radix_combine(radix_args(c, k, d_px, n_ct, seed, d_out), st));
+    } else {
+        LookupArgs a;
+        std::memset(&a, 0, sizeof(a));
+        for (int l = 0; l < c->L; ++l) a.q[l] = c->q[l];
+        a.L = c->L;
+        a.logn = c->logn;
+        a.n_ct = n_ct;
+        a.pixels = d_px;
+        a.lut = k->d_lut;
+        a.value_cts = k->d_values;
+        a.pool = k->d_pool;
+        a.pool_size = k->d_pool ? k->desc.pool_size : 0;
+        a.seed = seed;
+        a.id_base = 0;
+        a.out = d_out;
+        CK(launch_lookup_combine(a, st));
+        if (k->values.size() < 256) {  // values outside the cache
+            if (k->desc.miss_policy == 0) {
+                EncArgs e = enc_args(c, d_px, n_ct, seed, 0, d_out);
+                e.skip_lut = k->d_lut;
+                CK(launch_encrypt_fresh(e, st));
+            } else {
+                RadixArgs r = radix_args(c, k, d_px, n_ct, seed, d_out);
+                r.skip_lut = k->d_lut;
+                CK(launch_radix_combine(r, st));
+            }
+        }
+    }
+    meta->h = h;
+    meta->w = w;
+    meta->c = ch;
+    meta->level = (u32)(c->L - 1);
+    meta->scale = c->delta;
+    return ICHEE_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Image operations
+// ---------------------------------------------------------------------------------------
+static OpsArgs ops_base(const ichee_ctx* c, const ichee_ctimg_meta* m)
+{
+    OpsArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.logn = c->logn;
+    a.limbs = (int)m->level + 1;
+    a.n_ct = (u64)m->h * m->w * m->c;
+    for (int l = 0; l < a.limbs; ++l) {
+        a.q[l] = c->q[l];
+        a.mu[l] = c->rns.mu[l];
+    }
+    a.h = (int)m->h;
+    a.w = (int)m->w;
+    a.c = (int)m->c;
+    return a;
+}
+
+static void set_rescale(const ichee_ctx* c, OpsArgs& a)
+{
+    const int t = a.limbs - 1;
+    const u64 qt = c->q[t];
+    a.half_qt = (qt - 1) / 2;
+    for (int j = 0; j < t; ++j) {
+        const u64 qj = c->q[j];
+        a.qt_inv[j] = hm::invm(qt % qj, qj);
+        a.qt_inv_p[j] = hm::shoup_of(a.qt_inv[j], qj);
+        const u64 r = qt % qj;
+        a.neg_qt_mod[j] = r == 0 ? 0 : qj - r;
+    }
+}
+
+static void set_k0(const ichee_ctx* c, OpsArgs& a, double v, double scale)
+{
+    encode_const(c, v, scale, a.limbs, a.k0);
+    for (int l = 0; l < a.limbs; ++l) a.k0p[l] = hm::shoup_of(a.k0[l], c->q[l]);
+}
+
+static void set_k1(const ichee_ctx* c, OpsArgs& a, double v, double scale)
+{
+    encode_const(c, v, scale, a.limbs, a.k1);
+    for (int l = 0; l < a.limbs; ++l) a.k1p[l] = hm::shoup_of(a.k1[l], c->q[l]);
+}
+
+static bool same_scale(double a, double b) { return std::fabs(a - b) <= 1e-9 * std::fabs(a); }
+
+static ichee_status check_img(const ichee_ctx* c, const uint64_t* d, const ichee_ctimg_meta* m, const char* what)
+{
+    if (!d || !m) return fail(ICHEE_EINVAL, "%s: null operand", what);
+    if ((int)m->level >= c->L) return fail(ICHEE_ELEVEL, "%s: level %u >= %d", what, m->level, c->L);
+    if ((u64)m->h * m->w * m->c == 0) return fail(ICHEE_EINVAL, "%s: empty image", what);
+    if (!(m->scale > 0.0)) return fail(ICHEE_ESCALE, "%s: scale must be positive", what);
+    if (!is_device_ptr(d)) return fail(ICHEE_EINVAL, "%s: ciphertexts must be device memory", what);
+    return ICHEE_OK;
+}
+
+static ichee_status op_sqdiff(ichee_ctx* c, const uint64_t* d_a, const ichee_ctimg_meta* ma, const uint64_t* d_b,
+                              uint64_t* d_out, ichee_ctimg_meta* mout, cudaStream_t st);
+
+extern "C" ichee_status ichee_eval(ichee_ctx* c, ichee_op op, const uint64_t* d_a, const ichee_ctimg_meta* ma,
+                                   const uint64_t* d_b, const ichee_ctimg_meta* mb, const double* args, uint32_t n_args,
+                                   uint64_t* d_out, ichee_ctimg_meta* mout, void* stream)
+{
+    if (!c || !mout) return fail(ICHEE_EINVAL, "null argument");
+    CK(cudaSetDevice(c->device));
+    ichee_status s = check_img(c, d_a, ma, "a");
+    if (s != ICHEE_OK) return s;
+    if (!d_out || !is_device_ptr(d_out)) return fail(ICHEE_EINVAL, "output must be device memory");
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool binary = op == ICHEE_OP_ADD || op == ICHEE_OP_SUB || op == ICHEE_OP_BLEND || op == ICHEE_OP_SQDIFF_SUM;
+    if (binary) {
+        s = check_img(c, d_b, mb, "b");
+        if (s != ICHEE_OK) return s;
+        if (mb->level != ma->level) return fail(ICHEE_ELEVEL, "levels differ (%u vs %u)", ma->level, mb->level);
+        if (!same_scale(ma->scale, mb->scale)) return fail(ICHEE_ESCALE, "scales differ (%g vs %g)", ma->scale, mb->scale);
+        const bool bcast = op == ICHEE_OP_BLEND && mb->c == 1;
+        if (mb->h != ma->h || mb->w != ma->w || (mb->c != ma->c && !bcast))
+            return fail(ICHEE_EMISMATCH, "shapes differ");
+    }
+    const bool in_place_ok = op == ICHEE_OP_PTADD || op == ICHEE_OP_BRIGHTNESS || op == ICHEE_OP_WATERMARK_PIXEL;
+    if (d_out == d_a && !in_place_ok) return fail(ICHEE_EINVAL, "this operation cannot run in place");
+    OpsArgs a = ops_base(c, ma);
+    a.in0 = d_a;
+    a.in1 = d_b;
+    a.out = d_out;
+    ichee_ctimg_meta m = *ma;
+    switch (op) {
+    case ICHEE_OP_ADD:
+    case ICHEE_OP_SUB:
+        CK(launch_addsub(a, op == ICHEE_OP_SUB, st));
+        break;
+    case ICHEE_OP_PTADD:
+    case ICHEE_OP_BRIGHTNESS:
+    case ICHEE_OP_WATERMARK_PIXEL: {
+        if (!args) return fail(ICHEE_EINVAL, "missing op_args");
+        std::vector<u64> kadd;
+        a.k_lo = 0;
+        a.k_hi = a.n_ct;
+        if (op == ICHEE_OP_WATERMARK_PIXEL) {
+            if (n_args != 2) return fail(ICHEE_EINVAL, "watermark needs (x, index)");
+            const double idx = args[1];
+            if (!(idx >= 0) || idx >= (double)a.n_ct || idx != std::floor(idx))
+                return fail(ICHEE_EINVAL, "watermark index %g outside the image", idx);
+            a.k_lo = (u64)idx;
+            a.k_hi = a.k_lo + 1;
+            kadd.resize(a.limbs);
+            encode_const(c, args[0], ma->scale, a.limbs, kadd.data());
+        } else if (n_args == 1 || op == ICHEE_OP_BRIGHTNESS) {
+            if (n_args != 1) return fail(ICHEE_EINVAL, "brightness needs one argument");
+            kadd.resize(a.limbs);
+            encode_const(c, args[0], ma->scale, a.limbs, kadd.data());
+        } else if (n_args == a.n_ct) {
+            kadd.resize((size_t)a.n_ct * a.limbs);
+            for (u64 k = 0; k < a.n_ct; ++k) encode_const(c, args[k], ma->scale, a.limbs, kadd.data() + k * a.limbs);
+            a.kadd_per_ct = 1;
+        } else return fail(ICHEE_EINVAL, "ptadd needs 1 or n_ct arguments, got %u", n_args);
+        if (a.kadd_per_ct) {
+            CK(c->kadd.ensure(kadd.size() * 8));
+            CK(cudaMemcpyAsync(c->kadd.p, kadd.data(), kadd.size() * 8, cudaMemcpyHostToDevice, st));
+            a.kadd = (const u64*)c->kadd.p;
+        } else {
+            for (int l = 0; l < a.limbs; ++l) a.k0[l] = kadd[l];  // one constant: passed by value
+        }
+        CK(launch_ptadd(a, st));
+        // a per-ciphertext table lives in a staging buffer the next call reuses
+        if (a.kadd_per_ct) CK(cudaStreamSynchronize(st));
+        break;
+    }
+    case ICHEE_OP_PTMUL:
+        if (!args || n_args != 1) return fail(ICHEE_EINVAL, "ptmul needs one argument");
+        set_k0(c, a, args[0], c->delta);
+        CK(launch_ptmul(a, st));
+        m.scale = ma->scale * c->delta;
+        break;
+    case ICHEE_OP_RESCALE:
+        if (ma->level == 0) return fail(ICHEE_ELEVEL, "no limb left to drop");
+        set_rescale(c, a);
+        CK(launch_rescale(a, st));
+        m.level = ma->level - 1;
+        m.scale = ma->scale / (double)c->q[ma->level];
+        break;
+    case ICHEE_OP_MEANFILTER3:
+        if (ma->level == 0) return fail(ICHEE_ELEVEL, "mean filter needs a limb to drop");
+        if (c->n / 2 < 256) return fail(ICHEE_EUNSUPPORTED, "mean filter needs N >= 512");
+        set_k0(c, a, 1.0 / 9.0, c->delta);
+        set_rescale(c, a);
+        CK(launch_meanfilter3(a, st));
+        m.level = ma->level - 1;
+        m.scale = ma->scale * c->delta / (double)c->q[ma->level];
+        break;
+    case ICHEE_OP_BLEND:
+        if (!args || n_args != 1) return fail(ICHEE_EINVAL, "blend needs alpha");
+        if (ma->level == 0) return fail(ICHEE_ELEVEL, "blend needs a limb to drop");
+        set_k0(c, a, args[0], c->delta);
+        set_k1(c, a, 1.0 - args[0], c->delta);
+        set_rescale(c, a);
+        a.c_w = (int)mb->c;
+        CK(launch_blend(a, st));
+        m.level = ma->level - 1;
+        m.scale = ma->scale * c->delta / (double)c->q[ma->level];
+        break;
+    case ICHEE_OP_SQDIFF_SUM:
+        return op_sqdiff(c, d_a, ma, d_b, d_out, mout, st);
+    default:
+        return fail(ICHEE_EINVAL, "unknown op %d", (int)op);
+    }
+    *mout = m;
+    return ICHEE_OK;
+}
+
+// Matching (Sec. 4.4.3, reading R12): T = sum_k (a_k - b_k)^2 in the NTT domain, INTT,
+// relinearise, rescale.
+static ichee_status op_sqdiff(ichee_ctx* c, const uint64_t* d_a, const ichee_ctimg_meta* ma, const uint64_t* d_b,
+                              uint64_t* d_out, ichee_ctimg_meta* mout, cudaStream_t st)
+{
+    if (!c->have_evk) return fail(ICHEE_EUNSUPPORTED, "matching needs the evaluation key (ICHEE_WITH_EVK)");
+    if (ma->level == 0) return fail(ICHEE_ELEVEL, "matching needs a limb to drop");
+    const int limbs = (int)ma->level + 1;
+    const int n = c->n;
+    const int L = c->L;
+    int n_blocks = (c->num_sms / limbs) * limbs;
+    if (n_blocks < limbs) n_blocks = limbs;
+    const size_t partial_w = (size_t)n_blocks * 4 * n;
+    const size_t tensor_w = (size_t)3 * limbs * n;
+    const size_t digits_w = (size_t)limbs * (limbs + 1) * n;
+    const size_t acc_w = (size_t)2 * (limbs + 1) * n;
+    const size_t rel_w = (size_t)2 * limbs * n;
+    CK(c->scratch.ensure((partial_w + tensor_w + digits_w + acc_w + rel_w) * 8));
+    u64* partial = (u64*)c->scratch.p;
+    u64* tensor = partial + partial_w;
+    u64* digits = tensor + tensor_w;
+    u64* acc = digits + digits_w;
+    u64* rel = acc + acc_w;
+
+    SqDiffArgs sa;
+    std::memset(&sa, 0, sizeof(sa));
+    sa.rns = rns_prefix(c, limbs);
+    sa.limbs = limbs;
+    sa.n_ct = (u64)ma->h * ma->w * ma->c;
+    sa.a = d_a;
+    sa.b = d_b;
+    sa.partial = partial;
+    sa.n_blocks = n_blocks;
+    CK(launch_sqdiff_accumulate(sa, st));
+    CK(launch_sqdiff_reduce(sa.rns, limbs, partial, n_blocks, tensor, st));
+    std::vector<int> id = iota_idx(kMaxModuli);
+    CK(launch_ntt_inv(c->rns, batch(tensor, 3 * limbs, limbs, id.data()), st));
+    CK(launch_scale_const(c->rns, batch(tensor, 3 * limbs, limbs, id.data()), c->d_ninv, st));
+
+    RelinArgs ra;
+    std::memset(&ra, 0, sizeof(ra));
+    ra.rns = c->rns;
+    ra.L = L;
+    ra.limbs = limbs;
+    ra.evk_hat = c->d_evk_hat;
+    ra.evk_hat_p = c->d_evk_hat_p;
+    for (int m = 0; m < c->nmod; ++m) ra.mu[m] = c->rns.mu[m];
+    for (int j = 0; j < limbs; ++j) {
+        ra.p_inv[j] = hm::invm(c->P % c->q[j], c->q[j]);
+        ra.p_inv_p[j] = hm::shoup_of(ra.p_inv[j], c->q[j]);
+        const u64 r = c->P % c->q[j];
+        ra.neg_p_mod[j] = r == 0 ? 0 : c->q[j] - r;
+    }
+    std::vector<int> midx(limbs + 1);
+    for (int m = 0; m < limbs; ++m) midx[m] = m;
+    midx[limbs] = L;
+    CK(launch_relin_digits(ra, tensor + (size_t)2 * limbs * n, digits, st));
+    CK(launch_ntt_fwd(c->rns, batch(digits, limbs * (limbs + 1), limbs + 1, midx.data()), st));
+    CK(launch_relin_mac(ra, digits, acc, st));
+    CK(launch_ntt_inv(c->rns, batch(acc, 2 * (limbs + 1), limbs + 1, midx.data()), st));
+    CK(launch_relin_moddown(ra, tensor, acc, rel, st));
+
+    ichee_ctimg_meta one = *ma;
+    one.h = one.w = one.c = 1;
+    OpsArgs a = ops_base(c, &one);
+    a.in0 = rel;
+    a.out = d_out;
+    set_rescale(c, a);
+    CK(launch_rescale(a, st));
+    *mout = one;
+    mout->level = ma->level - 1;
+    mout->scale = ma->scale * ma->scale / (double)c->q[ma->level];
+    return ICHEE_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Decryption
+// ---------------------------------------------------------------------------------------
+static ichee_status decrypt_impl(ichee_ctx* c, const uint64_t* d_ct, const ichee_ctimg_meta* m, double* out,
+                                 uint64_t* residues, void* stream)
+{
+    if (!c || !out) return fail(ICHEE_EINVAL, "null argument");
+    if (!c->have_keys) return fail(ICHEE_EINVAL, "no secret key");
+    CK(cudaSetDevice(c->device));
+    ichee_status s = check_img(c, d_ct, m, "ciphertexts");
+    if (s != ICHEE_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const u64 n_ct = (u64)m->h * m->w * m->c;
+    const int nl = (int)m->level + 1;
+    const bool out_dev = is_device_ptr(out);
+    const bool res_dev = residues == nullptr || is_device_ptr(residues);
+    DecArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.logn = c->logn;
+    a.n_ct = n_ct;
+    for (int l = 0; l < nl; ++l) a.q[l] = c->q[l];
+    a.crt = c->crt[nl - 1];
+    a.srev = c->d_srev;
+    a.ct = d_ct;
+    a.scale = m->scale;
+    if (out_dev) a.out = out;
+    else {
+        CK(c->stage_out.ensure(n_ct * 8));
+        a.out = (double*)c->stage_out.p;
+    }
+    if (residues) {
+        if (res_dev) a.residues_out = residues;
+        else {
+            CK(c->stage_res.ensure(n_ct * nl * 8));
+            a.residues_out = (u64*)c->stage_res.p;
+        }
+    }
+    CK(launch_decrypt(a, st));
+    if (!out_dev) CK(cudaMemcpyAsync(out, a.out, n_ct * 8, cudaMemcpyDeviceToHost, st));
+    if (residues && !res_dev) CK(cudaMemcpyAsync(residues, a.residues_out, n_ct * nl * 8, cudaMemcpyDeviceToHost, st));
+    if (!out_dev || (residues && !res_dev)) CK(cudaStreamSynchronize(st));
+    return ICHEE_OK;
+}
+
+extern "C" ichee_status ichee_decrypt_image(ichee_ctx* c, const uint64_t* d_ct, const ichee_ctimg_meta* m, double* out,
+                                            void* stream)
+{
+    return decrypt_impl(c, d_ct, m, out, nullptr, stream);
+}
+
+extern "C" ichee_status ichee_decrypt_residues(ichee_ctx* c, const uint64_t* d_ct, const ichee_ctimg_meta* m,
+                                               double* out, uint64_t* residues, void* stream)
+{
+    if (!residues) return fail(ICHEE_EINVAL, "null residues");
+    return decrypt_impl(c, d_ct, m, out, residues, stream);
+}
+
+extern "C" ichee_status ichee_stream_status(ichee_ctx* c, void* stream)
+{
+    if (!c) return fail(ICHEE_EINVAL, "null context");
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    CK(cudaGetLastError());
+    int status = 0;
+    CK(cudaMemcpy(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status != 0) {
+        cudaMemset(c->d_status, 0, sizeof(int));
+        return fail(ICHEE_ETIMEOUT, "device status word %d", status);
+    }
+    return ICHEE_OK;
+}

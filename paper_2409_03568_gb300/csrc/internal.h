@@ -1,0 +1,89 @@
+// internal.h -- argument structures and kernel launchers shared by the translation units of
+// libichee (not part of the public C ABI, which is include/ichee.h).
+#pragma once
+#include "common.cuh"
+
+namespace ichee {
+
+constexpr int kMinLogN = 10;
+constexpr int kMaxLogN = 14;
+
+// Fresh public-key encryption of pixel values (Sec. 2.2.2, 3.1).
+struct EncArgs {
+    RnsArgs rns;               // moduli 0..L-1 = ciphertext primes
+    int L;                     // limbs written
+    u64 n_ct;                  // ciphertexts
+    const uint8_t* pixels;     // [n_ct] device
+    const u64* dm;             // [L][256] (Delta * p) mod q_l
+    const u64* pk_hat;         // [2][L][N] NTT(pk_b) * N^{-1}, bit-reversed order
+    const u64* pk_hat_p;       // [2][L][N] Shoup companions
+    const int32_t* skip_lut;   // optional [256]: skip pixel p when skip_lut[p] >= 0
+    u64 seed;
+    u64 id_base;               // ct id of ciphertext k is id_base + k
+    CdtTable cdt;
+    u64* out;                  // [n_ct][2][L][N]
+};
+
+// Radix-cached encryption: c = sum_k M[k][d'_k], M[k][d] = d * Enc(r^k) (Sec. 3.2, 3.3).
+struct RadixArgs {
+    u64 q[kMaxPrimes];
+    int L, logn;
+    u64 n_ct;
+    const uint8_t* pixels;
+    const u64* mult;           // [n_pow][2r+1][2][L][N]
+    int r, n_pow, randomize;
+    const int32_t* skip_lut;   // optional, as in EncArgs
+    u64 seed, id_base;
+    u64* out;
+};
+
+// Scanning / full cached encryption with the zero pool (Sec. 3.2, 3.3).
+struct LookupArgs {
+    u64 q[kMaxPrimes];
+    int L, logn;
+    u64 n_ct;
+    const uint8_t* pixels;
+    const int32_t* lut;        // [256] slot or -1 (missing values are skipped)
+    const u64* value_cts;      // [K][2][L][N]
+    const u64* pool;           // [M][2][L][N]
+    u32 pool_size;
+    u64 seed, id_base;
+    u64* out;
+};
+
+// Launchers (kernels_enc.cu). All launch on `stream` and return cudaGetLastError().
+cudaError_t launch_sample_small(int8_t* out, int n, u64 seed, u32 stream_id, u64 id, int gaussian,
+                                const CdtTable& cdt, cudaStream_t st);
+cudaError_t launch_sample_uniform(u64* out, int n, u64 q, u64 seed, u32 stream_id, u64 id, cudaStream_t st);
+// Batched transforms over polys [n_poly][N]; poly p uses modulus rns.q[midx[p % nl]].
+struct PolyBatch {
+    u64* data;
+    int n_poly;
+    int nl;
+    int midx[kMaxModuli];
+};
+cudaError_t launch_ntt_fwd(const RnsArgs& rns, const PolyBatch& b, cudaStream_t st);
+cudaError_t launch_ntt_inv(const RnsArgs& rns, const PolyBatch& b, cudaStream_t st);
+// out[p][i] = a[p][i] * b[p % b_period][i] mod q  (b_period polys of b repeat), full residues
+cudaError_t launch_pointwise_mul(const RnsArgs& rns, const PolyBatch& out, const u64* a, const u64* b,
+                                 int b_period, cudaStream_t st);
+// out[p][i] = out[p][i] * c_p mod q where c_p = cst[midx[p % nl]] (a per-modulus constant)
+cudaError_t launch_scale_const(const RnsArgs& rns, const PolyBatch& b, const u64* cst_per_mod, cudaStream_t st);
+// Shoup companions of [n_poly][N] residues
+cudaError_t launch_shoup_companions(const RnsArgs& rns, const PolyBatch& b, u64* out, cudaStream_t st);
+// Small signed int8 polynomial reduced into modulus rns.q[m]
+cudaError_t launch_small_to_mod(const int8_t* x, int n, u64 q, u64* out, cudaStream_t st);
+// out = -x + small(e) mod q (x full residues, e int8) for one poly
+cudaError_t launch_neg_add_small(const u64* x, const int8_t* e, int n, u64 q, u64* out, cudaStream_t st);
+// out = x + c*y mod q  (one poly)
+cudaError_t launch_axpy_const(u64* out, const u64* x, const u64* y, u64 c, int n, u64 q, u64 m0, u64 m1,
+                              cudaStream_t st);
+
+cudaError_t launch_encrypt_fresh(const EncArgs& a, cudaStream_t st);
+cudaError_t launch_radix_multiples(const u64* radix_cts, int n_pow, int r, const RnsArgs& rns, int L, u64* mult,
+                                   cudaStream_t st);
+cudaError_t launch_radix_combine(const RadixArgs& a, cudaStream_t st);
+cudaError_t launch_lookup_combine(const LookupArgs& a, cudaStream_t st);
+cudaError_t launch_histogram(const uint8_t* pixels, u64 n, u32* counts /*[256], zeroed*/, cudaStream_t st);
+
+}  // namespace ichee

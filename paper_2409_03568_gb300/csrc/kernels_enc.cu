@@ -1,0 +1,483 @@
+// kernels_enc.cu -- key generation helpers, fused fresh encryption (Sec. 2.2.2, 3.1) and the
+// cached encryption kernels (radix combine and value lookup with the zero pool, Sec. 3.2, 3.3).
+#include "internal.h"
+#include "ntt.cuh"
+
+namespace ichee {
+
+// ---------------------------------------------------------------------------------------
+// Samplers (Sec. 2.2.1 / 2.2.2). Coefficient i of a ternary polynomial uses word i%4 of
+// Philox block i/4; of a Gaussian one, words 2(i%2), 2(i%2)+1 of block i/2; of a uniform
+// one, the four words of block i as a 128-bit x giving floor(x*q / 2^128).
+// ---------------------------------------------------------------------------------------
+
+__global__ void k_sample_small(int8_t* out, int n, u64 seed, u32 stream_id, u64 id, int gaussian, CdtTable cdt)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (gaussian) {
+        Words4 w = philox(seed, stream_id, id, (u32)(i >> 1));
+        int h = 2 * (i & 1);
+        u64 u = (u64)w.w[h] | ((u64)w.w[h + 1] << 32);
+        out[i] = (int8_t)gauss_of(u, cdt);
+    } else {
+        Words4 w = philox(seed, stream_id, id, (u32)(i >> 2));
+        out[i] = (int8_t)ternary_of(w.w[i & 3]);
+    }
+}
+
+__global__ void k_sample_uniform(u64* out, int n, u64 q, u64 seed, u32 stream_id, u64 id)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Words4 w = philox(seed, stream_id, id, (u32)i);
+    u64 lo = (u64)w.w[0] | ((u64)w.w[1] << 32);
+    u64 hi = (u64)w.w[2] | ((u64)w.w[3] << 32);
+    // floor((hi*2^64 + lo) * q / 2^128) = floor((hi*q + floor(lo*q / 2^64)) / 2^64)
+    u64 carry = mulhi(lo, q);
+    u64 t_lo = hi * q;
+    u64 t_hi = mulhi(hi, q);
+    u64 s = t_lo + carry;
+    t_hi += (s < t_lo) ? 1 : 0;
+    out[i] = t_hi;
+}
+
+cudaError_t launch_sample_small(int8_t* out, int n, u64 seed, u32 stream_id, u64 id, int gaussian,
+                                const CdtTable& cdt, cudaStream_t st)
+{
+    k_sample_small<<<(n + 255) / 256, 256, 0, st>>>(out, n, seed, stream_id, id, gaussian, cdt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_uniform(u64* out, int n, u64 q, u64 seed, u32 stream_id, u64 id, cudaStream_t st)
+{
+    k_sample_uniform<<<(n + 255) / 256, 256, 0, st>>>(out, n, q, seed, stream_id, id);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Batched transforms in global memory (set-up paths and key switching).
+// ---------------------------------------------------------------------------------------
+
+template <int LOGN>
+__global__ void __launch_bounds__(NttShape<LOGN>::T) k_ntt_fwd(RnsArgs rns, PolyBatch b)
+{
+    extern __shared__ u64 sm[];
+    const int tid = threadIdx.x;
+    const int m = b.midx[blockIdx.x % b.nl];
+    const u64 q = rns.q[m];
+    u64* d = b.data + (size_t)blockIdx.x * (1 << LOGN);
+    u64 r[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) r[e] = d[elem_index<LOGN, 0>(tid, e)];
+    ntt_fwd_regs<LOGN>(sm, r, tid, rns.tab[m], q);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) d[elem_index<LOGN, NttShape<LOGN>::LAST>(tid, e)] = csub(csub(r[e], 2 * q), q);
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(NttShape<LOGN>::T) k_ntt_inv(RnsArgs rns, PolyBatch b)
+{
+    extern __shared__ u64 sm[];
+    const int tid = threadIdx.x;
+    const int m = b.midx[blockIdx.x % b.nl];
+    const u64 q = rns.q[m];
+    u64* d = b.data + (size_t)blockIdx.x * (1 << LOGN);
+    u64 r[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) r[e] = d[elem_index<LOGN, NttShape<LOGN>::LAST>(tid, e)];
+    ntt_inv_regs<LOGN>(sm, r, tid, rns.tab[m], q);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) d[elem_index<LOGN, 0>(tid, e)] = csub(r[e], q);
+}
+
+template <int LOGN>
+static cudaError_t ntt_launch(bool fwd, const RnsArgs& rns, const PolyBatch& b, cudaStream_t st)
+{
+    const int T = NttShape<LOGN>::T;
+    const size_t smem = sizeof(u64) << LOGN;
+    auto kern = fwd ? k_ntt_fwd<LOGN> : k_ntt_inv<LOGN>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<b.n_poly, T, smem, st>>>(rns, b);
+    return cudaGetLastError();
+}
+
+static cudaError_t ntt_dispatch(bool fwd, const RnsArgs& rns, const PolyBatch& b, cudaStream_t st)
+{
+    if (b.n_poly <= 0) return cudaSuccess;
+    switch (rns.logn) {
+    case 10: return ntt_launch<10>(fwd, rns, b, st);
+    case 11: return ntt_launch<11>(fwd, rns, b, st);
+    case 12: return ntt_launch<12>(fwd, rns, b, st);
+    case 13: return ntt_launch<13>(fwd, rns, b, st);
+    case 14: return ntt_launch<14>(fwd, rns, b, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_ntt_fwd(const RnsArgs& rns, const PolyBatch& b, cudaStream_t st) { return ntt_dispatch(true, rns, b, st); }
+cudaError_t launch_ntt_inv(const RnsArgs& rns, const PolyBatch& b, cudaStream_t st) { return ntt_dispatch(false, rns, b, st); }
+
+__global__ void k_pointwise_mul(RnsArgs rns, PolyBatch out, const u64* a, const u64* b, int b_period)
+{
+    const int n = 1 << rns.logn;
+    const int p = blockIdx.y;
+    const int m = out.midx[p % out.nl];
+    const u64 q = rns.q[m];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        u64 x = a[(size_t)p * n + i];
+        u64 y = b[(size_t)(p % b_period) * n + i];
+        out.data[(size_t)p * n + i] = mul_mod(x, y, q, rns.m0[m], rns.m1[m]);
+    }
+}
+
+cudaError_t launch_pointwise_mul(const RnsArgs& rns, const PolyBatch& out, const u64* a, const u64* b, int b_period,
+                                 cudaStream_t st)
+{
+    dim3 grid((1u << rns.logn) / 256, out.n_poly);
+    k_pointwise_mul<<<grid, 256, 0, st>>>(rns, out, a, b, b_period);
+    return cudaGetLastError();
+}
+
+__global__ void k_scale_const(RnsArgs rns, PolyBatch b, const u64* cst)
+{
+    const int n = 1 << rns.logn;
+    const int p = blockIdx.y;
+    const int m = b.midx[p % b.nl];
+    const u64 q = rns.q[m], c = cst[m];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        u64* x = b.data + (size_t)p * n + i;
+        *x = mul_mod(*x, c, q, rns.m0[m], rns.m1[m]);
+    }
+}
+
+cudaError_t launch_scale_const(const RnsArgs& rns, const PolyBatch& b, const u64* cst_per_mod, cudaStream_t st)
+{
+    dim3 grid((1u << rns.logn) / 256, b.n_poly);
+    k_scale_const<<<grid, 256, 0, st>>>(rns, b, cst_per_mod);
+    return cudaGetLastError();
+}
+
+// floor(w * 2^64 / q) by binary long division (w < q < 2^61)
+__device__ u64 shoup_companion(u64 w, u64 q)
+{
+    u64 rem = w, quo = 0;
+    for (int i = 0; i < 64; ++i) {
+        rem <<= 1;
+        quo <<= 1;
+        if (rem >= q) { rem -= q; quo |= 1; }
+    }
+    return quo;
+}
+
+__global__ void k_shoup_companions(RnsArgs rns, PolyBatch b, u64* out)
+{
+    const int n = 1 << rns.logn;
+    const int p = blockIdx.y;
+    const u64 q = rns.q[b.midx[p % b.nl]];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[(size_t)p * n + i] = shoup_companion(b.data[(size_t)p * n + i], q);
+}
+
+cudaError_t launch_shoup_companions(const RnsArgs& rns, const PolyBatch& b, u64* out, cudaStream_t st)
+{
+    dim3 grid((1u << rns.logn) / 256, b.n_poly);
+    k_shoup_companions<<<grid, 256, 0, st>>>(rns, b, out);
+    return cudaGetLastError();
+}
+
+__global__ void k_small_to_mod(const int8_t* x, int n, u64 q, u64* out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = small_mod(x[i], q);
+}
+
+cudaError_t launch_small_to_mod(const int8_t* x, int n, u64 q, u64* out, cudaStream_t st)
+{
+    k_small_to_mod<<<(n + 255) / 256, 256, 0, st>>>(x, n, q, out);
+    return cudaGetLastError();
+}
+
+__global__ void k_neg_add_small(const u64* x, const int8_t* e, int n, u64 q, u64* out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = add_mod(x[i] == 0 ? 0 : q - x[i], small_mod(e[i], q), q);
+}
+
+cudaError_t launch_neg_add_small(const u64* x, const int8_t* e, int n, u64 q, u64* out, cudaStream_t st)
+{
+    k_neg_add_small<<<(n + 255) / 256, 256, 0, st>>>(x, e, n, q, out);
+    return cudaGetLastError();
+}
+
+__global__ void k_axpy_const(u64* out, const u64* x, const u64* y, u64 c, int n, u64 q, u64 m0, u64 m1)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = add_mod(x[i], mul_mod(c, y[i], q, m0, m1), q);
+}
+
+cudaError_t launch_axpy_const(u64* out, const u64* x, const u64* y, u64 c, int n, u64 q, u64 m0, u64 m1,
+                              cudaStream_t st)
+{
+    k_axpy_const<<<(n + 255) / 256, 256, 0, st>>>(out, x, y, c, n, q, m0, m1);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Fused fresh encryption (Sec. 2.2.2 with reading R1): one thread block per ciphertext.
+//   sample v (ternary), e0, e1 (Gaussian) once into shared memory (int8), then per limb l:
+//   v^ = NTT(v); c_b = INTT(v^ . pk^_b) + e_b (+ Delta*p at coefficient 0 of c0)
+// pk^_b already carries the 1/N of the inverse transform. With KEEP_VHAT the transform of v
+// stays in registers for both products (3 transforms per limb); without it (N = 2^14,
+// register budget) it is recomputed (4 per limb).
+// ---------------------------------------------------------------------------------------
+
+template <int LOGN, bool KEEP_VHAT>
+__global__ void __launch_bounds__(NttShape<LOGN>::T, 1) k_encrypt_fresh(const EncArgs a)
+{
+    constexpr int N = 1 << LOGN;
+    constexpr int T = NttShape<LOGN>::T;
+    constexpr int LAST = NttShape<LOGN>::LAST;
+    extern __shared__ u64 smem[];
+    u64* buf = smem;
+    int8_t* sv = reinterpret_cast<int8_t*>(smem + N);
+    int8_t* se0 = sv + N;
+    int8_t* se1 = se0 + N;
+    const int tid = threadIdx.x;
+    const int L = a.L;
+
+    for (u64 k = blockIdx.x; k < a.n_ct; k += gridDim.x) {
+        const int p = a.pixels[k];
+        if (a.skip_lut != nullptr && a.skip_lut[p] >= 0) continue;  // uniform across the block
+        const u64 id = a.id_base + k;
+        __syncthreads();  // smem of the previous ciphertext no longer read
+        for (int b = tid; b < N / 4; b += T) {
+            Words4 w = philox(a.seed, kStreamV, id, (u32)b);
+            u32 packed = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) packed |= ((u32)(uint8_t)(int8_t)ternary_of(w.w[i])) << (8 * i);
+            reinterpret_cast<u32*>(sv)[b] = packed;
+        }
+        for (int b = tid; b < N / 2; b += T) {
+            Words4 w0 = philox(a.seed, kStreamE0, id, (u32)b);
+            Words4 w1 = philox(a.seed, kStreamE1, id, (u32)b);
+            int g00 = gauss_of((u64)w0.w[0] | ((u64)w0.w[1] << 32), a.cdt);
+            int g01 = gauss_of((u64)w0.w[2] | ((u64)w0.w[3] << 32), a.cdt);
+            int g10 = gauss_of((u64)w1.w[0] | ((u64)w1.w[1] << 32), a.cdt);
+            int g11 = gauss_of((u64)w1.w[2] | ((u64)w1.w[3] << 32), a.cdt);
+            reinterpret_cast<uint16_t*>(se0)[b] = (uint16_t)((uint8_t)g00 | ((uint16_t)(uint8_t)g01 << 8));
+            reinterpret_cast<uint16_t*>(se1)[b] = (uint16_t)((uint8_t)g10 | ((uint16_t)(uint8_t)g11 << 8));
+        }
+        __syncthreads();
+
+        for (int l = 0; l < L; ++l) {
+            const u64 q = a.rns.q[l];
+            const ModTables t = a.rns.tab[l];
+            u64 r[16];
+            u64 vh[KEEP_VHAT ? 16 : 1];
+            for (int pb = 0; pb < 2; ++pb) {
+                if (KEEP_VHAT && pb == 1) {
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) r[e] = vh[KEEP_VHAT ? e : 0];
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) r[e] = small_mod(sv[elem_index<LOGN, 0>(tid, e)], q);
+                    __syncthreads();
+                    ntt_fwd_regs<LOGN>(buf, r, tid, t, q);
+                    if constexpr (KEEP_VHAT) {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) vh[e] = r[e];
+                    }
+                }
+                const u64* pk = a.pk_hat + ((size_t)pb * L + l) * N;
+                const u64* pkp = a.pk_hat_p + ((size_t)pb * L + l) * N;
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int x = elem_index<LOGN, LAST>(tid, e);
+                    r[e] = shoup_lazy(r[e], __ldg(pk + x), __ldg(pkp + x), q);
+                }
+                __syncthreads();
+                ntt_inv_regs<LOGN>(buf, r, tid, t, q);
+                const int8_t* noise = pb == 0 ? se0 : se1;
+                u64* dst = a.out + ((k * 2 + pb) * (u64)L + l) * N;
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int x = elem_index<LOGN, 0>(tid, e);
+                    u64 v = add_mod(csub(r[e], q), small_mod(noise[x], q), q);
+                    if (pb == 0 && x == 0) v = add_mod(v, a.dm[l * 256 + p], q);
+                    __stcs(dst + x, v);
+                }
+            }
+        }
+    }
+}
+
+template <int LOGN>
+static cudaError_t enc_launch(const EncArgs& a, cudaStream_t st)
+{
+    constexpr bool keep = LOGN <= 13;
+    const int T = NttShape<LOGN>::T;
+    const size_t smem = (sizeof(u64) + 3) << LOGN;
+    cudaError_t e = cudaFuncSetAttribute(k_encrypt_fresh<LOGN, keep>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    u64 grid = a.n_ct < (u64)(1u << 30) ? a.n_ct : (u64)(1u << 30);
+    k_encrypt_fresh<LOGN, keep><<<(unsigned)grid, T, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_encrypt_fresh(const EncArgs& a, cudaStream_t st)
+{
+    if (a.n_ct == 0) return cudaSuccess;
+    switch (a.rns.logn) {
+    case 10: return enc_launch<10>(a, st);
+    case 11: return enc_launch<11>(a, st);
+    case 12: return enc_launch<12>(a, st);
+    case 13: return enc_launch<13>(a, st);
+    case 14: return enc_launch<14>(a, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Cached encryption.
+// ---------------------------------------------------------------------------------------
+
+// M[k][d + r] = d * Enc(r^k) mod q for d in [-r, r]: the multiples a radix combine can ask
+// for. Repeated homomorphic addition of a ciphertext (Sec. 3.2) equals this scalar multiple
+// residue for residue, so tabulating it once per cache changes no result.
+__global__ void k_radix_multiples(const u64* cts, int n_pow, int r, RnsArgs rns, int L, u64* mult)
+{
+    const int n = 1 << rns.logn;
+    const size_t ct_len = (size_t)2 * L * n;
+    const int slot = blockIdx.y;            // kk * (2r+1) + (d + r)
+    const int kk = slot / (2 * r + 1);
+    const int d = slot % (2 * r + 1) - r;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < ct_len; i += (size_t)gridDim.x * blockDim.x) {
+        const int l = (int)((i / n) % L);
+        const u64 q = rns.q[l];
+        const u64 c = cts[kk * ct_len + i];
+        mult[slot * ct_len + i] = mul_mod(c, small_mod(d, q), q, rns.m0[l], rns.m1[l]);
+    }
+}
+
+cudaError_t launch_radix_multiples(const u64* radix_cts, int n_pow, int r, const RnsArgs& rns, int L, u64* mult,
+                                       cudaStream_t st)
+{
+    dim3 grid(64, n_pow * (2 * r + 1));
+    k_radix_multiples<<<grid, 256, 0, st>>>(radix_cts, n_pow, r, rns, L, mult);
+    return cudaGetLastError();
+}
+
+// Radix combine: one block per ciphertext. Signed digits d'_k = d_k + b_k - r*b_{k+1} with b
+// from bit k of the pixel's randomness word (stream 3); c = sum_k M[k][d'_k], residue-wise
+// modular sums of cached rows, 16-byte loads, streaming 16-byte stores.
+__global__ void __launch_bounds__(256) k_radix_combine(const RadixArgs a)
+{
+    const int n = 1 << a.logn;
+    const size_t ct_len = (size_t)2 * a.L * n;
+    const int width = 2 * a.r + 1;
+    for (u64 k = blockIdx.x; k < a.n_ct; k += gridDim.x) {
+        const int p = a.pixels[k];
+        if (a.skip_lut != nullptr && a.skip_lut[p] >= 0) continue;
+        u32 bits = 0;
+        if (a.randomize) bits = philox(a.seed, kStreamRadixBits, a.id_base + k, 0).w[0];
+        const u64* src[8];
+        int ns = 0;
+        int rest = p;
+        for (int kk = 0; kk < a.n_pow; ++kk) {
+            int dk = rest % a.r;
+            rest /= a.r;
+            int bk = (a.randomize && kk >= 1) ? (int)((bits >> kk) & 1u) : 0;
+            int bk1 = (a.randomize && kk + 1 < a.n_pow) ? (int)((bits >> (kk + 1)) & 1u) : 0;
+            int d = dk + bk - a.r * bk1;
+            if (d != 0) src[ns++] = a.mult + ((size_t)kk * width + (d + a.r)) * ct_len;
+        }
+        ulonglong2* dst = reinterpret_cast<ulonglong2*>(a.out + k * ct_len);
+        for (int row = 0; row < 2 * a.L; ++row) {
+            const u64 q = a.q[row % a.L];
+            const size_t base = (size_t)row * n / 2;
+            for (int i = threadIdx.x; i < n / 2; i += blockDim.x) {
+                ulonglong2 acc = make_ulonglong2(0, 0);
+                for (int s = 0; s < ns; ++s) {
+                    ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(src[s]) + base + i);
+                    acc.x = add_mod(acc.x, v.x, q);
+                    acc.y = add_mod(acc.y, v.y, q);
+                }
+                __stcs(dst + base + i, acc);
+            }
+        }
+    }
+}
+
+cudaError_t launch_radix_combine(const RadixArgs& a, cudaStream_t st)
+{
+    if (a.n_ct == 0) return cudaSuccess;
+    unsigned grid = (unsigned)(a.n_ct < (1u << 30) ? a.n_ct : (1u << 30));
+    k_radix_combine<<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// Value lookup with the randomness pool: c = C[lut[p]] (+) Z[idx], idx = floor(w*M / 2^32)
+// from stream 4. Pixels whose value is not cached are left to another kernel.
+__global__ void __launch_bounds__(256) k_lookup_combine(const LookupArgs a)
+{
+    const int n = 1 << a.logn;
+    const size_t ct_len = (size_t)2 * a.L * n;
+    for (u64 k = blockIdx.x; k < a.n_ct; k += gridDim.x) {
+        const int slot = a.lut[a.pixels[k]];
+        if (slot < 0) continue;
+        const ulonglong2* c = reinterpret_cast<const ulonglong2*>(a.value_cts + (size_t)slot * ct_len);
+        const ulonglong2* z = nullptr;
+        if (a.pool_size > 0) {
+            u32 w = philox(a.seed, kStreamPool, a.id_base + k, 0).w[0];
+            u32 idx = (u32)(((u64)w * a.pool_size) >> 32);
+            z = reinterpret_cast<const ulonglong2*>(a.pool + (size_t)idx * ct_len);
+        }
+        ulonglong2* dst = reinterpret_cast<ulonglong2*>(a.out + k * ct_len);
+        for (int row = 0; row < 2 * a.L; ++row) {
+            const u64 q = a.q[row % a.L];
+            const size_t base = (size_t)row * n / 2;
+            for (int i = threadIdx.x; i < n / 2; i += blockDim.x) {
+                ulonglong2 v = __ldg(c + base + i);
+                if (z != nullptr) {
+                    ulonglong2 w = __ldg(z + base + i);
+                    v.x = add_mod(v.x, w.x, q);
+                    v.y = add_mod(v.y, w.y, q);
+                }
+                __stcs(dst + base + i, v);
+            }
+        }
+    }
+}
+
+cudaError_t launch_lookup_combine(const LookupArgs& a, cudaStream_t st)
+{
+    if (a.n_ct == 0) return cudaSuccess;
+    unsigned grid = (unsigned)(a.n_ct < (1u << 30) ? a.n_ct : (1u << 30));
+    k_lookup_combine<<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+__global__ void k_histogram(const uint8_t* px, u64 n, u32* counts)
+{
+    __shared__ u32 h[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x)
+        atomicAdd(&h[px[i]], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 256; i += blockDim.x)
+        if (h[i]) atomicAdd(&counts[i], h[i]);
+}
+
+cudaError_t launch_histogram(const uint8_t* pixels, u64 n, u32* counts, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    unsigned grid = (unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
+    k_histogram<<<grid, 256, 0, st>>>(pixels, n, counts);
+    return cudaGetLastError();
+}
+
+}  // namespace ichee

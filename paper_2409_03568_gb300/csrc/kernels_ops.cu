@@ -1,0 +1,401 @@
+// kernels_ops.cu -- ciphertext-wise image operations (Sec. 2.2.3, Sec. 4.4) and decryption
+// (Sec. 2.2.2). Ciphertexts are [n_ct][2][limbs][N] residues in the coefficient domain.
+#include "ops.h"
+
+namespace ichee {
+
+// ---------------------------------------------------------------------------------------
+// Rescale by the last prime q_t of a ciphertext with t+1 limbs (reading R10):
+//   c'_j = (c_j - [c_t]_centered) * q_t^{-1} mod q_j.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ u64 rescale_one(u64 cj, u64 ct, int j, const OpsArgs& a)
+{
+    const u64 qj = a.q[j];
+    u64 r = reduce64(ct, qj, a.mu[j]);
+    if (ct > a.half_qt) r = add_mod(r, a.neg_qt_mod[j], qj);  // (c_t - q_t) mod q_j
+    return shoup(sub_mod(cj, r, qj), a.qt_inv[j], a.qt_inv_p[j], qj);
+}
+
+// Elementwise add / sub of two images with the same shape (Sec. 2.2.3, Sec. 3.3).
+__global__ void k_addsub(const OpsArgs a, int subtract)
+{
+    const int n = 1 << a.logn;
+    const u64 total2 = a.n_ct * (u64)(2 * a.limbs) * (n / 2);
+    const ulonglong2* x = reinterpret_cast<const ulonglong2*>(a.in0);
+    const ulonglong2* y = reinterpret_cast<const ulonglong2*>(a.in1);
+    ulonglong2* o = reinterpret_cast<ulonglong2*>(a.out);
+    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total2; i += (u64)gridDim.x * blockDim.x) {
+        const int l = (int)((i / (n / 2)) % a.limbs);
+        const u64 q = a.q[l];
+        ulonglong2 u = __ldcs(x + i), v = __ldcs(y + i);
+        if (subtract) { u.x = sub_mod(u.x, v.x, q); u.y = sub_mod(u.y, v.y, q); }
+        else { u.x = add_mod(u.x, v.x, q); u.y = add_mod(u.y, v.y, q); }
+        __stcs(o + i, u);
+    }
+}
+
+// Plaintext constant add (brightness, Sec. 4.4.2; watermark pixel, Sec. 4.4.4): the encoded
+// constant touches coefficient 0 of c0 only. The residue added to limb l of ciphertext k is
+// kadd[k * limbs + l] (one constant per ciphertext) or k0[l] (one for all); only ciphertexts
+// in [k_lo, k_hi) change. With in0 != out the whole image is
+// copied first.
+__global__ void k_ptadd_copy(const OpsArgs a)
+{
+    const int n = 1 << a.logn;
+    const u64 total2 = a.n_ct * (u64)(2 * a.limbs) * (n / 2);
+    const ulonglong2* x = reinterpret_cast<const ulonglong2*>(a.in0);
+    ulonglong2* o = reinterpret_cast<ulonglong2*>(a.out);
+    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total2; i += (u64)gridDim.x * blockDim.x) {
+        ulonglong2 u = __ldcs(x + i);
+        const u64 row = i / (n / 2);               // (k * 2 + b) * limbs + l
+        const u64 within = i % (n / 2);
+        const int l = (int)(row % a.limbs);
+        const u64 kb = row / a.limbs;
+        const u64 k = kb / 2;
+        if (within == 0 && (kb & 1) == 0 && k >= a.k_lo && k < a.k_hi)
+            u.x = add_mod(u.x, a.kadd_per_ct ? a.kadd[k * a.limbs + l] : a.k0[l], a.q[l]);
+        __stcs(o + i, u);
+    }
+}
+
+__global__ void k_ptadd_inplace(const OpsArgs a)
+{
+    const int n = 1 << a.logn;
+    const u64 cnt = (a.k_hi - a.k_lo) * (u64)a.limbs;
+    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < cnt; i += (u64)gridDim.x * blockDim.x) {
+        const u64 k = a.k_lo + i / a.limbs;
+        const int l = (int)(i % a.limbs);
+        u64* c = a.out + ((k * 2) * a.limbs + l) * (u64)n;
+        *c = add_mod(*c, a.kadd_per_ct ? a.kadd[k * a.limbs + l] : a.k0[l], a.q[l]);
+    }
+}
+
+// Plaintext constant multiply: every residue times the encoded constant (Shoup).
+__global__ void k_ptmul(const OpsArgs a)
+{
+    const int n = 1 << a.logn;
+    const u64 total2 = a.n_ct * (u64)(2 * a.limbs) * (n / 2);
+    const ulonglong2* x = reinterpret_cast<const ulonglong2*>(a.in0);
+    ulonglong2* o = reinterpret_cast<ulonglong2*>(a.out);
+    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total2; i += (u64)gridDim.x * blockDim.x) {
+        const int l = (int)((i / (n / 2)) % a.limbs);
+        const u64 q = a.q[l];
+        ulonglong2 u = __ldcs(x + i);
+        u.x = shoup(u.x, a.k0[l], a.k0p[l], q);
+        u.y = shoup(u.y, a.k0[l], a.k0p[l], q);
+        __stcs(o + i, u);
+    }
+}
+
+// Rescale of a whole image: output has limbs-1 limbs. One thread per (ct, poly, coefficient
+// pair), all limbs.
+template <int LIMBS>
+__global__ void k_rescale(const OpsArgs a)
+{
+    const int n = 1 << a.logn;
+    const u64 total = a.n_ct * 2 * (u64)(n / 2);
+    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total; i += (u64)gridDim.x * blockDim.x) {
+        const u64 kb = i / (n / 2);
+        const int c = (int)(i % (n / 2));
+        const ulonglong2* src = reinterpret_cast<const ulonglong2*>(a.in0 + kb * LIMBS * (u64)n) + c;
+        ulonglong2* dst = reinterpret_cast<ulonglong2*>(a.out + kb * (LIMBS - 1) * (u64)n) + c;
+        const ulonglong2 last = __ldcs(src + (LIMBS - 1) * (n / 2));
+#pragma unroll
+        for (int j = 0; j < LIMBS - 1; ++j) {
+            ulonglong2 v = __ldcs(src + j * (n / 2));
+            v.x = rescale_one(v.x, last.x, j, a);
+            v.y = rescale_one(v.y, last.y, j, a);
+            __stcs(dst + j * (n / 2), v);
+        }
+    }
+}
+
+// Fused 3x3 mean filter (Sec. 4.4.1, reading R13): out(y,x) = Rescale(K9 * sum of the 9
+// clamp-to-edge neighbours). One block per (row y, channel, poly, coefficient chunk); each
+// thread owns one coefficient pair and walks the row left to right keeping the three column
+// sums of the window in registers, so every input row is loaded once per output row.
+template <int LIMBS>
+__global__ void __launch_bounds__(256) k_meanfilter3(const OpsArgs a)
+{
+    const int n = 1 << a.logn;
+    const int chunks = (n / 2) / blockDim.x;
+    const int h = a.h, w = a.w, C = a.c;
+    u64 bid = blockIdx.x;
+    const int y = (int)(bid % h); bid /= h;
+    const int chunk = (int)(bid % chunks); bid /= chunks;
+    const int b = (int)(bid % 2); bid /= 2;
+    const int ch = (int)bid;
+    const int c2 = chunk * blockDim.x + threadIdx.x;  // coefficient-pair index
+    const u64 ct_len2 = (u64)2 * LIMBS * (n / 2);
+    const u64 out_len2 = (u64)2 * (LIMBS - 1) * (n / 2);
+    const ulonglong2* in = reinterpret_cast<const ulonglong2*>(a.in0) + (u64)b * LIMBS * (n / 2) + c2;
+    ulonglong2* out = reinterpret_cast<ulonglong2*>(a.out) + (u64)b * (LIMBS - 1) * (n / 2) + c2;
+    const int ym = y > 0 ? y - 1 : 0, yp = y + 1 < h ? y + 1 : h - 1;
+
+    ulonglong2 col[3][LIMBS];
+    auto column = [&](int xx, ulonglong2 (&dst)[LIMBS]) {
+        const u64 k0 = ((u64)ym * w + xx) * C + ch, k1 = ((u64)y * w + xx) * C + ch, k2 = ((u64)yp * w + xx) * C + ch;
+#pragma unroll
+        for (int l = 0; l < LIMBS; ++l) {
+            const u64 q = a.q[l];
+            ulonglong2 v0 = __ldg(in + k0 * ct_len2 + l * (n / 2));
+            ulonglong2 v1 = __ldg(in + k1 * ct_len2 + l * (n / 2));
+            ulonglong2 v2 = __ldg(in + k2 * ct_len2 + l * (n / 2));
+            dst[l].x = add_mod(add_mod(v0.x, v1.x, q), v2.x, q);
+            dst[l].y = add_mod(add_mod(v0.y, v1.y, q), v2.y, q);
+        }
+    };
+    column(0, col[0]);  // x = -1 clamps to 0
+#pragma unroll
+    for (int l = 0; l < LIMBS; ++l) col[1][l] = col[0][l];
+    column(w > 1 ? 1 : 0, col[2]);
+    for (int x = 0; x < w; ++x) {
+        ulonglong2 t[LIMBS];
+#pragma unroll
+        for (int l = 0; l < LIMBS; ++l) {
+            const u64 q = a.q[l];
+            u64 sx = add_mod(add_mod(col[0][l].x, col[1][l].x, q), col[2][l].x, q);
+            u64 sy = add_mod(add_mod(col[0][l].y, col[1][l].y, q), col[2][l].y, q);
+            t[l].x = shoup(sx, a.k0[l], a.k0p[l], q);
+            t[l].y = shoup(sy, a.k0[l], a.k0p[l], q);
+        }
+        ulonglong2* o = out + (((u64)y * w + x) * C + ch) * out_len2;
+#pragma unroll
+        for (int j = 0; j < LIMBS - 1; ++j) {
+            ulonglong2 v;
+            v.x = rescale_one(t[j].x, t[LIMBS - 1].x, j, a);
+            v.y = rescale_one(t[j].y, t[LIMBS - 1].y, j, a);
+            __stcs(o + j * (n / 2), v);
+        }
+        if (x + 1 < w) {
+#pragma unroll
+            for (int l = 0; l < LIMBS; ++l) { col[0][l] = col[1][l]; col[1][l] = col[2][l]; }
+            column(x + 2 < w ? x + 2 : w - 1, col[2]);
+        }
+    }
+}
+
+// Fused watermark blend (reading R15): out = Rescale(Ka * I + Kb * W), W broadcast over
+// channels when it has one channel.
+template <int LIMBS>
+__global__ void k_blend(const OpsArgs a)
+{
+    const int n = 1 << a.logn;
+    const u64 total = a.n_ct * 2 * (u64)(n / 2);
+    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total; i += (u64)gridDim.x * blockDim.x) {
+        const u64 kb = i / (n / 2);
+        const int c = (int)(i % (n / 2));
+        const u64 k = kb / 2, b = kb % 2;
+        const u64 kw = (k / a.c) * a.c_w + (a.c_w == 1 ? 0 : k % a.c);
+        const ulonglong2* s0 = reinterpret_cast<const ulonglong2*>(a.in0 + kb * LIMBS * (u64)n) + c;
+        const ulonglong2* s1 = reinterpret_cast<const ulonglong2*>(a.in1 + (kw * 2 + b) * LIMBS * (u64)n) + c;
+        ulonglong2 t[LIMBS];
+#pragma unroll
+        for (int l = 0; l < LIMBS; ++l) {
+            const u64 q = a.q[l];
+            ulonglong2 u = __ldcs(s0 + l * (n / 2)), v = __ldg(s1 + l * (n / 2));
+            t[l].x = add_mod(shoup(u.x, a.k0[l], a.k0p[l], q), shoup(v.x, a.k1[l], a.k1p[l], q), q);
+            t[l].y = add_mod(shoup(u.y, a.k0[l], a.k0p[l], q), shoup(v.y, a.k1[l], a.k1p[l], q), q);
+        }
+        ulonglong2* dst = reinterpret_cast<ulonglong2*>(a.out + kb * (LIMBS - 1) * (u64)n) + c;
+#pragma unroll
+        for (int j = 0; j < LIMBS - 1; ++j) {
+            ulonglong2 v;
+            v.x = rescale_one(t[j].x, t[LIMBS - 1].x, j, a);
+            v.y = rescale_one(t[j].y, t[LIMBS - 1].y, j, a);
+            __stcs(dst + j * (n / 2), v);
+        }
+    }
+}
+
+// 192-bit two's-complement helpers for the CRT decode.
+struct U192 { u64 w0, w1, w2; };
+
+__device__ __forceinline__ void add192(U192& x, const U192& y)
+{
+    const u64 s0 = x.w0 + y.w0, c0 = s0 < x.w0;
+    const u64 s1 = x.w1 + y.w1;
+    u64 c1 = s1 < x.w1;
+    const u64 s1c = s1 + c0;
+    c1 += s1c < s1;
+    x.w0 = s0; x.w1 = s1c; x.w2 = x.w2 + y.w2 + c1;
+}
+
+__device__ __forceinline__ void sub192(U192& x, const U192& y)
+{
+    const u64 d0 = x.w0 - y.w0, b0 = x.w0 < y.w0;
+    const u64 d1 = x.w1 - y.w1;
+    u64 b1 = x.w1 < y.w1;
+    const u64 d1b = d1 - b0;
+    b1 += d1 < b0;
+    x.w0 = d0; x.w1 = d1b; x.w2 = x.w2 - y.w2 - b1;
+}
+
+// (y * W) mod 2^192 for a 64-bit y and a 3-word W
+__device__ __forceinline__ U192 mul192(u64 y, const u64 (&w)[3])
+{
+    const u64 p0 = y * w[0], h0 = mulhi(y, w[0]);
+    const u64 p1 = y * w[1], h1 = mulhi(y, w[1]);
+    const u64 p2 = y * w[2];
+    const u64 r1 = h0 + p1, c = r1 < h0;
+    U192 r = {p0, r1, h1 + p2 + c};
+    return r;
+}
+
+// ---------------------------------------------------------------------------------------
+// Decryption of coefficient 0 (Sec. 2.2.2, reading R2) and exact CRT decoding (reading R17).
+// (c0 + c1*s)_0 = c0_0 + sum_j c1_j * srev_j with srev_0 = s_0, srev_j = -s_{N-j}; s is
+// ternary, so the sum is signed additions only. One block per ciphertext.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_decrypt(const DecArgs a)
+{
+    const int n = 1 << a.logn;
+    const int nl = a.crt.nl;
+    __shared__ u64 red[8][2][kMaxPrimes];
+    for (u64 k = blockIdx.x; k < a.n_ct; k += gridDim.x) {
+        const u64* ct = a.ct + k * 2 * (u64)nl * n;
+        u64 pos[kMaxPrimes], neg[kMaxPrimes];
+        for (int l = 0; l < nl; ++l) { pos[l] = 0; neg[l] = 0; }
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const int sg = a.srev[j];
+            if (sg == 0) continue;
+            for (int l = 0; l < nl; ++l) {
+                const u64 v = __ldcs(ct + ((u64)nl + l) * n + j);
+                if (sg > 0) pos[l] = add_mod(pos[l], v, a.q[l]);
+                else neg[l] = add_mod(neg[l], v, a.q[l]);
+            }
+        }
+        for (int l = 0; l < nl; ++l) {
+            const u64 q = a.q[l];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                pos[l] = add_mod(pos[l], __shfl_down_sync(0xffffffffu, pos[l], off), q);
+                neg[l] = add_mod(neg[l], __shfl_down_sync(0xffffffffu, neg[l], off), q);
+            }
+        }
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (lane == 0)
+            for (int l = 0; l < nl; ++l) { red[warp][0][l] = pos[l]; red[warp][1][l] = neg[l]; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            u64 y[kMaxPrimes];
+            double v = 0.0;
+            for (int l = 0; l < nl; ++l) {
+                const u64 q = a.q[l];
+                u64 p = ct[(u64)l * n], m = 0;  // c0 coefficient 0
+                for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) {
+                    p = add_mod(p, red[wi][0][l], q);
+                    m = add_mod(m, red[wi][1][l], q);
+                }
+                const u64 res = sub_mod(p, m, q);
+                if (a.residues_out) a.residues_out[k * nl + l] = res;
+                y[l] = shoup(res, a.crt.inv[l], a.crt.invp[l], q);
+                v += (double)y[l] * a.crt.qinv[l];
+            }
+            // x = sum_l y_l * (Q/q_l) - round(sum_l y_l/q_l) * Q, the centered CRT value,
+            // held modulo 2^192 (exact for |x| < 2^191)
+            const u64 kq = (u64)rint(v);
+            U192 x = {0, 0, 0};
+            for (int l = 0; l < nl; ++l) add192(x, mul192(y[l], a.crt.qiw[l]));
+            sub192(x, mul192(kq, a.crt.qw));
+            const bool negv = (x.w2 >> 63) != 0;
+            if (negv) {
+                U192 z = {0, 0, 0};
+                sub192(z, x);
+                x = z;
+            }
+            const u64 x0 = x.w0, x1 = x.w1, x2 = x.w2;
+            const double mag = (double)x2 * 0x1p128 + (double)x1 * 0x1p64 + (double)x0;
+            const double val = mag / a.scale;
+            a.out[k] = negv ? -val : val;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Launchers.
+// ---------------------------------------------------------------------------------------
+static unsigned grid_for(u64 work, int threads)
+{
+    u64 g = (work + threads - 1) / threads;
+    const u64 cap = 152ull * 16;  // enough blocks to fill every SM several times over
+    if (g > cap) g = cap;
+    return (unsigned)(g == 0 ? 1 : g);
+}
+
+cudaError_t launch_addsub(const OpsArgs& a, bool subtract, cudaStream_t st)
+{
+    const u64 work = a.n_ct * (u64)(2 * a.limbs) * ((1u << a.logn) / 2);
+    k_addsub<<<grid_for(work, 256), 256, 0, st>>>(a, subtract ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ptadd(const OpsArgs& a, cudaStream_t st)
+{
+    if (a.out == a.in0) {
+        const u64 work = (a.k_hi - a.k_lo) * (u64)a.limbs;
+        if (work == 0) return cudaSuccess;
+        k_ptadd_inplace<<<grid_for(work, 256), 256, 0, st>>>(a);
+    } else {
+        const u64 work = a.n_ct * (u64)(2 * a.limbs) * ((1u << a.logn) / 2);
+        k_ptadd_copy<<<grid_for(work, 256), 256, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ptmul(const OpsArgs& a, cudaStream_t st)
+{
+    const u64 work = a.n_ct * (u64)(2 * a.limbs) * ((1u << a.logn) / 2);
+    k_ptmul<<<grid_for(work, 256), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+#define ICHEE_LIMB_SWITCH(KERNEL, GRID, BLOCK, ARGS)                          \
+    switch (ARGS.limbs) {                                                     \
+    case 2: KERNEL<2><<<GRID, BLOCK, 0, st>>>(ARGS); break;                   \
+    case 3: KERNEL<3><<<GRID, BLOCK, 0, st>>>(ARGS); break;                   \
+    case 4: KERNEL<4><<<GRID, BLOCK, 0, st>>>(ARGS); break;                   \
+    case 5: KERNEL<5><<<GRID, BLOCK, 0, st>>>(ARGS); break;                   \
+    case 6: KERNEL<6><<<GRID, BLOCK, 0, st>>>(ARGS); break;                   \
+    case 7: KERNEL<7><<<GRID, BLOCK, 0, st>>>(ARGS); break;                   \
+    case 8: KERNEL<8><<<GRID, BLOCK, 0, st>>>(ARGS); break;                   \
+    default: return cudaErrorInvalidValue;                                    \
+    }
+
+cudaError_t launch_rescale(const OpsArgs& a, cudaStream_t st)
+{
+    const u64 work = a.n_ct * 2 * (u64)((1u << a.logn) / 2);
+    const unsigned g = grid_for(work, 256);
+    ICHEE_LIMB_SWITCH(k_rescale, g, 256, a)
+    return cudaGetLastError();
+}
+
+cudaError_t launch_meanfilter3(const OpsArgs& a, cudaStream_t st)
+{
+    const int n = 1 << a.logn;
+    const int threads = 256;
+    const int chunks = (n / 2) / threads;
+    const u64 blocks = (u64)a.h * chunks * 2 * a.c;
+    if (blocks == 0) return cudaSuccess;
+    ICHEE_LIMB_SWITCH(k_meanfilter3, (unsigned)blocks, threads, a)
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blend(const OpsArgs& a, cudaStream_t st)
+{
+    const u64 work = a.n_ct * 2 * (u64)((1u << a.logn) / 2);
+    const unsigned g = grid_for(work, 256);
+    ICHEE_LIMB_SWITCH(k_blend, g, 256, a)
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decrypt(const DecArgs& a, cudaStream_t st)
+{
+    if (a.n_ct == 0) return cudaSuccess;
+    unsigned grid = (unsigned)(a.n_ct < (1u << 30) ? a.n_ct : (1u << 30));
+    k_decrypt<<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace ichee

@@ -1,0 +1,91 @@
+// ops.h -- argument structures and launchers of the image operations, decryption and the
+// matching / relinearisation kernels (internal to libichee).
+#pragma once
+#include "internal.h"
+
+namespace ichee {
+
+struct OpsArgs {
+    int logn;
+    int limbs;                      // limbs of the input ciphertexts
+    u64 n_ct;
+    u64 q[kMaxPrimes], mu[kMaxPrimes];
+    // plaintext constants per limb (Shoup pairs): k0 for the first operand, k1 for the second
+    u64 k0[kMaxPrimes], k0p[kMaxPrimes], k1[kMaxPrimes], k1p[kMaxPrimes];
+    // rescale by q_t, t = limbs - 1: q_t^{-1} mod q_j (Shoup), (-q_t) mod q_j, (q_t - 1) / 2
+    u64 qt_inv[kMaxPrimes], qt_inv_p[kMaxPrimes], neg_qt_mod[kMaxPrimes], half_qt;
+    // plaintext add to ciphertexts [k_lo, k_hi): kadd[k * limbs + l] if kadd_per_ct, else k0[l]
+    const u64* kadd;
+    int kadd_per_ct;
+    u64 k_lo, k_hi;
+    // image shape (mean filter), channels of the second operand (blend)
+    int h, w, c, c_w;
+    const u64* in0;
+    const u64* in1;
+    u64* out;
+};
+
+// Exact CRT for one level (nl limbs): x = sum_l y_l * (Q/q_l) - k*Q with
+// y_l = r_l * (Q/q_l)^{-1} mod q_l and k = round(sum_l y_l / q_l).
+struct CrtLevel {
+    int nl;
+    u64 inv[kMaxPrimes], invp[kMaxPrimes];
+    u64 qiw[kMaxPrimes][3];        // (Q/q_l) mod 2^192
+    u64 qw[3];                     // Q mod 2^192
+    double qinv[kMaxPrimes];       // 1/q_l
+};
+
+struct DecArgs {
+    int logn;
+    u64 n_ct;
+    u64 q[kMaxPrimes];
+    CrtLevel crt;
+    const int8_t* srev;            // [N] s_0, -s_{N-1}, ..., -s_1
+    const u64* ct;                 // [n_ct][2][nl][N]
+    double scale;
+    double* out;                   // [n_ct]
+    u64* residues_out;             // optional [n_ct][nl]
+};
+
+cudaError_t launch_addsub(const OpsArgs& a, bool subtract, cudaStream_t st);
+cudaError_t launch_ptadd(const OpsArgs& a, cudaStream_t st);
+cudaError_t launch_ptmul(const OpsArgs& a, cudaStream_t st);
+cudaError_t launch_rescale(const OpsArgs& a, cudaStream_t st);
+cudaError_t launch_meanfilter3(const OpsArgs& a, cudaStream_t st);
+cudaError_t launch_blend(const OpsArgs& a, cudaStream_t st);
+cudaError_t launch_decrypt(const DecArgs& a, cudaStream_t st);
+
+// Matching: sum over ciphertexts of (a - b)^2 as a degree-2 ciphertext in the NTT domain.
+struct SqDiffArgs {
+    RnsArgs rns;                   // moduli 0..limbs-1
+    int limbs;
+    u64 n_ct;
+    const u64* a;
+    const u64* b;
+    u64* partial;                  // [n_blocks][3][N] scratch: block j accumulates limb j % limbs
+    int n_blocks;
+};
+cudaError_t launch_sqdiff_accumulate(const SqDiffArgs& a, cudaStream_t st);
+// tensor[p][l][x] = sum over blocks j = l (mod limbs) of partial[j][p][x]
+cudaError_t launch_sqdiff_reduce(const RnsArgs& rns, int limbs, const u64* partial, int n_blocks, u64* tensor,
+                                 cudaStream_t st);
+
+// Key switching of a degree-2 ciphertext (reading R11).
+struct RelinArgs {
+    RnsArgs rns;                   // moduli q_0..q_{L-1}, P at index L
+    int L;                         // limbs of the key (full chain)
+    int limbs;                     // limbs of the ciphertext (t + 1)
+    const u64* evk_hat;            // [L][2][L+1][N] NTT domain
+    const u64* evk_hat_p;          // Shoup companions
+    u64 p_inv[kMaxPrimes], p_inv_p[kMaxPrimes];  // P^{-1} mod q_j (Shoup)
+    u64 neg_p_mod[kMaxPrimes];     // (-P) mod q_j
+    u64 mu[kMaxModuli];
+};
+// digits[j][m][N] = centered residue of d2 limb j lifted to modulus m (m = 0..limbs-1, then P)
+cudaError_t launch_relin_digits(const RelinArgs& a, const u64* d2, u64* digits, cudaStream_t st);
+// acc[b][m][N] = sum_j digits^[j][m] * evk^_j[b][m]
+cudaError_t launch_relin_mac(const RelinArgs& a, const u64* digits_hat, u64* acc, cudaStream_t st);
+// out_b[j] = d_b[j] + (acc_b[j] - [acc_b[P]]_centered) * P^{-1} mod q_j
+cudaError_t launch_relin_moddown(const RelinArgs& a, const u64* d01, const u64* acc, u64* out, cudaStream_t st);
+
+}  // namespace ichee

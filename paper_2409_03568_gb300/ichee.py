@@ -1,0 +1,303 @@
+"""ctypes binding of libichee.so, the C ABI declared in include/ichee.h.
+
+Argument marshalling only: every function here forwards to the entry point of the same name,
+converting Python values to C types and raising IcheeError on a non-OK status. All arithmetic
+on ciphertexts runs in the library's CUDA kernels; there is no CPU fallback, and importing this
+module fails loudly when libichee.so has not been built (paper_2409_03568_gb300.build).
+
+Device memory comes from PyTorch tensors (their data_ptr()) and streams from
+torch.cuda.Stream.cuda_stream; the helper class Context wraps the handles for tests and the
+benchmark.
+"""
+import ctypes
+import os
+import re
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libichee.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "ichee.h")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        "libichee.so is not built (expected at %s); run `python -c \"import __graft_entry__ as g; g.build()\"` "
+        "or `python paper_2409_03568_gb300/build.py`" % LIB_PATH)
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+MAX_PRIMES = 8
+OK, EINVAL, ENOMEM, ECUDA, ELEVEL, ESCALE, EMISMATCH, ETIMEOUT, EUNSUPPORTED = range(9)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ELEVEL", "ESCALE", "EMISMATCH", "ETIMEOUT", "EUNSUPPORTED"]
+
+CACHE_RADIX, CACHE_FREQ, CACHE_FULL = 0, 1, 2
+OP_ADD, OP_SUB, OP_PTADD, OP_PTMUL, OP_RESCALE, OP_MEANFILTER3, OP_BRIGHTNESS, OP_BLEND, OP_WATERMARK_PIXEL, \
+    OP_SQDIFF_SUM = range(10)
+WITH_EVK = 1
+
+
+class IcheeError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status, message))
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("log_n", ctypes.c_uint32), ("n_primes", ctypes.c_uint32),
+                ("prime_bits", ctypes.c_uint32 * MAX_PRIMES), ("special_bits", ctypes.c_uint32),
+                ("log2_scale", ctypes.c_uint32), ("sigma", ctypes.c_double), ("gauss_bound", ctypes.c_uint32)]
+
+
+class CtImgMeta(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_uint32), ("w", ctypes.c_uint32), ("c", ctypes.c_uint32),
+                ("level", ctypes.c_uint32), ("scale", ctypes.c_double)]
+
+    @property
+    def n_ct(self):
+        return self.h * self.w * self.c
+
+    def __repr__(self):
+        return "CtImgMeta(h=%d, w=%d, c=%d, level=%d, scale=%r)" % (self.h, self.w, self.c, self.level, self.scale)
+
+
+class CacheDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("radix_base", ctypes.c_uint32), ("radix_randomize", ctypes.c_uint32),
+                ("top_k", ctypes.c_uint32), ("pool_size", ctypes.c_uint32), ("miss_policy", ctypes.c_uint32)]
+
+
+_vp = ctypes.c_void_p
+_u64 = ctypes.c_uint64
+_u32 = ctypes.c_uint32
+_sz = ctypes.c_size_t
+_st = ctypes.c_int
+
+_SIGS = {
+    "ichee_ctx_create": (_st, [ctypes.POINTER(Params), ctypes.c_int, ctypes.POINTER(_vp)]),
+    "ichee_ctx_destroy": (None, [_vp]),
+    "ichee_ctx_primes": (_st, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
+    "ichee_keygen": (_st, [_vp, _u64, _u32, _vp]),
+    "ichee_export_key": (_st, [_vp, ctypes.c_int, _vp, _sz, _vp]),
+    "ichee_build_cache": (_st, [_vp, ctypes.POINTER(CacheDesc), _vp, _sz, _u64, ctypes.POINTER(_vp), _vp]),
+    "ichee_cache_free": (None, [_vp]),
+    "ichee_cache_info": (_st, [_vp, ctypes.POINTER(_u32), _vp, ctypes.POINTER(_u32)]),
+    "ichee_cache_export": (_st, [_vp, ctypes.c_int, _vp, _sz, _vp]),
+    "ichee_ct_bytes": (_st, [_vp, _u32, ctypes.POINTER(_sz)]),
+    "ichee_encrypt_image": (_st, [_vp, _vp, _vp, _u32, _u32, _u32, _u64, _vp, ctypes.POINTER(CtImgMeta), _vp]),
+    "ichee_eval": (_st, [_vp, ctypes.c_int, _vp, ctypes.POINTER(CtImgMeta), _vp, ctypes.POINTER(CtImgMeta),
+                         _vp, _u32, _vp, ctypes.POINTER(CtImgMeta), _vp]),
+    "ichee_decrypt_image": (_st, [_vp, _vp, ctypes.POINTER(CtImgMeta), _vp, _vp]),
+    "ichee_decrypt_residues": (_st, [_vp, _vp, ctypes.POINTER(CtImgMeta), _vp, _vp, _vp]),
+    "ichee_stream_status": (_st, [_vp, _vp]),
+    "ichee_last_error": (ctypes.c_char_p, []),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def header_functions(path=HEADER):
+    """Names of the functions include/ichee.h declares."""
+    with open(path) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^\s*(?:ichee_status|void|const char\*)\s+(ichee_\w+)\s*\(", text, re.M)))
+
+
+def ichee_last_error():
+    return _lib.ichee_last_error().decode()
+
+
+def _check(status):
+    if status != OK:
+        raise IcheeError(status, ichee_last_error())
+
+
+def _ptr(x):
+    """Integer address of a tensor / numpy array / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError("cannot take the address of %r" % type(x))
+
+
+def make_params(log_n, prime_bits, log2_scale, special_bits=0, sigma=3.2, gauss_bound=19):
+    p = Params()
+    p.log_n = log_n
+    p.n_primes = len(prime_bits)
+    for i, b in enumerate(prime_bits):
+        p.prime_bits[i] = b
+    p.special_bits = special_bits
+    p.log2_scale = log2_scale
+    p.sigma = sigma
+    p.gauss_bound = gauss_bound
+    return p
+
+
+def ichee_ctx_create(params, device=0):
+    h = _vp()
+    _check(_lib.ichee_ctx_create(ctypes.byref(params), device, ctypes.byref(h)))
+    return h
+
+
+def ichee_ctx_destroy(ctx):
+    _lib.ichee_ctx_destroy(ctx)
+
+
+def ichee_ctx_primes(ctx, n_primes):
+    q = (_u64 * n_primes)()
+    p = _u64()
+    _check(_lib.ichee_ctx_primes(ctx, q, ctypes.byref(p)))
+    return [int(x) for x in q], int(p.value)
+
+
+def ichee_keygen(ctx, seed, flags=0, stream=None):
+    _check(_lib.ichee_keygen(ctx, seed, flags, stream))
+
+
+def ichee_export_key(ctx, which, host_array, stream=None):
+    _check(_lib.ichee_export_key(ctx, which, _ptr(host_array), host_array.nbytes, stream))
+
+
+def ichee_build_cache(ctx, desc, scan=None, n_scan=0, seed=0, stream=None):
+    h = _vp()
+    _check(_lib.ichee_build_cache(ctx, ctypes.byref(desc), _ptr(scan), n_scan, seed, ctypes.byref(h), stream))
+    return h
+
+
+def ichee_cache_free(cache):
+    _lib.ichee_cache_free(cache)
+
+
+def ichee_cache_info(cache):
+    n = _u32()
+    pool = _u32()
+    vals = (ctypes.c_uint8 * 256)()
+    _check(_lib.ichee_cache_info(cache, ctypes.byref(n), vals, ctypes.byref(pool)))
+    return [int(v) for v in vals[:n.value]], int(pool.value)
+
+
+def ichee_cache_export(cache, part, host_array, stream=None):
+    _check(_lib.ichee_cache_export(cache, part, _ptr(host_array), host_array.nbytes, stream))
+
+
+def ichee_ct_bytes(ctx, level):
+    b = _sz()
+    _check(_lib.ichee_ct_bytes(ctx, level, ctypes.byref(b)))
+    return int(b.value)
+
+
+def ichee_encrypt_image(ctx, cache, pixels, h, w, c, seed, ct_out, stream=None):
+    m = CtImgMeta()
+    _check(_lib.ichee_encrypt_image(ctx, cache, _ptr(pixels), h, w, c, seed, _ptr(ct_out), ctypes.byref(m), stream))
+    return m
+
+
+def ichee_eval(ctx, op, a, ma, b=None, mb=None, args=(), out=None, stream=None):
+    m = CtImgMeta()
+    n = len(args)
+    arr = (ctypes.c_double * max(n, 1))(*args)
+    _check(_lib.ichee_eval(ctx, op, _ptr(a), ctypes.byref(ma), _ptr(b), ctypes.byref(mb) if mb is not None else None,
+                           arr if n else None, n, _ptr(out), ctypes.byref(m), stream))
+    return m
+
+
+def ichee_decrypt_image(ctx, ct, meta, out, stream=None):
+    _check(_lib.ichee_decrypt_image(ctx, _ptr(ct), ctypes.byref(meta), _ptr(out), stream))
+
+
+def ichee_decrypt_residues(ctx, ct, meta, out, residues, stream=None):
+    _check(_lib.ichee_decrypt_residues(ctx, _ptr(ct), ctypes.byref(meta), _ptr(out), _ptr(residues), stream))
+
+
+def ichee_stream_status(ctx, stream=None):
+    _check(_lib.ichee_stream_status(ctx, stream))
+
+
+class Context:
+    """Owner of one ichee_ctx handle plus helpers that allocate torch device buffers for
+    ciphertext images. Marshalling only."""
+
+    def __init__(self, log_n, prime_bits, log2_scale, special_bits=0, sigma=3.2, gauss_bound=19, device=0):
+        import torch  # noqa: F401  (CUDA context + allocator)
+        self.params = make_params(log_n, prime_bits, log2_scale, special_bits, sigma, gauss_bound)
+        self.n = 1 << log_n
+        self.L = len(prime_bits)
+        self.device = device
+        self.handle = ichee_ctx_create(self.params, device)
+        self.q, self.P = ichee_ctx_primes(self.handle, self.L)
+        self.caches = []
+
+    def close(self):
+        for c in self.caches:
+            ichee_cache_free(c)
+        self.caches = []
+        if self.handle:
+            ichee_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def stream():
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def keygen(self, seed, with_evk=False):
+        ichee_keygen(self.handle, seed, WITH_EVK if with_evk else 0, self.stream())
+
+    def ct_words(self, level):
+        return ichee_ct_bytes(self.handle, level) // 8
+
+    def empty_cts(self, n_ct, level):
+        import torch
+        return torch.empty(n_ct * self.ct_words(level), dtype=torch.int64, device="cuda:%d" % self.device)
+
+    def build_cache(self, kind, seed, radix_base=0, randomize=1, top_k=0, pool_size=0, miss_policy=0, scan=None):
+        d = CacheDesc()
+        d.kind = kind
+        d.radix_base = radix_base
+        d.radix_randomize = randomize
+        d.top_k = top_k
+        d.pool_size = pool_size
+        d.miss_policy = miss_policy
+        n_scan = 0 if scan is None else (scan.numel() if hasattr(scan, "numel") else scan.size)
+        h = ichee_build_cache(self.handle, d, scan, n_scan, seed, self.stream())
+        self.caches.append(h)
+        return h
+
+    def encrypt(self, pixels, h, w, c, seed, cache=None, out=None):
+        if out is None:
+            out = self.empty_cts(h * w * c, self.L - 1)
+        m = ichee_encrypt_image(self.handle, cache, pixels, h, w, c, seed, out, self.stream())
+        return out, m
+
+    def eval(self, op, a, ma, b=None, mb=None, args=(), out=None, out_n_ct=None, out_level=None):
+        if out is None:
+            lvl = ma.level if out_level is None else out_level
+            out = self.empty_cts(ma.n_ct if out_n_ct is None else out_n_ct, lvl)
+        m = ichee_eval(self.handle, op, a, ma, b, mb, args, out, self.stream())
+        return out, m
+
+    def decrypt(self, ct, meta, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(meta.n_ct, dtype=torch.float64, device="cuda:%d" % self.device)
+        ichee_decrypt_image(self.handle, ct, meta, out, self.stream())
+        return out
+
+    def decrypt_residues(self, ct, meta):
+        import torch
+        out = torch.empty(meta.n_ct, dtype=torch.float64, device="cuda:%d" % self.device)
+        res = torch.empty(meta.n_ct * (meta.level + 1), dtype=torch.int64, device="cuda:%d" % self.device)
+        ichee_decrypt_residues(self.handle, ct, meta, out, res, self.stream())
+        return out, res
+
+    def status(self):
+        ichee_stream_status(self.handle, self.stream())

@@ -1,0 +1,342 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, element by element.
+
+Ciphertexts must be bit-exact; decoded values agree with the oracle's exact decode within 1e-9
+relative and, for fresh encryptions, lie within 1e-3 of the pixel. Every input is seeded; the
+oracle recomputes its own keys, caches and ciphertexts from the same seeds and never takes a
+value from the CUDA path.
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle, Params
+from paper_2409_03568_gb300 import inputs, workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+KEY_SEED = 1234
+IMG_SEED = 99
+CACHE_SEED = 777
+
+
+@pytest.fixture(scope="module")
+def ichee():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2409_03568_gb300 import ichee as mod
+    return mod
+
+
+def oracle_for(wl, with_evk=False, key_seed=KEY_SEED):
+    o = Oracle(Params(wl["log_n"], wl["prime_bits"], wl["log2_scale"], wl.get("special_bits", 0)))
+    return o.keygen(key_seed, with_evk=with_evk)
+
+
+def gpu_for(ichee, wl, with_evk=False, key_seed=KEY_SEED):
+    ctx = ichee.Context(**W.ctx_kwargs(wl))
+    ctx.keygen(key_seed, with_evk=with_evk)
+    return ctx
+
+
+def as_cts(t, n_ct, limbs, n):
+    return t.cpu().numpy().view(np.uint64).reshape(n_ct, 2, limbs, n)
+
+
+# --------------------------------------------------------------------------- set-up
+@pytest.mark.parametrize("wl", [W.TOY, W.ENC8192, W.OPS8192, W.RING16384], ids=lambda w: w["name"])
+def test_primes_match_oracle(ichee, wl):
+    ctx = ichee.Context(**W.ctx_kwargs(wl))
+    o = Oracle(Params(wl["log_n"], wl["prime_bits"], wl["log2_scale"], wl.get("special_bits", 0)))
+    assert ctx.q == [int(x) for x in o.q]
+    assert ctx.P == o.P
+    ctx.close()
+
+
+@pytest.mark.parametrize("wl,evk", [(W.TOY, False), (W.OPS8192, True)], ids=["toy", "ops8192_evk"])
+def test_keys_bit_exact(ichee, wl, evk):
+    ctx = gpu_for(ichee, wl, with_evk=evk)
+    o = oracle_for(wl, with_evk=evk)
+    n, L = ctx.n, ctx.L
+    s = np.zeros(n, dtype=np.int8)
+    ichee.ichee_export_key(ctx.handle, 0, s)
+    assert np.array_equal(s, o.s)
+    pk = np.zeros((2, L, n), dtype=np.uint64)
+    ichee.ichee_export_key(ctx.handle, 1, pk)
+    assert np.array_equal(pk, o.pk)
+    if evk:
+        e = np.zeros((L, 2, L + 1, n), dtype=np.uint64)
+        ichee.ichee_export_key(ctx.handle, 2, e)
+        assert np.array_equal(e, o.evk)
+    ctx.close()
+
+
+# --------------------------------------------------------------------- fresh (a2, a3, a8)
+def test_fresh_toy_bit_exact_and_decodes(ichee):
+    wl = W.TOY
+    ctx = gpu_for(ichee, wl)
+    o = oracle_for(wl)
+    pix = W.image_for(wl).reshape(-1)
+    ct, meta = ctx.encrypt(torch.from_numpy(pix).cuda(), wl["h"], wl["w"], wl["c"], IMG_SEED)
+    assert (meta.h, meta.w, meta.c, meta.level) == (8, 8, 1, 1) and meta.scale == 2.0 ** 25
+    got = as_cts(ct, 64, 2, ctx.n)
+    ref = o.encrypt_pixels(pix, IMG_SEED)
+    assert np.array_equal(got, ref)
+    dec = ctx.decrypt(ct, meta).cpu().numpy()
+    np.testing.assert_allclose(dec, o.decrypt(ref, o.delta), rtol=1e-9, atol=0)
+    assert np.max(np.abs(dec - pix)) < 1e-3
+    # host pixels and host output through the same entry points
+    ct2, _ = ctx.encrypt(pix.copy(), wl["h"], wl["w"], wl["c"], IMG_SEED)
+    assert torch.equal(ct, ct2)
+    host_out = np.zeros(64, dtype=np.float64)
+    ichee.ichee_decrypt_image(ctx.handle, ct2, meta, host_out, ctx.stream())
+    assert np.array_equal(host_out, dec)
+    ctx.close()
+
+
+def test_fresh_enc8192_full_image_sampled(ichee):
+    wl = W.ENC8192
+    ctx = gpu_for(ichee, wl)
+    o = oracle_for(wl)
+    pix = W.image_for(wl).reshape(-1)
+    n_ct = pix.size
+    ct, meta = ctx.encrypt(torch.from_numpy(pix).cuda(), wl["h"], wl["w"], wl["c"], IMG_SEED)
+    got = as_cts(ct, n_ct, 3, ctx.n)
+    rng = np.random.default_rng(0)
+    idx = np.unique(np.concatenate([[0, 1, n_ct - 1], rng.choice(n_ct, 13, replace=False)]))
+    ref = o.encrypt_pixels(pix[idx], IMG_SEED, ids=idx.astype(np.uint64))
+    for j, k in enumerate(idx):
+        assert np.array_equal(got[k], ref[j]), k
+    dec = ctx.decrypt(ct, meta).cpu().numpy()
+    assert np.max(np.abs(dec - pix)) < 1e-3
+    np.testing.assert_allclose(dec[idx], o.decrypt(ref, o.delta), rtol=1e-9, atol=0)
+    ctx.close()
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (3, 5, 1), (7, 1, 3), (2, 2, 2)])
+def test_fresh_ragged_shapes_toy(ichee, shape):
+    wl = W.TOY
+    ctx = gpu_for(ichee, wl)
+    o = oracle_for(wl)
+    h, w, c = shape
+    pix = inputs.uniform_image(h, w, seed=5, channels=c).reshape(-1)
+    if pix.size >= 2:
+        pix[0], pix[-1] = 0, 255
+    ct, meta = ctx.encrypt(torch.from_numpy(pix).cuda(), h, w, c, 31)
+    assert np.array_equal(as_cts(ct, pix.size, 2, ctx.n), o.encrypt_pixels(pix, 31))
+    ctx.close()
+
+
+# -------------------------------------------------------------------- caches (a4, a5)
+@pytest.mark.parametrize("randomize", [1, 0])
+def test_radix16_toy_bit_exact(ichee, randomize):
+    wl = W.TOY
+    ctx = gpu_for(ichee, wl)
+    o = oracle_for(wl)
+    cache = ctx.build_cache(ichee.CACHE_RADIX, CACHE_SEED, radix_base=16, randomize=randomize)
+    oc = o.radix_cache(16, CACHE_SEED)
+    radix = np.zeros((2, 2, 2, ctx.n), dtype=np.uint64)
+    ichee.ichee_cache_export(cache, 2, radix)
+    assert np.array_equal(radix, oc["cts"])
+    pix = W.image_for(wl).reshape(-1)
+    ct, meta = ctx.encrypt(torch.from_numpy(pix).cuda(), 8, 8, 1, IMG_SEED, cache=cache)
+    ref = o.encrypt_radix(pix, oc, IMG_SEED, randomize=bool(randomize))
+    assert np.array_equal(as_cts(ct, 64, 2, ctx.n), ref)
+    dec = ctx.decrypt(ct, meta).cpu().numpy()
+    assert np.max(np.abs(dec - pix)) < 1e-3
+    ctx.close()
+
+
+@pytest.fixture(scope="module")
+def enc8192(ichee):
+    wl = W.ENC8192
+    ctx = gpu_for(ichee, wl)
+    o = oracle_for(wl)
+    pix = W.image_for(wl).reshape(-1)
+    yield wl, ctx, o, pix
+    ctx.close()
+
+
+@pytest.mark.parametrize("base", [10, 16])
+def test_radix_enc8192_sampled(ichee, enc8192, base):
+    wl, ctx, o, pix = enc8192
+    cache = ctx.build_cache(ichee.CACHE_RADIX, CACHE_SEED, radix_base=base, randomize=1)
+    oc = o.radix_cache(base, CACHE_SEED)
+    n_pow = oc["n_pow"]
+    radix = np.zeros((n_pow, 2, 3, ctx.n), dtype=np.uint64)
+    ichee.ichee_cache_export(cache, 2, radix)
+    assert np.array_equal(radix, oc["cts"])
+    ct, meta = ctx.encrypt(torch.from_numpy(pix).cuda(), 64, 64, 1, IMG_SEED, cache=cache)
+    got = as_cts(ct, pix.size, 3, ctx.n)
+    idx = np.unique(np.concatenate([[0, pix.size - 1], np.random.default_rng(base).choice(pix.size, 30, replace=False)]))
+    ref = o.encrypt_radix(pix[idx], oc, IMG_SEED, ids=idx.astype(np.uint64))
+    for j, k in enumerate(idx):
+        assert np.array_equal(got[k], ref[j]), k
+    dec = ctx.decrypt(ct, meta).cpu().numpy()
+    assert np.max(np.abs(dec - pix)) < 1e-3
+
+
+@pytest.mark.parametrize("kind", ["freq", "full", "freq_radix_miss"])
+def test_lookup_enc8192_sampled(ichee, enc8192, kind):
+    wl, ctx, o, pix = enc8192
+    if kind == "freq":
+        cache = ctx.build_cache(ichee.CACHE_FREQ, CACHE_SEED, top_k=32, pool_size=64, scan=torch.from_numpy(pix).cuda())
+        oc = o.freq_cache(pix, 32, 64, CACHE_SEED)
+        miss = 0
+    elif kind == "freq_radix_miss":
+        cache = ctx.build_cache(ichee.CACHE_FREQ, CACHE_SEED, top_k=32, pool_size=16, miss_policy=1, radix_base=16,
+                                scan=pix.copy())
+        oc = o.freq_cache(pix, 32, 16, CACHE_SEED, radix_base=16)
+        miss = 1
+    else:
+        cache = ctx.build_cache(ichee.CACHE_FULL, CACHE_SEED, pool_size=64)
+        oc = o.full_cache(64, CACHE_SEED)
+        miss = 0
+    values, pool = ichee.ichee_cache_info(cache)
+    assert values == oc["values"] and pool == oc["pool_size"]
+    vc = np.zeros((len(values), 2, 3, ctx.n), dtype=np.uint64)
+    ichee.ichee_cache_export(cache, 0, vc)
+    assert np.array_equal(vc, oc["cts"])
+    zc = np.zeros((pool, 2, 3, ctx.n), dtype=np.uint64)
+    ichee.ichee_cache_export(cache, 1, zc)
+    assert np.array_equal(zc, oc["pool"])
+    ct, meta = ctx.encrypt(torch.from_numpy(pix).cuda(), 64, 64, 1, IMG_SEED, cache=cache)
+    got = as_cts(ct, pix.size, 3, ctx.n)
+    lut = oc["lut"]
+    hits = np.nonzero(lut[pix] >= 0)[0]
+    misses = np.nonzero(lut[pix] < 0)[0]
+    rng = np.random.default_rng(7)
+    idx = np.concatenate([rng.choice(hits, min(12, len(hits)), replace=False),
+                          rng.choice(misses, min(6, len(misses)), replace=False) if len(misses) else []]).astype(np.int64)
+    ref = o.encrypt_lookup(pix[idx], oc, IMG_SEED, miss_policy=miss, ids=idx.astype(np.uint64))
+    for j, k in enumerate(idx):
+        assert np.array_equal(got[k], ref[j]), (k, int(pix[k]))
+    dec = ctx.decrypt(ct, meta).cpu().numpy()
+    assert np.max(np.abs(dec - pix)) < 1e-3
+
+
+# ------------------------------------------------------------- small-ring ops (a6, a7)
+SMALL_OPS = dict(name="ops_n1024_l4", log_n=10, prime_bits=[60, 40, 40, 40], log2_scale=40, special_bits=61)
+
+
+@pytest.fixture(scope="module")
+def small_ops(ichee):
+    wl = SMALL_OPS
+    ctx = gpu_for(ichee, wl, with_evk=True)
+    o = oracle_for(wl, with_evk=True)
+    h, w, c = 5, 6, 3
+    img = inputs.random_field_image(h, w, seed=3, channels=c).reshape(-1)
+    img2 = inputs.noisy_copy(img, seed=6)
+    wm = inputs.binary_pattern(h, w, seed=5).reshape(-1)
+    g = {}
+    g["a"], g["ma"] = ctx.encrypt(torch.from_numpy(img).cuda(), h, w, c, 11)
+    g["b"], g["mb"] = ctx.encrypt(torch.from_numpy(img2).cuda(), h, w, c, 12)
+    g["w"], g["mw"] = ctx.encrypt(torch.from_numpy(wm).cuda(), h, w, 1, 13)
+    r = {"a": o.encrypt_pixels(img, 11), "b": o.encrypt_pixels(img2, 12), "w": o.encrypt_pixels(wm, 13)}
+    for k in "abw":
+        assert np.array_equal(as_cts(g[k], r[k].shape[0], 4, ctx.n), r[k])
+    yield ctx, o, (h, w, c), (img, img2, wm), g, r
+    ctx.close()
+
+
+def test_ops_add_sub_ptmul_rescale_small(ichee, small_ops):
+    ctx, o, (h, w, c), _, g, r = small_ops
+    n, nct = ctx.n, h * w * c
+    out, m = ctx.eval(ichee.OP_ADD, g["a"], g["ma"], g["b"], g["mb"])
+    assert np.array_equal(as_cts(out, nct, 4, n), o.add(r["a"], r["b"]))
+    out, m = ctx.eval(ichee.OP_SUB, g["a"], g["ma"], g["b"], g["mb"])
+    assert np.array_equal(as_cts(out, nct, 4, n), o.sub(r["a"], r["b"]))
+    out, m = ctx.eval(ichee.OP_PTMUL, g["a"], g["ma"], args=(-0.37,))
+    ref, sc = o.ptmul(r["a"], o.delta, -0.37)
+    assert np.array_equal(as_cts(out, nct, 4, n), ref)
+    assert m.scale == float(sc) and m.level == 3
+    out2, m2 = ctx.eval(ichee.OP_RESCALE, out, m, out_level=2)
+    ref2 = o.rescale(ref)
+    assert np.array_equal(as_cts(out2, nct, 3, n), ref2)
+    assert m2.level == 2
+    np.testing.assert_allclose(m2.scale, float(sc / int(o.q[3])), rtol=1e-15)
+    dec = ctx.decrypt(out2, m2).cpu().numpy()
+    np.testing.assert_allclose(dec, o.decrypt(ref2, sc / int(o.q[3])), rtol=1e-9)
+
+
+def test_ops_brightness_watermark_small(ichee, small_ops):
+    ctx, o, (h, w, c), (img, _, _), g, r = small_ops
+    n, nct = ctx.n, h * w * c
+    beta = inputs.brightness_beta(4)
+    out, m = ctx.eval(ichee.OP_BRIGHTNESS, g["a"], g["ma"], args=(beta,))
+    ref, sc = o.brightness(r["a"], o.delta, beta)
+    assert np.array_equal(as_cts(out, nct, 4, n), ref)
+    assert np.max(np.abs(ctx.decrypt(out, m).cpu().numpy() - (img + beta))) < 1e-3
+    out, m = ctx.eval(ichee.OP_WATERMARK_PIXEL, g["a"], g["ma"], args=(5.0, 17))
+    ref, _ = o.watermark_pixel(r["a"], o.delta, 5.0, 17)
+    assert np.array_equal(as_cts(out, nct, 4, n), ref)
+    # in place on a copy
+    cp = g["a"].clone()
+    ctx.eval(ichee.OP_WATERMARK_PIXEL, cp, g["ma"], args=(5.0, 17), out=cp)
+    assert torch.equal(cp, out)
+    # one constant per ciphertext
+    vals = np.linspace(-3, 3, nct)
+    out, m = ctx.eval(ichee.OP_PTADD, g["a"], g["ma"], args=tuple(vals))
+    ref = o.add_int(r["a"], [o.encode_const(v, o.delta) for v in vals])
+    assert np.array_equal(as_cts(out, nct, 4, n), ref)
+
+
+def test_ops_meanfilter_blend_small(ichee, small_ops):
+    ctx, o, (h, w, c), (img, _, wm), g, r = small_ops
+    n, nct = ctx.n, h * w * c
+    out, m = ctx.eval(ichee.OP_MEANFILTER3, g["a"], g["ma"], out_level=2)
+    ref, sc = o.meanfilter3(r["a"], o.delta, h, w, c)
+    assert np.array_equal(as_cts(out, nct, 3, n), ref)
+    np.testing.assert_allclose(m.scale, float(sc), rtol=1e-15)
+    dec = ctx.decrypt(out, m).cpu().numpy()
+    np.testing.assert_allclose(dec, o.decrypt(ref, sc), rtol=1e-9)
+    out, m = ctx.eval(ichee.OP_BLEND, g["a"], g["ma"], g["w"], g["mw"], args=(0.9,), out_level=2)
+    ref, sc = o.blend(r["a"], r["w"], o.delta, 0.9, c, 1)
+    assert np.array_equal(as_cts(out, nct, 3, n), ref)
+
+
+def test_ops_match_small(ichee, small_ops):
+    ctx, o, (h, w, c), (img, img2, _), g, r = small_ops
+    out, m = ctx.eval(ichee.OP_SQDIFF_SUM, g["a"], g["ma"], g["b"], g["mb"], out_n_ct=1, out_level=2)
+    ref, sc = o.match(r["a"], r["b"], o.delta)
+    assert np.array_equal(as_cts(out, 1, 3, ctx.n), ref)
+    assert (m.h, m.w, m.c, m.level) == (1, 1, 1, 2)
+    dec = ctx.decrypt(out, m).cpu().numpy()
+    np.testing.assert_allclose(dec, o.decrypt(ref, sc), rtol=1e-9)
+    plain = float(((img.astype(np.float64) - img2) ** 2).sum())
+    assert abs(dec[0] - plain) < 1e-2
+
+
+# ------------------------------------------------------------------------ errors
+def test_error_paths(ichee):
+    wl = W.TOY
+    ctx = gpu_for(ichee, wl)
+    pix = torch.zeros(4, dtype=torch.uint8, device="cuda")
+    with pytest.raises(ichee.IcheeError) as e:
+        ctx.encrypt(pix, 0, 2, 2, 1)
+    assert e.value.status == ichee.EINVAL
+    host_out = np.zeros(ctx.ct_words(1) * 4, dtype=np.uint64)
+    with pytest.raises(ichee.IcheeError) as e:
+        ichee.ichee_encrypt_image(ctx.handle, None, pix, 2, 2, 1, 1, host_out, ctx.stream())
+    assert e.value.status == ichee.EINVAL
+    ct, m = ctx.encrypt(pix, 2, 2, 1, 1)
+    r1, m1 = ctx.eval(ichee.OP_RESCALE, ct, m, out_level=0)
+    with pytest.raises(ichee.IcheeError) as e:
+        ctx.eval(ichee.OP_RESCALE, r1, m1)
+    assert e.value.status == ichee.ELEVEL
+    p2, mp = ctx.eval(ichee.OP_PTMUL, ct, m, args=(2.0,))
+    with pytest.raises(ichee.IcheeError) as e:
+        ctx.eval(ichee.OP_ADD, ct, m, p2, mp)
+    assert e.value.status == ichee.ESCALE
+    with pytest.raises(ichee.IcheeError) as e:
+        ctx.eval(ichee.OP_SQDIFF_SUM, ct, m, ct, m, out_n_ct=1)
+    assert e.value.status == ichee.EUNSUPPORTED
+    other = gpu_for(ichee, wl)
+    cache = other.build_cache(ichee.CACHE_RADIX, 1, radix_base=16)
+    with pytest.raises(ichee.IcheeError) as e:
+        ctx.encrypt(pix, 2, 2, 1, 1, cache=cache)
+    assert e.value.status == ichee.EMISMATCH
+    with pytest.raises(ichee.IcheeError):
+        ichee.Context(log_n=9, prime_bits=[30], log2_scale=20)
+    ctx.status()
+    other.close()
+    ctx.close()
