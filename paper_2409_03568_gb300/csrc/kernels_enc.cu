@@ -60,7 +60,7 @@ cudaError_t launch_sample_uniform(u64* out, int n, u64 q, u64 seed, u32 stream_i
 // ---------------------------------------------------------------------------------------
 
 template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::T) k_ntt_fwd(RnsArgs rns, PolyBatch b)
+__global__ void __launch_bounds__(NttShape<LOGN>::T) k_ntt_fwd(const __grid_constant__ RnsArgs rns, const __grid_constant__ PolyBatch b)
 {
     extern __shared__ u64 sm[];
     const int tid = threadIdx.x;
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_ntt_fwd(RnsArgs rns, Poly
 }
 
 template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::T) k_ntt_inv(RnsArgs rns, PolyBatch b)
+__global__ void __launch_bounds__(NttShape<LOGN>::T) k_ntt_inv(const __grid_constant__ RnsArgs rns, const __grid_constant__ PolyBatch b)
 {
     extern __shared__ u64 sm[];
     const int tid = threadIdx.x;
@@ -234,7 +234,7 @@ cudaError_t launch_axpy_const(u64* out, const u64* x, const u64* y, u64 c, int n
 // ---------------------------------------------------------------------------------------
 
 template <int LOGN, bool KEEP_VHAT>
-__global__ void __launch_bounds__(NttShape<LOGN>::T, 1) k_encrypt_fresh(const EncArgs a)
+__global__ void __launch_bounds__(NttShape<LOGN>::T, 1) k_encrypt_fresh(const __grid_constant__ EncArgs a)
 {
     constexpr int N = 1 << LOGN;
     constexpr int T = NttShape<LOGN>::T;
@@ -373,7 +373,7 @@ cudaError_t launch_radix_multiples(const u64* radix_cts, int n_pow, int r, const
 // Radix combine: one block per ciphertext. Signed digits d'_k = d_k + b_k - r*b_{k+1} with b
 // from bit k of the pixel's randomness word (stream 3); c = sum_k M[k][d'_k], residue-wise
 // modular sums of cached rows, 16-byte loads, streaming 16-byte stores.
-__global__ void __launch_bounds__(256) k_radix_combine(const RadixArgs a)
+__global__ void __launch_bounds__(256) k_radix_combine(const __grid_constant__ RadixArgs a)
 {
     const int n = 1 << a.logn;
     const size_t ct_len = (size_t)2 * a.L * n;
@@ -421,7 +421,7 @@ cudaError_t launch_radix_combine(const RadixArgs& a, cudaStream_t st)
 
 // Value lookup with the randomness pool: c = C[lut[p]] (+) Z[idx], idx = floor(w*M / 2^32)
 // from stream 4. Pixels whose value is not cached are left to another kernel.
-__global__ void __launch_bounds__(256) k_lookup_combine(const LookupArgs a)
+__global__ void __launch_bounds__(256) k_lookup_combine(const __grid_constant__ LookupArgs a)
 {
     const int n = 1 << a.logn;
     const size_t ct_len = (size_t)2 * a.L * n;

@@ -9,13 +9,17 @@ namespace ichee {
 // One block per SM-sized share of the work: block j owns limb l = j % limbs and every
 // (n_blocks/limbs)-th ciphertext. Per ciphertext it forms d = a - b for its limb, transforms
 // d0 and d1, and accumulates (d0^2, 2 d0 d1, d1^2) position by position into its own slice of
-// the scratch buffer (each position is owned by one thread, so no atomics are needed).
-template <int LOGN, bool KEEP>
-__global__ void __launch_bounds__(NttShape<LOGN>::T, 1) k_sqdiff_accumulate(const SqDiffArgs a)
+// the scratch buffer (each position is owned by one thread, so no atomics are needed). The
+// transform of d0 waits in a second shared-memory buffer (SMEM_D0) or, for the 2^14 ring whose
+// buffers do not both fit, in the fourth scratch row.
+template <int LOGN, bool SMEM_D0>
+__global__ void __launch_bounds__(NttShape<LOGN>::T, 1) k_sqdiff_accumulate(const __grid_constant__ SqDiffArgs a)
 {
     constexpr int N = 1 << LOGN;
     constexpr int LAST = NttShape<LOGN>::LAST;
     extern __shared__ u64 buf[];
+    u64* acc = a.partial + (size_t)blockIdx.x * 4 * N;
+    u64* d0buf = SMEM_D0 ? buf + N : acc + 3 * N;
     const int tid = threadIdx.x;
     const int limbs = a.limbs;
     const int l = blockIdx.x % limbs;
@@ -24,7 +28,6 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T, 1) k_sqdiff_accumulate(cons
     const u64 q = a.rns.q[l];
     const u64 m0 = a.rns.m0[l], m1 = a.rns.m1[l];
     const ModTables t = a.rns.tab[l];
-    u64* acc = a.partial + (size_t)blockIdx.x * 4 * N;
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
         const int x = elem_index<LOGN, LAST>(tid, e);
@@ -35,11 +38,13 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T, 1) k_sqdiff_accumulate(cons
     for (u64 k = start; k < a.n_ct; k += stride) {
         const u64* A = a.a + k * 2 * (u64)limbs * N;
         const u64* B = a.b + k * 2 * (u64)limbs * N;
-        u64 r[16];
-        u64 d0h[KEEP ? 16 : 1];
+        // d_b = a_b - b_b for b = 0, 1, transformed and parked: d0 in its own buffer (or the
+        // fourth scratch row), d1 in the transform buffer once every thread is done reading it
+#pragma unroll 1
         for (int pb = 0; pb < 2; ++pb) {
             const u64* pa = A + ((u64)pb * limbs + l) * N;
             const u64* pbb = B + ((u64)pb * limbs + l) * N;
+            u64 r[16];
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
                 const int x = elem_index<LOGN, 0>(tid, e);
@@ -47,22 +52,19 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T, 1) k_sqdiff_accumulate(cons
             }
             __syncthreads();
             ntt_fwd_regs<LOGN>(buf, r, tid, t, q);
-            if (pb == 0) {
+            __syncthreads();
+            u64* dst = pb == 0 ? d0buf : buf;
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    const u64 v = csub(csub(r[e], 2 * q), q);
-                    if constexpr (KEEP) d0h[e] = v;
-                    else acc[3 * N + elem_index<LOGN, LAST>(tid, e)] = v;
-                }
+            for (int e = 0; e < 16; ++e) {
+                const int x = elem_index<LOGN, LAST>(tid, e);
+                dst[SMEM_D0 || pb ? swz(x) : x] = csub(csub(r[e], 2 * q), q);
             }
         }
-#pragma unroll
+#pragma unroll 1
         for (int e = 0; e < 16; ++e) {
             const int x = elem_index<LOGN, LAST>(tid, e);
-            const u64 d1 = csub(csub(r[e], 2 * q), q);
-            u64 d0;
-            if constexpr (KEEP) d0 = d0h[e];
-            else d0 = acc[3 * N + x];
+            const u64 d1 = buf[swz(x)];
+            const u64 d0 = SMEM_D0 ? d0buf[swz(x)] : d0buf[x];
             const u64 t0 = mul_mod(d0, d0, q, m0, m1);
             u64 t1 = mul_mod(d0, d1, q, m0, m1);
             t1 = add_mod(t1, t1, q);
@@ -78,7 +80,7 @@ template <int LOGN>
 static cudaError_t sqdiff_launch(const SqDiffArgs& a, cudaStream_t st)
 {
     constexpr bool keep = LOGN <= 13;
-    const size_t smem = sizeof(u64) << LOGN;
+    const size_t smem = (keep ? 2 : 1) * (sizeof(u64) << LOGN);
     cudaError_t e = cudaFuncSetAttribute(k_sqdiff_accumulate<LOGN, keep>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -124,7 +126,7 @@ cudaError_t launch_sqdiff_reduce(const RnsArgs& rns, int limbs, const u64* parti
 // Relinearisation by hybrid key switching with one special prime P (reading R11).
 // ---------------------------------------------------------------------------------------
 
-__global__ void k_relin_digits(const RelinArgs a, const u64* d2, u64* digits)
+__global__ void k_relin_digits(const __grid_constant__ RelinArgs a, const u64* d2, u64* digits)
 {
     const int n = 1 << a.rns.logn;
     const int nm = a.limbs + 1;
@@ -153,7 +155,7 @@ cudaError_t launch_relin_digits(const RelinArgs& a, const u64* d2, u64* digits, 
     return cudaGetLastError();
 }
 
-__global__ void k_relin_mac(const RelinArgs a, const u64* digits_hat, u64* acc)
+__global__ void k_relin_mac(const __grid_constant__ RelinArgs a, const u64* digits_hat, u64* acc)
 {
     const int n = 1 << a.rns.logn;
     const int nm = a.limbs + 1;
@@ -179,7 +181,7 @@ cudaError_t launch_relin_mac(const RelinArgs& a, const u64* digits_hat, u64* acc
     return cudaGetLastError();
 }
 
-__global__ void k_relin_moddown(const RelinArgs a, const u64* d01, const u64* acc, u64* out)
+__global__ void k_relin_moddown(const __grid_constant__ RelinArgs a, const u64* d01, const u64* acc, u64* out)
 {
     const int n = 1 << a.rns.logn;
     const int nm = a.limbs + 1;

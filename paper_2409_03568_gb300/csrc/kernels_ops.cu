@@ -17,7 +17,7 @@ __device__ __forceinline__ u64 rescale_one(u64 cj, u64 ct, int j, const OpsArgs&
 }
 
 // Elementwise add / sub of two images with the same shape (Sec. 2.2.3, Sec. 3.3).
-__global__ void k_addsub(const OpsArgs a, int subtract)
+__global__ void k_addsub(const __grid_constant__ OpsArgs a, int subtract)
 {
     const int n = 1 << a.logn;
     const u64 total2 = a.n_ct * (u64)(2 * a.limbs) * (n / 2);
@@ -39,7 +39,7 @@ __global__ void k_addsub(const OpsArgs a, int subtract)
 // kadd[k * limbs + l] (one constant per ciphertext) or k0[l] (one for all); only ciphertexts
 // in [k_lo, k_hi) change. With in0 != out the whole image is
 // copied first.
-__global__ void k_ptadd_copy(const OpsArgs a)
+__global__ void k_ptadd_copy(const __grid_constant__ OpsArgs a)
 {
     const int n = 1 << a.logn;
     const u64 total2 = a.n_ct * (u64)(2 * a.limbs) * (n / 2);
@@ -58,7 +58,7 @@ __global__ void k_ptadd_copy(const OpsArgs a)
     }
 }
 
-__global__ void k_ptadd_inplace(const OpsArgs a)
+__global__ void k_ptadd_inplace(const __grid_constant__ OpsArgs a)
 {
     const int n = 1 << a.logn;
     const u64 cnt = (a.k_hi - a.k_lo) * (u64)a.limbs;
@@ -71,7 +71,7 @@ __global__ void k_ptadd_inplace(const OpsArgs a)
 }
 
 // Plaintext constant multiply: every residue times the encoded constant (Shoup).
-__global__ void k_ptmul(const OpsArgs a)
+__global__ void k_ptmul(const __grid_constant__ OpsArgs a)
 {
     const int n = 1 << a.logn;
     const u64 total2 = a.n_ct * (u64)(2 * a.limbs) * (n / 2);
@@ -90,7 +90,7 @@ __global__ void k_ptmul(const OpsArgs a)
 // Rescale of a whole image: output has limbs-1 limbs. One thread per (ct, poly, coefficient
 // pair), all limbs.
 template <int LIMBS>
-__global__ void k_rescale(const OpsArgs a)
+__global__ void k_rescale(const __grid_constant__ OpsArgs a)
 {
     const int n = 1 << a.logn;
     const u64 total = a.n_ct * 2 * (u64)(n / 2);
@@ -115,7 +115,7 @@ __global__ void k_rescale(const OpsArgs a)
 // thread owns one coefficient pair and walks the row left to right keeping the three column
 // sums of the window in registers, so every input row is loaded once per output row.
 template <int LIMBS>
-__global__ void __launch_bounds__(256) k_meanfilter3(const OpsArgs a)
+__global__ void __launch_bounds__(256) k_meanfilter3(const __grid_constant__ OpsArgs a)
 {
     const int n = 1 << a.logn;
     const int chunks = (n / 2) / blockDim.x;
@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(256) k_meanfilter3(const OpsArgs a)
 // Fused watermark blend (reading R15): out = Rescale(Ka * I + Kb * W), W broadcast over
 // channels when it has one channel.
 template <int LIMBS>
-__global__ void k_blend(const OpsArgs a)
+__global__ void k_blend(const __grid_constant__ OpsArgs a)
 {
     const int n = 1 << a.logn;
     const u64 total = a.n_ct * 2 * (u64)(n / 2);
@@ -247,7 +247,7 @@ __device__ __forceinline__ U192 mul192(u64 y, const u64 (&w)[3])
 // (c0 + c1*s)_0 = c0_0 + sum_j c1_j * srev_j with srev_0 = s_0, srev_j = -s_{N-j}; s is
 // ternary, so the sum is signed additions only. One block per ciphertext.
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_decrypt(const DecArgs a)
+__global__ void __launch_bounds__(256) k_decrypt(const __grid_constant__ DecArgs a)
 {
     const int n = 1 << a.logn;
     const int nl = a.crt.nl;
