@@ -226,6 +226,27 @@ ichee_status ichee_decrypt_residues(ichee_ctx* ctx, const uint64_t* d_ct, const 
                                     uint64_t* residues_out, void* stream);
 
 /*
+ * Matching (the ICHEE_OP_SQDIFF_SUM operation) for callers that cannot allocate device
+ * memory: processes whose GPU memory is handed out by their own arena or pool, or loops that
+ * must not risk the device-wide synchronisation cudaMalloc / cudaFree can cause. The paper
+ * has no counterpart; this is an interface for such callers. Same arguments, checks and
+ * result as ichee_eval with ICHEE_OP_SQDIFF_SUM (d_a, d_b: device inputs; d_out: caller's
+ * device output of one ciphertext at level - 1; *mout receives its metadata), but no call to
+ * cudaMalloc, cudaFree or any other allocating routine: the working memory is one static
+ * device array of ICHEE_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
+ * the process exits. The first call on each device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call before any stream
+ * capture. All calls share the array and it keeps the last call's contents (the kernels
+ * overwrite or zero everything they read), so calls that overlap on the GPU -- on different
+ * streams, or from different contexts on one device -- race: order them. A shape whose
+ * working set exceeds the array fails with ICHEE_EINVAL and a message giving both sizes.
+ */
+#define ICHEE_NOALLOC_SCRATCH_BYTES (32u << 20)
+ichee_status ichee_sqdiff_sum_noalloc(ichee_ctx* ctx, const uint64_t* d_a, const ichee_ctimg_meta* ma,
+                                      const uint64_t* d_b, const ichee_ctimg_meta* mb, uint64_t* d_out,
+                                      ichee_ctimg_meta* mout, void* stream);
+
+/*
  * Wait for `stream` and collect errors of work enqueued on it (CUDA launch or execution
  * errors, the context's device-side status word). Returns ICHEE_OK, ICHEE_ECUDA or
  * ICHEE_ETIMEOUT and clears the status word.

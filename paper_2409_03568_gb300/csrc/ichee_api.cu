@@ -1026,3 +1026,135 @@ extern "C" ichee_status ichee_stream_status(ichee_ctx* c, void* stream)
     }
     return ICHEE_OK;
 }
+
+// ---------------------------------------------------------------------------------------
+// Matching without device allocation (ichee_sqdiff_sum_noalloc)
+//
+// For callers that cannot allocate device memory during their work: processes whose HBM is
+// handed out by their own arena or a serving framework's pool, and latency-critical loops
+// that must not risk the device-wide synchronisation cudaMalloc / cudaFree can cause. The
+// scratch that ICHEE_OP_SQDIFF_SUM allocates lives here instead in one file-scope device
+// array of ICHEE_NOALLOC_SCRATCH_BYTES, which every GPU that loads this library holds until
+// the process exits. Host code cannot use the array's name as a device address; the address
+// comes from cudaGetSymbolAddress, once per device, on that device's first call.
+// ---------------------------------------------------------------------------------------
+#include <mutex>
+
+static __device__ __align__(256) uint64_t g_noalloc_scratch[ICHEE_NOALLOC_SCRATCH_BYTES / 8];
+
+static std::mutex g_noalloc_mu;
+static u64* g_noalloc_addr[64] = {};
+
+// Device address of the scratch array for `device` (which must be current).
+static ichee_status noalloc_scratch(int device, u64** out)
+{
+    if (device < 0 || device >= 64) return fail(ICHEE_EINVAL, "device %d out of range", device);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess)
+            return fail(ICHEE_ECUDA, "cudaGetSymbolAddress(scratch) on device %d: %s", device, cudaGetErrorString(e));
+        g_noalloc_addr[device] = (u64*)p;
+    }
+    *out = g_noalloc_addr[device];
+    return ICHEE_OK;
+}
+
+extern "C" ichee_status ichee_sqdiff_sum_noalloc(ichee_ctx* c, const uint64_t* d_a, const ichee_ctimg_meta* ma,
+                                                 const uint64_t* d_b, const ichee_ctimg_meta* mb, uint64_t* d_out,
+                                                 ichee_ctimg_meta* mout, void* stream)
+{
+    if (!c || !mout) return fail(ICHEE_EINVAL, "null argument");
+    CK(cudaSetDevice(c->device));
+    ichee_status s = check_img(c, d_a, ma, "a");
+    if (s != ICHEE_OK) return s;
+    s = check_img(c, d_b, mb, "b");
+    if (s != ICHEE_OK) return s;
+    if (!d_out || !is_device_ptr(d_out)) return fail(ICHEE_EINVAL, "output must be device memory");
+    if (mb->level != ma->level) return fail(ICHEE_ELEVEL, "levels differ (%u vs %u)", ma->level, mb->level);
+    if (!same_scale(ma->scale, mb->scale)) return fail(ICHEE_ESCALE, "scales differ (%g vs %g)", ma->scale, mb->scale);
+    if (mb->h != ma->h || mb->w != ma->w || mb->c != ma->c) return fail(ICHEE_EMISMATCH, "shapes differ");
+    if (!c->have_evk) return fail(ICHEE_EUNSUPPORTED, "matching needs the evaluation key (ICHEE_WITH_EVK)");
+    if (ma->level == 0) return fail(ICHEE_ELEVEL, "matching needs a limb to drop");
+    const int limbs = (int)ma->level + 1;
+    const size_t n = (size_t)c->n;
+    const int L = c->L;
+    // fixed part: tensor, digits, key-switch accumulators, relinearised result; then one
+    // 4-row slice per accumulating block, as many blocks as fit (a multiple of limbs)
+    const size_t tensor_w = (size_t)3 * limbs * n;
+    const size_t digits_w = (size_t)limbs * (limbs + 1) * n;
+    const size_t acc_w = (size_t)2 * (limbs + 1) * n;
+    const size_t rel_w = (size_t)2 * limbs * n;
+    const size_t fixed_w = tensor_w + digits_w + acc_w + rel_w;
+    const size_t cap_w = ICHEE_NOALLOC_SCRATCH_BYTES / 8;
+    const size_t slice_w = 4 * n;
+    const size_t fit = fixed_w < cap_w ? (cap_w - fixed_w) / slice_w : 0;
+    int n_blocks = (c->num_sms / limbs) * limbs;
+    if (n_blocks < limbs) n_blocks = limbs;
+    if ((size_t)n_blocks > fit) n_blocks = (int)((fit / limbs) * limbs);
+    if (n_blocks < limbs)
+        return fail(ICHEE_EINVAL, "matching at N=%zu with %d limbs needs %zu bytes of scratch; the allocation-free "
+                    "scratch holds %u bytes", n, limbs, (fixed_w + (size_t)limbs * slice_w) * 8,
+                    (unsigned)ICHEE_NOALLOC_SCRATCH_BYTES);
+    u64* base = nullptr;
+    s = noalloc_scratch(c->device, &base);
+    if (s != ICHEE_OK) return s;
+    u64* tensor = base;
+    u64* digits = tensor + tensor_w;
+    u64* acc = digits + digits_w;
+    u64* rel = acc + acc_w;
+    u64* partial = rel + rel_w;   // the accumulate kernel zeroes its own slices
+    cudaStream_t st = (cudaStream_t)stream;
+
+    SqDiffArgs sa;
+    std::memset(&sa, 0, sizeof(sa));
+    sa.rns = rns_prefix(c, limbs);
+    sa.limbs = limbs;
+    sa.n_ct = (u64)ma->h * ma->w * ma->c;
+    sa.a = d_a;
+    sa.b = d_b;
+    sa.partial = partial;
+    sa.n_blocks = n_blocks;
+    CK(launch_sqdiff_accumulate(sa, st));
+    CK(launch_sqdiff_reduce(sa.rns, limbs, partial, n_blocks, tensor, st));
+    int id[kMaxModuli];
+    for (int m = 0; m < kMaxModuli; ++m) id[m] = m;
+    CK(launch_ntt_inv(c->rns, batch(tensor, 3 * limbs, limbs, id), st));
+    CK(launch_scale_const(c->rns, batch(tensor, 3 * limbs, limbs, id), c->d_ninv, st));
+
+    RelinArgs ra;
+    std::memset(&ra, 0, sizeof(ra));
+    ra.rns = c->rns;
+    ra.L = L;
+    ra.limbs = limbs;
+    ra.evk_hat = c->d_evk_hat;
+    ra.evk_hat_p = c->d_evk_hat_p;
+    for (int m = 0; m < c->nmod; ++m) ra.mu[m] = c->rns.mu[m];
+    for (int j = 0; j < limbs; ++j) {
+        ra.p_inv[j] = hm::invm(c->P % c->q[j], c->q[j]);
+        ra.p_inv_p[j] = hm::shoup_of(ra.p_inv[j], c->q[j]);
+        const u64 r = c->P % c->q[j];
+        ra.neg_p_mod[j] = r == 0 ? 0 : c->q[j] - r;
+    }
+    int midx[kMaxModuli];
+    for (int m = 0; m < limbs; ++m) midx[m] = m;
+    midx[limbs] = L;
+    CK(launch_relin_digits(ra, tensor + (size_t)2 * limbs * n, digits, st));
+    CK(launch_ntt_fwd(c->rns, batch(digits, limbs * (limbs + 1), limbs + 1, midx), st));
+    CK(launch_relin_mac(ra, digits, acc, st));
+    CK(launch_ntt_inv(c->rns, batch(acc, 2 * (limbs + 1), limbs + 1, midx), st));
+    CK(launch_relin_moddown(ra, tensor, acc, rel, st));
+
+    ichee_ctimg_meta one = *ma;
+    one.h = one.w = one.c = 1;
+    OpsArgs a = ops_base(c, &one);
+    a.in0 = rel;
+    a.out = d_out;
+    set_rescale(c, a);
+    CK(launch_rescale(a, st));
+    *mout = one;
+    mout->level = ma->level - 1;
+    mout->scale = ma->scale * ma->scale / (double)c->q[ma->level];
+    return ICHEE_OK;
+}

@@ -85,6 +85,8 @@ _SIGS = {
                          _vp, _u32, _vp, ctypes.POINTER(CtImgMeta), _vp]),
     "ichee_decrypt_image": (_st, [_vp, _vp, ctypes.POINTER(CtImgMeta), _vp, _vp]),
     "ichee_decrypt_residues": (_st, [_vp, _vp, ctypes.POINTER(CtImgMeta), _vp, _vp, _vp]),
+    "ichee_sqdiff_sum_noalloc": (_st, [_vp, _vp, ctypes.POINTER(CtImgMeta), _vp, ctypes.POINTER(CtImgMeta), _vp,
+                                       ctypes.POINTER(CtImgMeta), _vp]),
     "ichee_stream_status": (_st, [_vp, _vp]),
     "ichee_last_error": (ctypes.c_char_p, []),
 }
@@ -210,6 +212,14 @@ def ichee_decrypt_image(ctx, ct, meta, out, stream=None):
 
 def ichee_decrypt_residues(ctx, ct, meta, out, residues, stream=None):
     _check(_lib.ichee_decrypt_residues(ctx, _ptr(ct), ctypes.byref(meta), _ptr(out), _ptr(residues), stream))
+
+
+def ichee_sqdiff_sum_noalloc(ctx, a, ma, b, mb, out, stream=None):
+    """Matching into a caller-provided output without any device allocation (see ichee.h)."""
+    m = CtImgMeta()
+    _check(_lib.ichee_sqdiff_sum_noalloc(ctx, _ptr(a), ctypes.byref(ma), _ptr(b), ctypes.byref(mb), _ptr(out),
+                                         ctypes.byref(m), stream))
+    return m
 
 
 def ichee_stream_status(ctx, stream=None):
