@@ -259,6 +259,7 @@ extern "C" ichee_status ichee_ctx_create(const ichee_params* p, int device, iche
             cl.inv[i] = hm::invm(qi_mod, c->q[i]);
             cl.invp[i] = hm::shoup_of(cl.inv[i], c->q[i]);
             cl.qinv[i] = 1.0 / (double)c->q[i];
+            cl.mu[i] = (u64)(((hm::u128)1 << 64) / c->q[i]);
         }
     }
     if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess) return cleanup(fail(ICHEE_ENOMEM, "status"));
@@ -754,6 +755,18 @@ static void set_k1(const ichee_ctx* c, OpsArgs& a, double v, double scale)
     for (int l = 0; l < a.limbs; ++l) a.k1p[l] = hm::shoup_of(a.k1[l], c->q[l]);
 }
 
+// Constants of a fused multiply + rescale: K * q_t^{-1} mod q_j for the kept limbs.
+static void fold_constants(const ichee_ctx* c, OpsArgs& a)
+{
+    for (int j = 0; j < a.limbs - 1; ++j) {
+        const u64 qj = c->q[j];
+        a.k0r[j] = hm::mulm(a.k0[j], a.qt_inv[j], qj);
+        a.k0rp[j] = hm::shoup_of(a.k0r[j], qj);
+        a.k1r[j] = hm::mulm(a.k1[j], a.qt_inv[j], qj);
+        a.k1rp[j] = hm::shoup_of(a.k1r[j], qj);
+    }
+}
+
 static bool same_scale(double a, double b) { return std::fabs(a - b) <= 1e-9 * std::fabs(a); }
 
 static ichee_status check_img(const ichee_ctx* c, const uint64_t* d, const ichee_ctimg_meta* m, const char* what)
@@ -856,6 +869,7 @@ extern "C" ichee_status ichee_eval(ichee_ctx* c, ichee_op op, const uint64_t* d_
         if (c->n / 2 < 256) return fail(ICHEE_EUNSUPPORTED, "mean filter needs N >= 512");
         set_k0(c, a, 1.0 / 9.0, c->delta);
         set_rescale(c, a);
+        fold_constants(c, a);
         CK(launch_meanfilter3(a, st));
         m.level = ma->level - 1;
         m.scale = ma->scale * c->delta / (double)c->q[ma->level];
@@ -866,6 +880,7 @@ extern "C" ichee_status ichee_eval(ichee_ctx* c, ichee_op op, const uint64_t* d_
         set_k0(c, a, args[0], c->delta);
         set_k1(c, a, 1.0 - args[0], c->delta);
         set_rescale(c, a);
+        fold_constants(c, a);
         a.c_w = (int)mb->c;
         CK(launch_blend(a, st));
         m.level = ma->level - 1;

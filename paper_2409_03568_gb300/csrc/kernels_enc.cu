@@ -67,12 +67,12 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_ntt_fwd(const __grid_cons
     const int m = b.midx[blockIdx.x % b.nl];
     const u64 q = rns.q[m];
     u64* d = b.data + (size_t)blockIdx.x * (1 << LOGN);
-    u64 r[16];
+    u64 r[1][16];
 #pragma unroll
-    for (int e = 0; e < 16; ++e) r[e] = d[elem_index<LOGN, 0>(tid, e)];
-    ntt_fwd_regs<LOGN>(sm, r, tid, rns.tab[m], q);
+    for (int e = 0; e < 16; ++e) r[0][e] = d[elem_index<LOGN, 0>(tid, e)];
+    ntt_fwd_regs<LOGN, 1>(sm, r, tid, rns.tab[m], q);
 #pragma unroll
-    for (int e = 0; e < 16; ++e) d[elem_index<LOGN, NttShape<LOGN>::LAST>(tid, e)] = csub(csub(r[e], 2 * q), q);
+    for (int e = 0; e < 16; ++e) d[elem_index<LOGN, NttShape<LOGN>::LAST>(tid, e)] = csub(csub(r[0][e], 2 * q), q);
 }
 
 template <int LOGN>
@@ -83,12 +83,12 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_ntt_inv(const __grid_cons
     const int m = b.midx[blockIdx.x % b.nl];
     const u64 q = rns.q[m];
     u64* d = b.data + (size_t)blockIdx.x * (1 << LOGN);
-    u64 r[16];
+    u64 r[1][16];
 #pragma unroll
-    for (int e = 0; e < 16; ++e) r[e] = d[elem_index<LOGN, NttShape<LOGN>::LAST>(tid, e)];
-    ntt_inv_regs<LOGN>(sm, r, tid, rns.tab[m], q);
+    for (int e = 0; e < 16; ++e) r[0][e] = d[elem_index<LOGN, NttShape<LOGN>::LAST>(tid, e)];
+    ntt_inv_regs<LOGN, 1>(sm, r, tid, rns.tab[m], q);
 #pragma unroll
-    for (int e = 0; e < 16; ++e) d[elem_index<LOGN, 0>(tid, e)] = csub(r[e], q);
+    for (int e = 0; e < 16; ++e) d[elem_index<LOGN, 0>(tid, e)] = csub(r[0][e], q);
 }
 
 template <int LOGN>
@@ -230,7 +230,8 @@ cudaError_t launch_axpy_const(u64* out, const u64* x, const u64* y, u64 c, int n
 //   v^ = NTT(v); c_b = INTT(v^ . pk^_b) + e_b (+ Delta*p at coefficient 0 of c0)
 // pk^_b already carries the 1/N of the inverse transform. With KEEP_VHAT the transform of v
 // stays in registers for both products (3 transforms per limb); without it (N = 2^14,
-// register budget) it is recomputed (4 per limb).
+// register budget) it is recomputed (4 per limb). The first forward stage multiplies by a
+// ternary operand and needs no product.
 // ---------------------------------------------------------------------------------------
 
 template <int LOGN, bool KEEP_VHAT>
@@ -274,20 +275,20 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T, 1) k_encrypt_fresh(const __
         for (int l = 0; l < L; ++l) {
             const u64 q = a.rns.q[l];
             const ModTables t = a.rns.tab[l];
-            u64 r[16];
+            u64 r[1][16];
             u64 vh[KEEP_VHAT ? 16 : 1];
             for (int pb = 0; pb < 2; ++pb) {
                 if (KEEP_VHAT && pb == 1) {
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) r[e] = vh[KEEP_VHAT ? e : 0];
+                    for (int e = 0; e < 16; ++e) r[0][e] = vh[KEEP_VHAT ? e : 0];
                 } else {
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) r[e] = small_mod(sv[elem_index<LOGN, 0>(tid, e)], q);
+                    for (int e = 0; e < 16; ++e) r[0][e] = small_mod(sv[elem_index<LOGN, 0>(tid, e)], q);
                     __syncthreads();
-                    ntt_fwd_regs<LOGN>(buf, r, tid, t, q);
+                    ntt_fwd_regs<LOGN, 1, true>(buf, r, tid, t, q);
                     if constexpr (KEEP_VHAT) {
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) vh[e] = r[e];
+                        for (int e = 0; e < 16; ++e) vh[e] = r[0][e];
                     }
                 }
                 const u64* pk = a.pk_hat + ((size_t)pb * L + l) * N;
@@ -295,16 +296,16 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T, 1) k_encrypt_fresh(const __
 #pragma unroll
                 for (int e = 0; e < 16; ++e) {
                     const int x = elem_index<LOGN, LAST>(tid, e);
-                    r[e] = shoup_lazy(r[e], __ldg(pk + x), __ldg(pkp + x), q);
+                    r[0][e] = shoup_lazy(r[0][e], __ldg(pk + x), __ldg(pkp + x), q);
                 }
                 __syncthreads();
-                ntt_inv_regs<LOGN>(buf, r, tid, t, q);
+                ntt_inv_regs<LOGN, 1>(buf, r, tid, t, q);
                 const int8_t* noise = pb == 0 ? se0 : se1;
                 u64* dst = a.out + ((k * 2 + pb) * (u64)L + l) * N;
 #pragma unroll
                 for (int e = 0; e < 16; ++e) {
                     const int x = elem_index<LOGN, 0>(tid, e);
-                    u64 v = add_mod(csub(r[e], q), small_mod(noise[x], q), q);
+                    u64 v = add_mod(csub(r[0][e], q), small_mod(noise[x], q), q);
                     if (pb == 0 && x == 0) v = add_mod(v, a.dm[l * 256 + p], q);
                     __stcs(dst + x, v);
                 }

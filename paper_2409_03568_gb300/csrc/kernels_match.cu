@@ -11,7 +11,7 @@ namespace ichee {
 // d0 and d1, and accumulates (d0^2, 2 d0 d1, d1^2) position by position into its own slice of
 // the scratch buffer (each position is owned by one thread, so no atomics are needed). The
 // transform of d0 waits in a second shared-memory buffer (SMEM_D0) or, for the 2^14 ring whose
-// buffers do not both fit, in the fourth scratch row.
+// buffers do not both fit, in the fourth scratch row; d1's waits in the transform buffer.
 template <int LOGN, bool SMEM_D0>
 __global__ void __launch_bounds__(NttShape<LOGN>::T, 1) k_sqdiff_accumulate(const __grid_constant__ SqDiffArgs a)
 {
@@ -38,26 +38,24 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T, 1) k_sqdiff_accumulate(cons
     for (u64 k = start; k < a.n_ct; k += stride) {
         const u64* A = a.a + k * 2 * (u64)limbs * N;
         const u64* B = a.b + k * 2 * (u64)limbs * N;
-        // d_b = a_b - b_b for b = 0, 1, transformed and parked: d0 in its own buffer (or the
-        // fourth scratch row), d1 in the transform buffer once every thread is done reading it
 #pragma unroll 1
         for (int pb = 0; pb < 2; ++pb) {
             const u64* pa = A + ((u64)pb * limbs + l) * N;
             const u64* pbb = B + ((u64)pb * limbs + l) * N;
-            u64 r[16];
+            u64 r[1][16];
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
                 const int x = elem_index<LOGN, 0>(tid, e);
-                r[e] = sub_mod(__ldcs(pa + x), __ldcs(pbb + x), q);
+                r[0][e] = sub_mod(__ldcs(pa + x), __ldcs(pbb + x), q);
             }
             __syncthreads();
-            ntt_fwd_regs<LOGN>(buf, r, tid, t, q);
+            ntt_fwd_regs<LOGN, 1>(buf, r, tid, t, q);
             __syncthreads();
             u64* dst = pb == 0 ? d0buf : buf;
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
                 const int x = elem_index<LOGN, LAST>(tid, e);
-                dst[SMEM_D0 || pb ? swz(x) : x] = csub(csub(r[e], 2 * q), q);
+                dst[SMEM_D0 || pb ? swz(x) : x] = csub(csub(r[0][e], 2 * q), q);
             }
         }
 #pragma unroll 1

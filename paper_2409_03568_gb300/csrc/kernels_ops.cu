@@ -7,13 +7,23 @@ namespace ichee {
 // ---------------------------------------------------------------------------------------
 // Rescale by the last prime q_t of a ciphertext with t+1 limbs (reading R10):
 //   c'_j = (c_j - [c_t]_centered) * q_t^{-1} mod q_j.
+// Since q_t * q_t^{-1} = 1 mod q_j this is c_j q_t^{-1} - c_t q_t^{-1} + [c_t > (q_t-1)/2]:
+// two Shoup products (both accept any 64-bit operand, so c_t needs no reduction mod q_j).
+// A constant K multiplied in before the rescale folds into the first product as
+// K q_t^{-1} mod q_j.
 // ---------------------------------------------------------------------------------------
+__device__ __forceinline__ u64 rescale_fold(u64 prod_j, u64 ct, int j, const OpsArgs& a)
+{
+    // prod_j in [0, 2 q_j): the already scaled c_j q_t^{-1} (or sum K c_j q_t^{-1})
+    const u64 qj = a.q[j];
+    const u64 b = shoup_lazy(ct, a.qt_inv[j], a.qt_inv_p[j], qj);
+    u64 v = csub(csub(prod_j + 2 * qj - b, 2 * qj), qj);
+    return ct > a.half_qt ? add_mod(v, 1, qj) : v;
+}
+
 __device__ __forceinline__ u64 rescale_one(u64 cj, u64 ct, int j, const OpsArgs& a)
 {
-    const u64 qj = a.q[j];
-    u64 r = reduce64(ct, qj, a.mu[j]);
-    if (ct > a.half_qt) r = add_mod(r, a.neg_qt_mod[j], qj);  // (c_t - q_t) mod q_j
-    return shoup(sub_mod(cj, r, qj), a.qt_inv[j], a.qt_inv_p[j], qj);
+    return rescale_fold(shoup_lazy(cj, a.qt_inv[j], a.qt_inv_p[j], a.q[j]), ct, j, a);
 }
 
 // Elementwise add / sub of two images with the same shape (Sec. 2.2.3, Sec. 3.3).
@@ -113,7 +123,9 @@ __global__ void k_rescale(const __grid_constant__ OpsArgs a)
 // Fused 3x3 mean filter (Sec. 4.4.1, reading R13): out(y,x) = Rescale(K9 * sum of the 9
 // clamp-to-edge neighbours). One block per (row y, channel, poly, coefficient chunk); each
 // thread owns one coefficient pair and walks the row left to right keeping the three column
-// sums of the window in registers, so every input row is loaded once per output row.
+// sums of the window in registers, so every input row is loaded once per output row. Residues
+// are below 2^60, so the 9-term sums fit 64 bits unreduced and go straight into the Shoup
+// products (K9 for the dropped limb, K9 q_t^{-1} for the kept ones).
 template <int LIMBS>
 __global__ void __launch_bounds__(256) k_meanfilter3(const __grid_constant__ OpsArgs a)
 {
@@ -137,34 +149,30 @@ __global__ void __launch_bounds__(256) k_meanfilter3(const __grid_constant__ Ops
         const u64 k0 = ((u64)ym * w + xx) * C + ch, k1 = ((u64)y * w + xx) * C + ch, k2 = ((u64)yp * w + xx) * C + ch;
 #pragma unroll
         for (int l = 0; l < LIMBS; ++l) {
-            const u64 q = a.q[l];
             ulonglong2 v0 = __ldg(in + k0 * ct_len2 + l * (n / 2));
             ulonglong2 v1 = __ldg(in + k1 * ct_len2 + l * (n / 2));
             ulonglong2 v2 = __ldg(in + k2 * ct_len2 + l * (n / 2));
-            dst[l].x = add_mod(add_mod(v0.x, v1.x, q), v2.x, q);
-            dst[l].y = add_mod(add_mod(v0.y, v1.y, q), v2.y, q);
+            dst[l].x = v0.x + v1.x + v2.x;
+            dst[l].y = v0.y + v1.y + v2.y;
         }
     };
     column(0, col[0]);  // x = -1 clamps to 0
 #pragma unroll
     for (int l = 0; l < LIMBS; ++l) col[1][l] = col[0][l];
     column(w > 1 ? 1 : 0, col[2]);
+    const u64 qt = a.q[LIMBS - 1];
     for (int x = 0; x < w; ++x) {
-        ulonglong2 t[LIMBS];
-#pragma unroll
-        for (int l = 0; l < LIMBS; ++l) {
-            const u64 q = a.q[l];
-            u64 sx = add_mod(add_mod(col[0][l].x, col[1][l].x, q), col[2][l].x, q);
-            u64 sy = add_mod(add_mod(col[0][l].y, col[1][l].y, q), col[2][l].y, q);
-            t[l].x = shoup(sx, a.k0[l], a.k0p[l], q);
-            t[l].y = shoup(sy, a.k0[l], a.k0p[l], q);
-        }
+        const u64 sx = col[0][LIMBS - 1].x + col[1][LIMBS - 1].x + col[2][LIMBS - 1].x;
+        const u64 sy = col[0][LIMBS - 1].y + col[1][LIMBS - 1].y + col[2][LIMBS - 1].y;
+        const u64 tx = shoup(sx, a.k0[LIMBS - 1], a.k0p[LIMBS - 1], qt);
+        const u64 ty = shoup(sy, a.k0[LIMBS - 1], a.k0p[LIMBS - 1], qt);
         ulonglong2* o = out + (((u64)y * w + x) * C + ch) * out_len2;
 #pragma unroll
         for (int j = 0; j < LIMBS - 1; ++j) {
+            const u64 qj = a.q[j];
             ulonglong2 v;
-            v.x = rescale_one(t[j].x, t[LIMBS - 1].x, j, a);
-            v.y = rescale_one(t[j].y, t[LIMBS - 1].y, j, a);
+            v.x = rescale_fold(shoup_lazy(col[0][j].x + col[1][j].x + col[2][j].x, a.k0r[j], a.k0rp[j], qj), tx, j, a);
+            v.y = rescale_fold(shoup_lazy(col[0][j].y + col[1][j].y + col[2][j].y, a.k0r[j], a.k0rp[j], qj), ty, j, a);
             __stcs(o + j * (n / 2), v);
         }
         if (x + 1 < w) {
@@ -176,12 +184,13 @@ __global__ void __launch_bounds__(256) k_meanfilter3(const __grid_constant__ Ops
 }
 
 // Fused watermark blend (reading R15): out = Rescale(Ka * I + Kb * W), W broadcast over
-// channels when it has one channel.
+// channels when it has one channel. The kept limbs use Ka q_t^{-1}, Kb q_t^{-1}.
 template <int LIMBS>
 __global__ void k_blend(const __grid_constant__ OpsArgs a)
 {
     const int n = 1 << a.logn;
     const u64 total = a.n_ct * 2 * (u64)(n / 2);
+    const int t = LIMBS - 1;
     for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total; i += (u64)gridDim.x * blockDim.x) {
         const u64 kb = i / (n / 2);
         const int c = (int)(i % (n / 2));
@@ -189,21 +198,21 @@ __global__ void k_blend(const __grid_constant__ OpsArgs a)
         const u64 kw = (k / a.c) * a.c_w + (a.c_w == 1 ? 0 : k % a.c);
         const ulonglong2* s0 = reinterpret_cast<const ulonglong2*>(a.in0 + kb * LIMBS * (u64)n) + c;
         const ulonglong2* s1 = reinterpret_cast<const ulonglong2*>(a.in1 + (kw * 2 + b) * LIMBS * (u64)n) + c;
-        ulonglong2 t[LIMBS];
-#pragma unroll
-        for (int l = 0; l < LIMBS; ++l) {
-            const u64 q = a.q[l];
-            ulonglong2 u = __ldcs(s0 + l * (n / 2)), v = __ldg(s1 + l * (n / 2));
-            t[l].x = add_mod(shoup(u.x, a.k0[l], a.k0p[l], q), shoup(v.x, a.k1[l], a.k1p[l], q), q);
-            t[l].y = add_mod(shoup(u.y, a.k0[l], a.k0p[l], q), shoup(v.y, a.k1[l], a.k1p[l], q), q);
-        }
+        const u64 qt = a.q[t];
+        const ulonglong2 ut = __ldcs(s0 + t * (n / 2)), wt = __ldg(s1 + t * (n / 2));
+        const u64 tx = add_mod(shoup(ut.x, a.k0[t], a.k0p[t], qt), shoup(wt.x, a.k1[t], a.k1p[t], qt), qt);
+        const u64 ty = add_mod(shoup(ut.y, a.k0[t], a.k0p[t], qt), shoup(wt.y, a.k1[t], a.k1p[t], qt), qt);
         ulonglong2* dst = reinterpret_cast<ulonglong2*>(a.out + kb * (LIMBS - 1) * (u64)n) + c;
 #pragma unroll
         for (int j = 0; j < LIMBS - 1; ++j) {
-            ulonglong2 v;
-            v.x = rescale_one(t[j].x, t[LIMBS - 1].x, j, a);
-            v.y = rescale_one(t[j].y, t[LIMBS - 1].y, j, a);
-            __stcs(dst + j * (n / 2), v);
+            const u64 qj = a.q[j];
+            const ulonglong2 u = __ldcs(s0 + j * (n / 2)), v = __ldg(s1 + j * (n / 2));
+            const u64 px = csub(shoup_lazy(u.x, a.k0r[j], a.k0rp[j], qj) + shoup_lazy(v.x, a.k1r[j], a.k1rp[j], qj), 2 * qj);
+            const u64 py = csub(shoup_lazy(u.y, a.k0r[j], a.k0rp[j], qj) + shoup_lazy(v.y, a.k1r[j], a.k1rp[j], qj), 2 * qj);
+            ulonglong2 o;
+            o.x = rescale_fold(px, tx, j, a);
+            o.y = rescale_fold(py, ty, j, a);
+            __stcs(dst + j * (n / 2), o);
         }
     }
 }
@@ -252,30 +261,38 @@ __global__ void __launch_bounds__(256) k_decrypt(const __grid_constant__ DecArgs
     const int n = 1 << a.logn;
     const int nl = a.crt.nl;
     __shared__ u64 red[8][2][kMaxPrimes];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint16_t* s2 = reinterpret_cast<const uint16_t*>(a.srev);
     for (u64 k = blockIdx.x; k < a.n_ct; k += gridDim.x) {
         const u64* ct = a.ct + k * 2 * (u64)nl * n;
-        u64 pos[kMaxPrimes], neg[kMaxPrimes];
-        for (int l = 0; l < nl; ++l) { pos[l] = 0; neg[l] = 0; }
-        for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            const int sg = a.srev[j];
-            if (sg == 0) continue;
-            for (int l = 0; l < nl; ++l) {
-                const u64 v = __ldcs(ct + ((u64)nl + l) * n + j);
-                if (sg > 0) pos[l] = add_mod(pos[l], v, a.q[l]);
-                else neg[l] = add_mod(neg[l], v, a.q[l]);
-            }
-        }
         for (int l = 0; l < nl; ++l) {
-            const u64 q = a.q[l];
+            const u64 q = a.q[l], mu = a.crt.mu[l];
+            const ulonglong2* c1 = reinterpret_cast<const ulonglong2*>(ct + ((u64)nl + l) * n);
+            // residues are below 2^60: up to 8 of them (plus a reduced partial sum) fit 64 bits,
+            // so the signed sums are reduced once every four coefficient pairs
+            u64 pos = 0, neg = 0;
+            int pending = 0;
+            for (int j2 = threadIdx.x; j2 < n / 2; j2 += blockDim.x) {
+                const ulonglong2 v = __ldcs(c1 + j2);
+                const uint16_t sg = __ldg(s2 + j2);
+                const int s0 = (int8_t)(sg & 0xff), s1 = (int8_t)(sg >> 8);
+                pos += (s0 > 0 ? v.x : 0) + (s1 > 0 ? v.y : 0);
+                neg += (s0 < 0 ? v.x : 0) + (s1 < 0 ? v.y : 0);
+                if (++pending == 4) {
+                    pos = reduce64(pos, q, mu);
+                    neg = reduce64(neg, q, mu);
+                    pending = 0;
+                }
+            }
+            pos = reduce64(pos, q, mu);
+            neg = reduce64(neg, q, mu);
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
-                pos[l] = add_mod(pos[l], __shfl_down_sync(0xffffffffu, pos[l], off), q);
-                neg[l] = add_mod(neg[l], __shfl_down_sync(0xffffffffu, neg[l], off), q);
+                pos = add_mod(pos, __shfl_down_sync(0xffffffffu, pos, off), q);
+                neg = add_mod(neg, __shfl_down_sync(0xffffffffu, neg, off), q);
             }
+            if (lane == 0) { red[warp][0][l] = pos; red[warp][1][l] = neg; }
         }
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        if (lane == 0)
-            for (int l = 0; l < nl; ++l) { red[warp][0][l] = pos[l]; red[warp][1][l] = neg[l]; }
         __syncthreads();
         if (threadIdx.x == 0) {
             u64 y[kMaxPrimes];
@@ -304,8 +321,7 @@ __global__ void __launch_bounds__(256) k_decrypt(const __grid_constant__ DecArgs
                 sub192(z, x);
                 x = z;
             }
-            const u64 x0 = x.w0, x1 = x.w1, x2 = x.w2;
-            const double mag = (double)x2 * 0x1p128 + (double)x1 * 0x1p64 + (double)x0;
+            const double mag = (double)x.w2 * 0x1p128 + (double)x.w1 * 0x1p64 + (double)x.w0;
             const double val = mag / a.scale;
             a.out[k] = negv ? -val : val;
         }

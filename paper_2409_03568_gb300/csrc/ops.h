@@ -14,6 +14,8 @@ struct OpsArgs {
     u64 k0[kMaxPrimes], k0p[kMaxPrimes], k1[kMaxPrimes], k1p[kMaxPrimes];
     // rescale by q_t, t = limbs - 1: q_t^{-1} mod q_j (Shoup), (-q_t) mod q_j, (q_t - 1) / 2
     u64 qt_inv[kMaxPrimes], qt_inv_p[kMaxPrimes], neg_qt_mod[kMaxPrimes], half_qt;
+    // constants already multiplied by q_t^{-1} mod q_j (Shoup pairs), for fused multiply + rescale
+    u64 k0r[kMaxPrimes], k0rp[kMaxPrimes], k1r[kMaxPrimes], k1rp[kMaxPrimes];
     // plaintext add to ciphertexts [k_lo, k_hi): kadd[k * limbs + l] if kadd_per_ct, else k0[l]
     const u64* kadd;
     int kadd_per_ct;
@@ -33,6 +35,7 @@ struct CrtLevel {
     u64 qiw[kMaxPrimes][3];        // (Q/q_l) mod 2^192
     u64 qw[3];                     // Q mod 2^192
     double qinv[kMaxPrimes];       // 1/q_l
+    u64 mu[kMaxPrimes];            // floor(2^64 / q_l)
 };
 
 struct DecArgs {
