@@ -225,6 +225,90 @@ ichee_status ichee_decrypt_image(ichee_ctx* ctx, const uint64_t* d_ct, const ich
 ichee_status ichee_decrypt_residues(ichee_ctx* ctx, const uint64_t* d_ct, const ichee_ctimg_meta* meta, double* out,
                                     uint64_t* residues_out, void* stream);
 
+/* ------------------------------------------------------------------------------------------
+ * Ragged batches. Many images of different shapes go through one launch of a persistent
+ * kernel (per chunk of 64 images); every image gets exactly the ciphertexts and results the
+ * single-image call would give it. Batched calls take host arrays of DEVICE pointers (one per
+ * image), never allocate device memory and never synchronise, so a sequence of them can be
+ * captured into a CUDA graph (ichee_graph_begin / ichee_graph_end).
+ * ------------------------------------------------------------------------------------------ */
+
+/* One image of a batch: shape and the seed of its encryption randomness. */
+typedef struct {
+    uint32_t h, w, c;
+    uint64_t seed;
+} ichee_image_desc;
+
+/*
+ * Pixel-level encryption of n_images images (Sec. 3.1; cache semantics as in
+ * ichee_encrypt_image). pixels[i]: device, h*w*c bytes; d_ct_out[i]: device, h*w*c
+ * ciphertexts at level L-1. Image i equals ichee_encrypt_image(..., images[i].seed, ...).
+ * metas_out[i] (host) receives its metadata. Errors: EINVAL, EMISMATCH, ECUDA.
+ */
+ichee_status ichee_encrypt_batch(ichee_ctx* ctx, const ichee_cache* cache, const uint8_t* const* pixels,
+                                 const ichee_image_desc* images, uint32_t n_images, uint64_t* const* d_ct_out,
+                                 ichee_ctimg_meta* metas_out, void* stream);
+
+/*
+ * A batched image operation over n_images device images of one level and scale:
+ * ICHEE_OP_MEANFILTER3 (Sec. 4.4.1), ICHEE_OP_BRIGHTNESS / ICHEE_OP_PTADD (Sec. 4.4.2; args:
+ * one constant per image) and ICHEE_OP_BLEND (args: alpha; d_b[i] the pattern of image i with
+ * c or 1 channels). Results equal the single-image ichee_eval per image. Outputs must not
+ * alias inputs. Other operations return ICHEE_EUNSUPPORTED.
+ */
+ichee_status ichee_eval_batch(ichee_ctx* ctx, ichee_op op, const uint64_t* const* d_a, const ichee_ctimg_meta* ma,
+                              const uint64_t* const* d_b, const ichee_ctimg_meta* mb, const double* op_args,
+                              uint32_t n_args, uint64_t* const* d_out, ichee_ctimg_meta* mout, uint32_t n_images,
+                              void* stream);
+
+/* Batched decryption (Sec. 2.2.2) of n_images device images of one level into device doubles
+ * d_out[i] (h*w*c each), decoded with each image's scale. */
+ichee_status ichee_decrypt_batch(ichee_ctx* ctx, const uint64_t* const* d_ct, const ichee_ctimg_meta* metas,
+                                 double* const* d_out, uint32_t n_images, void* stream);
+
+/* Kernels whose launch shape the autotuner chooses. */
+#define ICHEE_TUNE_RADIX 1u
+#define ICHEE_TUNE_LOOKUP 2u
+#define ICHEE_TUNE_MEANFILTER 3u
+
+typedef struct {
+    uint32_t kind;            /* ICHEE_TUNE_* */
+    uint32_t threads;         /* threads per block */
+    uint32_t blocks_per_sm;   /* persistent grid = blocks_per_sm x SM count */
+    float ms;                 /* best of two timed runs */
+} ichee_tune_entry;
+
+/*
+ * Autotuner for the batched encrypt-then-mean-filter pipeline: runs the batched encryption of
+ * `cache` (fresh if NULL: nothing to tune) and the batched mean filter on the given batch with
+ * every candidate launch shape (threads per block x resident blocks per SM), timed with CUDA
+ * events on `stream`, and keeps the fastest shapes in the context for later batched calls.
+ * d_ct and d_filtered receive valid outputs (the last run). report (host, *n_report entries,
+ * may be NULL) receives every timing; *n_report is set to the number of timings. Synchronises
+ * `stream`. Run it before capturing a graph that should use the tuned shapes.
+ */
+ichee_status ichee_autotune_batch(ichee_ctx* ctx, const ichee_cache* cache, const uint8_t* const* pixels,
+                                  const ichee_image_desc* images, uint32_t n_images, uint64_t* const* d_ct,
+                                  uint64_t* const* d_filtered, ichee_tune_entry* report, uint32_t* n_report,
+                                  void* stream);
+
+/* The launch shape the context currently uses for a kernel kind (ICHEE_TUNE_*). */
+ichee_status ichee_tuned_shape(const ichee_ctx* ctx, uint32_t kind, uint32_t* threads, uint32_t* blocks_per_sm);
+
+typedef struct ichee_graph ichee_graph;
+
+/*
+ * CUDA graphs of batched pipelines. ichee_graph_begin starts capturing `stream` (a
+ * non-default stream; thread-local capture); the caller then issues batched calls on it;
+ * ichee_graph_end stops the capture and instantiates the graph (*out, freed by
+ * ichee_graph_destroy). ichee_graph_launch replays it on any stream: same buffers, same
+ * inputs, bit-identical results. Only the batched entry points are meant for capture.
+ */
+ichee_status ichee_graph_begin(ichee_ctx* ctx, void* stream);
+ichee_status ichee_graph_end(ichee_ctx* ctx, void* stream, ichee_graph** out);
+ichee_status ichee_graph_launch(ichee_graph* graph, void* stream);
+void ichee_graph_destroy(ichee_graph* graph);
+
 /*
  * Matching (the ICHEE_OP_SQDIFF_SUM operation) for callers that cannot allocate device
  * memory: processes whose GPU memory is handed out by their own arena or pool, or loops that

@@ -1,0 +1,121 @@
+// api_internal.h -- library-internal definitions shared by the host translation units:
+// context and cache objects, error reporting, and argument-building helpers.
+#pragma once
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/ichee.h"
+#include "host_math.h"
+#include "ops.h"
+
+namespace ichee {
+
+// Thread-local error message; returns `st`.
+ichee_status fail(ichee_status st, const char* fmt, ...);
+
+#define CK(call)                                                                           \
+    do {                                                                                   \
+        cudaError_t _e = (call);                                                           \
+        if (_e != cudaSuccess) return ::ichee::fail(ICHEE_ECUDA, "%s failed: %s", #call, cudaGetErrorString(_e)); \
+    } while (0)
+
+}  // namespace ichee
+
+using ichee::u64;
+using ichee::u32;
+using ichee::RnsArgs;
+using ichee::CdtTable;
+using ichee::CrtLevel;
+using ichee::LaunchShape;
+using ichee::kMaxModuli;
+using ichee::kMaxPrimes;
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t want)
+    {
+        if (want <= bytes) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e == cudaSuccess) bytes = want;
+        return e;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+};
+
+struct ichee_ctx {
+    ichee_params params;
+    int device = 0;
+    int logn = 0, n = 0, L = 0, nmod = 0;
+    u64 q[kMaxModuli] = {};
+    u64 P = 0;
+    double delta = 0;
+    RnsArgs rns;                 // all moduli (q_0..q_{L-1}, then P), device tables
+    CdtTable cdt;
+    u64* d_tables = nullptr;     // [nmod][4][N]
+    u64* d_dm = nullptr;         // [L][256]
+    u64* d_ninv = nullptr;       // [nmod] N^{-1} mod modulus
+    CrtLevel crt[kMaxPrimes];    // index nl - 1
+    bool have_keys = false, have_evk = false;
+    std::vector<int8_t> h_s;
+    int8_t* d_s = nullptr;
+    int8_t* d_srev = nullptr;
+    u64* d_pk = nullptr;         // [2][L][N]
+    u64* d_pk_hat = nullptr;
+    u64* d_pk_hat_p = nullptr;
+    u64* d_evk = nullptr;        // [L][2][L+1][N]
+    u64* d_evk_hat = nullptr;
+    u64* d_evk_hat_p = nullptr;
+    DevBuf stage_in, stage_out, stage_res, scratch, kadd;
+    int* d_status = nullptr;
+    int num_sms = 0;
+    // launch shapes of the persistent batched kernels (defaults; ichee_autotune_batch refines)
+    LaunchShape shape_radix = {256, 8}, shape_lookup = {256, 8}, shape_meanfilter = {256, 6};
+    LaunchShape shape_blend = {256, 8}, shape_ptadd = {256, 8}, shape_decrypt = {256, 8};
+};
+
+struct ichee_cache {
+    ichee_ctx* ctx = nullptr;
+    ichee_cache_desc desc;
+    std::vector<int> values;
+    int32_t h_lut[256];
+    int32_t* d_lut = nullptr;
+    u64* d_values = nullptr;     // [K][2][L][N]
+    u64* d_pool = nullptr;       // [M][2][L][N]
+    int radix_base = 0, n_pow = 0, radix_randomize = 0;
+    u64* d_radix = nullptr;      // [n_pow][2][L][N]
+    u64* d_mult = nullptr;       // [n_pow][2r+1][2][L][N]
+};
+
+constexpr u64 kIdPoolBase = 1ull << 32;
+constexpr u64 kIdRadixBase = 1ull << 33;
+
+
+namespace ichee {
+size_t ct_words(const ichee_ctx* c, int limbs);
+bool is_device_ptr(const void* p);
+RnsArgs rns_prefix(const ichee_ctx* c, int limbs);
+PolyBatch batch(u64* data, int n_poly, int nl, const int* midx);
+void encode_const(const ichee_ctx* c, double value, double scale, int limbs, u64* out);
+EncArgs enc_args(const ichee_ctx* c, const uint8_t* d_pix, u64 n_ct, u64 seed, u64 id_base, u64* out);
+RadixArgs radix_args(const ichee_ctx* c, const ichee_cache* k, const uint8_t* d_pix, u64 n_ct, u64 seed, u64* out);
+LookupArgs lookup_args(const ichee_ctx* c, const ichee_cache* k, const uint8_t* d_pix, u64 n_ct, u64 seed, u64* out);
+OpsArgs ops_base(const ichee_ctx* c, const ichee_ctimg_meta* m);
+void set_rescale(const ichee_ctx* c, OpsArgs& a);
+void set_k0(const ichee_ctx* c, OpsArgs& a, double v, double scale);
+void set_k1(const ichee_ctx* c, OpsArgs& a, double v, double scale);
+void fold_constants(const ichee_ctx* c, OpsArgs& a);
+bool same_scale(double a, double b);
+ichee_status check_img(const ichee_ctx* c, const uint64_t* d, const ichee_ctimg_meta* m, const char* what);
+DecArgs dec_args(const ichee_ctx* c, int nl);
+}  // namespace ichee

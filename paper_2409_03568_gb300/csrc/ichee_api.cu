@@ -1,17 +1,11 @@
 // ichee_api.cu -- the C ABI of libichee (include/ichee.h): argument checks, set-up, and the
 // launch sequences of key generation, cache building, encryption, image operations and
 // decryption. Every arithmetic step on ciphertexts runs in the kernels of kernels_*.cu.
-#include <cstdarg>
-#include <cstdio>
-#include <cstring>
 #include <algorithm>
 #include <cmath>
 #include <string>
-#include <vector>
 
-#include "../../include/ichee.h"
-#include "host_math.h"
-#include "ops.h"
+#include "api_internal.h"
 
 using namespace ichee;
 namespace hm = ichee::host;
@@ -21,7 +15,7 @@ namespace hm = ichee::host;
 // ---------------------------------------------------------------------------------------
 static thread_local char g_err[512] = "";
 
-static ichee_status fail(ichee_status st, const char* fmt, ...)
+ichee_status ichee::fail(ichee_status st, const char* fmt, ...)
 {
     va_list ap;
     va_start(ap, fmt);
@@ -30,85 +24,14 @@ static ichee_status fail(ichee_status st, const char* fmt, ...)
     return st;
 }
 
-#define CK(call)                                                                           \
-    do {                                                                                   \
-        cudaError_t _e = (call);                                                           \
-        if (_e != cudaSuccess) return fail(ICHEE_ECUDA, "%s failed: %s", #call, cudaGetErrorString(_e)); \
-    } while (0)
-
 extern "C" const char* ichee_last_error(void) { return g_err; }
 
 // ---------------------------------------------------------------------------------------
 // Context and cache
 // ---------------------------------------------------------------------------------------
-struct DevBuf {
-    void* p = nullptr;
-    size_t bytes = 0;
-    cudaError_t ensure(size_t want)
-    {
-        if (want <= bytes) return cudaSuccess;
-        if (p) cudaFree(p);
-        p = nullptr;
-        bytes = 0;
-        cudaError_t e = cudaMalloc(&p, want);
-        if (e == cudaSuccess) bytes = want;
-        return e;
-    }
-    void release()
-    {
-        if (p) cudaFree(p);
-        p = nullptr;
-        bytes = 0;
-    }
-};
+size_t ichee::ct_words(const ichee_ctx* c, int limbs) { return (size_t)2 * limbs * c->n; }
 
-struct ichee_ctx {
-    ichee_params params;
-    int device = 0;
-    int logn = 0, n = 0, L = 0, nmod = 0;
-    u64 q[kMaxModuli] = {};
-    u64 P = 0;
-    double delta = 0;
-    RnsArgs rns;                 // all moduli (q_0..q_{L-1}, then P), device tables
-    CdtTable cdt;
-    u64* d_tables = nullptr;     // [nmod][4][N]
-    u64* d_dm = nullptr;         // [L][256]
-    u64* d_ninv = nullptr;       // [nmod] N^{-1} mod modulus
-    CrtLevel crt[kMaxPrimes];    // index nl - 1
-    bool have_keys = false, have_evk = false;
-    std::vector<int8_t> h_s;
-    int8_t* d_s = nullptr;
-    int8_t* d_srev = nullptr;
-    u64* d_pk = nullptr;         // [2][L][N]
-    u64* d_pk_hat = nullptr;
-    u64* d_pk_hat_p = nullptr;
-    u64* d_evk = nullptr;        // [L][2][L+1][N]
-    u64* d_evk_hat = nullptr;
-    u64* d_evk_hat_p = nullptr;
-    DevBuf stage_in, stage_out, stage_res, scratch, kadd;
-    int* d_status = nullptr;
-    int num_sms = 0;
-};
-
-struct ichee_cache {
-    ichee_ctx* ctx = nullptr;
-    ichee_cache_desc desc;
-    std::vector<int> values;
-    int32_t h_lut[256];
-    int32_t* d_lut = nullptr;
-    u64* d_values = nullptr;     // [K][2][L][N]
-    u64* d_pool = nullptr;       // [M][2][L][N]
-    int radix_base = 0, n_pow = 0, radix_randomize = 0;
-    u64* d_radix = nullptr;      // [n_pow][2][L][N]
-    u64* d_mult = nullptr;       // [n_pow][2r+1][2][L][N]
-};
-
-static const u64 kIdPoolBase = 1ull << 32;
-static const u64 kIdRadixBase = 1ull << 33;
-
-static size_t ct_words(const ichee_ctx* c, int limbs) { return (size_t)2 * limbs * c->n; }
-
-static bool is_device_ptr(const void* p)
+bool ichee::is_device_ptr(const void* p)
 {
     if (p == nullptr) return false;
     cudaPointerAttributes at;
@@ -119,14 +42,14 @@ static bool is_device_ptr(const void* p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-static RnsArgs rns_prefix(const ichee_ctx* c, int limbs)
+RnsArgs ichee::rns_prefix(const ichee_ctx* c, int limbs)
 {
     RnsArgs r = c->rns;
     r.n_mod = limbs;
     return r;
 }
 
-static PolyBatch batch(u64* data, int n_poly, int nl, const int* midx)
+PolyBatch ichee::batch(u64* data, int n_poly, int nl, const int* midx)
 {
     PolyBatch b;
     b.data = data;
@@ -144,7 +67,7 @@ static std::vector<int> iota_idx(int n)
 }
 
 // Residue of llround(value * scale) in every limb.
-static void encode_const(const ichee_ctx* c, double value, double scale, int limbs, u64* out)
+void ichee::encode_const(const ichee_ctx* c, double value, double scale, int limbs, u64* out)
 {
     const long long k = llround(value * scale);
     for (int l = 0; l < limbs; ++l) out[l] = hm::signed_mod(k, c->q[l]);
@@ -450,7 +373,7 @@ extern "C" ichee_status ichee_export_key(ichee_ctx* c, int which, void* host_out
 // ---------------------------------------------------------------------------------------
 // Encryption (Sec. 2.2.2, 3.1) and cached encryption (Sec. 3.2, 3.3)
 // ---------------------------------------------------------------------------------------
-static EncArgs enc_args(const ichee_ctx* c, const uint8_t* d_pix, u64 n_ct, u64 seed, u64 id_base, u64* out)
+EncArgs ichee::enc_args(const ichee_ctx* c, const uint8_t* d_pix, u64 n_ct, u64 seed, u64 id_base, u64* out)
 {
     EncArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -469,7 +392,7 @@ static EncArgs enc_args(const ichee_ctx* c, const uint8_t* d_pix, u64 n_ct, u64 
     return a;
 }
 
-static RadixArgs radix_args(const ichee_ctx* c, const ichee_cache* k, const uint8_t* d_pix, u64 n_ct, u64 seed, u64* out)
+RadixArgs ichee::radix_args(const ichee_ctx* c, const ichee_cache* k, const uint8_t* d_pix, u64 n_ct, u64 seed, u64* out)
 {
     RadixArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -485,6 +408,37 @@ static RadixArgs radix_args(const ichee_ctx* c, const ichee_cache* k, const uint
     a.seed = seed;
     a.id_base = 0;
     a.out = out;
+    return a;
+}
+
+LookupArgs ichee::lookup_args(const ichee_ctx* c, const ichee_cache* k, const uint8_t* d_pix, u64 n_ct, u64 seed,
+                              u64* out)
+{
+    LookupArgs a;
+    std::memset(&a, 0, sizeof(a));
+    for (int l = 0; l < c->L; ++l) a.q[l] = c->q[l];
+    a.L = c->L;
+    a.logn = c->logn;
+    a.n_ct = n_ct;
+    a.pixels = d_pix;
+    a.lut = k->d_lut;
+    a.value_cts = k->d_values;
+    a.pool = k->d_pool;
+    a.pool_size = k->d_pool ? k->desc.pool_size : 0;
+    a.seed = seed;
+    a.id_base = 0;
+    a.out = out;
+    return a;
+}
+
+DecArgs ichee::dec_args(const ichee_ctx* c, int nl)
+{
+    DecArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.logn = c->logn;
+    for (int l = 0; l < nl; ++l) a.q[l] = c->q[l];
+    a.crt = c->crt[nl - 1];
+    a.srev = c->d_srev;
     return a;
 }
 
@@ -674,20 +628,7 @@ extern "C" ichee_status ichee_encrypt_image(ichee_ctx* c, const ichee_cache* k, 
     } else if (k->desc.kind == ICHEE_CACHE_RADIX) {
         CK(launch_radix_combine(radix_args(c, k, d_px, n_ct, seed, d_out), st));
     } else {
-        LookupArgs a;
-        std::memset(&a, 0, sizeof(a));
-        for (int l = 0; l < c->L; ++l) a.q[l] = c->q[l];
-        a.L = c->L;
-        a.logn = c->logn;
-        a.n_ct = n_ct;
-        a.pixels = d_px;
-        a.lut = k->d_lut;
-        a.value_cts = k->d_values;
-        a.pool = k->d_pool;
-        a.pool_size = k->d_pool ? k->desc.pool_size : 0;
-        a.seed = seed;
-        a.id_base = 0;
-        a.out = d_out;
+        LookupArgs a = lookup_args(c, k, d_px, n_ct, seed, d_out);
         CK(launch_lookup_combine(a, st));
         if (k->values.size() < 256) {  // values outside the cache
             if (k->desc.miss_policy == 0) {
@@ -712,7 +653,7 @@ extern "C" ichee_status ichee_encrypt_image(ichee_ctx* c, const ichee_cache* k, 
 // ---------------------------------------------------------------------------------------
 // Image operations
 // ---------------------------------------------------------------------------------------
-static OpsArgs ops_base(const ichee_ctx* c, const ichee_ctimg_meta* m)
+OpsArgs ichee::ops_base(const ichee_ctx* c, const ichee_ctimg_meta* m)
 {
     OpsArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -729,7 +670,7 @@ static OpsArgs ops_base(const ichee_ctx* c, const ichee_ctimg_meta* m)
     return a;
 }
 
-static void set_rescale(const ichee_ctx* c, OpsArgs& a)
+void ichee::set_rescale(const ichee_ctx* c, OpsArgs& a)
 {
     const int t = a.limbs - 1;
     const u64 qt = c->q[t];
@@ -743,20 +684,20 @@ static void set_rescale(const ichee_ctx* c, OpsArgs& a)
     }
 }
 
-static void set_k0(const ichee_ctx* c, OpsArgs& a, double v, double scale)
+void ichee::set_k0(const ichee_ctx* c, OpsArgs& a, double v, double scale)
 {
     encode_const(c, v, scale, a.limbs, a.k0);
     for (int l = 0; l < a.limbs; ++l) a.k0p[l] = hm::shoup_of(a.k0[l], c->q[l]);
 }
 
-static void set_k1(const ichee_ctx* c, OpsArgs& a, double v, double scale)
+void ichee::set_k1(const ichee_ctx* c, OpsArgs& a, double v, double scale)
 {
     encode_const(c, v, scale, a.limbs, a.k1);
     for (int l = 0; l < a.limbs; ++l) a.k1p[l] = hm::shoup_of(a.k1[l], c->q[l]);
 }
 
 // Constants of a fused multiply + rescale: K * q_t^{-1} mod q_j for the kept limbs.
-static void fold_constants(const ichee_ctx* c, OpsArgs& a)
+void ichee::fold_constants(const ichee_ctx* c, OpsArgs& a)
 {
     for (int j = 0; j < a.limbs - 1; ++j) {
         const u64 qj = c->q[j];
@@ -767,9 +708,9 @@ static void fold_constants(const ichee_ctx* c, OpsArgs& a)
     }
 }
 
-static bool same_scale(double a, double b) { return std::fabs(a - b) <= 1e-9 * std::fabs(a); }
+bool ichee::same_scale(double a, double b) { return std::fabs(a - b) <= 1e-9 * std::fabs(a); }
 
-static ichee_status check_img(const ichee_ctx* c, const uint64_t* d, const ichee_ctimg_meta* m, const char* what)
+ichee_status ichee::check_img(const ichee_ctx* c, const uint64_t* d, const ichee_ctimg_meta* m, const char* what)
 {
     if (!d || !m) return fail(ICHEE_EINVAL, "%s: null operand", what);
     if ((int)m->level >= c->L) return fail(ICHEE_ELEVEL, "%s: level %u >= %d", what, m->level, c->L);

@@ -51,6 +51,41 @@ struct LookupArgs {
     u64* out;
 };
 
+// A ragged batch: up to kMaxSegs images ("segments") in one launch. Work item g of the launch
+// belongs to segment s with start[s] <= g < start[s + 1] and is item g - start[s] of it. The
+// table travels as a kernel argument (no device memory, nothing to allocate).
+constexpr int kMaxSegs = 64;
+struct SegTable {
+    int n;
+    u64 start[kMaxSegs + 1];
+    const uint8_t* px[kMaxSegs];      // pixel input (encryption)
+    const u64* in0[kMaxSegs];         // ciphertext inputs
+    const u64* in1[kMaxSegs];
+    u64* out[kMaxSegs];               // ciphertext output
+    double* dout[kMaxSegs];           // decoded output (decryption)
+    u64 seed[kMaxSegs];
+    uint32_t h[kMaxSegs], w[kMaxSegs], c[kMaxSegs], c1[kMaxSegs];
+    double scale[kMaxSegs];
+    u64 kadd[kMaxSegs][kMaxPrimes];   // per-segment plaintext constant residues
+};
+
+__device__ __forceinline__ int seg_of(const SegTable& t, u64 g)
+{
+    int lo = 0, hi = t.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (t.start[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Launch shape of a persistent batched kernel (chosen by the autotuner).
+struct LaunchShape {
+    int threads;       // per block
+    int blocks_per_sm;
+};
+
 // Launchers (kernels_enc.cu). All launch on `stream` and return cudaGetLastError().
 cudaError_t launch_sample_small(int8_t* out, int n, u64 seed, u32 stream_id, u64 id, int gaussian,
                                 const CdtTable& cdt, cudaStream_t st);
@@ -85,5 +120,15 @@ cudaError_t launch_radix_multiples(const u64* radix_cts, int n_pow, int r, const
 cudaError_t launch_radix_combine(const RadixArgs& a, cudaStream_t st);
 cudaError_t launch_lookup_combine(const LookupArgs& a, cudaStream_t st);
 cudaError_t launch_histogram(const uint8_t* pixels, u64 n, u32* counts /*[256], zeroed*/, cudaStream_t st);
+
+// Batched encryption over a SegTable whose items are ciphertexts (px, out, seed per segment;
+// ciphertext k of a segment has ct id k, as in a single-image call). The uniform fields of the
+// argument structs (keys, cache tables, moduli) apply to every segment; their per-image fields
+// (pixels, n_ct, seed, out) are ignored.
+cudaError_t launch_encrypt_fresh_batch(const EncArgs& a, const SegTable& t, int num_sms, cudaStream_t st);
+cudaError_t launch_radix_combine_batch(const RadixArgs& a, const SegTable& t, LaunchShape ls, int num_sms,
+                                       cudaStream_t st);
+cudaError_t launch_lookup_combine_batch(const LookupArgs& a, const SegTable& t, LaunchShape ls, int num_sms,
+                                        cudaStream_t st);
 
 }  // namespace ichee

@@ -234,83 +234,106 @@ cudaError_t launch_axpy_const(u64* out, const u64* x, const u64* y, u64 c, int n
 // ternary operand and needs no product.
 // ---------------------------------------------------------------------------------------
 
+// Shared memory of one encryption block: the transform buffer (N words) followed by v, e0, e1
+// as int8 (3N bytes).
 template <int LOGN, bool KEEP_VHAT>
-__global__ void __launch_bounds__(NttShape<LOGN>::T, 1) k_encrypt_fresh(const __grid_constant__ EncArgs a)
+__device__ __forceinline__ void encrypt_ct(const EncArgs& a, int p, u64 seed, u64 id, u64* ct, u64* smem)
 {
     constexpr int N = 1 << LOGN;
     constexpr int T = NttShape<LOGN>::T;
     constexpr int LAST = NttShape<LOGN>::LAST;
-    extern __shared__ u64 smem[];
     u64* buf = smem;
     int8_t* sv = reinterpret_cast<int8_t*>(smem + N);
     int8_t* se0 = sv + N;
     int8_t* se1 = se0 + N;
     const int tid = threadIdx.x;
     const int L = a.L;
+    __syncthreads();  // smem of the previous ciphertext no longer read
+    for (int b = tid; b < N / 4; b += T) {
+        Words4 w = philox(seed, kStreamV, id, (u32)b);
+        u32 packed = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) packed |= ((u32)(uint8_t)(int8_t)ternary_of(w.w[i])) << (8 * i);
+        reinterpret_cast<u32*>(sv)[b] = packed;
+    }
+    for (int b = tid; b < N / 2; b += T) {
+        Words4 w0 = philox(seed, kStreamE0, id, (u32)b);
+        Words4 w1 = philox(seed, kStreamE1, id, (u32)b);
+        int g00 = gauss_of((u64)w0.w[0] | ((u64)w0.w[1] << 32), a.cdt);
+        int g01 = gauss_of((u64)w0.w[2] | ((u64)w0.w[3] << 32), a.cdt);
+        int g10 = gauss_of((u64)w1.w[0] | ((u64)w1.w[1] << 32), a.cdt);
+        int g11 = gauss_of((u64)w1.w[2] | ((u64)w1.w[3] << 32), a.cdt);
+        reinterpret_cast<uint16_t*>(se0)[b] = (uint16_t)((uint8_t)g00 | ((uint16_t)(uint8_t)g01 << 8));
+        reinterpret_cast<uint16_t*>(se1)[b] = (uint16_t)((uint8_t)g10 | ((uint16_t)(uint8_t)g11 << 8));
+    }
+    __syncthreads();
 
+    for (int l = 0; l < L; ++l) {
+        const u64 q = a.rns.q[l];
+        const ModTables t = a.rns.tab[l];
+        u64 r[1][16];
+        u64 vh[KEEP_VHAT ? 16 : 1];
+        for (int pb = 0; pb < 2; ++pb) {
+            if (KEEP_VHAT && pb == 1) {
+#pragma unroll
+                for (int e = 0; e < 16; ++e) r[0][e] = vh[KEEP_VHAT ? e : 0];
+            } else {
+#pragma unroll
+                for (int e = 0; e < 16; ++e) r[0][e] = small_mod(sv[elem_index<LOGN, 0>(tid, e)], q);
+                __syncthreads();
+                ntt_fwd_regs<LOGN, 1, true>(buf, r, tid, t, q);
+                if constexpr (KEEP_VHAT) {
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) vh[e] = r[0][e];
+                }
+            }
+            const u64* pk = a.pk_hat + ((size_t)pb * L + l) * N;
+            const u64* pkp = a.pk_hat_p + ((size_t)pb * L + l) * N;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int x = elem_index<LOGN, LAST>(tid, e);
+                r[0][e] = shoup_lazy(r[0][e], __ldg(pk + x), __ldg(pkp + x), q);
+            }
+            __syncthreads();
+            ntt_inv_regs<LOGN, 1>(buf, r, tid, t, q);
+            const int8_t* noise = pb == 0 ? se0 : se1;
+            u64* dst = ct + ((u64)pb * L + l) * N;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int x = elem_index<LOGN, 0>(tid, e);
+                u64 v = add_mod(csub(r[0][e], q), small_mod(noise[x], q), q);
+                if (pb == 0 && x == 0) v = add_mod(v, a.dm[l * 256 + p], q);
+                __stcs(dst + x, v);
+            }
+        }
+    }
+}
+
+template <int LOGN, bool KEEP_VHAT>
+__global__ void __launch_bounds__(NttShape<LOGN>::T, 1) k_encrypt_fresh(const __grid_constant__ EncArgs a)
+{
+    extern __shared__ u64 smem[];
+    const u64 ct_len = (u64)2 * a.L << LOGN;
     for (u64 k = blockIdx.x; k < a.n_ct; k += gridDim.x) {
         const int p = a.pixels[k];
         if (a.skip_lut != nullptr && a.skip_lut[p] >= 0) continue;  // uniform across the block
-        const u64 id = a.id_base + k;
-        __syncthreads();  // smem of the previous ciphertext no longer read
-        for (int b = tid; b < N / 4; b += T) {
-            Words4 w = philox(a.seed, kStreamV, id, (u32)b);
-            u32 packed = 0;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) packed |= ((u32)(uint8_t)(int8_t)ternary_of(w.w[i])) << (8 * i);
-            reinterpret_cast<u32*>(sv)[b] = packed;
-        }
-        for (int b = tid; b < N / 2; b += T) {
-            Words4 w0 = philox(a.seed, kStreamE0, id, (u32)b);
-            Words4 w1 = philox(a.seed, kStreamE1, id, (u32)b);
-            int g00 = gauss_of((u64)w0.w[0] | ((u64)w0.w[1] << 32), a.cdt);
-            int g01 = gauss_of((u64)w0.w[2] | ((u64)w0.w[3] << 32), a.cdt);
-            int g10 = gauss_of((u64)w1.w[0] | ((u64)w1.w[1] << 32), a.cdt);
-            int g11 = gauss_of((u64)w1.w[2] | ((u64)w1.w[3] << 32), a.cdt);
-            reinterpret_cast<uint16_t*>(se0)[b] = (uint16_t)((uint8_t)g00 | ((uint16_t)(uint8_t)g01 << 8));
-            reinterpret_cast<uint16_t*>(se1)[b] = (uint16_t)((uint8_t)g10 | ((uint16_t)(uint8_t)g11 << 8));
-        }
-        __syncthreads();
+        encrypt_ct<LOGN, KEEP_VHAT>(a, p, a.seed, a.id_base + k, a.out + k * ct_len, smem);
+    }
+}
 
-        for (int l = 0; l < L; ++l) {
-            const u64 q = a.rns.q[l];
-            const ModTables t = a.rns.tab[l];
-            u64 r[1][16];
-            u64 vh[KEEP_VHAT ? 16 : 1];
-            for (int pb = 0; pb < 2; ++pb) {
-                if (KEEP_VHAT && pb == 1) {
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) r[0][e] = vh[KEEP_VHAT ? e : 0];
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) r[0][e] = small_mod(sv[elem_index<LOGN, 0>(tid, e)], q);
-                    __syncthreads();
-                    ntt_fwd_regs<LOGN, 1, true>(buf, r, tid, t, q);
-                    if constexpr (KEEP_VHAT) {
-#pragma unroll
-                        for (int e = 0; e < 16; ++e) vh[e] = r[0][e];
-                    }
-                }
-                const u64* pk = a.pk_hat + ((size_t)pb * L + l) * N;
-                const u64* pkp = a.pk_hat_p + ((size_t)pb * L + l) * N;
-#pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    const int x = elem_index<LOGN, LAST>(tid, e);
-                    r[0][e] = shoup_lazy(r[0][e], __ldg(pk + x), __ldg(pkp + x), q);
-                }
-                __syncthreads();
-                ntt_inv_regs<LOGN, 1>(buf, r, tid, t, q);
-                const int8_t* noise = pb == 0 ? se0 : se1;
-                u64* dst = a.out + ((k * 2 + pb) * (u64)L + l) * N;
-#pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    const int x = elem_index<LOGN, 0>(tid, e);
-                    u64 v = add_mod(csub(r[0][e], q), small_mod(noise[x], q), q);
-                    if (pb == 0 && x == 0) v = add_mod(v, a.dm[l * 256 + p], q);
-                    __stcs(dst + x, v);
-                }
-            }
-        }
+template <int LOGN, bool KEEP_VHAT>
+__global__ void __launch_bounds__(NttShape<LOGN>::T, 1) k_encrypt_fresh_batch(const __grid_constant__ EncArgs a,
+                                                                              const __grid_constant__ SegTable t)
+{
+    extern __shared__ u64 smem[];
+    const u64 ct_len = (u64)2 * a.L << LOGN;
+    const u64 total = t.start[t.n];
+    for (u64 g = blockIdx.x; g < total; g += gridDim.x) {
+        const int s = seg_of(t, g);
+        const u64 k = g - t.start[s];
+        const int p = t.px[s][k];
+        if (a.skip_lut != nullptr && a.skip_lut[p] >= 0) continue;
+        encrypt_ct<LOGN, KEEP_VHAT>(a, p, t.seed[s], k, t.out[s] + k * ct_len, smem);
     }
 }
 
@@ -326,6 +349,35 @@ static cudaError_t enc_launch(const EncArgs& a, cudaStream_t st)
     u64 grid = a.n_ct < (u64)(1u << 30) ? a.n_ct : (u64)(1u << 30);
     k_encrypt_fresh<LOGN, keep><<<(unsigned)grid, T, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+template <int LOGN>
+static cudaError_t enc_batch_launch(const EncArgs& a, const SegTable& t, int num_sms, cudaStream_t st)
+{
+    constexpr bool keep = LOGN <= 13;
+    const int T = NttShape<LOGN>::T;
+    const size_t smem = (sizeof(u64) + 3) << LOGN;
+    cudaError_t e = cudaFuncSetAttribute(k_encrypt_fresh_batch<LOGN, keep>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const u64 total = t.start[t.n];
+    const u64 cap = (u64)num_sms * 4;   // persistent: a few resident blocks per SM
+    const unsigned grid = (unsigned)(total < cap ? total : cap);
+    k_encrypt_fresh_batch<LOGN, keep><<<grid, T, smem, st>>>(a, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_encrypt_fresh_batch(const EncArgs& a, const SegTable& t, int num_sms, cudaStream_t st)
+{
+    if (t.n <= 0 || t.start[t.n] == 0) return cudaSuccess;
+    switch (a.rns.logn) {
+    case 10: return enc_batch_launch<10>(a, t, num_sms, st);
+    case 11: return enc_batch_launch<11>(a, t, num_sms, st);
+    case 12: return enc_batch_launch<12>(a, t, num_sms, st);
+    case 13: return enc_batch_launch<13>(a, t, num_sms, st);
+    case 14: return enc_batch_launch<14>(a, t, num_sms, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_encrypt_fresh(const EncArgs& a, cudaStream_t st)
@@ -374,41 +426,61 @@ cudaError_t launch_radix_multiples(const u64* radix_cts, int n_pow, int r, const
 // Radix combine: one block per ciphertext. Signed digits d'_k = d_k + b_k - r*b_{k+1} with b
 // from bit k of the pixel's randomness word (stream 3); c = sum_k M[k][d'_k], residue-wise
 // modular sums of cached rows, 16-byte loads, streaming 16-byte stores.
-__global__ void __launch_bounds__(256) k_radix_combine(const __grid_constant__ RadixArgs a)
+__device__ __forceinline__ void radix_ct(const RadixArgs& a, int p, u64 seed, u64 id, u64* ct)
 {
     const int n = 1 << a.logn;
     const size_t ct_len = (size_t)2 * a.L * n;
     const int width = 2 * a.r + 1;
+    u32 bits = 0;
+    if (a.randomize) bits = philox(seed, kStreamRadixBits, id, 0).w[0];
+    const u64* src[8];
+    int ns = 0;
+    int rest = p;
+    for (int kk = 0; kk < a.n_pow; ++kk) {
+        int dk = rest % a.r;
+        rest /= a.r;
+        int bk = (a.randomize && kk >= 1) ? (int)((bits >> kk) & 1u) : 0;
+        int bk1 = (a.randomize && kk + 1 < a.n_pow) ? (int)((bits >> (kk + 1)) & 1u) : 0;
+        int d = dk + bk - a.r * bk1;
+        if (d != 0) src[ns++] = a.mult + ((size_t)kk * width + (d + a.r)) * ct_len;
+    }
+    ulonglong2* dst = reinterpret_cast<ulonglong2*>(ct);
+    for (int row = 0; row < 2 * a.L; ++row) {
+        const u64 q = a.q[row % a.L];
+        const size_t base = (size_t)row * n / 2;
+        for (int i = threadIdx.x; i < n / 2; i += blockDim.x) {
+            ulonglong2 acc = make_ulonglong2(0, 0);
+            for (int s = 0; s < ns; ++s) {
+                ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(src[s]) + base + i);
+                acc.x = add_mod(acc.x, v.x, q);
+                acc.y = add_mod(acc.y, v.y, q);
+            }
+            __stcs(dst + base + i, acc);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_radix_combine(const __grid_constant__ RadixArgs a)
+{
+    const size_t ct_len = (size_t)2 * a.L << a.logn;
     for (u64 k = blockIdx.x; k < a.n_ct; k += gridDim.x) {
         const int p = a.pixels[k];
         if (a.skip_lut != nullptr && a.skip_lut[p] >= 0) continue;
-        u32 bits = 0;
-        if (a.randomize) bits = philox(a.seed, kStreamRadixBits, a.id_base + k, 0).w[0];
-        const u64* src[8];
-        int ns = 0;
-        int rest = p;
-        for (int kk = 0; kk < a.n_pow; ++kk) {
-            int dk = rest % a.r;
-            rest /= a.r;
-            int bk = (a.randomize && kk >= 1) ? (int)((bits >> kk) & 1u) : 0;
-            int bk1 = (a.randomize && kk + 1 < a.n_pow) ? (int)((bits >> (kk + 1)) & 1u) : 0;
-            int d = dk + bk - a.r * bk1;
-            if (d != 0) src[ns++] = a.mult + ((size_t)kk * width + (d + a.r)) * ct_len;
-        }
-        ulonglong2* dst = reinterpret_cast<ulonglong2*>(a.out + k * ct_len);
-        for (int row = 0; row < 2 * a.L; ++row) {
-            const u64 q = a.q[row % a.L];
-            const size_t base = (size_t)row * n / 2;
-            for (int i = threadIdx.x; i < n / 2; i += blockDim.x) {
-                ulonglong2 acc = make_ulonglong2(0, 0);
-                for (int s = 0; s < ns; ++s) {
-                    ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(src[s]) + base + i);
-                    acc.x = add_mod(acc.x, v.x, q);
-                    acc.y = add_mod(acc.y, v.y, q);
-                }
-                __stcs(dst + base + i, acc);
-            }
-        }
+        radix_ct(a, p, a.seed, a.id_base + k, a.out + k * ct_len);
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_radix_combine_batch(const __grid_constant__ RadixArgs a,
+                                                              const __grid_constant__ SegTable t)
+{
+    const size_t ct_len = (size_t)2 * a.L << a.logn;
+    const u64 total = t.start[t.n];
+    for (u64 g = blockIdx.x; g < total; g += gridDim.x) {
+        const int s = seg_of(t, g);
+        const u64 k = g - t.start[s];
+        const int p = t.px[s][k];
+        if (a.skip_lut != nullptr && a.skip_lut[p] >= 0) continue;
+        radix_ct(a, p, t.seed[s], k, t.out[s] + k * ct_len);
     }
 }
 
@@ -422,35 +494,79 @@ cudaError_t launch_radix_combine(const RadixArgs& a, cudaStream_t st)
 
 // Value lookup with the randomness pool: c = C[lut[p]] (+) Z[idx], idx = floor(w*M / 2^32)
 // from stream 4. Pixels whose value is not cached are left to another kernel.
-__global__ void __launch_bounds__(256) k_lookup_combine(const __grid_constant__ LookupArgs a)
+__device__ __forceinline__ void lookup_ct(const LookupArgs& a, int slot, u64 seed, u64 id, u64* ct)
 {
     const int n = 1 << a.logn;
     const size_t ct_len = (size_t)2 * a.L * n;
+    const ulonglong2* c = reinterpret_cast<const ulonglong2*>(a.value_cts + (size_t)slot * ct_len);
+    const ulonglong2* z = nullptr;
+    if (a.pool_size > 0) {
+        u32 w = philox(seed, kStreamPool, id, 0).w[0];
+        u32 idx = (u32)(((u64)w * a.pool_size) >> 32);
+        z = reinterpret_cast<const ulonglong2*>(a.pool + (size_t)idx * ct_len);
+    }
+    ulonglong2* dst = reinterpret_cast<ulonglong2*>(ct);
+    for (int row = 0; row < 2 * a.L; ++row) {
+        const u64 q = a.q[row % a.L];
+        const size_t base = (size_t)row * n / 2;
+        for (int i = threadIdx.x; i < n / 2; i += blockDim.x) {
+            ulonglong2 v = __ldg(c + base + i);
+            if (z != nullptr) {
+                ulonglong2 w = __ldg(z + base + i);
+                v.x = add_mod(v.x, w.x, q);
+                v.y = add_mod(v.y, w.y, q);
+            }
+            __stcs(dst + base + i, v);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_lookup_combine(const __grid_constant__ LookupArgs a)
+{
+    const size_t ct_len = (size_t)2 * a.L << a.logn;
     for (u64 k = blockIdx.x; k < a.n_ct; k += gridDim.x) {
         const int slot = a.lut[a.pixels[k]];
         if (slot < 0) continue;
-        const ulonglong2* c = reinterpret_cast<const ulonglong2*>(a.value_cts + (size_t)slot * ct_len);
-        const ulonglong2* z = nullptr;
-        if (a.pool_size > 0) {
-            u32 w = philox(a.seed, kStreamPool, a.id_base + k, 0).w[0];
-            u32 idx = (u32)(((u64)w * a.pool_size) >> 32);
-            z = reinterpret_cast<const ulonglong2*>(a.pool + (size_t)idx * ct_len);
-        }
-        ulonglong2* dst = reinterpret_cast<ulonglong2*>(a.out + k * ct_len);
-        for (int row = 0; row < 2 * a.L; ++row) {
-            const u64 q = a.q[row % a.L];
-            const size_t base = (size_t)row * n / 2;
-            for (int i = threadIdx.x; i < n / 2; i += blockDim.x) {
-                ulonglong2 v = __ldg(c + base + i);
-                if (z != nullptr) {
-                    ulonglong2 w = __ldg(z + base + i);
-                    v.x = add_mod(v.x, w.x, q);
-                    v.y = add_mod(v.y, w.y, q);
-                }
-                __stcs(dst + base + i, v);
-            }
-        }
+        lookup_ct(a, slot, a.seed, a.id_base + k, a.out + k * ct_len);
     }
+}
+
+__global__ void __launch_bounds__(1024) k_lookup_combine_batch(const __grid_constant__ LookupArgs a,
+                                                               const __grid_constant__ SegTable t)
+{
+    const size_t ct_len = (size_t)2 * a.L << a.logn;
+    const u64 total = t.start[t.n];
+    for (u64 g = blockIdx.x; g < total; g += gridDim.x) {
+        const int s = seg_of(t, g);
+        const u64 k = g - t.start[s];
+        const int slot = a.lut[t.px[s][k]];
+        if (slot < 0) continue;
+        lookup_ct(a, slot, t.seed[s], k, t.out[s] + k * ct_len);
+    }
+}
+
+static unsigned persistent_grid(u64 total, LaunchShape ls, int num_sms)
+{
+    const u64 cap = (u64)num_sms * (ls.blocks_per_sm > 0 ? ls.blocks_per_sm : 1);
+    return (unsigned)(total < cap ? total : cap);
+}
+
+cudaError_t launch_radix_combine_batch(const RadixArgs& a, const SegTable& t, LaunchShape ls, int num_sms,
+                                       cudaStream_t st)
+{
+    const u64 total = t.n > 0 ? t.start[t.n] : 0;
+    if (total == 0) return cudaSuccess;
+    k_radix_combine_batch<<<persistent_grid(total, ls, num_sms), ls.threads, 0, st>>>(a, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lookup_combine_batch(const LookupArgs& a, const SegTable& t, LaunchShape ls, int num_sms,
+                                        cudaStream_t st)
+{
+    const u64 total = t.n > 0 ? t.start[t.n] : 0;
+    if (total == 0) return cudaSuccess;
+    k_lookup_combine_batch<<<persistent_grid(total, ls, num_sms), ls.threads, 0, st>>>(a, t);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_lookup_combine(const LookupArgs& a, cudaStream_t st)

@@ -127,21 +127,15 @@ __global__ void k_rescale(const __grid_constant__ OpsArgs a)
 // are below 2^60, so the 9-term sums fit 64 bits unreduced and go straight into the Shoup
 // products (K9 for the dropped limb, K9 q_t^{-1} for the kept ones).
 template <int LIMBS>
-__global__ void __launch_bounds__(256) k_meanfilter3(const __grid_constant__ OpsArgs a)
+__device__ __forceinline__ void meanfilter_row(const OpsArgs& a, const u64* in0, u64* out0, int h, int w, int C, int y,
+                                               int chunk, int b, int ch)
 {
     const int n = 1 << a.logn;
-    const int chunks = (n / 2) / blockDim.x;
-    const int h = a.h, w = a.w, C = a.c;
-    u64 bid = blockIdx.x;
-    const int y = (int)(bid % h); bid /= h;
-    const int chunk = (int)(bid % chunks); bid /= chunks;
-    const int b = (int)(bid % 2); bid /= 2;
-    const int ch = (int)bid;
     const int c2 = chunk * blockDim.x + threadIdx.x;  // coefficient-pair index
     const u64 ct_len2 = (u64)2 * LIMBS * (n / 2);
     const u64 out_len2 = (u64)2 * (LIMBS - 1) * (n / 2);
-    const ulonglong2* in = reinterpret_cast<const ulonglong2*>(a.in0) + (u64)b * LIMBS * (n / 2) + c2;
-    ulonglong2* out = reinterpret_cast<ulonglong2*>(a.out) + (u64)b * (LIMBS - 1) * (n / 2) + c2;
+    const ulonglong2* in = reinterpret_cast<const ulonglong2*>(in0) + (u64)b * LIMBS * (n / 2) + c2;
+    ulonglong2* out = reinterpret_cast<ulonglong2*>(out0) + (u64)b * (LIMBS - 1) * (n / 2) + c2;
     const int ym = y > 0 ? y - 1 : 0, yp = y + 1 < h ? y + 1 : h - 1;
 
     ulonglong2 col[3][LIMBS];
@@ -183,36 +177,117 @@ __global__ void __launch_bounds__(256) k_meanfilter3(const __grid_constant__ Ops
     }
 }
 
+// One block per (row y, coefficient chunk, poly, channel).
+template <int LIMBS>
+__global__ void __launch_bounds__(256) k_meanfilter3(const __grid_constant__ OpsArgs a)
+{
+    const int chunks = ((1 << a.logn) / 2) / blockDim.x;
+    u64 bid = blockIdx.x;
+    const int y = (int)(bid % a.h); bid /= a.h;
+    const int chunk = (int)(bid % chunks); bid /= chunks;
+    const int b = (int)(bid % 2); bid /= 2;
+    meanfilter_row<LIMBS>(a, a.in0, a.out, a.h, a.w, a.c, y, chunk, b, (int)bid);
+}
+
+// Ragged batch: segment s has h*chunks*2*c items, in the order of the single-image kernel.
+template <int LIMBS>
+__global__ void __launch_bounds__(1024) k_meanfilter3_batch(const __grid_constant__ OpsArgs a,
+                                                            const __grid_constant__ SegTable t)
+{
+    const int chunks = ((1 << a.logn) / 2) / blockDim.x;
+    const u64 total = t.start[t.n];
+    for (u64 g = blockIdx.x; g < total; g += gridDim.x) {
+        const int s = seg_of(t, g);
+        u64 i = g - t.start[s];
+        const int h = (int)t.h[s];
+        const int y = (int)(i % h); i /= h;
+        const int chunk = (int)(i % chunks); i /= chunks;
+        const int b = (int)(i % 2); i /= 2;
+        meanfilter_row<LIMBS>(a, t.in0[s], t.out[s], h, (int)t.w[s], (int)t.c[s], y, chunk, b, (int)i);
+    }
+}
+
 // Fused watermark blend (reading R15): out = Rescale(Ka * I + Kb * W), W broadcast over
-// channels when it has one channel. The kept limbs use Ka q_t^{-1}, Kb q_t^{-1}.
+// channels when it has one channel. The kept limbs use Ka q_t^{-1}, Kb q_t^{-1}. One call
+// handles coefficient pair c of polynomial b of one ciphertext.
+template <int LIMBS>
+__device__ __forceinline__ void blend_pair(const OpsArgs& a, const u64* ci, const u64* cw, u64* co, int b, int c)
+{
+    const int n = 1 << a.logn;
+    const int t = LIMBS - 1;
+    const ulonglong2* s0 = reinterpret_cast<const ulonglong2*>(ci + (u64)b * LIMBS * n) + c;
+    const ulonglong2* s1 = reinterpret_cast<const ulonglong2*>(cw + (u64)b * LIMBS * n) + c;
+    const u64 qt = a.q[t];
+    const ulonglong2 ut = __ldcs(s0 + t * (n / 2)), wt = __ldg(s1 + t * (n / 2));
+    const u64 tx = add_mod(shoup(ut.x, a.k0[t], a.k0p[t], qt), shoup(wt.x, a.k1[t], a.k1p[t], qt), qt);
+    const u64 ty = add_mod(shoup(ut.y, a.k0[t], a.k0p[t], qt), shoup(wt.y, a.k1[t], a.k1p[t], qt), qt);
+    ulonglong2* dst = reinterpret_cast<ulonglong2*>(co + (u64)b * (LIMBS - 1) * n) + c;
+#pragma unroll
+    for (int j = 0; j < LIMBS - 1; ++j) {
+        const u64 qj = a.q[j];
+        const ulonglong2 u = __ldcs(s0 + j * (n / 2)), v = __ldg(s1 + j * (n / 2));
+        const u64 px = csub(shoup_lazy(u.x, a.k0r[j], a.k0rp[j], qj) + shoup_lazy(v.x, a.k1r[j], a.k1rp[j], qj), 2 * qj);
+        const u64 py = csub(shoup_lazy(u.y, a.k0r[j], a.k0rp[j], qj) + shoup_lazy(v.y, a.k1r[j], a.k1rp[j], qj), 2 * qj);
+        ulonglong2 o;
+        o.x = rescale_fold(px, tx, j, a);
+        o.y = rescale_fold(py, ty, j, a);
+        __stcs(dst + j * (n / 2), o);
+    }
+}
+
 template <int LIMBS>
 __global__ void k_blend(const __grid_constant__ OpsArgs a)
 {
     const int n = 1 << a.logn;
     const u64 total = a.n_ct * 2 * (u64)(n / 2);
-    const int t = LIMBS - 1;
     for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total; i += (u64)gridDim.x * blockDim.x) {
         const u64 kb = i / (n / 2);
         const int c = (int)(i % (n / 2));
-        const u64 k = kb / 2, b = kb % 2;
+        const u64 k = kb / 2;
+        const int b = (int)(kb % 2);
         const u64 kw = (k / a.c) * a.c_w + (a.c_w == 1 ? 0 : k % a.c);
-        const ulonglong2* s0 = reinterpret_cast<const ulonglong2*>(a.in0 + kb * LIMBS * (u64)n) + c;
-        const ulonglong2* s1 = reinterpret_cast<const ulonglong2*>(a.in1 + (kw * 2 + b) * LIMBS * (u64)n) + c;
-        const u64 qt = a.q[t];
-        const ulonglong2 ut = __ldcs(s0 + t * (n / 2)), wt = __ldg(s1 + t * (n / 2));
-        const u64 tx = add_mod(shoup(ut.x, a.k0[t], a.k0p[t], qt), shoup(wt.x, a.k1[t], a.k1p[t], qt), qt);
-        const u64 ty = add_mod(shoup(ut.y, a.k0[t], a.k0p[t], qt), shoup(wt.y, a.k1[t], a.k1p[t], qt), qt);
-        ulonglong2* dst = reinterpret_cast<ulonglong2*>(a.out + kb * (LIMBS - 1) * (u64)n) + c;
-#pragma unroll
-        for (int j = 0; j < LIMBS - 1; ++j) {
-            const u64 qj = a.q[j];
-            const ulonglong2 u = __ldcs(s0 + j * (n / 2)), v = __ldg(s1 + j * (n / 2));
-            const u64 px = csub(shoup_lazy(u.x, a.k0r[j], a.k0rp[j], qj) + shoup_lazy(v.x, a.k1r[j], a.k1rp[j], qj), 2 * qj);
-            const u64 py = csub(shoup_lazy(u.y, a.k0r[j], a.k0rp[j], qj) + shoup_lazy(v.y, a.k1r[j], a.k1rp[j], qj), 2 * qj);
-            ulonglong2 o;
-            o.x = rescale_fold(px, tx, j, a);
-            o.y = rescale_fold(py, ty, j, a);
-            __stcs(dst + j * (n / 2), o);
+        blend_pair<LIMBS>(a, a.in0 + k * 2 * LIMBS * (u64)n, a.in1 + kw * 2 * LIMBS * (u64)n,
+                          a.out + k * 2 * (LIMBS - 1) * (u64)n, b, c);
+    }
+}
+
+// Ragged batch: one block per ciphertext; W of segment s has c1[s] channels.
+template <int LIMBS>
+__global__ void __launch_bounds__(1024) k_blend_batch(const __grid_constant__ OpsArgs a,
+                                                      const __grid_constant__ SegTable t)
+{
+    const int n = 1 << a.logn;
+    const u64 total = t.start[t.n];
+    for (u64 g = blockIdx.x; g < total; g += gridDim.x) {
+        const int s = seg_of(t, g);
+        const u64 k = g - t.start[s];
+        const u64 C = t.c[s], Cw = t.c1[s];
+        const u64 kw = (k / C) * Cw + (Cw == 1 ? 0 : k % C);
+        const u64* ci = t.in0[s] + k * 2 * LIMBS * (u64)n;
+        const u64* cw = t.in1[s] + kw * 2 * LIMBS * (u64)n;
+        u64* co = t.out[s] + k * 2 * (LIMBS - 1) * (u64)n;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) blend_pair<LIMBS>(a, ci, cw, co, i / (n / 2), i % (n / 2));
+    }
+}
+
+// Plaintext add of a per-segment constant (brightness of each request), ciphertext copied:
+// one block per ciphertext.
+__global__ void __launch_bounds__(1024) k_ptadd_batch(const __grid_constant__ OpsArgs a,
+                                                      const __grid_constant__ SegTable t)
+{
+    const int n = 1 << a.logn;
+    const int limbs = a.limbs;
+    const u64 total = t.start[t.n];
+    for (u64 g = blockIdx.x; g < total; g += gridDim.x) {
+        const int s = seg_of(t, g);
+        const u64 k = g - t.start[s];
+        const ulonglong2* src = reinterpret_cast<const ulonglong2*>(t.in0[s] + k * 2 * (u64)limbs * n);
+        ulonglong2* dst = reinterpret_cast<ulonglong2*>(t.out[s] + k * 2 * (u64)limbs * n);
+        for (int i = threadIdx.x; i < limbs * n; i += blockDim.x) {
+            ulonglong2 v = __ldcs(src + i);
+            const int row = i / (n / 2);                 // b * limbs + l
+            if (i % (n / 2) == 0 && row < limbs) v.x = add_mod(v.x, t.kadd[s][row], a.q[row]);
+            __stcs(dst + i, v);
         }
     }
 }
@@ -256,76 +331,98 @@ __device__ __forceinline__ U192 mul192(u64 y, const u64 (&w)[3])
 // (c0 + c1*s)_0 = c0_0 + sum_j c1_j * srev_j with srev_0 = s_0, srev_j = -s_{N-j}; s is
 // ternary, so the sum is signed additions only. One block per ciphertext.
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_decrypt(const __grid_constant__ DecArgs a)
+// One block (whole warps, at most 32 of them) decrypts one ciphertext; `red` is the block's
+// shared scratch. Ends with a barrier, so the caller may reuse `red` at once.
+__device__ __forceinline__ void decrypt_ct(const DecArgs& a, const u64* ct, double scale, double* out,
+                                           u64* residues, u64 (*red)[2][kMaxPrimes])
 {
     const int n = 1 << a.logn;
     const int nl = a.crt.nl;
-    __shared__ u64 red[8][2][kMaxPrimes];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint16_t* s2 = reinterpret_cast<const uint16_t*>(a.srev);
-    for (u64 k = blockIdx.x; k < a.n_ct; k += gridDim.x) {
-        const u64* ct = a.ct + k * 2 * (u64)nl * n;
-        for (int l = 0; l < nl; ++l) {
-            const u64 q = a.q[l], mu = a.crt.mu[l];
-            const ulonglong2* c1 = reinterpret_cast<const ulonglong2*>(ct + ((u64)nl + l) * n);
-            // residues are below 2^60: up to 8 of them (plus a reduced partial sum) fit 64 bits,
-            // so the signed sums are reduced once every four coefficient pairs
-            u64 pos = 0, neg = 0;
-            int pending = 0;
-            for (int j2 = threadIdx.x; j2 < n / 2; j2 += blockDim.x) {
-                const ulonglong2 v = __ldcs(c1 + j2);
-                const uint16_t sg = __ldg(s2 + j2);
-                const int s0 = (int8_t)(sg & 0xff), s1 = (int8_t)(sg >> 8);
-                pos += (s0 > 0 ? v.x : 0) + (s1 > 0 ? v.y : 0);
-                neg += (s0 < 0 ? v.x : 0) + (s1 < 0 ? v.y : 0);
-                if (++pending == 4) {
-                    pos = reduce64(pos, q, mu);
-                    neg = reduce64(neg, q, mu);
-                    pending = 0;
-                }
+    for (int l = 0; l < nl; ++l) {
+        const u64 q = a.q[l], mu = a.crt.mu[l];
+        const ulonglong2* c1 = reinterpret_cast<const ulonglong2*>(ct + ((u64)nl + l) * n);
+        // residues are below 2^60: up to 8 of them (plus a reduced partial sum) fit 64 bits,
+        // so the signed sums are reduced once every four coefficient pairs
+        u64 pos = 0, neg = 0;
+        int pending = 0;
+        for (int j2 = threadIdx.x; j2 < n / 2; j2 += blockDim.x) {
+            const ulonglong2 v = __ldcs(c1 + j2);
+            const uint16_t sg = __ldg(s2 + j2);
+            const int s0 = (int8_t)(sg & 0xff), s1 = (int8_t)(sg >> 8);
+            pos += (s0 > 0 ? v.x : 0) + (s1 > 0 ? v.y : 0);
+            neg += (s0 < 0 ? v.x : 0) + (s1 < 0 ? v.y : 0);
+            if (++pending == 4) {
+                pos = reduce64(pos, q, mu);
+                neg = reduce64(neg, q, mu);
+                pending = 0;
             }
-            pos = reduce64(pos, q, mu);
-            neg = reduce64(neg, q, mu);
+        }
+        pos = reduce64(pos, q, mu);
+        neg = reduce64(neg, q, mu);
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                pos = add_mod(pos, __shfl_down_sync(0xffffffffu, pos, off), q);
-                neg = add_mod(neg, __shfl_down_sync(0xffffffffu, neg, off), q);
-            }
-            if (lane == 0) { red[warp][0][l] = pos; red[warp][1][l] = neg; }
+        for (int off = 16; off > 0; off >>= 1) {
+            pos = add_mod(pos, __shfl_down_sync(0xffffffffu, pos, off), q);
+            neg = add_mod(neg, __shfl_down_sync(0xffffffffu, neg, off), q);
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            u64 y[kMaxPrimes];
-            double v = 0.0;
-            for (int l = 0; l < nl; ++l) {
-                const u64 q = a.q[l];
-                u64 p = ct[(u64)l * n], m = 0;  // c0 coefficient 0
-                for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) {
-                    p = add_mod(p, red[wi][0][l], q);
-                    m = add_mod(m, red[wi][1][l], q);
-                }
-                const u64 res = sub_mod(p, m, q);
-                if (a.residues_out) a.residues_out[k * nl + l] = res;
-                y[l] = shoup(res, a.crt.inv[l], a.crt.invp[l], q);
-                v += (double)y[l] * a.crt.qinv[l];
+        if (lane == 0) { red[warp][0][l] = pos; red[warp][1][l] = neg; }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        u64 y[kMaxPrimes];
+        double v = 0.0;
+        for (int l = 0; l < nl; ++l) {
+            const u64 q = a.q[l];
+            u64 p = ct[(u64)l * n], m = 0;  // c0 coefficient 0
+            for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) {
+                p = add_mod(p, red[wi][0][l], q);
+                m = add_mod(m, red[wi][1][l], q);
             }
-            // x = sum_l y_l * (Q/q_l) - round(sum_l y_l/q_l) * Q, the centered CRT value,
-            // held modulo 2^192 (exact for |x| < 2^191)
-            const u64 kq = (u64)rint(v);
-            U192 x = {0, 0, 0};
-            for (int l = 0; l < nl; ++l) add192(x, mul192(y[l], a.crt.qiw[l]));
-            sub192(x, mul192(kq, a.crt.qw));
-            const bool negv = (x.w2 >> 63) != 0;
-            if (negv) {
-                U192 z = {0, 0, 0};
-                sub192(z, x);
-                x = z;
-            }
-            const double mag = (double)x.w2 * 0x1p128 + (double)x.w1 * 0x1p64 + (double)x.w0;
-            const double val = mag / a.scale;
-            a.out[k] = negv ? -val : val;
+            const u64 res = sub_mod(p, m, q);
+            if (residues) residues[l] = res;
+            y[l] = shoup(res, a.crt.inv[l], a.crt.invp[l], q);
+            v += (double)y[l] * a.crt.qinv[l];
         }
-        __syncthreads();
+        // x = sum_l y_l * (Q/q_l) - round(sum_l y_l/q_l) * Q, the centered CRT value, held
+        // modulo 2^192 (exact for |x| < 2^191)
+        const u64 kq = (u64)rint(v);
+        U192 x = {0, 0, 0};
+        for (int l = 0; l < nl; ++l) add192(x, mul192(y[l], a.crt.qiw[l]));
+        sub192(x, mul192(kq, a.crt.qw));
+        const bool negv = (x.w2 >> 63) != 0;
+        if (negv) {
+            U192 z = {0, 0, 0};
+            sub192(z, x);
+            x = z;
+        }
+        const double mag = (double)x.w2 * 0x1p128 + (double)x.w1 * 0x1p64 + (double)x.w0;
+        const double val = mag / scale;
+        *out = negv ? -val : val;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_decrypt(const __grid_constant__ DecArgs a)
+{
+    __shared__ u64 red[32][2][kMaxPrimes];
+    const int nl = a.crt.nl;
+    for (u64 k = blockIdx.x; k < a.n_ct; k += gridDim.x)
+        decrypt_ct(a, a.ct + k * 2 * (u64)nl * (1u << a.logn), a.scale, a.out + k,
+                   a.residues_out ? a.residues_out + k * nl : nullptr, red);
+}
+
+// Ragged batch: segment s decrypts in0[s] (at the level of `a`) into dout[s] with scale[s].
+__global__ void __launch_bounds__(1024) k_decrypt_batch(const __grid_constant__ DecArgs a,
+                                                        const __grid_constant__ SegTable t)
+{
+    __shared__ u64 red[32][2][kMaxPrimes];
+    const int nl = a.crt.nl;
+    const u64 total = t.start[t.n];
+    for (u64 g = blockIdx.x; g < total; g += gridDim.x) {
+        const int s = seg_of(t, g);
+        const u64 k = g - t.start[s];
+        decrypt_ct(a, t.in0[s] + k * 2 * (u64)nl * (1u << a.logn), t.scale[s], t.dout[s] + k, nullptr, red);
     }
 }
 
@@ -367,6 +464,18 @@ cudaError_t launch_ptmul(const OpsArgs& a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+#define ICHEE_LIMB_SWITCH_T(KERNEL, GRID, BLOCK, ARGS, TABLE)                \
+    switch (ARGS.limbs) {                                                     \
+    case 2: KERNEL<2><<<GRID, BLOCK, 0, st>>>(ARGS, TABLE); break;            \
+    case 3: KERNEL<3><<<GRID, BLOCK, 0, st>>>(ARGS, TABLE); break;            \
+    case 4: KERNEL<4><<<GRID, BLOCK, 0, st>>>(ARGS, TABLE); break;            \
+    case 5: KERNEL<5><<<GRID, BLOCK, 0, st>>>(ARGS, TABLE); break;            \
+    case 6: KERNEL<6><<<GRID, BLOCK, 0, st>>>(ARGS, TABLE); break;            \
+    case 7: KERNEL<7><<<GRID, BLOCK, 0, st>>>(ARGS, TABLE); break;            \
+    case 8: KERNEL<8><<<GRID, BLOCK, 0, st>>>(ARGS, TABLE); break;            \
+    default: return cudaErrorInvalidValue;                                    \
+    }
+
 #define ICHEE_LIMB_SWITCH(KERNEL, GRID, BLOCK, ARGS)                          \
     switch (ARGS.limbs) {                                                     \
     case 2: KERNEL<2><<<GRID, BLOCK, 0, st>>>(ARGS); break;                   \
@@ -403,6 +512,46 @@ cudaError_t launch_blend(const OpsArgs& a, cudaStream_t st)
     const u64 work = a.n_ct * 2 * (u64)((1u << a.logn) / 2);
     const unsigned g = grid_for(work, 256);
     ICHEE_LIMB_SWITCH(k_blend, g, 256, a)
+    return cudaGetLastError();
+}
+
+static unsigned persistent_grid(u64 total, LaunchShape ls, int num_sms)
+{
+    const u64 cap = (u64)num_sms * (ls.blocks_per_sm > 0 ? ls.blocks_per_sm : 1);
+    return (unsigned)(total < cap ? total : cap);
+}
+
+cudaError_t launch_meanfilter3_batch(const OpsArgs& a, const SegTable& t, LaunchShape ls, int num_sms, cudaStream_t st)
+{
+    const u64 total = t.n > 0 ? t.start[t.n] : 0;
+    if (total == 0) return cudaSuccess;
+    const unsigned g = persistent_grid(total, ls, num_sms);
+    ICHEE_LIMB_SWITCH_T(k_meanfilter3_batch, g, ls.threads, a, t)
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blend_batch(const OpsArgs& a, const SegTable& t, LaunchShape ls, int num_sms, cudaStream_t st)
+{
+    const u64 total = t.n > 0 ? t.start[t.n] : 0;
+    if (total == 0) return cudaSuccess;
+    const unsigned g = persistent_grid(total, ls, num_sms);
+    ICHEE_LIMB_SWITCH_T(k_blend_batch, g, ls.threads, a, t)
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ptadd_batch(const OpsArgs& a, const SegTable& t, LaunchShape ls, int num_sms, cudaStream_t st)
+{
+    const u64 total = t.n > 0 ? t.start[t.n] : 0;
+    if (total == 0) return cudaSuccess;
+    k_ptadd_batch<<<persistent_grid(total, ls, num_sms), ls.threads, 0, st>>>(a, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decrypt_batch(const DecArgs& a, const SegTable& t, LaunchShape ls, int num_sms, cudaStream_t st)
+{
+    const u64 total = t.n > 0 ? t.start[t.n] : 0;
+    if (total == 0) return cudaSuccess;
+    k_decrypt_batch<<<persistent_grid(total, ls, num_sms), ls.threads, 0, st>>>(a, t);
     return cudaGetLastError();
 }
 

@@ -58,6 +58,13 @@ cudaError_t launch_meanfilter3(const OpsArgs& a, cudaStream_t st);
 cudaError_t launch_blend(const OpsArgs& a, cudaStream_t st);
 cudaError_t launch_decrypt(const DecArgs& a, cudaStream_t st);
 
+// Ragged batches (SegTable items: ciphertexts, or mean-filter rows x chunks x polys x channels).
+// All segments share the level, the scale class and the constants of `a`.
+cudaError_t launch_meanfilter3_batch(const OpsArgs& a, const SegTable& t, LaunchShape ls, int num_sms, cudaStream_t st);
+cudaError_t launch_blend_batch(const OpsArgs& a, const SegTable& t, LaunchShape ls, int num_sms, cudaStream_t st);
+cudaError_t launch_ptadd_batch(const OpsArgs& a, const SegTable& t, LaunchShape ls, int num_sms, cudaStream_t st);
+cudaError_t launch_decrypt_batch(const DecArgs& a, const SegTable& t, LaunchShape ls, int num_sms, cudaStream_t st);
+
 // Matching: sum over ciphertexts of (a - b)^2 as a degree-2 ciphertext in the NTT domain.
 struct SqDiffArgs {
     RnsArgs rns;                   // moduli 0..limbs-1

@@ -63,6 +63,17 @@ class CacheDesc(ctypes.Structure):
                 ("top_k", ctypes.c_uint32), ("pool_size", ctypes.c_uint32), ("miss_policy", ctypes.c_uint32)]
 
 
+class ImageDesc(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_uint32), ("w", ctypes.c_uint32), ("c", ctypes.c_uint32), ("seed", ctypes.c_uint64)]
+
+
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_uint32), ("threads", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
+                ("ms", ctypes.c_float)]
+
+
+TUNE_RADIX, TUNE_LOOKUP, TUNE_MEANFILTER = 1, 2, 3
+
 _vp = ctypes.c_void_p
 _u64 = ctypes.c_uint64
 _u32 = ctypes.c_uint32
@@ -87,6 +98,21 @@ _SIGS = {
     "ichee_decrypt_residues": (_st, [_vp, _vp, ctypes.POINTER(CtImgMeta), _vp, _vp, _vp]),
     "ichee_sqdiff_sum_noalloc": (_st, [_vp, _vp, ctypes.POINTER(CtImgMeta), _vp, ctypes.POINTER(CtImgMeta), _vp,
                                        ctypes.POINTER(CtImgMeta), _vp]),
+    "ichee_encrypt_batch": (_st, [_vp, _vp, ctypes.POINTER(_vp), ctypes.POINTER(ImageDesc), _u32,
+                                  ctypes.POINTER(_vp), ctypes.POINTER(CtImgMeta), _vp]),
+    "ichee_eval_batch": (_st, [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(CtImgMeta), ctypes.POINTER(_vp),
+                               ctypes.POINTER(CtImgMeta), _vp, _u32, ctypes.POINTER(_vp), ctypes.POINTER(CtImgMeta),
+                               _u32, _vp]),
+    "ichee_decrypt_batch": (_st, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(CtImgMeta), ctypes.POINTER(_vp), _u32,
+                                  _vp]),
+    "ichee_autotune_batch": (_st, [_vp, _vp, ctypes.POINTER(_vp), ctypes.POINTER(ImageDesc), _u32,
+                                   ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(TuneEntry),
+                                   ctypes.POINTER(_u32), _vp]),
+    "ichee_tuned_shape": (_st, [_vp, _u32, ctypes.POINTER(_u32), ctypes.POINTER(_u32)]),
+    "ichee_graph_begin": (_st, [_vp, _vp]),
+    "ichee_graph_end": (_st, [_vp, _vp, ctypes.POINTER(_vp)]),
+    "ichee_graph_launch": (_st, [_vp, _vp]),
+    "ichee_graph_destroy": (None, [_vp]),
     "ichee_stream_status": (_st, [_vp, _vp]),
     "ichee_last_error": (ctypes.c_char_p, []),
 }
@@ -220,6 +246,81 @@ def ichee_sqdiff_sum_noalloc(ctx, a, ma, b, mb, out, stream=None):
     _check(_lib.ichee_sqdiff_sum_noalloc(ctx, _ptr(a), ctypes.byref(ma), _ptr(b), ctypes.byref(mb), _ptr(out),
                                          ctypes.byref(m), stream))
     return m
+
+
+def _ptrs(xs):
+    return (_vp * max(len(xs), 1))(*[_ptr(x) for x in xs])
+
+
+def _descs(shapes, seeds):
+    arr = (ImageDesc * len(shapes))()
+    for i, ((h, w, c), sd) in enumerate(zip(shapes, seeds)):
+        arr[i].h, arr[i].w, arr[i].c, arr[i].seed = h, w, c, sd
+    return arr
+
+
+def ichee_encrypt_batch(ctx, cache, pixels, shapes, seeds, ct_outs, stream=None):
+    """Encrypt images (device pixel tensors, shapes [(h, w, c)], seeds) into ct_outs; returns metas."""
+    n = len(shapes)
+    metas = (CtImgMeta * n)()
+    _check(_lib.ichee_encrypt_batch(ctx, cache, _ptrs(pixels), _descs(shapes, seeds), n, _ptrs(ct_outs), metas,
+                                    stream))
+    return list(metas)
+
+
+def _metas(ms):
+    arr = (CtImgMeta * len(ms))()
+    for i, m in enumerate(ms):
+        arr[i] = m
+    return arr
+
+
+def ichee_eval_batch(ctx, op, a, ma, b=None, mb=None, args=(), outs=None, stream=None):
+    n = len(a)
+    mout = (CtImgMeta * n)()
+    nargs = len(args)
+    arr = (ctypes.c_double * max(nargs, 1))(*args)
+    _check(_lib.ichee_eval_batch(ctx, op, _ptrs(a), _metas(ma), _ptrs(b) if b is not None else None,
+                                 _metas(mb) if mb is not None else None, arr if nargs else None, nargs, _ptrs(outs),
+                                 mout, n, stream))
+    return list(mout)
+
+
+def ichee_decrypt_batch(ctx, cts, metas, outs, stream=None):
+    _check(_lib.ichee_decrypt_batch(ctx, _ptrs(cts), _metas(metas), _ptrs(outs), len(cts), stream))
+
+
+def ichee_autotune_batch(ctx, cache, pixels, shapes, seeds, cts, filtered, stream=None, max_report=64):
+    n = len(shapes)
+    rep = (TuneEntry * max_report)()
+    nrep = _u32(max_report)
+    _check(_lib.ichee_autotune_batch(ctx, cache, _ptrs(pixels), _descs(shapes, seeds), n, _ptrs(cts), _ptrs(filtered),
+                                     rep, ctypes.byref(nrep), stream))
+    return [(e.kind, e.threads, e.blocks_per_sm, e.ms) for e in rep[:min(nrep.value, max_report)]]
+
+
+def ichee_tuned_shape(ctx, kind):
+    t, b = _u32(), _u32()
+    _check(_lib.ichee_tuned_shape(ctx, kind, ctypes.byref(t), ctypes.byref(b)))
+    return int(t.value), int(b.value)
+
+
+def ichee_graph_begin(ctx, stream):
+    _check(_lib.ichee_graph_begin(ctx, stream))
+
+
+def ichee_graph_end(ctx, stream):
+    g = _vp()
+    _check(_lib.ichee_graph_end(ctx, stream, ctypes.byref(g)))
+    return g
+
+
+def ichee_graph_launch(graph, stream=None):
+    _check(_lib.ichee_graph_launch(graph, stream))
+
+
+def ichee_graph_destroy(graph):
+    _lib.ichee_graph_destroy(graph)
 
 
 def ichee_stream_status(ctx, stream=None):
