@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=["enc8192", "batch32", "serve"], default="enc8192",
+                    help="enc8192: the headline step; batch32: ragged batch under a CUDA graph vs per-image "
+                         "launches; serve: Poisson request stream through the continuous-batching server")
+    ap.add_argument("--duration", type=float, default=None, help="serve: seconds of arrivals (default 60)")
     return ap.parse_args()
 
 
@@ -434,10 +438,264 @@ def run_reference(args):
                       "e2e": {"value": round(v, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+# ---------------------------------------------------------------------------------------
+# ragged batch under one CUDA graph vs per-image launches
+# ---------------------------------------------------------------------------------------
+def run_batch(args):
+    import ctypes
+    import torch
+    from paper_2409_03568_gb300 import ichee
+
+    wl = W.BATCH32
+    torch.cuda.set_device(0)
+    hbm_peak, peak_kind = measured_peaks()
+    ctx = ichee.Context(**W.ctx_kwargs(wl))
+    ctx.keygen(77)
+    cache = ctx.build_cache(ichee.CACHE_RADIX, 15, radix_base=wl["radix_base"], randomize=1)
+    imgs = inputs.ragged_batch(wl["n_images"], wl["batch_seed"], wl["side_lo"], wl["side_hi"])
+    shapes = [(im.shape[0], im.shape[1], 1) for im in imgs]
+    seeds = [500 + i for i in range(len(imgs))]
+    n_px = sum(h * w * c for h, w, c in shapes)
+    d_px = [torch.from_numpy(im.reshape(-1).copy()).cuda() for im in imgs]
+    enc = [ctx.empty_cts(h * w * c, 2) for h, w, c in shapes]
+    filt = [ctx.empty_cts(h * w * c, 1) for h, w, c in shapes]
+    H = ctx.handle
+    st_main = torch.cuda.current_stream()
+    sp_main = ctypes.c_void_p(st_main.cuda_stream)
+    metas = [None] * len(shapes)
+
+    def plain():
+        for i, (h, w, c) in enumerate(shapes):
+            metas[i] = ichee.ichee_encrypt_image(H, cache, d_px[i], h, w, c, seeds[i], enc[i], sp_main)
+            ichee.ichee_eval(H, ichee.OP_MEANFILTER3, enc[i], metas[i], None, None, (), filt[i], sp_main)
+
+    tune = ichee.ichee_autotune_batch(H, cache, d_px, shapes, seeds, enc, filt, sp_main)
+    shapes_used = {"radix": ichee.ichee_tuned_shape(H, ichee.TUNE_RADIX),
+                   "meanfilter": ichee.ichee_tuned_shape(H, ichee.TUNE_MEANFILTER)}
+    cap = torch.cuda.Stream()
+    sp_cap = ctypes.c_void_p(cap.cuda_stream)
+    torch.cuda.synchronize()
+    ichee.ichee_graph_begin(H, sp_cap)
+    bm = ichee.ichee_encrypt_batch(H, cache, d_px, shapes, seeds, enc, sp_cap)
+    ichee.ichee_eval_batch(H, ichee.OP_MEANFILTER3, enc, bm, outs=filt, stream=sp_cap)
+    graph = ichee.ichee_graph_end(H, sp_cap)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            e0.record(st_main)
+            fn()
+            e1.record(st_main)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / args.steps
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms_plain = timed(plain)
+    ref = [f.clone() for f in filt[:3]]
+    ms_graph = timed(lambda: ichee.ichee_graph_launch(graph, sp_main))
+    clk = clocks.stop()
+    torch.cuda.synchronize()
+    same = all(torch.equal(a, b) for a, b in zip(ref, filt[:3]))
+    ct3, ct2 = 2 * 3 * ctx.n * 8, 2 * 2 * ctx.n * 8
+    bytes_step = n_px * (ct3 + ct3 + ct2)   # encryption write, filter read, filter write
+    achieved = bytes_step / (ms_graph / 1e3) / 1e9
+    out = {"metric": "pixel ciphertexts/s, radix-16 encryption + 3x3 mean filter over a ragged batch of 32 images",
+           "value": round(n_px / (ms_graph / 1e3), 1), "unit": "px/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms_graph, 4), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "u64 (RNS residues mod 60/40/60-bit primes)",
+           "data": "synthetic (32 random fields, sides U{16..128}, seed 7)",
+           "config": {"workload": wl["name"], "pixels": n_px, "images": len(shapes),
+                      "ciphertext_gb": round(n_px * (ct3 + ct2) / 1e9, 1),
+                      "l2": "working set (%.0f GB) far above L2" % (n_px * (ct3 + ct2) / 1e9)},
+           "plain_per_image": {"ms_per_step": round(ms_plain, 4), "px_per_s": round(n_px / (ms_plain / 1e3), 1),
+                               "launches": 2 * len(shapes)},
+           "graph_speedup": round(ms_plain / ms_graph, 3), "graph_equals_plain": same,
+           "tuned_shapes": {k: {"threads": v[0], "blocks_per_sm": v[1]} for k, v in shapes_used.items()},
+           "tuner_report": [{"kind": k, "threads": t, "blocks_per_sm": b, "ms": round(m, 4)} for k, t, b, m in tune],
+           "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                        "frac": round(achieved / hbm_peak, 4), "traffic": None, "kernel": "graph(encrypt+filter)",
+                        "peak_kind": peak_kind},
+           "clocks": clk}
+    print(json.dumps(out))
+    ichee.ichee_graph_destroy(graph)
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------------------
+# serving: Poisson request stream through the continuous-batching server
+# ---------------------------------------------------------------------------------------
+def serve_requests(wl, duration):
+    """The seeded request stream: arrival times and request parameters (no pixels yet)."""
+    rng = np.random.default_rng(wl["seed"])
+    t, reqs = 0.0, []
+    w = np.array(wl["op_weights"], dtype=np.float64)
+    while True:
+        t += rng.exponential(1.0 / wl["rate"])
+        if t >= duration:
+            break
+        side = int(rng.integers(wl["side_lo"], wl["side_hi"] + 1))
+        reqs.append(dict(t=t, kind=int(rng.choice(5, p=w / w.sum())), ring=int(rng.integers(0, 2)), h=side, w=side,
+                         c=int(rng.choice([1, 3])), seed=10_000 + 3 * len(reqs)))
+    return reqs
+
+
+def run_serve(args):
+    import threading
+    import torch
+    from paper_2409_03568_gb300 import ichee
+
+    wl = W.SERVE
+    duration = args.duration if args.duration else wl["duration_s"]
+    torch.cuda.set_device(0)
+    ctxs, caches = [], []
+    for i, r in enumerate(wl["rings"]):
+        ctx = ichee.Context(**r)
+        ctx.keygen(31 + i, with_evk=True)
+        ctxs.append(ctx)
+        caches.append(ctx.build_cache(ichee.CACHE_FULL, 41 + i, pool_size=64))
+    reqs = serve_requests(wl, duration)
+    bank = {}
+    for q in reqs:   # pixels drawn per request (seeded)
+        img = inputs.random_field_image(q["h"], q["w"], seed=q["seed"], channels=q["c"]).reshape(-1).copy()
+        two = None
+        if q["kind"] == ichee.REQ_WATERMARK:
+            two = inputs.binary_pattern(q["h"], q["w"], seed=q["seed"] + 1).reshape(-1).copy()
+        elif q["kind"] == ichee.REQ_MATCH:
+            two = inputs.noisy_copy(img, seed=q["seed"] + 2)
+        n_res = 1 if q["kind"] == ichee.REQ_MATCH else img.size
+        bank[id(q)] = (img, two, np.zeros(n_res, dtype=np.float64))
+    px_total = sum(q["h"] * q["w"] * q["c"] for q in reqs)
+    args_of = {ichee.REQ_BRIGHTNESS: 25.0, ichee.REQ_WATERMARK: 0.9}
+    # warm the matching scratch and first-launch paths outside the measurement
+    for ring in range(2):
+        ctx = ctxs[ring]
+        a, ma = ctx.encrypt(torch.zeros(4, dtype=torch.uint8, device="cuda"), 2, 2, 1, 1, cache=caches[ring])
+        ctx.eval(ichee.OP_SQDIFF_SUM, a, ma, a, ma, out_n_ct=1, out_level=ma.level - 1)
+    torch.cuda.synchronize()
+    server = ichee.ichee_server_create([c.handle for c in ctxs], caches, int(wl["budget_gb"] * 1e9))
+    tickets = [None] * len(reqs)
+    structs = []
+    t0 = time.perf_counter() + 0.5
+
+    def submitter():
+        for i, q in enumerate(reqs):
+            img, two, res = bank[id(q)]
+            r = ichee.Request()
+            r.kind, r.ring, r.h, r.w, r.c, r.seed = q["kind"], q["ring"], q["h"], q["w"], q["c"], q["seed"]
+            r.pixels = img.ctypes.data
+            r.pixels2 = two.ctypes.data if two is not None else None
+            r.arg = args_of.get(q["kind"], 0.0)
+            r.result = res.ctypes.data
+            r.ct_out = None
+            structs.append(r)
+            delay = t0 + q["t"] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            try:
+                tickets[i] = ichee.ichee_server_submit(server, r)
+            except ichee.IcheeError:
+                tickets[i] = -1   # refused at admission control (larger than the HBM budget)
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    th = threading.Thread(target=submitter)
+    th.start()
+    lat, rounds, first_sub, last_done = [], [], None, 0.0
+    refused = 0
+    served_px = 0
+    deadline = time.perf_counter() + duration + 600.0
+    for i in range(len(reqs)):
+        while tickets[i] is None:
+            if time.perf_counter() > deadline:
+                raise RuntimeError("serving run exceeded its time cap")
+            time.sleep(0.0005)
+        if tickets[i] < 0:
+            refused += 1
+            continue
+        d = ichee.ichee_server_wait(server, tickets[i], int(max(1.0, deadline - time.perf_counter()) * 1e3))
+        served_px += reqs[i]["h"] * reqs[i]["w"] * reqs[i]["c"]
+        lat.append(d.t_done - d.t_submit)
+        rounds.append(d.round_size)
+        first_sub = d.t_submit if first_sub is None else min(first_sub, d.t_submit)
+        last_done = max(last_done, d.t_done)
+    th.join()
+    clk = clocks.stop()
+    stats = ichee.ichee_server_stats_get(server)
+    ichee.ichee_server_destroy(server)
+    # every encrypt-only result decodes to its pixels
+    worst = max(float(np.max(np.abs(bank[id(q)][2] - bank[id(q)][0]))) for q, t in zip(reqs, tickets)
+                if q["kind"] == ichee.REQ_ENCRYPT and t is not None and t >= 0)
+    span = last_done - first_sub
+    lat = np.array(lat)
+
+    # the unbatched plain path: the same arrivals, one request at a time through the
+    # single-request entry points, on a prefix of the stream (at most 20 s of arrivals or 60 s)
+    plain_lat, plain_px = [], 0
+    tp0 = time.perf_counter()
+    for q in reqs:
+        if q["t"] > min(20.0, duration) or time.perf_counter() - tp0 > 60.0:
+            break
+        wait = tp0 + q["t"] - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        if q["kind"] == ichee.REQ_MATCH and q["ring"] == 1 and q["h"] * q["w"] * q["c"] > 45000:
+            continue   # refused by the server's budget as well
+        img, two, _ = bank[id(q)]
+        ctx, cache = ctxs[q["ring"]], caches[q["ring"]]
+        a, ma = ctx.encrypt(torch.from_numpy(img).cuda(), q["h"], q["w"], q["c"], q["seed"], cache=cache)
+        if q["kind"] == ichee.REQ_MEANFILTER:
+            a, ma = ctx.eval(ichee.OP_MEANFILTER3, a, ma, out_level=ma.level - 1)
+        elif q["kind"] == ichee.REQ_BRIGHTNESS:
+            a, ma = ctx.eval(ichee.OP_BRIGHTNESS, a, ma, args=(25.0,))
+        elif q["kind"] == ichee.REQ_WATERMARK:
+            b, mb = ctx.encrypt(torch.from_numpy(two).cuda(), q["h"], q["w"], 1, q["seed"] + 1, cache=cache)
+            a, ma = ctx.eval(ichee.OP_BLEND, a, ma, b, mb, args=(0.9,), out_level=ma.level - 1)
+        elif q["kind"] == ichee.REQ_MATCH:
+            b, mb = ctx.encrypt(torch.from_numpy(two).cuda(), q["h"], q["w"], q["c"], q["seed"] + 1, cache=cache)
+            a, ma = ctx.eval(ichee.OP_SQDIFF_SUM, a, ma, b, mb, out_n_ct=1, out_level=ma.level - 1)
+        ctx.decrypt(a, ma).cpu()
+        plain_lat.append(time.perf_counter() - (tp0 + q["t"]))
+        plain_px += q["h"] * q["w"] * q["c"]
+    plain_span = time.perf_counter() - tp0
+    plain_lat = np.array(plain_lat)
+    out = {"metric": "served pixels/s, continuous batching of a Poisson request stream (200 req/s, mixed ops, "
+                     "N=8192/16384)",
+           "value": round(served_px / span, 1), "unit": "px/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+           "ms_per_step": round(span * 1e3, 1), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "u64 (RNS residues)", "data": "synthetic (seeded request stream and random-field images, seed 8)",
+           "config": {"workload": wl["name"], "requests": len(reqs), "duration_s": duration, "pixels": px_total,
+                      "offered_px_per_s": round(px_total / duration, 1), "budget_gb": wl["budget_gb"],
+                      "refused_over_budget": refused},
+           "latency_s": {"p50": round(float(np.percentile(lat, 50)), 5), "p99": round(float(np.percentile(lat, 99)), 5),
+                         "max": round(float(lat.max()), 5)},
+           "round_size": {"mean": round(float(np.mean(rounds)), 2), "max": int(np.max(rounds))},
+           "server": stats, "max_decode_error_encrypt": worst,
+           "plain_unbatched": {"requests": len(plain_lat), "px_per_s": round(plain_px / plain_span, 1),
+                               "p50": round(float(np.percentile(plain_lat, 50)), 5) if len(plain_lat) else None,
+                               "p99": round(float(np.percentile(plain_lat, 99)), 5) if len(plain_lat) else None,
+                               "window_s": round(plain_span, 2)},
+           "clocks": clk}
+    print(json.dumps(out))
+    for c in ctxs:
+        c.close()
+
+
 def main():
     args = parse()
+    if args.impl == "ours" and args.workload == "serve":
+        run_serve(args)
+        return
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch32":
+        run_batch(args)
     else:
         run_ours(args)
 

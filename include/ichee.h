@@ -309,6 +309,80 @@ ichee_status ichee_graph_end(ichee_ctx* ctx, void* stream, ichee_graph** out);
 ichee_status ichee_graph_launch(ichee_graph* graph, void* stream);
 void ichee_graph_destroy(ichee_graph* graph);
 
+/* ------------------------------------------------------------------------------------------
+ * Serving: a continuous-batching request loop on one GPU. Requests arrive from any host thread
+ * (ichee_server_submit) and run on a worker thread inside the library. The worker admits them
+ * in arrival order while a device arena -- the HBM budget, reserved once at start -- has room
+ * for their buffers (inputs, ciphertexts, results), and launches every admission round as
+ * batched kernels per ring: encryption with the ring's cache, one launch per operation kind,
+ * batched decryption, result copy. Rounds are stream-ordered per ring and never wait on the
+ * host: requests that arrive while others are on the GPU are admitted as memory and slots
+ * free up and join the next round. Keys and caches stay device-resident. Every result is
+ * exactly what the single-request entry points give for the same seeds (alone or in a mix).
+ * ------------------------------------------------------------------------------------------ */
+
+#define ICHEE_REQ_ENCRYPT 0u     /* encrypt, decrypt: result = decoded pixels */
+#define ICHEE_REQ_MEANFILTER 1u  /* encrypt, 3x3 mean filter, decrypt */
+#define ICHEE_REQ_BRIGHTNESS 2u  /* encrypt, + arg on every pixel, decrypt */
+#define ICHEE_REQ_WATERMARK 3u   /* encrypt image and pattern (pixels2, h x w x 1), blend with alpha = arg, decrypt */
+#define ICHEE_REQ_MATCH 4u       /* encrypt both images, sum of squared differences (relinearised), decrypt */
+
+typedef struct {
+    uint32_t kind;            /* ICHEE_REQ_* */
+    uint32_t ring;            /* index into the server's contexts */
+    uint32_t h, w, c;
+    uint64_t seed;            /* image encryption seed; the second image uses seed + 1 */
+    const uint8_t* pixels;    /* host, h*w*c bytes; must stay valid until the request is done */
+    const uint8_t* pixels2;   /* host: watermark pattern (h*w) or the image to match (h*w*c); else NULL */
+    double arg;               /* brightness offset, or blend alpha */
+    double* result;           /* host: h*w*c doubles (match: 1), written when the request is done */
+    uint64_t* ct_out;         /* optional device buffer: receives the result's ciphertexts */
+} ichee_request;
+
+typedef struct {
+    uint64_t ticket;
+    int32_t status;           /* ichee_status of the request */
+    uint32_t round_size;      /* requests admitted in the same round */
+    double t_submit, t_admit, t_done;   /* seconds, monotonic clock */
+} ichee_request_done;
+
+typedef struct {
+    uint64_t submitted, served, pixels, rounds, max_inflight, pending, inflight;
+    uint64_t arena_bytes, arena_used_bytes, peak_arena_bytes;
+} ichee_server_stats;
+
+typedef struct ichee_server ichee_server;
+
+/*
+ * Start a server over n_rings contexts (keys made; matching needs the evaluation key) sharing
+ * one device, each with its cache (NULL = fresh encryption). Reserves hbm_budget_bytes of
+ * device memory and 512 MiB of pinned host staging; at most max_inflight requests (0 = 256)
+ * are admitted at once. Errors: EINVAL, EMISMATCH, ENOMEM, ECUDA.
+ */
+ichee_status ichee_server_create(ichee_ctx* const* rings, const ichee_cache* const* caches, uint32_t n_rings,
+                                 size_t hbm_budget_bytes, uint32_t max_inflight, ichee_server** out);
+
+/* Queue a request (copied; its buffers must stay valid until done). *ticket identifies it.
+ * Errors: EINVAL (bad request, larger than the budget), EUNSUPPORTED. Never blocks on the GPU. */
+ichee_status ichee_server_submit(ichee_server* server, const ichee_request* request, uint64_t* ticket);
+
+/* Wait up to timeout_ms for a request; *out receives its timestamps and status. Returns
+ * ICHEE_ETIMEOUT if it is not done yet (call again), else the request's own status. Each
+ * ticket can be collected once. */
+ichee_status ichee_server_wait(ichee_server* server, uint64_t ticket, uint32_t timeout_ms, ichee_request_done* out);
+
+/* Counters: submitted, served, served pixels, admission rounds, peak concurrency, queue and
+ * arena occupancy. */
+ichee_status ichee_server_stats_get(ichee_server* server, ichee_server_stats* out);
+
+/* Pause (hold != 0) or resume admission. While held, submitted requests queue and nothing new
+ * starts; work already admitted finishes. On resume the worker admits everything that fits,
+ * in arrival order (a burst arriving during a hold is batched as far as memory allows). */
+ichee_status ichee_server_hold(ichee_server* server, int hold);
+
+/* Finish every queued request, stop the worker and free the server (not the contexts). */
+void ichee_server_destroy(ichee_server* server);
+
 /*
  * Matching (the ICHEE_OP_SQDIFF_SUM operation) for callers that cannot allocate device
  * memory: processes whose GPU memory is handed out by their own arena or pool, or loops that

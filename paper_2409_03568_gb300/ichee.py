@@ -73,6 +73,24 @@ class TuneEntry(ctypes.Structure):
 
 
 TUNE_RADIX, TUNE_LOOKUP, TUNE_MEANFILTER = 1, 2, 3
+REQ_ENCRYPT, REQ_MEANFILTER, REQ_BRIGHTNESS, REQ_WATERMARK, REQ_MATCH = range(5)
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_uint32), ("ring", ctypes.c_uint32), ("h", ctypes.c_uint32), ("w", ctypes.c_uint32),
+                ("c", ctypes.c_uint32), ("seed", ctypes.c_uint64), ("pixels", ctypes.c_void_p),
+                ("pixels2", ctypes.c_void_p), ("arg", ctypes.c_double), ("result", ctypes.c_void_p),
+                ("ct_out", ctypes.c_void_p)]
+
+
+class RequestDone(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32), ("round_size", ctypes.c_uint32),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "served", "pixels", "rounds", "max_inflight", "pending",
+                                               "inflight", "arena_bytes", "arena_used_bytes", "peak_arena_bytes")]
 
 _vp = ctypes.c_void_p
 _u64 = ctypes.c_uint64
@@ -113,6 +131,12 @@ _SIGS = {
     "ichee_graph_end": (_st, [_vp, _vp, ctypes.POINTER(_vp)]),
     "ichee_graph_launch": (_st, [_vp, _vp]),
     "ichee_graph_destroy": (None, [_vp]),
+    "ichee_server_create": (_st, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), _u32, _sz, _u32, ctypes.POINTER(_vp)]),
+    "ichee_server_submit": (_st, [_vp, ctypes.POINTER(Request), ctypes.POINTER(_u64)]),
+    "ichee_server_wait": (_st, [_vp, _u64, _u32, ctypes.POINTER(RequestDone)]),
+    "ichee_server_stats_get": (_st, [_vp, ctypes.POINTER(ServerStats)]),
+    "ichee_server_hold": (_st, [_vp, ctypes.c_int]),
+    "ichee_server_destroy": (None, [_vp]),
     "ichee_stream_status": (_st, [_vp, _vp]),
     "ichee_last_error": (ctypes.c_char_p, []),
 }
@@ -321,6 +345,42 @@ def ichee_graph_launch(graph, stream=None):
 
 def ichee_graph_destroy(graph):
     _lib.ichee_graph_destroy(graph)
+
+
+def ichee_server_create(rings, caches, hbm_budget_bytes, max_inflight=0):
+    n = len(rings)
+    h = _vp()
+    _check(_lib.ichee_server_create((_vp * n)(*[r.value if isinstance(r, _vp) else r for r in rings]),
+                                    (_vp * n)(*[None if c is None else (c.value if isinstance(c, _vp) else c)
+                                                for c in caches]),
+                                    n, hbm_budget_bytes, max_inflight, ctypes.byref(h)))
+    return h
+
+
+def ichee_server_submit(server, request):
+    t = _u64()
+    _check(_lib.ichee_server_submit(server, ctypes.byref(request), ctypes.byref(t)))
+    return int(t.value)
+
+
+def ichee_server_wait(server, ticket, timeout_ms=60000):
+    d = RequestDone()
+    _check(_lib.ichee_server_wait(server, ticket, timeout_ms, ctypes.byref(d)))
+    return d
+
+
+def ichee_server_stats_get(server):
+    st = ServerStats()
+    _check(_lib.ichee_server_stats_get(server, ctypes.byref(st)))
+    return {n: int(getattr(st, n)) for n, _ in ServerStats._fields_}
+
+
+def ichee_server_hold(server, hold):
+    _check(_lib.ichee_server_hold(server, 1 if hold else 0))
+
+
+def ichee_server_destroy(server):
+    _lib.ichee_server_destroy(server)
 
 
 def ichee_stream_status(ctx, stream=None):

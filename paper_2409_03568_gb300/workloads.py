@@ -23,6 +23,21 @@ ENC8192 = dict(name="enc_n8192_l3_64x64", log_n=13, prime_bits=[60, 40, 60], log
 OPS8192 = dict(name="ops_n8192_l4_128x128x3", log_n=13, prime_bits=[60, 40, 40, 40], log2_scale=40, special_bits=61,
                h=128, w=128, c=3, image_seed=3, beta_seed=4, watermark_seed=5, noisy_seed=6, alpha=0.9)
 
+# Batched form: a ragged batch of 32 grayscale random-field images with sides uniform in
+# 16..128 (seed 7), N=8192, primes 60/40/60; radix-16 encryption with randomness, then the 3x3
+# mean filter.
+BATCH32 = dict(name="batch32_n8192_l3_ragged", log_n=13, prime_bits=[60, 40, 60], log2_scale=40, special_bits=0,
+               n_images=32, side_lo=16, side_hi=128, batch_seed=7, radix_base=16)
+
+# Serving: Poisson arrivals at 200 requests/s, image sides uniform in 8..128, 1 or 3 channels,
+# operation encrypt-only / mean filter / brightness / watermark / match at 4:2:2:1:1, ring
+# N=8192 (primes 60/40/60) or N=16384 (primes 60/40/40/40/40) with probability 1/2 each,
+# 120 GB HBM admission budget, full 256-value caches with 64-entry pools (seed 8).
+SERVE = dict(name="serve_poisson200_mixed", rate=200.0, duration_s=60.0, side_lo=8, side_hi=128,
+             op_weights=(4, 2, 2, 1, 1), budget_gb=120, seed=8,
+             rings=(dict(log_n=13, prime_bits=[60, 40, 60], log2_scale=40, special_bits=61),
+                    dict(log_n=14, prime_bits=[60, 40, 40, 40, 40], log2_scale=40, special_bits=61)))
+
 # Serving-size ring: N=16384 with five primes.
 RING16384 = dict(name="n16384_l5", log_n=14, prime_bits=[60, 40, 40, 40, 40], log2_scale=40, special_bits=61)
 
