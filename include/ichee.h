@@ -266,10 +266,29 @@ ichee_status ichee_eval_batch(ichee_ctx* ctx, ichee_op op, const uint64_t* const
 ichee_status ichee_decrypt_batch(ichee_ctx* ctx, const uint64_t* const* d_ct, const ichee_ctimg_meta* metas,
                                  double* const* d_out, uint32_t n_images, void* stream);
 
+/*
+ * Radix encryption + 3x3 mean filter of a ragged batch (Sec. 3.2, 3.3, 4.4.1). The fused
+ * persistent kernel assembles each filtered row's 3 x w neighbourhood ciphertexts from the
+ * radix cache on the fly instead of re-reading them, and writes each encrypted pixel once.
+ * Which schedule runs -- this fused kernel, or the batched encryption followed by the batched
+ * mean filter -- is the autotuner's choice (two kernels until ichee_autotune_batch has timed
+ * both). Outputs are identical either way, and to ichee_encrypt_batch followed by
+ * ichee_eval_batch(MEANFILTER3):
+ * d_ct_out[i] (level L-1) and d_filtered_out[i] (level L-2), all device. Needs a radix cache
+ * (else ICHEE_EUNSUPPORTED) and images at most 16384 / n_pow pixels wide.
+ */
+ichee_status ichee_encrypt_meanfilter_batch(ichee_ctx* ctx, const ichee_cache* cache, const uint8_t* const* pixels,
+                                            const ichee_image_desc* images, uint32_t n_images,
+                                            uint64_t* const* d_ct_out, uint64_t* const* d_filtered_out,
+                                            ichee_ctimg_meta* metas_ct, ichee_ctimg_meta* metas_filtered,
+                                            void* stream);
+
 /* Kernels whose launch shape the autotuner chooses. */
 #define ICHEE_TUNE_RADIX 1u
 #define ICHEE_TUNE_LOOKUP 2u
 #define ICHEE_TUNE_MEANFILTER 3u
+#define ICHEE_TUNE_FUSED 4u
+#define ICHEE_TUNE_SCHEDULE 5u   /* ichee_tuned_shape: *threads = 1 if the fused kernel runs, 0 for two kernels */
 
 typedef struct {
     uint32_t kind;            /* ICHEE_TUNE_* */
@@ -280,7 +299,8 @@ typedef struct {
 
 /*
  * Autotuner for the batched encrypt-then-mean-filter pipeline: runs the batched encryption of
- * `cache` (fresh if NULL: nothing to tune) and the batched mean filter on the given batch with
+ * `cache` (fresh if NULL: nothing to tune), the fused radix pipeline (radix caches) and the
+ * batched mean filter on the given batch with
  * every candidate launch shape (threads per block x resident blocks per SM), timed with CUDA
  * events on `stream`, and keeps the fastest shapes in the context for later batched calls.
  * d_ct and d_filtered receive valid outputs (the last run). report (host, *n_report entries,

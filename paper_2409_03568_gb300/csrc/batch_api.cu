@@ -130,7 +130,93 @@ ichee_status decrypt_chunked(ichee_ctx* c, const uint64_t* const* d_ct, const ic
     return ICHEE_OK;
 }
 
+ichee_status fused_chunked(ichee_ctx* c, const ichee_cache* k, const uint8_t* const* px, const ichee_image_desc* images,
+                           uint32_t n, uint64_t* const* enc, uint64_t* const* filt, LaunchShape ls, cudaStream_t st)
+{
+    ichee_ctimg_meta m0;
+    m0.h = images[0].h;
+    m0.w = images[0].w;
+    m0.c = images[0].c;
+    m0.level = (u32)(c->L - 1);
+    m0.scale = c->delta;
+    OpsArgs base = ops_base(c, &m0);
+    set_k0(c, base, 1.0 / 9.0, c->delta);
+    set_rescale(c, base);
+    fold_constants(c, base);
+    const RadixArgs ra = radix_args(c, k, nullptr, 0, 0, nullptr);
+    const int chunks = (c->n / 2) / ls.threads;
+    for (uint32_t first = 0; first < n; first += kMaxSegs) {
+        const int cnt = (int)std::min<uint32_t>(kMaxSegs, n - first);
+        SegTable t;
+        std::memset(&t, 0, sizeof(t));
+        fill_starts(t, first, cnt, [&](uint32_t i) { return (u64)images[i].h * chunks * 2 * images[i].c; });
+        int max_w = 1;
+        for (int sg = 0; sg < cnt; ++sg) {
+            const uint32_t i = first + sg;
+            t.px[sg] = px[i];
+            t.out[sg] = enc[i];
+            t.out2[sg] = filt[i];
+            t.seed[sg] = images[i].seed;
+            t.h[sg] = images[i].h;
+            t.w[sg] = images[i].w;
+            t.c[sg] = images[i].c;
+            max_w = std::max<int>(max_w, (int)images[i].w);
+        }
+        CK(launch_radix_meanfilter3_batch(ra, base, t, max_w, ls, c->num_sms, st));
+    }
+    return ICHEE_OK;
+}
+
 }  // namespace
+
+extern "C" ichee_status ichee_encrypt_meanfilter_batch(ichee_ctx* c, const ichee_cache* k, const uint8_t* const* pixels,
+                                                       const ichee_image_desc* images, uint32_t n_images,
+                                                       uint64_t* const* d_ct_out, uint64_t* const* d_filtered_out,
+                                                       ichee_ctimg_meta* metas_ct, ichee_ctimg_meta* metas_filtered,
+                                                       void* stream)
+{
+    if (!c || !k || !pixels || !d_ct_out || !d_filtered_out || !metas_ct || !metas_filtered)
+        return fail(ICHEE_EINVAL, "null argument");
+    if (!c->have_keys) return fail(ICHEE_EINVAL, "run ichee_keygen first");
+    if (k->ctx != c) return fail(ICHEE_EMISMATCH, "cache belongs to another context");
+    if (k->desc.kind != ICHEE_CACHE_RADIX) return fail(ICHEE_EUNSUPPORTED, "the fused pipeline needs a radix cache");
+    if (c->L < 2) return fail(ICHEE_ELEVEL, "the mean filter needs a limb to drop");
+    if (c->n / 2 < c->shape_fused.threads) return fail(ICHEE_EUNSUPPORTED, "ring too small");
+    ichee_status s = check_desc(images, n_images);
+    if (s != ICHEE_OK) return s;
+    for (uint32_t i = 0; i < n_images; ++i) {
+        if (!pixels[i] || !d_ct_out[i] || !d_filtered_out[i]) return fail(ICHEE_EINVAL, "null buffer for image %u", i);
+        if ((size_t)3 * images[i].w * k->n_pow > 48 * 1024) return fail(ICHEE_EUNSUPPORTED, "image %u too wide", i);
+    }
+    CK(cudaSetDevice(c->device));
+    if (c->fused_schedule == 1) {
+        s = fused_chunked(c, k, pixels, images, n_images, d_ct_out, d_filtered_out, c->shape_fused, (cudaStream_t)stream);
+    } else {
+        std::vector<ichee_ctimg_meta> m(n_images);
+        for (uint32_t i = 0; i < n_images; ++i) {
+            m[i].h = images[i].h;
+            m[i].w = images[i].w;
+            m[i].c = images[i].c;
+            m[i].level = (u32)(c->L - 1);
+            m[i].scale = c->delta;
+        }
+        s = encrypt_chunked(c, k, pixels, images, n_images, d_ct_out, (cudaStream_t)stream);
+        if (s == ICHEE_OK)
+            s = meanfilter_chunked(c, d_ct_out, m.data(), d_filtered_out, n_images, c->shape_meanfilter,
+                                   (cudaStream_t)stream);
+    }
+    if (s != ICHEE_OK) return s;
+    for (uint32_t i = 0; i < n_images; ++i) {
+        metas_ct[i].h = metas_filtered[i].h = images[i].h;
+        metas_ct[i].w = metas_filtered[i].w = images[i].w;
+        metas_ct[i].c = metas_filtered[i].c = images[i].c;
+        metas_ct[i].level = (u32)(c->L - 1);
+        metas_ct[i].scale = c->delta;
+        metas_filtered[i].level = (u32)(c->L - 2);
+        metas_filtered[i].scale = c->delta * c->delta / (double)c->q[c->L - 1];
+    }
+    return ICHEE_OK;
+}
 
 extern "C" ichee_status ichee_encrypt_batch(ichee_ctx* c, const ichee_cache* k, const uint8_t* const* pixels,
                                             const ichee_image_desc* images, uint32_t n_images,
@@ -347,6 +433,30 @@ extern "C" ichee_status ichee_autotune_batch(ichee_ctx* c, const ichee_cache* k,
         }
         c->shape_meanfilter = best;
     }
+    // fused radix encryption + mean filter, and the schedule ichee_encrypt_meanfilter_batch uses
+    if (radix) {
+        bool fits = true;
+        for (uint32_t i = 0; i < n_images; ++i) fits = fits && (size_t)3 * images[i].w * k->n_pow <= 48 * 1024;
+        LaunchShape best = c->shape_fused;
+        float best_ms = 1e30f;
+        for (const LaunchShape& ls : cands) {
+            if (!fits || c->n / 2 < ls.threads) continue;
+            float ms;
+            s = time_it([&] { return fused_chunked(c, k, pixels, images, n_images, d_ct, d_filtered, ls, st); }, &ms);
+            if (s != ICHEE_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
+            record(ICHEE_TUNE_FUSED, ls, ms);
+            if (ms < best_ms) { best_ms = ms; best = ls; }
+        }
+        c->shape_fused = best;
+        float two_ms;
+        s = time_it([&] {
+            ichee_status r = encrypt_chunked(c, k, pixels, images, n_images, d_ct, st);
+            return r != ICHEE_OK ? r : meanfilter_chunked(c, d_ct, metas.data(), d_filtered, n_images,
+                                                          c->shape_meanfilter, st);
+        }, &two_ms);
+        if (s != ICHEE_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
+        c->fused_schedule = (fits && best_ms < two_ms) ? 1 : 0;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (n_report) *n_report = nrep;
@@ -361,6 +471,8 @@ extern "C" ichee_status ichee_tuned_shape(const ichee_ctx* c, uint32_t kind, uin
     case ICHEE_TUNE_RADIX: ls = c->shape_radix; break;
     case ICHEE_TUNE_LOOKUP: ls = c->shape_lookup; break;
     case ICHEE_TUNE_MEANFILTER: ls = c->shape_meanfilter; break;
+    case ICHEE_TUNE_FUSED: ls = c->shape_fused; break;
+    case ICHEE_TUNE_SCHEDULE: *threads = (uint32_t)c->fused_schedule; *blocks_per_sm = 0; return ICHEE_OK;
     default: return fail(ICHEE_EINVAL, "unknown kernel kind %u", kind);
     }
     *threads = (uint32_t)ls.threads;

@@ -62,6 +62,7 @@ struct SegTable {
     const u64* in0[kMaxSegs];         // ciphertext inputs
     const u64* in1[kMaxSegs];
     u64* out[kMaxSegs];               // ciphertext output
+    u64* out2[kMaxSegs];              // second ciphertext output (fused encrypt + filter)
     double* dout[kMaxSegs];           // decoded output (decryption)
     u64 seed[kMaxSegs];
     uint32_t h[kMaxSegs], w[kMaxSegs], c[kMaxSegs], c1[kMaxSegs];

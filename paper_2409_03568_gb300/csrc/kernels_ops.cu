@@ -207,6 +207,112 @@ __global__ void __launch_bounds__(1024) k_meanfilter3_batch(const __grid_constan
     }
 }
 
+// Fused radix encryption + 3x3 mean filter (Sec. 3.2, 3.3 and 4.4.1) for a ragged batch. Each
+// item is one (row y, coefficient chunk, poly, channel) of one image, as in the batched mean
+// filter, but the ciphertexts of the 3 x w neighbourhood rows are assembled on the fly from
+// the cached multiples d * Enc(r^k) (L2-resident) instead of being read back from HBM: the
+// block first writes every pixel's multiple-table rows for the three image rows into shared
+// memory (signed digits with the pixel's randomness bits), then walks the row with the window
+// column sums in registers. The centre row's ciphertexts are the encryption output (each
+// written once); the filtered row is the second output. Residues equal those of the radix
+// combine kernel followed by the mean filter.
+template <int LIMBS>
+__global__ void __launch_bounds__(512) k_radix_meanfilter3_batch(const __grid_constant__ RadixArgs ra,
+                                                                 const __grid_constant__ OpsArgs a,
+                                                                 const __grid_constant__ SegTable t)
+{
+    extern __shared__ int8_t sdig[];   // [3][w][n_pow]: d' + r per cached power (r = digit 0)
+    const int n = 1 << a.logn;
+    const int chunks = (n / 2) / blockDim.x;
+    const int npow = ra.n_pow, r = ra.r, width = 2 * r + 1;
+    const size_t ct_words_in = (size_t)2 * LIMBS * n;
+    const u64 total = t.start[t.n];
+    for (u64 g = blockIdx.x; g < total; g += gridDim.x) {
+        const int s = seg_of(t, g);
+        u64 i = g - t.start[s];
+        const int h = (int)t.h[s], w = (int)t.w[s], C = (int)t.c[s];
+        const int y = (int)(i % h); i /= h;
+        const int chunk = (int)(i % chunks); i /= chunks;
+        const int b = (int)(i % 2); i /= 2;
+        const int ch = (int)i;
+        const int rows[3] = {y > 0 ? y - 1 : 0, y, y + 1 < h ? y + 1 : h - 1};
+        __syncthreads();  // previous item done with the digit rows
+        for (int idx = threadIdx.x; idx < 3 * w; idx += blockDim.x) {
+            const int rr = idx / w, x = idx % w;
+            const u64 k = ((u64)rows[rr] * w + x) * C + ch;
+            int p = t.px[s][k];
+            u32 bits = 0;
+            if (ra.randomize) bits = philox(t.seed[s], kStreamRadixBits, k, 0).w[0];
+            for (int kk = 0; kk < npow; ++kk) {
+                const int dk = p % r;
+                p /= r;
+                const int bk = (ra.randomize && kk >= 1) ? (int)((bits >> kk) & 1u) : 0;
+                const int bk1 = (ra.randomize && kk + 1 < npow) ? (int)((bits >> (kk + 1)) & 1u) : 0;
+                sdig[(rr * w + x) * npow + kk] = (int8_t)(dk + bk - r * bk1 + r);
+            }
+        }
+        __syncthreads();
+        const int c2 = chunk * blockDim.x + threadIdx.x;
+        // value of pixel (row rr, column x) at (poly b, limb l, coefficient pair c2)
+        auto enc_val = [&](int rr, int x, int l) {
+            const u64 q = a.q[l];
+            ulonglong2 acc = make_ulonglong2(0, 0);
+            const int8_t* dg = sdig + (rr * w + x) * npow;
+            for (int kk = 0; kk < npow; ++kk) {
+                const int di = dg[kk];
+                if (di == r) continue;
+                const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(
+                    ra.mult + ((size_t)kk * width + di) * ct_words_in + ((size_t)b * LIMBS + l) * n) + c2);
+                acc.x = add_mod(acc.x, v.x, q);
+                acc.y = add_mod(acc.y, v.y, q);
+            }
+            return acc;
+        };
+        ulonglong2* enc_row = reinterpret_cast<ulonglong2*>(t.out[s]);
+        const u64 ct_len2 = (u64)2 * LIMBS * (n / 2);
+        const u64 out_len2 = (u64)2 * (LIMBS - 1) * (n / 2);
+        int written = 0;  // next column of the centre row whose encryption is still to be stored
+        ulonglong2 col[3][LIMBS];
+        auto column = [&](int xx, ulonglong2 (&dst)[LIMBS]) {
+#pragma unroll
+            for (int l = 0; l < LIMBS; ++l) {
+                const ulonglong2 v0 = enc_val(0, xx, l), v1 = enc_val(1, xx, l), v2 = enc_val(2, xx, l);
+                if (xx == written)
+                    __stcs(enc_row + (((u64)y * w + xx) * C + ch) * ct_len2 + ((u64)b * LIMBS + l) * (n / 2) + c2, v1);
+                dst[l].x = v0.x + v1.x + v2.x;
+                dst[l].y = v0.y + v1.y + v2.y;
+            }
+            if (xx == written) ++written;
+        };
+        column(0, col[0]);
+#pragma unroll
+        for (int l = 0; l < LIMBS; ++l) col[1][l] = col[0][l];
+        column(w > 1 ? 1 : 0, col[2]);
+        const u64 qt = a.q[LIMBS - 1];
+        ulonglong2* out = reinterpret_cast<ulonglong2*>(t.out2[s]) + (u64)b * (LIMBS - 1) * (n / 2) + c2;
+        for (int x = 0; x < w; ++x) {
+            const u64 sx = col[0][LIMBS - 1].x + col[1][LIMBS - 1].x + col[2][LIMBS - 1].x;
+            const u64 sy = col[0][LIMBS - 1].y + col[1][LIMBS - 1].y + col[2][LIMBS - 1].y;
+            const u64 tx = shoup(sx, a.k0[LIMBS - 1], a.k0p[LIMBS - 1], qt);
+            const u64 ty = shoup(sy, a.k0[LIMBS - 1], a.k0p[LIMBS - 1], qt);
+            ulonglong2* o = out + (((u64)y * w + x) * C + ch) * out_len2;
+#pragma unroll
+            for (int j = 0; j < LIMBS - 1; ++j) {
+                const u64 qj = a.q[j];
+                ulonglong2 v;
+                v.x = rescale_fold(shoup_lazy(col[0][j].x + col[1][j].x + col[2][j].x, a.k0r[j], a.k0rp[j], qj), tx, j, a);
+                v.y = rescale_fold(shoup_lazy(col[0][j].y + col[1][j].y + col[2][j].y, a.k0r[j], a.k0rp[j], qj), ty, j, a);
+                __stcs(o + j * (n / 2), v);
+            }
+            if (x + 1 < w) {
+#pragma unroll
+                for (int l = 0; l < LIMBS; ++l) { col[0][l] = col[1][l]; col[1][l] = col[2][l]; }
+                column(x + 2 < w ? x + 2 : w - 1, col[2]);
+            }
+        }
+    }
+}
+
 // Fused watermark blend (reading R15): out = Rescale(Ka * I + Kb * W), W broadcast over
 // channels when it has one channel. The kept limbs use Ka q_t^{-1}, Kb q_t^{-1}. One call
 // handles coefficient pair c of polynomial b of one ciphertext.
@@ -527,6 +633,27 @@ cudaError_t launch_meanfilter3_batch(const OpsArgs& a, const SegTable& t, Launch
     if (total == 0) return cudaSuccess;
     const unsigned g = persistent_grid(total, ls, num_sms);
     ICHEE_LIMB_SWITCH_T(k_meanfilter3_batch, g, ls.threads, a, t)
+    return cudaGetLastError();
+}
+
+cudaError_t launch_radix_meanfilter3_batch(const RadixArgs& ra, const OpsArgs& a, const SegTable& t, int max_w,
+                                           LaunchShape ls, int num_sms, cudaStream_t st)
+{
+    const u64 total = t.n > 0 ? t.start[t.n] : 0;
+    if (total == 0) return cudaSuccess;
+    const unsigned g = persistent_grid(total, ls, num_sms);
+    const size_t smem = (size_t)3 * max_w * ra.n_pow;
+    if (smem > 48 * 1024) return cudaErrorInvalidValue;
+    switch (a.limbs) {
+    case 2: k_radix_meanfilter3_batch<2><<<g, ls.threads, smem, st>>>(ra, a, t); break;
+    case 3: k_radix_meanfilter3_batch<3><<<g, ls.threads, smem, st>>>(ra, a, t); break;
+    case 4: k_radix_meanfilter3_batch<4><<<g, ls.threads, smem, st>>>(ra, a, t); break;
+    case 5: k_radix_meanfilter3_batch<5><<<g, ls.threads, smem, st>>>(ra, a, t); break;
+    case 6: k_radix_meanfilter3_batch<6><<<g, ls.threads, smem, st>>>(ra, a, t); break;
+    case 7: k_radix_meanfilter3_batch<7><<<g, ls.threads, smem, st>>>(ra, a, t); break;
+    case 8: k_radix_meanfilter3_batch<8><<<g, ls.threads, smem, st>>>(ra, a, t); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -72,7 +72,7 @@ class TuneEntry(ctypes.Structure):
                 ("ms", ctypes.c_float)]
 
 
-TUNE_RADIX, TUNE_LOOKUP, TUNE_MEANFILTER = 1, 2, 3
+TUNE_RADIX, TUNE_LOOKUP, TUNE_MEANFILTER, TUNE_FUSED, TUNE_SCHEDULE = 1, 2, 3, 4, 5
 REQ_ENCRYPT, REQ_MEANFILTER, REQ_BRIGHTNESS, REQ_WATERMARK, REQ_MATCH = range(5)
 
 
@@ -118,6 +118,9 @@ _SIGS = {
                                        ctypes.POINTER(CtImgMeta), _vp]),
     "ichee_encrypt_batch": (_st, [_vp, _vp, ctypes.POINTER(_vp), ctypes.POINTER(ImageDesc), _u32,
                                   ctypes.POINTER(_vp), ctypes.POINTER(CtImgMeta), _vp]),
+    "ichee_encrypt_meanfilter_batch": (_st, [_vp, _vp, ctypes.POINTER(_vp), ctypes.POINTER(ImageDesc), _u32,
+                                             ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(CtImgMeta),
+                                             ctypes.POINTER(CtImgMeta), _vp]),
     "ichee_eval_batch": (_st, [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(CtImgMeta), ctypes.POINTER(_vp),
                                ctypes.POINTER(CtImgMeta), _vp, _u32, ctypes.POINTER(_vp), ctypes.POINTER(CtImgMeta),
                                _u32, _vp]),
@@ -290,6 +293,14 @@ def ichee_encrypt_batch(ctx, cache, pixels, shapes, seeds, ct_outs, stream=None)
     _check(_lib.ichee_encrypt_batch(ctx, cache, _ptrs(pixels), _descs(shapes, seeds), n, _ptrs(ct_outs), metas,
                                     stream))
     return list(metas)
+
+
+def ichee_encrypt_meanfilter_batch(ctx, cache, pixels, shapes, seeds, ct_outs, filtered_outs, stream=None):
+    n = len(shapes)
+    mc, mf = (CtImgMeta * n)(), (CtImgMeta * n)()
+    _check(_lib.ichee_encrypt_meanfilter_batch(ctx, cache, _ptrs(pixels), _descs(shapes, seeds), n, _ptrs(ct_outs),
+                                               _ptrs(filtered_outs), mc, mf, stream))
+    return list(mc), list(mf)
 
 
 def _metas(ms):

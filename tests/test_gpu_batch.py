@@ -157,7 +157,8 @@ def test_graph_replay_and_autotune(ichee, ctx8192):
     filt = [ctx.empty_cts(h * w * c, 1) for (h, w, c) in shapes]
     rep = ichee.ichee_autotune_batch(ctx.handle, cache, d_px, shapes, seeds, enc, filt, ctx.stream())
     kinds = {k for k, *_ in rep}
-    assert kinds == {ichee.TUNE_RADIX, ichee.TUNE_MEANFILTER}
+    assert kinds == {ichee.TUNE_RADIX, ichee.TUNE_FUSED, ichee.TUNE_MEANFILTER}
+    assert ichee.ichee_tuned_shape(ctx.handle, ichee.TUNE_SCHEDULE)[0] in (0, 1)
     t, b = ichee.ichee_tuned_shape(ctx.handle, ichee.TUNE_MEANFILTER)
     best = min((e for e in rep if e[0] == ichee.TUNE_MEANFILTER), key=lambda e: e[3])
     assert (t, b) == (best[1], best[2])
@@ -192,6 +193,28 @@ def test_graph_replay_and_autotune(ichee, ctx8192):
         for i in range(len(shapes)):
             assert torch.equal(enc[i], ref_enc[i]) and torch.equal(filt[i], ref_filt[i]), i
     ichee.ichee_graph_destroy(graph)
+
+
+@pytest.mark.parametrize("base,randomize", [(16, 1), (10, 1), (16, 0)])
+def test_fused_encrypt_meanfilter_equals_two_steps(ichee, ctx8192, base, randomize):
+    ctx = ctx8192
+    shapes, imgs = ragged_images(6, seed=20 + base + randomize, lo=1, hi=11)
+    shapes[1] = (1, 7, 3)
+    imgs[1] = inputs.random_field_image(1, 7, seed=5, channels=3).reshape(-1).copy()
+    shapes[2] = (6, 1, 1)
+    imgs[2] = inputs.random_field_image(6, 1, seed=6).reshape(-1).copy()
+    seeds = [5000 + i for i in range(len(shapes))]
+    cache = ctx.build_cache(ichee.CACHE_RADIX, 51 + base, radix_base=base, randomize=randomize)
+    d_px = [torch.from_numpy(im).cuda() for im in imgs]
+    enc = [ctx.empty_cts(h * w * c, 2) for (h, w, c) in shapes]
+    filt = [ctx.empty_cts(h * w * c, 1) for (h, w, c) in shapes]
+    mc, mf = ichee.ichee_encrypt_meanfilter_batch(ctx.handle, cache, d_px, shapes, seeds, enc, filt, ctx.stream())
+    for i, (h, w, c) in enumerate(shapes):
+        e, m = ctx.encrypt(d_px[i], h, w, c, seeds[i], cache=cache)
+        f, fm = ctx.eval(ichee.OP_MEANFILTER3, e, m, out_level=1)
+        assert torch.equal(enc[i], e), i
+        assert torch.equal(filt[i], f), i
+        assert mf[i].scale == fm.scale and mf[i].level == fm.level and mc[i].level == m.level
 
 
 def test_batch_errors(ichee, ctx8192):

@@ -306,6 +306,38 @@ def test_ops_match_small(ichee, small_ops):
     assert abs(dec[0] - plain) < 1e-2
 
 
+# ------------------------------------------------------------- the 2^14 ring (serving size)
+def test_ring16384_keys_encryption_and_matching(ichee):
+    """N = 16384, five primes: the transform and encryption kernels of this ring recompute
+    NTT(v) per product and the matching accumulator parks d0 in global scratch."""
+    wl = W.RING16384
+    ctx = gpu_for(ichee, wl, with_evk=True)
+    o = oracle_for(wl, with_evk=True)
+    n, L = ctx.n, ctx.L
+    pk = np.zeros((2, L, n), dtype=np.uint64)
+    ichee.ichee_export_key(ctx.handle, 1, pk)
+    assert np.array_equal(pk, o.pk)
+    evk = np.zeros((L, 2, L + 1, n), dtype=np.uint64)
+    ichee.ichee_export_key(ctx.handle, 2, evk)
+    assert np.array_equal(evk, o.evk)
+    a = inputs.random_field_image(3, 2, seed=14).reshape(-1).copy()
+    b = inputs.noisy_copy(a, seed=15)
+    ga, ma = ctx.encrypt(torch.from_numpy(a).cuda(), 3, 2, 1, 61)
+    gb, mb = ctx.encrypt(torch.from_numpy(b).cuda(), 3, 2, 1, 62)
+    ra, rb = o.encrypt_pixels(a, 61), o.encrypt_pixels(b, 62)
+    assert np.array_equal(as_cts(ga, 6, L, n), ra)
+    assert np.array_equal(as_cts(gb, 6, L, n), rb)
+    assert np.max(np.abs(ctx.decrypt(ga, ma).cpu().numpy() - a)) < 1e-3
+    out, m = ctx.eval(ichee.OP_SQDIFF_SUM, ga, ma, gb, mb, out_n_ct=1, out_level=L - 2)
+    ref, sc = o.match(ra, rb, o.delta)
+    assert np.array_equal(as_cts(out, 1, L - 1, n), ref)
+    assert abs(ctx.decrypt(out, m).cpu().numpy()[0] - float(((a.astype(float) - b) ** 2).sum())) < 1e-2
+    mf, mm = ctx.eval(ichee.OP_MEANFILTER3, ga, ma, out_level=L - 2)
+    rf, sf = o.meanfilter3(ra, o.delta, 3, 2, 1)
+    assert np.array_equal(as_cts(mf, 6, L - 1, n), rf)
+    ctx.close()
+
+
 # ------------------------------------------------------------------------ errors
 def test_error_paths(ichee):
     wl = W.TOY
