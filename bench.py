@@ -71,6 +71,22 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_over_ranks(ms, units):
+    """Across the ranks of one job (one process per GPU, replicas): the slowest rank's timed
+    span and the sum of the units every rank processed. Identity without torch.distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms, units
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.barrier()
+    return float(t.item()), int(u.item())
+
+
 # ---------------------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------------------
@@ -230,15 +246,10 @@ def run_ours(args):
             phase_ms[name] += events[name][0].elapsed_time(events[name][1])
     torch.cuda.synchronize()
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.barrier()
-        total_ms = float(t.item())
+    total_ms, units_all = reduce_over_ranks(total_ms, len(methods) * n_px * args.steps)
     ms_step = total_ms / args.steps
     phase_ms = {k: v / args.steps for k, v in phase_ms.items()}
-    units_step = len(methods) * n_px
-    value = units_step * world / (ms_step / 1e3)
+    value = units_all / (total_ms / 1e3)
 
     # roofline of every kernel-level phase (algorithmic work per launch / event time)
     n = ctx.n
@@ -349,7 +360,8 @@ def e2e_ours(args, ctx, ichee, img, wm_ct, wm_meta, nz_ct, nz_meta, beta, caches
         t0 = time.perf_counter()
         step()
         tot += time.perf_counter() - t0
-    units = len(methods) * n_px * args.steps * world
+    tot_ms, units = reduce_over_ranks(tot * 1e3, len(methods) * n_px * args.steps)
+    tot = tot_ms / 1e3
     return {"value": round(units / tot, 1), "unit": UNIT, "h2d_bytes_per_step": len(methods) * n_px,
             "d2h_bytes_per_step": (len(methods) + 3) * n_px * 8 + 8,
             "ms_per_step": round(tot / args.steps * 1e3, 3), "timing": "host wall clock around each step"}
