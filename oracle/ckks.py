@@ -352,6 +352,17 @@ class Oracle:
         r = self.relin(t)[None]
         return self.rescale(r), Fraction(scale) * Fraction(scale) / int(self.q[lim - 1])
 
+    def sqdiff_image(self, a, b, scale):
+        """Squared difference pixel by pixel (the per-pixel form of Sec. 4.4.3, reading R12):
+        for every ciphertext pair d = a - b, d (x) d, relinearised and rescaled on its own.
+        Returns ([count][2][limbs-1][n], scale)."""
+        lim = self._limbs(a)
+        out = np.zeros((a.shape[0], 2, lim - 1, self.n), dtype=np.uint64)
+        for k in range(a.shape[0]):
+            t = self.sqdiff_sum_raw(a[k:k + 1], b[k:k + 1])
+            out[k] = self.rescale(self.relin(t)[None])[0]
+        return out, Fraction(scale) * Fraction(scale) / int(self.q[lim - 1])
+
     # ------------------------------------------------------------- decrypt
     def decrypt_residues(self, ct):
         """Coefficient 0 of c0 + c1*s per limb (Sec. 2.2.2), [count][limbs]."""

@@ -402,6 +402,30 @@ def test_relin_depends_on_evk_sign(small4):
     assert abs(bb - 49) > 1.0
 
 
+def test_sqdiff_image_matches_plaintext_squares(small4):
+    """Per-pixel squared difference: every decrypted output equals (p_a - p_b)^2 (FP64)."""
+    o = small4
+    pa = np.array([0, 255, 100, 37, 200, 1], dtype=np.uint8)
+    pb = np.array([255, 0, 37, 100, 200, 2], dtype=np.uint8)
+    ca = o.encrypt_pixels(pa, seed=51)
+    cb = o.encrypt_pixels(pb, seed=52)
+    out, sc = o.sqdiff_image(ca, cb, o.delta)
+    assert out.shape == (6, 2, o.L - 1, o.n)
+    assert sc == Fraction(o.delta) ** 2 / int(o.q[o.L - 1])
+    ref = (pa.astype(np.float64) - pb) ** 2
+    np.testing.assert_allclose(o.decrypt(out, sc), ref, atol=1e-3, rtol=0)
+
+
+def test_sqdiff_image_one_pixel_equals_match(small4):
+    """For a one-pixel image the per-pixel and the summed forms are the same computation."""
+    o = small4
+    ca = o.encrypt_pixels(np.array([91], dtype=np.uint8), seed=53)
+    cb = o.encrypt_pixels(np.array([12], dtype=np.uint8), seed=54)
+    per_px, s1 = o.sqdiff_image(ca, cb, o.delta)
+    summed, s2 = o.match(ca, cb, o.delta)
+    assert s1 == s2 and np.array_equal(per_px, summed)
+
+
 # ------------------------------------------------------------------- caches (Sec. 3)
 def _radix_cache_small(base):
     o = Oracle(Params(6, [40, 40], 20)).keygen(3)
