@@ -111,8 +111,11 @@ typedef enum {
     ICHEE_OP_BRIGHTNESS = 6,     /* Sec. 4.4.2: + beta on every pixel; args: beta */
     ICHEE_OP_BLEND = 7,          /* alpha * a + (1 - alpha) * b, rescaled; args: alpha; b has c or 1 channels */
     ICHEE_OP_WATERMARK_PIXEL = 8,/* Sec. 4.4.4: + x at one ciphertext; args: x, index */
-    ICHEE_OP_SQDIFF_SUM = 9      /* Sec. 4.4.3: sum over ciphertexts of (a - b)^2, relinearised
+    ICHEE_OP_SQDIFF_SUM = 9,     /* Sec. 4.4.3: sum over ciphertexts of (a - b)^2, relinearised
                                     with the evaluation key and rescaled; output one ciphertext */
+    ICHEE_OP_SQDIFF = 10         /* per-pixel form of Sec. 4.4.3: (a_k - b_k)^2 for every ciphertext,
+                                    each relinearised and rescaled; output an image of a's shape at
+                                    level - 1, scale = scale^2 / q_level */
 } ichee_op;
 
 #define ICHEE_WITH_EVK 1u
@@ -141,7 +144,8 @@ ichee_status ichee_ctx_primes(const ichee_ctx* ctx, uint64_t* q_out, uint64_t* p
 /*
  * Key generation (Sec. 2.2.2, KeyGen steps 1-3): secret s ternary, public key
  * pk = (-a*s + e, a), and with flags & ICHEE_WITH_EVK the evaluation key used by
- * ICHEE_OP_SQDIFF_SUM (hybrid key switching with the special prime; needs special_bits > 0).
+ * ICHEE_OP_SQDIFF_SUM and ICHEE_OP_SQDIFF (hybrid key switching with the special prime; needs
+ * special_bits > 0).
  * Deterministic in `seed`. Keys stay in the context. Enqueued on `stream`; the call waits for
  * its own set-up copies. Errors: EINVAL (evk without a special prime), ECUDA.
  */

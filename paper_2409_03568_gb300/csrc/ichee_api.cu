@@ -722,6 +722,8 @@ ichee_status ichee::check_img(const ichee_ctx* c, const uint64_t* d, const ichee
 
 static ichee_status op_sqdiff(ichee_ctx* c, const uint64_t* d_a, const ichee_ctimg_meta* ma, const uint64_t* d_b,
                               uint64_t* d_out, ichee_ctimg_meta* mout, cudaStream_t st);
+static ichee_status op_sqdiff_image(ichee_ctx* c, const uint64_t* d_a, const ichee_ctimg_meta* ma,
+                                    const uint64_t* d_b, uint64_t* d_out, ichee_ctimg_meta* mout, cudaStream_t st);
 
 extern "C" ichee_status ichee_eval(ichee_ctx* c, ichee_op op, const uint64_t* d_a, const ichee_ctimg_meta* ma,
                                    const uint64_t* d_b, const ichee_ctimg_meta* mb, const double* args, uint32_t n_args,
@@ -733,7 +735,8 @@ extern "C" ichee_status ichee_eval(ichee_ctx* c, ichee_op op, const uint64_t* d_
     if (s != ICHEE_OK) return s;
     if (!d_out || !is_device_ptr(d_out)) return fail(ICHEE_EINVAL, "output must be device memory");
     cudaStream_t st = (cudaStream_t)stream;
-    const bool binary = op == ICHEE_OP_ADD || op == ICHEE_OP_SUB || op == ICHEE_OP_BLEND || op == ICHEE_OP_SQDIFF_SUM;
+    const bool binary = op == ICHEE_OP_ADD || op == ICHEE_OP_SUB || op == ICHEE_OP_BLEND || op == ICHEE_OP_SQDIFF_SUM ||
+                        op == ICHEE_OP_SQDIFF;
     if (binary) {
         s = check_img(c, d_b, mb, "b");
         if (s != ICHEE_OK) return s;
@@ -829,6 +832,9 @@ extern "C" ichee_status ichee_eval(ichee_ctx* c, ichee_op op, const uint64_t* d_
         break;
     case ICHEE_OP_SQDIFF_SUM:
         return op_sqdiff(c, d_a, ma, d_b, d_out, mout, st);
+    case ICHEE_OP_SQDIFF:
+        if (d_out == d_b) return fail(ICHEE_EINVAL, "this operation cannot run in place");
+        return op_sqdiff_image(c, d_a, ma, d_b, d_out, mout, st);
     default:
         return fail(ICHEE_EINVAL, "unknown op %d", (int)op);
     }
@@ -908,6 +914,54 @@ static ichee_status op_sqdiff(ichee_ctx* c, const uint64_t* d_a, const ichee_cti
     *mout = one;
     mout->level = ma->level - 1;
     mout->scale = ma->scale * ma->scale / (double)c->q[ma->level];
+    return ICHEE_OK;
+}
+
+// Per-pixel squared difference (per-pixel form of Sec. 4.4.3): one persistent kernel; each
+// block relinearises and rescales one pixel at a time in its own scratch.
+static ichee_status op_sqdiff_image(ichee_ctx* c, const uint64_t* d_a, const ichee_ctimg_meta* ma,
+                                    const uint64_t* d_b, uint64_t* d_out, ichee_ctimg_meta* mout, cudaStream_t st)
+{
+    if (!c->have_evk) return fail(ICHEE_EUNSUPPORTED, "squared difference needs the evaluation key (ICHEE_WITH_EVK)");
+    if (ma->level == 0) return fail(ICHEE_ELEVEL, "squared difference needs a limb to drop");
+    const int limbs = (int)ma->level + 1;
+    const int t = limbs - 1;
+    const u64 n_ct = (u64)ma->h * ma->w * ma->c;
+    const int grid = sqdiff_image_grid(c->logn, n_ct, c->num_sms);
+    CK(c->scratch.ensure((size_t)grid * sqdiff_image_scratch_words(c->logn, limbs) * 8));
+    SqImgArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.rns = c->rns;
+    a.L = c->L;
+    a.limbs = limbs;
+    a.n_ct = n_ct;
+    a.a = d_a;
+    a.b = d_b;
+    a.out = d_out;
+    a.scratch = (u64*)c->scratch.p;
+    a.evk_hat = c->d_evk_hat;
+    a.evk_hat_p = c->d_evk_hat_p;
+    const u64 qt = c->q[t];
+    a.half_qt = (qt - 1) / 2;
+    for (int j = 0; j < limbs; ++j) {
+        const u64 qj = c->q[j];
+        a.ninv[j] = hm::invm((u64)c->n % qj, qj);
+        a.ninv_p[j] = hm::shoup_of(a.ninv[j], qj);
+        a.pn[j] = hm::mulm(c->P % qj, a.ninv[j], qj);
+        a.pn_p[j] = hm::shoup_of(a.pn[j], qj);
+        a.p_inv[j] = hm::invm(c->P % qj, qj);
+        a.p_inv_p[j] = hm::shoup_of(a.p_inv[j], qj);
+        const u64 r = c->P % qj;
+        a.neg_p_mod[j] = r == 0 ? 0 : qj - r;
+        if (j < t) {
+            a.qt_inv[j] = hm::invm(qt % qj, qj);
+            a.qt_inv_p[j] = hm::shoup_of(a.qt_inv[j], qj);
+        }
+    }
+    CK(launch_sqdiff_image(a, grid, st));
+    *mout = *ma;
+    mout->level = ma->level - 1;
+    mout->scale = ma->scale * ma->scale / (double)qt;
     return ICHEE_OK;
 }
 

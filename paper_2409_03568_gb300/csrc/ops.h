@@ -96,6 +96,30 @@ struct RelinArgs {
     u64 neg_p_mod[kMaxPrimes];     // (-P) mod q_j
     u64 mu[kMaxModuli];
 };
+// Per-pixel squared difference with relinearisation and rescale (one output ciphertext per
+// input pair). Moduli: q_0..q_{limbs-1} of the ciphertexts, P at index L of rns.
+struct SqImgArgs {
+    RnsArgs rns;
+    int L;                         // limbs of the key (full chain)
+    int limbs;                     // limbs of the input ciphertexts (t + 1)
+    u64 n_ct;
+    const u64* a;                  // [n_ct][2][limbs][N]
+    const u64* b;
+    u64* out;                      // [n_ct][2][limbs-1][N]
+    u64* scratch;                  // [gridDim.x][3 limbs + 2][N], private to each block
+    const u64* evk_hat;            // [L][2][L+1][N] NTT domain, N^{-1} folded in
+    const u64* evk_hat_p;
+    u64 ninv[kMaxPrimes], ninv_p[kMaxPrimes];    // N^{-1} mod q_j (Shoup)
+    u64 pn[kMaxPrimes], pn_p[kMaxPrimes];        // P N^{-1} mod q_j (Shoup)
+    u64 p_inv[kMaxPrimes], p_inv_p[kMaxPrimes];  // P^{-1} mod q_j (Shoup)
+    u64 neg_p_mod[kMaxPrimes];                   // (-P) mod q_j
+    u64 qt_inv[kMaxPrimes], qt_inv_p[kMaxPrimes], half_qt;  // rescale by q_t, t = limbs - 1
+};
+// Words of per-block scratch, and the persistent grid for n_ct ciphertexts on this device.
+size_t sqdiff_image_scratch_words(int logn, int limbs);
+int sqdiff_image_grid(int logn, u64 n_ct, int num_sms);
+cudaError_t launch_sqdiff_image(const SqImgArgs& a, int grid, cudaStream_t st);
+
 // digits[j][m][N] = centered residue of d2 limb j lifted to modulus m (m = 0..limbs-1, then P)
 cudaError_t launch_relin_digits(const RelinArgs& a, const u64* d2, u64* digits, cudaStream_t st);
 // acc[b][m][N] = sum_j digits^[j][m] * evk^_j[b][m]

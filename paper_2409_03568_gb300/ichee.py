@@ -30,7 +30,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ELEVEL", "ESCALE", "EMISMATC
 
 CACHE_RADIX, CACHE_FREQ, CACHE_FULL = 0, 1, 2
 OP_ADD, OP_SUB, OP_PTADD, OP_PTMUL, OP_RESCALE, OP_MEANFILTER3, OP_BRIGHTNESS, OP_BLEND, OP_WATERMARK_PIXEL, \
-    OP_SQDIFF_SUM = range(10)
+    OP_SQDIFF_SUM, OP_SQDIFF = range(11)
 WITH_EVK = 1
 
 

@@ -128,6 +128,23 @@ def test_bench_cfg_matching(ichee, bench_cfg):
     np.testing.assert_allclose(ctx.decrypt(gout, gm).cpu().numpy(), o.decrypt(ref, sc), rtol=1e-9)
 
 
+def test_bench_cfg_sqdiff_image_sampled(ichee, bench_cfg):
+    """Per-pixel squared difference over the whole 64x64 image: sampled ciphertexts bit for
+    bit, every pixel's decoded value against the plaintext square."""
+    ctx, o, (h, w, c), (img, _, noisy), g = bench_cfg
+    n_ct = h * w * c
+    out, m = ctx.eval(ichee.OP_SQDIFF, g["a"], g["ma"], g["b"], g["mb"], out_level=1)
+    got = as_cts(out, n_ct, 2, ctx.n)
+    idx = sample_idx(n_ct, 4, 6)
+    ra = o.encrypt_pixels(img[idx], SEED_A, ids=idx.astype(np.uint64))
+    rb = o.encrypt_pixels(noisy[idx], SEED_B, ids=idx.astype(np.uint64))
+    ref, sc = o.sqdiff_image(ra, rb, o.delta)
+    for j, k in enumerate(idx):
+        assert np.array_equal(got[k], ref[j]), k
+    dec = ctx.decrypt(out, m).cpu().numpy()
+    assert np.max(np.abs(dec - (img.astype(np.float64) - noisy) ** 2)) < 0.05
+
+
 @pytest.fixture(scope="module")
 def ops_full(ichee):
     wl = W.OPS8192

@@ -5,6 +5,8 @@ relative and, for fresh encryptions, lie within 1e-3 of the pixel. Every input i
 oracle recomputes its own keys, caches and ciphertexts from the same seeds and never takes a
 value from the CUDA path.
 """
+from fractions import Fraction
+
 import numpy as np
 import pytest
 
@@ -306,6 +308,51 @@ def test_ops_match_small(ichee, small_ops):
     assert abs(dec[0] - plain) < 1e-2
 
 
+def test_ops_sqdiff_image_small(ichee, small_ops):
+    """Per-pixel squared difference, every ciphertext bit for bit, at the top level and one
+    level down (the evaluation key's limbs truncated)."""
+    ctx, o, (h, w, c), (img, img2, _), g, r = small_ops
+    n, nct = ctx.n, h * w * c
+    out, m = ctx.eval(ichee.OP_SQDIFF, g["a"], g["ma"], g["b"], g["mb"], out_level=2)
+    ref, sc = o.sqdiff_image(r["a"], r["b"], o.delta)
+    assert np.array_equal(as_cts(out, nct, 3, n), ref)
+    assert (m.h, m.w, m.c, m.level) == (h, w, c, 2)
+    np.testing.assert_allclose(m.scale, float(sc), rtol=1e-15)
+    dec = ctx.decrypt(out, m).cpu().numpy()
+    np.testing.assert_allclose(dec, o.decrypt(ref, sc), rtol=1e-9)
+    assert np.max(np.abs(dec - (img.astype(np.float64) - img2) ** 2)) < 1e-3
+    # one level down: x 1.0 at scale Delta, then rescale, keeps the scale near Delta
+    def down(ct, meta):
+        p, mp = ctx.eval(ichee.OP_PTMUL, ct, meta, args=(1.0,))
+        return ctx.eval(ichee.OP_RESCALE, p, mp, out_level=2)
+
+    a2, ma2 = down(g["a"], g["ma"])
+    b2, mb2 = down(g["b"], g["mb"])
+    out2, m2 = ctx.eval(ichee.OP_SQDIFF, a2, ma2, b2, mb2, out_level=1)
+    ra2 = o.rescale(o.ptmul(r["a"], o.delta, 1.0)[0])
+    rb2 = o.rescale(o.ptmul(r["b"], o.delta, 1.0)[0])
+    sc_in = Fraction(o.delta) * o.delta / int(o.q[3])
+    ref2, sc2 = o.sqdiff_image(ra2, rb2, sc_in)
+    assert np.array_equal(as_cts(out2, nct, 2, n), ref2)
+    np.testing.assert_allclose(m2.scale, float(sc2), rtol=1e-12)
+    assert np.max(np.abs(ctx.decrypt(out2, m2).cpu().numpy() - (img.astype(np.float64) - img2) ** 2)) < 1e-2
+
+
+def test_ops_sqdiff_image_more_pixels_than_blocks(ichee, small_ops):
+    """700 ciphertexts: more than one persistent block's worth, every output compared."""
+    ctx, o = small_ops[0], small_ops[1]
+    h, w, c = 10, 35, 2
+    a = inputs.random_field_image(h, w, seed=31, channels=c).reshape(-1)
+    b = inputs.noisy_copy(a, seed=32)
+    ga, ma = ctx.encrypt(torch.from_numpy(a).cuda(), h, w, c, 33)
+    gb, mb = ctx.encrypt(torch.from_numpy(b).cuda(), h, w, c, 34)
+    out, m = ctx.eval(ichee.OP_SQDIFF, ga, ma, gb, mb, out_level=2)
+    ref, sc = o.sqdiff_image(o.encrypt_pixels(a, 33), o.encrypt_pixels(b, 34), o.delta)
+    got = as_cts(out, h * w * c, 3, ctx.n)
+    bad = [k for k in range(h * w * c) if not np.array_equal(got[k], ref[k])]
+    assert not bad, bad[:10]
+
+
 # ------------------------------------------------------------- the 2^14 ring (serving size)
 def test_ring16384_keys_encryption_and_matching(ichee):
     """N = 16384, five primes: the transform and encryption kernels of this ring recompute
@@ -335,6 +382,10 @@ def test_ring16384_keys_encryption_and_matching(ichee):
     mf, mm = ctx.eval(ichee.OP_MEANFILTER3, ga, ma, out_level=L - 2)
     rf, sf = o.meanfilter3(ra, o.delta, 3, 2, 1)
     assert np.array_equal(as_cts(mf, 6, L - 1, n), rf)
+    sq, ms = ctx.eval(ichee.OP_SQDIFF, ga, ma, gb, mb, out_level=L - 2)
+    rs, ss = o.sqdiff_image(ra, rb, o.delta)
+    assert np.array_equal(as_cts(sq, 6, L - 1, n), rs)
+    assert np.max(np.abs(ctx.decrypt(sq, ms).cpu().numpy() - (a.astype(float) - b) ** 2)) < 1e-2
     ctx.close()
 
 
@@ -361,6 +412,9 @@ def test_error_paths(ichee):
     assert e.value.status == ichee.ESCALE
     with pytest.raises(ichee.IcheeError) as e:
         ctx.eval(ichee.OP_SQDIFF_SUM, ct, m, ct, m, out_n_ct=1)
+    assert e.value.status == ichee.EUNSUPPORTED
+    with pytest.raises(ichee.IcheeError) as e:
+        ctx.eval(ichee.OP_SQDIFF, ct, m, ct, m)
     assert e.value.status == ichee.EUNSUPPORTED
     other = gpu_for(ichee, wl)
     cache = other.build_cache(ichee.CACHE_RADIX, 1, radix_base=16)
