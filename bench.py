@@ -43,7 +43,7 @@ SM_MAX_MHZ = 2070.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -52,6 +52,8 @@ def parse():
                     help="enc8192: the headline step; batch32: ragged batch under a CUDA graph vs per-image "
                          "launches; serve: Poisson request stream through the continuous-batching server")
     ap.add_argument("--duration", type=float, default=None, help="serve: seconds of arrivals (default 60)")
+    ap.add_argument("--op", choices=sorted(SINGLE_OPS), default=None,
+                    help="time one operation of the enc8192 workload on its own (for kernel profiles)")
     return ap.parse_args()
 
 
@@ -306,6 +308,7 @@ def run_ours(args):
         "gpu_launches": None,
         "clocks": clk,
     }
+    out["extras"] = extras_ours(args, ctx, ichee, enc_out["fresh"], metas["fresh"], nz_ct, nz_meta, flush, alu_peak)
     # launches of our kernels per step: 1 per encryption (2 for the frequent-value cache),
     # 1 per mean filter / brightness / blend, matching: 1 accumulate + 1 reduce + 2 inverse
     # transform/scale + digits + transform + MAC + transform + mod-down + rescale, 1 per decrypt
@@ -321,6 +324,34 @@ def run_ours(args):
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def extras_ours(args, ctx, ichee, a, ma, b, mb, flush, alu_peak):
+    """Operations outside the step, timed the same way (CUDA events on the library's stream,
+    L2 flushed before each launch): the per-pixel squared difference (ICHEE_OP_SQDIFF), one
+    relinearisation and rescale per pixel of the 64x64 image."""
+    import torch
+    n, L, logn = ctx.n, ma.level + 1, ctx.n.bit_length() - 1
+    n_px = ma.n_ct
+    out = ctx.empty_cts(n_px, L - 2)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for _ in range(args.warmup):
+        ichee.ichee_eval(ctx.handle, ichee.OP_SQDIFF, a, ma, b, mb, (), out, ctx.stream())
+    for e0, e1 in ev:
+        flush.zero_()
+        e0.record()
+        ichee.ichee_eval(ctx.handle, ichee.OP_SQDIFF, a, ma, b, mb, (), out, ctx.stream())
+        e1.record()
+    torch.cuda.synchronize()
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / len(ev)
+    # transforms: 2L forward (d) + L inverse (t2) + (L+1) x (L forward digits + 2 inverse);
+    # pointwise: tensor 3LN, key-switch MAC 2L(L+1)N, P t folding 2LN, mod-down and rescale 4LN
+    n_tr = L * L + 6 * L + 2
+    modmul = n_tr * (n // 2) * logn + 3 * L * n + 2 * L * (L + 1) * n + 2 * L * n + 4 * L * n
+    ach = n_px * modmul / (ms / 1e3) / 1e9
+    return {"sqdiff_image": {"ms": round(ms, 4), "px_per_s": round(n_px / (ms / 1e3), 1), "transforms_per_px": n_tr,
+                             "bound": "alu", "achieved": round(ach, 1), "peak": round(alu_peak, 1),
+                             "unit": "Gmodmul/s", "frac": round(ach / alu_peak, 4)}}
 
 
 def e2e_ours(args, ctx, ichee, img, wm_ct, wm_meta, nz_ct, nz_meta, beta, caches, methods, enc_out, ops_out, st, world):
@@ -712,8 +743,71 @@ def run_serve(args):
         c.close()
 
 
+SINGLE_OPS = ("fresh", "radix16", "full256_pool64", "meanfilter3", "brightness", "blend", "match", "sqdiff_image",
+              "decrypt")
+
+
+def run_single_op(args):
+    """One operation of the 64x64, N = 8192 workload, launched warmup + steps times (L2 flushed
+    before each launch, CUDA events on the library's stream). Prints its mean time."""
+    import torch
+    from paper_2409_03568_gb300 import ichee
+    wl = W.ENC8192
+    ctx = ichee.Context(**W.ctx_kwargs(wl))
+    ctx.keygen(2024, with_evk=True)
+    h, w, c = wl["h"], wl["w"], wl["c"]
+    img = W.image_for(wl).reshape(-1)
+    d_img = torch.from_numpy(img).cuda()
+    a, ma = ctx.encrypt(d_img, h, w, c, 7)
+    b = mb = wm = mw = None   # second operands only where the operation takes one
+    if args.op in ("match", "sqdiff_image"):
+        b, mb = ctx.encrypt(torch.from_numpy(inputs.noisy_copy(img, seed=6)).cuda(), h, w, c, 22)
+    if args.op == "blend":
+        wm, mw = ctx.encrypt(torch.from_numpy(inputs.binary_pattern(h, w, seed=5).reshape(-1)).cuda(), h, w, 1, 21)
+    st, H, L = ctx.stream(), ctx.handle, ctx.L
+    cache = None
+    if args.op == "radix16":
+        cache = ctx.build_cache(ichee.CACHE_RADIX, 11, radix_base=16, randomize=1)
+    elif args.op == "full256_pool64":
+        cache = ctx.build_cache(ichee.CACHE_FULL, 14, pool_size=64)
+    enc = ctx.empty_cts(h * w * c, L - 1) if args.op in ("fresh", "radix16", "full256_pool64", "brightness") else None
+    out = ctx.empty_cts(h * w * c if args.op != "match" else 1, L - 2)
+    dec = torch.empty(h * w * c, dtype=torch.float64, device="cuda")
+    ops = {"meanfilter3": (ichee.OP_MEANFILTER3, None, None, ()), "brightness": (ichee.OP_BRIGHTNESS, None, None, (7.5,)),
+           "blend": (ichee.OP_BLEND, wm, mw, (0.9,)), "match": (ichee.OP_SQDIFF_SUM, b, mb, ()),
+           "sqdiff_image": (ichee.OP_SQDIFF, b, mb, ())}
+
+    def once():
+        if args.op in ("fresh", "radix16", "full256_pool64"):
+            ichee.ichee_encrypt_image(H, cache, d_img, h, w, c, 7, enc, st)
+        elif args.op == "decrypt":
+            ichee.ichee_decrypt_image(H, a, ma, dec, st)
+        else:
+            op, x, mx, arg = ops[args.op]
+            ichee.ichee_eval(H, op, a, ma, x, mx, arg, enc if op == ichee.OP_BRIGHTNESS else out, st)
+
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        flush.zero_()
+        once()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for e0, e1 in ev:
+        flush.zero_()
+        e0.record()
+        once()
+        e1.record()
+    torch.cuda.synchronize()
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / len(ev)
+    print(json.dumps({"op": args.op, "workload": wl["name"], "steps": args.steps, "warmup": args.warmup,
+                      "ms": round(ms, 4), "px_per_s": round(h * w * c / (ms / 1e3), 1)}))
+    ctx.close()
+
+
 def main():
     args = parse()
+    if args.op:
+        run_single_op(args)
+        return
     if args.impl == "ours" and args.workload == "serve":
         run_serve(args)
         return

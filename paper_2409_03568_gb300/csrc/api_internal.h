@@ -62,7 +62,7 @@ struct ichee_ctx {
     double delta = 0;
     RnsArgs rns;                 // all moduli (q_0..q_{L-1}, then P), device tables
     CdtTable cdt;
-    u64* d_tables = nullptr;     // [nmod][4][N]
+    u64* d_tables = nullptr;     // [nmod][2][N][2]: (twiddle, Shoup companion), forward then inverse
     u64* d_dm = nullptr;         // [L][256]
     u64* d_ninv = nullptr;       // [nmod] N^{-1} mod modulus
     CrtLevel crt[kMaxPrimes];    // index nl - 1

@@ -124,10 +124,8 @@ __device__ __forceinline__ u64 small_mod(int x, u64 q) { return x < 0 ? q - (u64
 // --------------------------------------------------------------------------------------
 
 struct ModTables {
-    const u64* tw;    // [N] psi^{bitrev(k)}, forward twiddles (bit-reversed order)
-    const u64* twp;   // [N] Shoup companions
-    const u64* itw;   // [N] psi^{-bitrev(k)}, inverse twiddles
-    const u64* itwp;  // [N]
+    const ulonglong2* tw;   // [N] (psi^{bitrev(k)}, Shoup companion): forward twiddles, bit-reversed order
+    const ulonglong2* itw;  // [N] (psi^{-bitrev(k)}, Shoup companion): inverse twiddles
 };
 
 struct RnsArgs {

@@ -131,8 +131,15 @@ extern "C" ichee_status ichee_ctx_create(const ichee_params* p, int device, iche
     std::vector<u64> ninv(c->nmod);
     for (int m = 0; m < c->nmod; ++m) {
         const u64 qm = c->q[m];
-        std::vector<u64> t = hm::twiddles(qm, (unsigned)c->logn);
-        if (cudaMemcpy(c->d_tables + (size_t)m * 4 * c->n, t.data(), t.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+        const std::vector<u64> t = hm::twiddles(qm, (unsigned)c->logn);   // [tw | twp | itw | itwp]
+        std::vector<u64> pairs(t.size());                                     // [(tw, twp)] then [(itw, itwp)]
+        for (int d = 0; d < 2; ++d)
+            for (int k = 0; k < c->n; ++k) {
+                pairs[((size_t)d * c->n + k) * 2] = t[(size_t)(2 * d) * c->n + k];
+                pairs[((size_t)d * c->n + k) * 2 + 1] = t[(size_t)(2 * d + 1) * c->n + k];
+            }
+        if (cudaMemcpy(c->d_tables + (size_t)m * 4 * c->n, pairs.data(), pairs.size() * 8, cudaMemcpyHostToDevice) !=
+            cudaSuccess)
             return cleanup(fail(ICHEE_ECUDA, "upload tables"));
         c->rns.q[m] = qm;
         c->rns.mu[m] = (u64)(((hm::u128)1 << 64) / qm);
@@ -140,10 +147,8 @@ extern "C" ichee_status ichee_ctx_create(const ichee_params* p, int device, iche
         c->rns.m0[m] = (u64)big;
         c->rns.m1[m] = (u64)(big >> 64);
         const u64* base = c->d_tables + (size_t)m * 4 * c->n;
-        c->rns.tab[m].tw = base;
-        c->rns.tab[m].twp = base + c->n;
-        c->rns.tab[m].itw = base + 2 * (size_t)c->n;
-        c->rns.tab[m].itwp = base + 3 * (size_t)c->n;
+        c->rns.tab[m].tw = reinterpret_cast<const ulonglong2*>(base);
+        c->rns.tab[m].itw = reinterpret_cast<const ulonglong2*>(base + 2 * (size_t)c->n);
         ninv[m] = hm::invm((u64)c->n % qm, qm);
     }
     if (cudaMalloc(&c->d_ninv, 8 * (size_t)c->nmod) != cudaSuccess) return cleanup(fail(ICHEE_ENOMEM, "ninv"));

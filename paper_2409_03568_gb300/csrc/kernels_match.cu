@@ -131,27 +131,32 @@ cudaError_t launch_sqdiff_reduce(const RnsArgs& rns, int limbs, const u64* parti
 //      inverse transform, so INTT(acc_b) = P t_b + key-switched part and
 //      (INTT(acc_b) - [acc_b mod P]) P^{-1} is the relinearised limb m;
 //   3. the relinearised limb q_t is kept; every other limb is rescaled against it and stored.
-// That is L^2 + 6L + 2 transforms per pixel (t2 is the only tensor limb inverse-transformed).
-// The block's scratch ([3 limbs + 2][N] words: t0^, t1^, t2 per limb, then the two P
-// accumulators) is private, so it stays in L2 while the block works on the pixel. Every
-// global scratch word a thread reads was written by the same thread, except where a slot is
-// read in one layout and rewritten in the other across an inverse transform, whose barriers
-// order all reads before any write.
+// That is L^2 + 6L + 2 transforms per pixel (t2 is the only tensor limb inverse-transformed),
+// all in the compact pass form so the chain fits the instruction cache.
+// Every intermediate word is produced and consumed by the same thread (the transforms move
+// data between threads only through their own shared buffer), so the block's scratch
+// ([3 limbs + 2][N] words: t0^, t1^, t2 per limb, then the two P accumulators) is stored
+// thread-major -- element e of thread tid at e * T + tid -- which makes every scratch access
+// coalesced and needs no barrier of its own. The key-switching accumulators of modulus q_m
+// build up in the t0^ / t1^ slots of limb m (the P accumulators in their own slots); keeping
+// them in shared memory instead was slower, because the larger carve-out leaves too little
+// L1 for the twiddle tables.
 // ---------------------------------------------------------------------------------------
 template <int LOGN>
 __global__ void __launch_bounds__(NttShape<LOGN>::T) k_sqdiff_image(const __grid_constant__ SqImgArgs a)
 {
     constexpr int N = 1 << LOGN;
+    constexpr int T = NttShape<LOGN>::T;
     constexpr int LAST = NttShape<LOGN>::LAST;
     extern __shared__ u64 sm[];
     const int tid = threadIdx.x;
     const int limbs = a.limbs, L = a.L;
     const int t = limbs - 1;
-    u64* S = a.scratch + (size_t)blockIdx.x * (3 * limbs + 2) * N;
-    u64* T0 = S;                          // [limbs][N] t0^, then the accumulator of poly 0
-    u64* T1 = S + (size_t)limbs * N;      // [limbs][N] t1^, then the accumulator of poly 1
-    u64* T2 = S + (size_t)2 * limbs * N;  // [limbs][N] d1^, then t2 in the coefficient domain
-    u64* AP = S + (size_t)3 * limbs * N;  // [2][N] accumulators modulo P
+    u64* S = a.scratch + (size_t)blockIdx.x * (3 * limbs + 2) * N + tid;   // thread-major slots
+    u64* T0 = S;                          // [limbs] t0^, then the poly-0 accumulator / relinearised q_t limb
+    u64* T1 = S + (size_t)limbs * N;      // [limbs] t1^, likewise for poly 1
+    u64* T2 = S + (size_t)2 * limbs * N;  // [limbs] d1^, then t2 in the coefficient domain
+    u64* AP = S + (size_t)3 * limbs * N;  // [2] accumulators modulo P, then their inverse transforms
     const u64 P = a.rns.q[L];
     const u64 halfP = (P - 1) / 2;
     for (u64 k = blockIdx.x; k < a.n_ct; k += gridDim.x) {
@@ -161,6 +166,9 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_sqdiff_image(const __grid
 #pragma unroll 1
         for (int l = 0; l < limbs; ++l) {
             const u64 q = a.rns.q[l];
+            u64* t0 = T0 + (size_t)l * N;
+            u64* t1 = T1 + (size_t)l * N;
+            u64* t2 = T2 + (size_t)l * N;
 #pragma unroll 1
             for (int pb = 0; pb < 2; ++pb) {
                 const u64* pa = A + ((u64)pb * limbs + l) * N;
@@ -171,40 +179,40 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_sqdiff_image(const __grid
                     r[0][e] = sub_mod(__ldcs(pa + x), __ldcs(pq + x), q);
                 }
                 __syncthreads();
-                ntt_fwd_regs<LOGN, 1>(sm, r, tid, a.rns.tab[l], q);
-                u64* dst = (pb == 0 ? T0 : T2) + (size_t)l * N;
+                ntt_fwd_regs<LOGN, 1, false, true>(sm, r, tid, a.rns.tab[l], q);
+                u64* dst = pb == 0 ? t0 : t2;
 #pragma unroll
-                for (int e = 0; e < 16; ++e) dst[elem_index<LOGN, LAST>(tid, e)] = csub(csub(r[0][e], 2 * q), q);
+                for (int e = 0; e < 16; ++e) dst[e * T] = csub(csub(r[0][e], 2 * q), q);
             }
             const u64 m0 = a.rns.m0[l], m1 = a.rns.m1[l];
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
-                const size_t x = (size_t)l * N + elem_index<LOGN, LAST>(tid, e);
-                const u64 d0 = T0[x], d1 = T2[x];
-                T0[x] = mul_mod(d0, d0, q, m0, m1);
+                const u64 d0 = t0[e * T], d1 = t2[e * T];
+                t0[e * T] = mul_mod(d0, d0, q, m0, m1);
                 const u64 c = mul_mod(d0, d1, q, m0, m1);
-                T1[x] = add_mod(c, c, q);
+                t1[e * T] = add_mod(c, c, q);
                 r[0][e] = shoup(mul_mod(d1, d1, q, m0, m1), a.ninv[l], a.ninv_p[l], q);
             }
             __syncthreads();
-            ntt_inv_regs<LOGN, 1>(sm, r, tid, a.rns.tab[l], q);
+            ntt_inv_regs<LOGN, 1, true>(sm, r, tid, a.rns.tab[l], q);
 #pragma unroll
-            for (int e = 0; e < 16; ++e) T2[(size_t)l * N + elem_index<LOGN, 0>(tid, e)] = csub(r[0][e], q);
+            for (int e = 0; e < 16; ++e) t2[e * T] = csub(r[0][e], q);
         }
 #pragma unroll 1
         for (int step = 0; step <= limbs; ++step) {
             const int m = step == 0 ? -1 : (step == 1 ? t : step - 2);   // -1: the special prime
             const int mod = m < 0 ? L : m;
             const u64 q = a.rns.q[mod], mu = a.rns.mu[mod];
-            u64* acc0 = m < 0 ? AP : T0 + (size_t)m * N;
+            u64* acc0 = m < 0 ? AP : T0 + (size_t)m * N;    // t0^ on entry, then the accumulator
             u64* acc1 = m < 0 ? AP + N : T1 + (size_t)m * N;
 #pragma unroll 1
             for (int j = 0; j < limbs; ++j) {
                 const u64 qj = a.rns.q[j];
                 const u64 half = (qj - 1) / 2;
+                const u64* t2 = T2 + (size_t)j * N;
 #pragma unroll
                 for (int e = 0; e < 16; ++e) {
-                    const u64 v = T2[(size_t)j * N + elem_index<LOGN, 0>(tid, e)];
+                    const u64 v = t2[e * T];
                     if (v <= half) {
                         r[0][e] = reduce64(v, q, mu);
                     } else {
@@ -213,7 +221,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_sqdiff_image(const __grid
                     }
                 }
                 __syncthreads();
-                ntt_fwd_regs<LOGN, 1>(sm, r, tid, a.rns.tab[mod], q);
+                ntt_fwd_regs<LOGN, 1, false, true>(sm, r, tid, a.rns.tab[mod], q);
                 const u64* e0 = a.evk_hat + (((size_t)j * 2 + 0) * (L + 1) + mod) * N;
                 const u64* e0p = a.evk_hat_p + (((size_t)j * 2 + 0) * (L + 1) + mod) * N;
                 const u64* e1 = a.evk_hat + (((size_t)j * 2 + 1) * (L + 1) + mod) * N;
@@ -226,48 +234,47 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_sqdiff_image(const __grid
                     const u64 p1 = shoup(d, __ldg(e1 + x), __ldg(e1p + x), q);
                     u64 s0, s1;
                     if (j > 0) {
-                        s0 = acc0[x];
-                        s1 = acc1[x];
+                        s0 = acc0[e * T];
+                        s1 = acc1[e * T];
                     } else if (m >= 0) {
-                        s0 = shoup(acc0[x], a.pn[m], a.pn_p[m], q);
-                        s1 = shoup(acc1[x], a.pn[m], a.pn_p[m], q);
+                        s0 = shoup(acc0[e * T], a.pn[m], a.pn_p[m], q);
+                        s1 = shoup(acc1[e * T], a.pn[m], a.pn_p[m], q);
                     } else {
                         s0 = s1 = 0;
                     }
-                    acc0[x] = add_mod(s0, p0, q);
-                    acc1[x] = add_mod(s1, p1, q);
+                    acc0[e * T] = add_mod(s0, p0, q);
+                    acc1[e * T] = add_mod(s1, p1, q);
                 }
             }
 #pragma unroll 1
             for (int pb = 0; pb < 2; ++pb) {
                 u64* acc = pb == 0 ? acc0 : acc1;
 #pragma unroll
-                for (int e = 0; e < 16; ++e) r[0][e] = acc[elem_index<LOGN, LAST>(tid, e)];
+                for (int e = 0; e < 16; ++e) r[0][e] = acc[e * T];
                 __syncthreads();
-                ntt_inv_regs<LOGN, 1>(sm, r, tid, a.rns.tab[mod], q);
+                ntt_inv_regs<LOGN, 1, true>(sm, r, tid, a.rns.tab[mod], q);
                 if (m < 0) {
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) acc[elem_index<LOGN, 0>(tid, e)] = csub(r[0][e], q);
+                    for (int e = 0; e < 16; ++e) acc[e * T] = csub(r[0][e], q);
                     continue;
                 }
                 const u64* last = (pb == 0 ? T0 : T1) + (size_t)t * N;
                 u64* o = a.out + ((k * 2 + pb) * (u64)t + m) * N;
 #pragma unroll
                 for (int e = 0; e < 16; ++e) {
-                    const int x = elem_index<LOGN, 0>(tid, e);
-                    const u64 ap = AP[(size_t)pb * N + x];
+                    const u64 ap = AP[(size_t)pb * N + e * T];
                     u64 lp = reduce64(ap, q, mu);
                     if (ap > halfP) lp = add_mod(lp, a.neg_p_mod[m], q);   // (ap - P) mod q_m
                     const u64 md = shoup(sub_mod(csub(r[0][e], q), lp, q), a.p_inv[m], a.p_inv_p[m], q);
                     if (m == t) {
-                        acc[x] = md;                  // relinearised limb q_t, the rescale's divisor
+                        acc[e * T] = md;              // relinearised limb q_t, the rescale's divisor
                     } else {
-                        const u64 ct = last[x];
+                        const u64 ct = last[e * T];
                         const u64 u = shoup_lazy(md, a.qt_inv[m], a.qt_inv_p[m], q);
                         const u64 w = shoup_lazy(ct, a.qt_inv[m], a.qt_inv_p[m], q);
                         u64 v = csub(csub(u + 2 * q - w, 2 * q), q);
                         if (ct > a.half_qt) v = add_mod(v, 1, q);
-                        __stcs(o + x, v);
+                        __stcs(o + elem_index<LOGN, 0>(tid, e), v);
                     }
                 }
             }
@@ -278,13 +285,16 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_sqdiff_image(const __grid
 size_t sqdiff_image_scratch_words(int logn, int limbs) { return (size_t)(3 * limbs + 2) << logn; }
 
 template <int LOGN>
+static size_t sqimg_smem() { return sizeof(u64) << LOGN; }
+
+template <int LOGN>
 static cudaError_t sqimg_prepare(int* blocks_per_sm)
 {
-    const size_t smem = sizeof(u64) << LOGN;
-    cudaError_t e = cudaFuncSetAttribute(k_sqdiff_image<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = k_sqdiff_image<LOGN>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sqimg_smem<LOGN>());
     if (e != cudaSuccess) return e;
     if (blocks_per_sm)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_sqdiff_image<LOGN>, NttShape<LOGN>::T, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, NttShape<LOGN>::T, sqimg_smem<LOGN>());
     return e;
 }
 
@@ -308,18 +318,23 @@ int sqdiff_image_grid(int logn, u64 n_ct, int num_sms)
     return (int)(n_ct < cap ? n_ct : cap);
 }
 
+template <int LOGN>
+static void sqimg_launch(const SqImgArgs& a, int grid, cudaStream_t st)
+{
+    k_sqdiff_image<LOGN><<<grid, NttShape<LOGN>::T, sqimg_smem<LOGN>(), st>>>(a);
+}
+
 cudaError_t launch_sqdiff_image(const SqImgArgs& a, int grid, cudaStream_t st)
 {
     if (grid <= 0 || a.n_ct == 0) return cudaSuccess;
     cudaError_t e = sqimg_prepare_any(a.rns.logn, nullptr);
     if (e != cudaSuccess) return e;
-    const size_t smem = sizeof(u64) << a.rns.logn;
     switch (a.rns.logn) {
-    case 10: k_sqdiff_image<10><<<grid, NttShape<10>::T, smem, st>>>(a); break;
-    case 11: k_sqdiff_image<11><<<grid, NttShape<11>::T, smem, st>>>(a); break;
-    case 12: k_sqdiff_image<12><<<grid, NttShape<12>::T, smem, st>>>(a); break;
-    case 13: k_sqdiff_image<13><<<grid, NttShape<13>::T, smem, st>>>(a); break;
-    case 14: k_sqdiff_image<14><<<grid, NttShape<14>::T, smem, st>>>(a); break;
+    case 10: sqimg_launch<10>(a, grid, st); break;
+    case 11: sqimg_launch<11>(a, grid, st); break;
+    case 12: sqimg_launch<12>(a, grid, st); break;
+    case 13: sqimg_launch<13>(a, grid, st); break;
+    case 14: sqimg_launch<14>(a, grid, st); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
