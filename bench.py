@@ -40,6 +40,29 @@ SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 
 
+# DRAM traffic per launch of a kernel, from one ncu capture of the bench's launch of it
+# (profiles/k_encrypt_fresh_enc_n8192_64x64.md: dram__bytes.sum.per_second x duration), valid
+# while the files that kernel is compiled from are unchanged; otherwise the roofline reports
+# traffic null.
+NCU_TRAFFIC = {
+    "fresh": {"bytes": 1.553e9, "sha256_16": "ed439e34c803f9ce",
+              "sources": ["paper_2409_03568_gb300/csrc/kernels_enc.cu", "paper_2409_03568_gb300/csrc/ntt.cuh",
+                          "paper_2409_03568_gb300/csrc/common.cuh", "paper_2409_03568_gb300/csrc/internal.h"]},
+}
+
+
+def ncu_traffic(kernel):
+    import hashlib
+    rec = NCU_TRAFFIC.get(kernel)
+    if rec is None:
+        return None
+    h = hashlib.sha256()
+    for f in rec["sources"]:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return rec["bytes"] if h.hexdigest()[:16] == rec["sha256_16"] else None
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -290,7 +313,10 @@ def run_ours(args):
     roof["kernel"] = dominant
     roof["peak_kind"] = peak_kind if roof["bound"] == "hbm" else "derived: %d SMs x %.0f MHz x %d IMAD/clk / %d IMAD per modmul" % (
         SM_COUNT, SM_MAX_MHZ, IMAD_PER_SM_CLK, IMAD_PER_MODMUL)
-    roof["traffic"] = None
+    roof["traffic"] = ncu_traffic(dominant)
+    if roof["traffic"] is not None:
+        roof["traffic_unit"] = "bytes per launch (DRAM read + write, ncu)"
+        roof["algorithmic_bytes"] = n_px * ct_bytes
 
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
