@@ -64,7 +64,8 @@ struct ichee_ctx {
     CdtTable cdt;
     u64* d_tables = nullptr;     // [nmod][2][N][2]: (twiddle, Shoup companion), forward then inverse
     u64* d_dm = nullptr;         // [L][256]
-    u64* d_ninv = nullptr;       // [nmod] N^{-1} mod modulus
+    u64* d_ninv = nullptr;       // [nmod] N^{-1} mod modulus, then [nmod] N^{-1} 2^64 (d_ninv_r)
+    u64* d_ninv_r = nullptr;     // inside d_ninv: not freed separately
     CrtLevel crt[kMaxPrimes];    // index nl - 1
     bool have_keys = false, have_evk = false;
     std::vector<int8_t> h_s;

@@ -69,6 +69,19 @@ __device__ __forceinline__ u64 mul_mod(u64 a, u64 b, u64 q, u64 m0, u64 m1)
     return r;
 }
 
+// Montgomery product a*b*2^{-64} mod q for a, b < q < 2^62, q odd, qinv = -q^{-1} mod 2^64
+// (Montgomery, Math. Comp. 44, 1985): with m = (ab mod 2^64) * qinv mod 2^64, ab + mq is a
+// multiple of 2^64 and (ab + mq) / 2^64 < 2q. The low words of ab and mq sum to 0 or 2^64, so
+// the carry into the high word is (ab mod 2^64 != 0). Callers fold the factor 2^64 into a
+// constant applied later.
+__device__ __forceinline__ u64 mont_mul(u64 a, u64 b, u64 q, u64 qinv)
+{
+    const u64 lo = a * b;
+    const u64 m = lo * qinv;
+    const u64 t = mulhi(a, b) + mulhi(m, q) + (lo != 0 ? 1 : 0);
+    return csub(t, q);
+}
+
 // --------------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): key = per-call seed, counter =
 // (block, stream, id lo, id hi). Every random draw of the library is a pure function of
@@ -134,6 +147,7 @@ struct RnsArgs {
     u64 q[kMaxModuli];
     u64 mu[kMaxModuli];         // floor(2^64 / q)
     u64 m0[kMaxModuli], m1[kMaxModuli];  // floor(2^128 / q) as two words
+    u64 qinv[kMaxModuli];       // -q^{-1} mod 2^64 (Montgomery)
     ModTables tab[kMaxModuli];
 };
 

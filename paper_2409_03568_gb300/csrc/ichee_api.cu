@@ -146,13 +146,19 @@ extern "C" ichee_status ichee_ctx_create(const ichee_params* p, int device, iche
         const hm::u128 big = ~(hm::u128)0 / qm;  // floor(2^128 / q): q is odd, so 2^128 - 1 gives the same
         c->rns.m0[m] = (u64)big;
         c->rns.m1[m] = (u64)(big >> 64);
+        u64 inv = qm;                       // Newton iteration for q^{-1} mod 2^64 (q odd)
+        for (int it = 0; it < 6; ++it) inv *= 2 - qm * inv;
+        c->rns.qinv[m] = 0 - inv;
         const u64* base = c->d_tables + (size_t)m * 4 * c->n;
         c->rns.tab[m].tw = reinterpret_cast<const ulonglong2*>(base);
         c->rns.tab[m].itw = reinterpret_cast<const ulonglong2*>(base + 2 * (size_t)c->n);
         ninv[m] = hm::invm((u64)c->n % qm, qm);
     }
-    if (cudaMalloc(&c->d_ninv, 8 * (size_t)c->nmod) != cudaSuccess) return cleanup(fail(ICHEE_ENOMEM, "ninv"));
-    cudaMemcpy(c->d_ninv, ninv.data(), 8 * (size_t)c->nmod, cudaMemcpyHostToDevice);
+    if (cudaMalloc(&c->d_ninv, 16 * (size_t)c->nmod) != cudaSuccess) return cleanup(fail(ICHEE_ENOMEM, "ninv"));
+    for (int m = 0; m < c->nmod; ++m)   // N^{-1} 2^64: undoes a Montgomery product's 2^{-64} as well
+        ninv.push_back(hm::mulm(ninv[m], (u64)(((hm::u128)1 << 64) % c->q[m]), c->q[m]));
+    cudaMemcpy(c->d_ninv, ninv.data(), 16 * (size_t)c->nmod, cudaMemcpyHostToDevice);
+    c->d_ninv_r = c->d_ninv + c->nmod;
 
     // Delta * p mod q_l for p = 0..255
     std::vector<u64> dm((size_t)c->L * 256);
@@ -884,7 +890,7 @@ static ichee_status op_sqdiff(ichee_ctx* c, const uint64_t* d_a, const ichee_cti
     CK(launch_sqdiff_reduce(sa.rns, limbs, partial, n_blocks, tensor, st));
     std::vector<int> id = iota_idx(kMaxModuli);
     CK(launch_ntt_inv(c->rns, batch(tensor, 3 * limbs, limbs, id.data()), st));
-    CK(launch_scale_const(c->rns, batch(tensor, 3 * limbs, limbs, id.data()), c->d_ninv, st));
+    CK(launch_scale_const(c->rns, batch(tensor, 3 * limbs, limbs, id.data()), c->d_ninv_r, st));
 
     RelinArgs ra;
     std::memset(&ra, 0, sizeof(ra));
@@ -950,7 +956,8 @@ static ichee_status op_sqdiff_image(ichee_ctx* c, const uint64_t* d_a, const ich
     a.half_qt = (qt - 1) / 2;
     for (int j = 0; j < limbs; ++j) {
         const u64 qj = c->q[j];
-        a.ninv[j] = hm::invm((u64)c->n % qj, qj);
+        const u64 r64 = (u64)(((hm::u128)1 << 64) % qj);   // undoes the tensor's Montgomery 2^{-64}
+        a.ninv[j] = hm::mulm(hm::invm((u64)c->n % qj, qj), r64, qj);
         a.ninv_p[j] = hm::shoup_of(a.ninv[j], qj);
         a.pn[j] = hm::mulm(c->P % qj, a.ninv[j], qj);
         a.pn_p[j] = hm::shoup_of(a.pn[j], qj);
@@ -1136,7 +1143,7 @@ extern "C" ichee_status ichee_sqdiff_sum_noalloc(ichee_ctx* c, const uint64_t* d
     int id[kMaxModuli];
     for (int m = 0; m < kMaxModuli; ++m) id[m] = m;
     CK(launch_ntt_inv(c->rns, batch(tensor, 3 * limbs, limbs, id), st));
-    CK(launch_scale_const(c->rns, batch(tensor, 3 * limbs, limbs, id), c->d_ninv, st));
+    CK(launch_scale_const(c->rns, batch(tensor, 3 * limbs, limbs, id), c->d_ninv_r, st));
 
     RelinArgs ra;
     std::memset(&ra, 0, sizeof(ra));

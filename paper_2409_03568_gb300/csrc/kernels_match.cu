@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T, 1) k_sqdiff_accumulate(cons
     const u64 stride = a.n_blocks / limbs;
     const u64 start = blockIdx.x / limbs;
     const u64 q = a.rns.q[l];
-    const u64 m0 = a.rns.m0[l], m1 = a.rns.m1[l];
+    const u64 qinv = a.rns.qinv[l];
     const ModTables t = a.rns.tab[l];
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
@@ -63,10 +63,10 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T, 1) k_sqdiff_accumulate(cons
             const int x = elem_index<LOGN, LAST>(tid, e);
             const u64 d1 = buf[swz(x)];
             const u64 d0 = SMEM_D0 ? d0buf[swz(x)] : d0buf[x];
-            const u64 t0 = mul_mod(d0, d0, q, m0, m1);
-            u64 t1 = mul_mod(d0, d1, q, m0, m1);
+            const u64 t0 = mont_mul(d0, d0, q, qinv);   // every term carries 2^{-64}, undone after the INTT
+            u64 t1 = mont_mul(d0, d1, q, qinv);
             t1 = add_mod(t1, t1, q);
-            const u64 t2 = mul_mod(d1, d1, q, m0, m1);
+            const u64 t2 = mont_mul(d1, d1, q, qinv);
             acc[x] = add_mod(acc[x], t0, q);
             acc[N + x] = add_mod(acc[N + x], t1, q);
             acc[2 * N + x] = add_mod(acc[2 * N + x], t2, q);
@@ -125,9 +125,10 @@ cudaError_t launch_sqdiff_reduce(const RnsArgs& rns, int limbs, const u64* parti
 // ciphertext pair (the per-pixel form of Sec. 4.4.3; Relin as in reading R11, rescale as in
 // R10). A persistent block takes one pixel at a time and runs the whole chain on it:
 //   1. per limb l: d^ = NTT(a - b) for both polynomials; t0^ = d0^2, t1^ = 2 d0 d1 stay in the
-//      NTT domain; t2 = INTT(d1^2) (N^{-1} folded into the product);
+//      NTT domain; t2 = INTT(d1^2) (N^{-1} folded into the product). The squares are
+//      Montgomery products, so each carries 2^{-64}; the constants below carry 2^64;
 //   2. per modulus m (P first, then q_t, then q_0..q_{t-1}): acc_b = sum_j NTT([t2]_j lifted
-//      to m) * evk^_j[b][m]; for m != P the term P t_b is added as (P N^{-1}) t_b^ before the
+//      to m) * evk^_j[b][m]; for m != P the term P t_b is added as (P N^{-1} 2^64) t_b^ before the
 //      inverse transform, so INTT(acc_b) = P t_b + key-switched part and
 //      (INTT(acc_b) - [acc_b mod P]) P^{-1} is the relinearised limb m;
 //   3. the relinearised limb q_t is kept; every other limb is rescaled against it and stored.
@@ -184,14 +185,14 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_sqdiff_image(const __grid
 #pragma unroll
                 for (int e = 0; e < 16; ++e) dst[e * T] = csub(csub(r[0][e], 2 * q), q);
             }
-            const u64 m0 = a.rns.m0[l], m1 = a.rns.m1[l];
+            const u64 qinv = a.rns.qinv[l];   // Montgomery products: 2^64 is folded into ninv and pn
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
                 const u64 d0 = t0[e * T], d1 = t2[e * T];
-                t0[e * T] = mul_mod(d0, d0, q, m0, m1);
-                const u64 c = mul_mod(d0, d1, q, m0, m1);
+                t0[e * T] = mont_mul(d0, d0, q, qinv);
+                const u64 c = mont_mul(d0, d1, q, qinv);
                 t1[e * T] = add_mod(c, c, q);
-                r[0][e] = shoup(mul_mod(d1, d1, q, m0, m1), a.ninv[l], a.ninv_p[l], q);
+                r[0][e] = shoup(mont_mul(d1, d1, q, qinv), a.ninv[l], a.ninv_p[l], q);
             }
             __syncthreads();
             ntt_inv_regs<LOGN, 1, true>(sm, r, tid, a.rns.tab[l], q);

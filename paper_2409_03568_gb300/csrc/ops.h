@@ -109,8 +109,8 @@ struct SqImgArgs {
     u64* scratch;                  // [gridDim.x][3 limbs + 2][N], private to each block
     const u64* evk_hat;            // [L][2][L+1][N] NTT domain, N^{-1} folded in
     const u64* evk_hat_p;
-    u64 ninv[kMaxPrimes], ninv_p[kMaxPrimes];    // N^{-1} mod q_j (Shoup)
-    u64 pn[kMaxPrimes], pn_p[kMaxPrimes];        // P N^{-1} mod q_j (Shoup)
+    u64 ninv[kMaxPrimes], ninv_p[kMaxPrimes];    // N^{-1} 2^64 mod q_j (Shoup; 2^64 undoes the tensor's Montgomery factor)
+    u64 pn[kMaxPrimes], pn_p[kMaxPrimes];        // P N^{-1} 2^64 mod q_j (Shoup)
     u64 p_inv[kMaxPrimes], p_inv_p[kMaxPrimes];  // P^{-1} mod q_j (Shoup)
     u64 neg_p_mod[kMaxPrimes];                   // (-P) mod q_j
     u64 qt_inv[kMaxPrimes], qt_inv_p[kMaxPrimes], half_qt;  // rescale by q_t, t = limbs - 1
