@@ -444,18 +444,36 @@ __device__ __forceinline__ void radix_ct(const RadixArgs& a, int p, u64 seed, u6
         int d = dk + bk - a.r * bk1;
         if (d != 0) src[ns++] = a.mult + ((size_t)kk * width + (d + a.r)) * ct_len;
     }
+    // Row by row (one modulus per row); four coefficient pairs per thread and round, their
+    // loads issued together.
     ulonglong2* dst = reinterpret_cast<ulonglong2*>(ct);
+    const int half = n / 2;
     for (int row = 0; row < 2 * a.L; ++row) {
         const u64 q = a.q[row % a.L];
-        const size_t base = (size_t)row * n / 2;
-        for (int i = threadIdx.x; i < n / 2; i += blockDim.x) {
-            ulonglong2 acc = make_ulonglong2(0, 0);
+        const size_t base = (size_t)row * half;
+        for (int i0 = threadIdx.x; i0 < half; i0 += 4 * blockDim.x) {
+            ulonglong2 acc[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] = make_ulonglong2(0, 0);
             for (int s = 0; s < ns; ++s) {
-                ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(src[s]) + base + i);
-                acc.x = add_mod(acc.x, v.x, q);
-                acc.y = add_mod(acc.y, v.y, q);
+                const ulonglong2* sp = reinterpret_cast<const ulonglong2*>(src[s]) + base;
+                ulonglong2 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + u * blockDim.x;
+                    v[u] = i < half ? __ldg(sp + i) : make_ulonglong2(0, 0);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    acc[u].x = add_mod(acc[u].x, v[u].x, q);
+                    acc[u].y = add_mod(acc[u].y, v[u].y, q);
+                }
             }
-            __stcs(dst + base + i, acc);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + u * blockDim.x;
+                if (i < half) __stcs(dst + base + i, acc[u]);
+            }
         }
     }
 }
@@ -505,18 +523,29 @@ __device__ __forceinline__ void lookup_ct(const LookupArgs& a, int slot, u64 see
         u32 idx = (u32)(((u64)w * a.pool_size) >> 32);
         z = reinterpret_cast<const ulonglong2*>(a.pool + (size_t)idx * ct_len);
     }
+    // The ciphertext as one run of 2L N/2 coefficient pairs; four pairs per thread and round,
+    // their loads issued together.
     ulonglong2* dst = reinterpret_cast<ulonglong2*>(ct);
-    for (int row = 0; row < 2 * a.L; ++row) {
-        const u64 q = a.q[row % a.L];
-        const size_t base = (size_t)row * n / 2;
-        for (int i = threadIdx.x; i < n / 2; i += blockDim.x) {
-            ulonglong2 v = __ldg(c + base + i);
+    const int half_log = a.logn - 1;
+    const int total = (2 * a.L) << half_log;
+    for (int i0 = threadIdx.x; i0 < total; i0 += 4 * blockDim.x) {
+        ulonglong2 v[4], w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * blockDim.x;
+            v[u] = i < total ? __ldg(c + i) : make_ulonglong2(0, 0);
+            w[u] = (i < total && z != nullptr) ? __ldg(z + i) : make_ulonglong2(0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i >= total) continue;
             if (z != nullptr) {
-                ulonglong2 w = __ldg(z + base + i);
-                v.x = add_mod(v.x, w.x, q);
-                v.y = add_mod(v.y, w.y, q);
+                const u64 q = a.q[(i >> half_log) % a.L];
+                v[u].x = add_mod(v[u].x, w[u].x, q);
+                v[u].y = add_mod(v[u].y, w[u].y, q);
             }
-            __stcs(dst + base + i, v);
+            __stcs(dst + i, v[u]);
         }
     }
 }

@@ -449,24 +449,28 @@ __device__ __forceinline__ void decrypt_ct(const DecArgs& a, const u64* ct, doub
     for (int l = 0; l < nl; ++l) {
         const u64 q = a.q[l], mu = a.crt.mu[l];
         const ulonglong2* c1 = reinterpret_cast<const ulonglong2*>(ct + ((u64)nl + l) * n);
-        // residues are below 2^60: up to 8 of them (plus a reduced partial sum) fit 64 bits,
-        // so the signed sums are reduced once every four coefficient pairs
+        // residues are below 2^60: 8 of them plus a reduced partial sum fit 64 bits, so the
+        // signed sums are reduced once per four coefficient pairs; the four loads of a round
+        // are issued together to keep several requests in flight per thread
         u64 pos = 0, neg = 0;
-        int pending = 0;
-        for (int j2 = threadIdx.x; j2 < n / 2; j2 += blockDim.x) {
-            const ulonglong2 v = __ldcs(c1 + j2);
-            const uint16_t sg = __ldg(s2 + j2);
-            const int s0 = (int8_t)(sg & 0xff), s1 = (int8_t)(sg >> 8);
-            pos += (s0 > 0 ? v.x : 0) + (s1 > 0 ? v.y : 0);
-            neg += (s0 < 0 ? v.x : 0) + (s1 < 0 ? v.y : 0);
-            if (++pending == 4) {
-                pos = reduce64(pos, q, mu);
-                neg = reduce64(neg, q, mu);
-                pending = 0;
+        for (int j0 = threadIdx.x; j0 < n / 2; j0 += 4 * blockDim.x) {
+            ulonglong2 v[4];
+            uint16_t sg[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j2 = j0 + u * blockDim.x;
+                v[u] = j2 < n / 2 ? __ldcs(c1 + j2) : make_ulonglong2(0, 0);
+                sg[u] = j2 < n / 2 ? __ldg(s2 + j2) : (uint16_t)0;
             }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int s0 = (int8_t)(sg[u] & 0xff), s1 = (int8_t)(sg[u] >> 8);
+                pos += (s0 > 0 ? v[u].x : 0) + (s1 > 0 ? v[u].y : 0);
+                neg += (s0 < 0 ? v[u].x : 0) + (s1 < 0 ? v[u].y : 0);
+            }
+            pos = reduce64(pos, q, mu);
+            neg = reduce64(neg, q, mu);
         }
-        pos = reduce64(pos, q, mu);
-        neg = reduce64(neg, q, mu);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             pos = add_mod(pos, __shfl_down_sync(0xffffffffu, pos, off), q);
