@@ -523,29 +523,31 @@ __device__ __forceinline__ void lookup_ct(const LookupArgs& a, int slot, u64 see
         u32 idx = (u32)(((u64)w * a.pool_size) >> 32);
         z = reinterpret_cast<const ulonglong2*>(a.pool + (size_t)idx * ct_len);
     }
-    // The ciphertext as one run of 2L N/2 coefficient pairs; four pairs per thread and round,
-    // their loads issued together.
+    // Row by row (one modulus per row); four coefficient pairs per thread and round, their
+    // loads issued together.
     ulonglong2* dst = reinterpret_cast<ulonglong2*>(ct);
-    const int half_log = a.logn - 1;
-    const int total = (2 * a.L) << half_log;
-    for (int i0 = threadIdx.x; i0 < total; i0 += 4 * blockDim.x) {
-        ulonglong2 v[4], w[4];
+    const int half = n / 2;
+    for (int row = 0; row < 2 * a.L; ++row) {
+        const u64 q = a.q[row % a.L];
+        const size_t base = (size_t)row * half;
+        for (int i0 = threadIdx.x; i0 < half; i0 += 4 * blockDim.x) {
+            ulonglong2 v[4], w[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = i0 + u * blockDim.x;
-            v[u] = i < total ? __ldg(c + i) : make_ulonglong2(0, 0);
-            w[u] = (i < total && z != nullptr) ? __ldg(z + i) : make_ulonglong2(0, 0);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = i0 + u * blockDim.x;
-            if (i >= total) continue;
-            if (z != nullptr) {
-                const u64 q = a.q[(i >> half_log) % a.L];
-                v[u].x = add_mod(v[u].x, w[u].x, q);
-                v[u].y = add_mod(v[u].y, w[u].y, q);
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + u * blockDim.x;
+                v[u] = i < half ? __ldg(c + base + i) : make_ulonglong2(0, 0);
+                w[u] = (i < half && z != nullptr) ? __ldg(z + base + i) : make_ulonglong2(0, 0);
             }
-            __stcs(dst + i, v[u]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + u * blockDim.x;
+                if (i >= half) continue;
+                if (z != nullptr) {
+                    v[u].x = add_mod(v[u].x, w[u].x, q);
+                    v[u].y = add_mod(v[u].y, w[u].y, q);
+                }
+                __stcs(dst + base + i, v[u]);
+            }
         }
     }
 }
