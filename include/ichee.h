@@ -272,14 +272,14 @@ ichee_status ichee_decrypt_batch(ichee_ctx* ctx, const uint64_t* const* d_ct, co
 
 /*
  * Radix encryption + 3x3 mean filter of a ragged batch (Sec. 3.2, 3.3, 4.4.1). The fused
- * persistent kernel assembles each filtered row's 3 x w neighbourhood ciphertexts from the
- * radix cache on the fly instead of re-reading them, and writes each encrypted pixel once.
- * Which schedule runs -- this fused kernel, or the batched encryption followed by the batched
- * mean filter -- is the autotuner's choice (two kernels until ichee_autotune_batch has timed
- * both). Outputs are identical either way, and to ichee_encrypt_batch followed by
- * ichee_eval_batch(MEANFILTER3):
+ * persistent kernel walks each image strip by strip from top to bottom, rebuilds every pixel's
+ * ciphertext once from the radix cache, writes it, and forms the filter's sums in registers and
+ * shared memory instead of reading the ciphertexts back from HBM. Which schedule runs -- this fused
+ * kernel, or the batched encryption followed by the batched mean filter -- is the autotuner's
+ * choice (two kernels until ichee_autotune_batch has timed both). Outputs are identical either
+ * way, and to ichee_encrypt_batch followed by ichee_eval_batch(MEANFILTER3):
  * d_ct_out[i] (level L-1) and d_filtered_out[i] (level L-2), all device. Needs a radix cache
- * (else ICHEE_EUNSUPPORTED) and images at most 16384 / n_pow pixels wide.
+ * (else ICHEE_EUNSUPPORTED).
  */
 ichee_status ichee_encrypt_meanfilter_batch(ichee_ctx* ctx, const ichee_cache* cache, const uint8_t* const* pixels,
                                             const ichee_image_desc* images, uint32_t n_images,
@@ -318,6 +318,14 @@ ichee_status ichee_autotune_batch(ichee_ctx* ctx, const ichee_cache* cache, cons
 
 /* The launch shape the context currently uses for a kernel kind (ICHEE_TUNE_*). */
 ichee_status ichee_tuned_shape(const ichee_ctx* ctx, uint32_t kind, uint32_t* threads, uint32_t* blocks_per_sm);
+
+/*
+ * Set the launch shape of a kernel kind (e.g. tuning results saved from an earlier run), or with
+ * ICHEE_TUNE_SCHEDULE the encrypt + mean-filter schedule (threads = 1: fused kernel, 0: two
+ * kernels; blocks_per_sm ignored). threads: 128, 256 or 512 (the fused kernel also 1024);
+ * blocks_per_sm: 1..32. Results do not depend on shapes or schedule. Errors: EINVAL.
+ */
+ichee_status ichee_set_tuned_shape(ichee_ctx* ctx, uint32_t kind, uint32_t threads, uint32_t blocks_per_sm);
 
 typedef struct ichee_graph ichee_graph;
 

@@ -144,13 +144,13 @@ ichee_status fused_chunked(ichee_ctx* c, const ichee_cache* k, const uint8_t* co
     set_rescale(c, base);
     fold_constants(c, base);
     const RadixArgs ra = radix_args(c, k, nullptr, 0, 0, nullptr);
-    const int chunks = (c->n / 2) / ls.threads;
     for (uint32_t first = 0; first < n; first += kMaxSegs) {
         const int cnt = (int)std::min<uint32_t>(kMaxSegs, n - first);
         SegTable t;
         std::memset(&t, 0, sizeof(t));
-        fill_starts(t, first, cnt, [&](uint32_t i) { return (u64)images[i].h * chunks * 2 * images[i].c; });
-        int max_w = 1;
+        fill_starts(t, first, cnt, [&](uint32_t i) {
+            return fused_items(c->logn, c->L, ls.threads, images[i].w, images[i].c);
+        });
         for (int sg = 0; sg < cnt; ++sg) {
             const uint32_t i = first + sg;
             t.px[sg] = px[i];
@@ -160,9 +160,8 @@ ichee_status fused_chunked(ichee_ctx* c, const ichee_cache* k, const uint8_t* co
             t.h[sg] = images[i].h;
             t.w[sg] = images[i].w;
             t.c[sg] = images[i].c;
-            max_w = std::max<int>(max_w, (int)images[i].w);
         }
-        CK(launch_radix_meanfilter3_batch(ra, base, t, max_w, ls, c->num_sms, st));
+        CK(launch_radix_meanfilter3_batch(ra, base, t, ls, c->num_sms, st));
     }
     return ICHEE_OK;
 }
@@ -181,13 +180,10 @@ extern "C" ichee_status ichee_encrypt_meanfilter_batch(ichee_ctx* c, const ichee
     if (k->ctx != c) return fail(ICHEE_EMISMATCH, "cache belongs to another context");
     if (k->desc.kind != ICHEE_CACHE_RADIX) return fail(ICHEE_EUNSUPPORTED, "the fused pipeline needs a radix cache");
     if (c->L < 2) return fail(ICHEE_ELEVEL, "the mean filter needs a limb to drop");
-    if (c->n / 2 < c->shape_fused.threads) return fail(ICHEE_EUNSUPPORTED, "ring too small");
     ichee_status s = check_desc(images, n_images);
     if (s != ICHEE_OK) return s;
-    for (uint32_t i = 0; i < n_images; ++i) {
+    for (uint32_t i = 0; i < n_images; ++i)
         if (!pixels[i] || !d_ct_out[i] || !d_filtered_out[i]) return fail(ICHEE_EINVAL, "null buffer for image %u", i);
-        if ((size_t)3 * images[i].w * k->n_pow > 48 * 1024) return fail(ICHEE_EUNSUPPORTED, "image %u too wide", i);
-    }
     CK(cudaSetDevice(c->device));
     if (c->fused_schedule == 1) {
         s = fused_chunked(c, k, pixels, images, n_images, d_ct_out, d_filtered_out, c->shape_fused, (cudaStream_t)stream);
@@ -435,12 +431,10 @@ extern "C" ichee_status ichee_autotune_batch(ichee_ctx* c, const ichee_cache* k,
     }
     // fused radix encryption + mean filter, and the schedule ichee_encrypt_meanfilter_batch uses
     if (radix) {
-        bool fits = true;
-        for (uint32_t i = 0; i < n_images; ++i) fits = fits && (size_t)3 * images[i].w * k->n_pow <= 48 * 1024;
+        const LaunchShape fcands[] = {{256, 4}, {512, 2}, {1024, 1}, {1024, 2}};
         LaunchShape best = c->shape_fused;
         float best_ms = 1e30f;
-        for (const LaunchShape& ls : cands) {
-            if (!fits || c->n / 2 < ls.threads) continue;
+        for (const LaunchShape& ls : fcands) {
             float ms;
             s = time_it([&] { return fused_chunked(c, k, pixels, images, n_images, d_ct, d_filtered, ls, st); }, &ms);
             if (s != ICHEE_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
@@ -455,7 +449,7 @@ extern "C" ichee_status ichee_autotune_batch(ichee_ctx* c, const ichee_cache* k,
                                                           c->shape_meanfilter, st);
         }, &two_ms);
         if (s != ICHEE_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
-        c->fused_schedule = (fits && best_ms < two_ms) ? 1 : 0;
+        c->fused_schedule = best_ms < two_ms ? 1 : 0;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -529,4 +523,29 @@ extern "C" void ichee_graph_destroy(ichee_graph* g)
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);
     delete g;
+}
+
+extern "C" ichee_status ichee_set_tuned_shape(ichee_ctx* c, uint32_t kind, uint32_t threads, uint32_t blocks_per_sm)
+{
+    if (!c) return fail(ICHEE_EINVAL, "null context");
+    if (kind == ICHEE_TUNE_SCHEDULE) {
+        if (threads > 1) return fail(ICHEE_EINVAL, "schedule must be 0 (two kernels) or 1 (fused)");
+        c->fused_schedule = (int)threads;
+        return ICHEE_OK;
+    }
+    const bool fused = kind == ICHEE_TUNE_FUSED;
+    if (!(threads == 128 || threads == 256 || threads == 512 || (fused && threads == 1024)))
+        return fail(ICHEE_EINVAL, "threads %u not supported for kind %u", threads, kind);
+    if (blocks_per_sm < 1 || blocks_per_sm > 32) return fail(ICHEE_EINVAL, "blocks_per_sm %u outside [1, 32]", blocks_per_sm);
+    if ((kind == ICHEE_TUNE_MEANFILTER) && (uint32_t)(c->n / 2) < threads)
+        return fail(ICHEE_EINVAL, "threads %u above N/2 for the mean filter", threads);
+    const LaunchShape ls = {(int)threads, (int)blocks_per_sm};
+    switch (kind) {
+    case ICHEE_TUNE_RADIX: c->shape_radix = ls; break;
+    case ICHEE_TUNE_LOOKUP: c->shape_lookup = ls; break;
+    case ICHEE_TUNE_MEANFILTER: c->shape_meanfilter = ls; break;
+    case ICHEE_TUNE_FUSED: c->shape_fused = ls; break;
+    default: return fail(ICHEE_EINVAL, "unknown kernel kind %u", kind);
+    }
+    return ICHEE_OK;
 }

@@ -208,108 +208,133 @@ __global__ void __launch_bounds__(1024) k_meanfilter3_batch(const __grid_constan
 }
 
 // Fused radix encryption + 3x3 mean filter (Sec. 3.2, 3.3 and 4.4.1) for a ragged batch. Each
-// item is one (row y, coefficient chunk, poly, channel) of one image, as in the batched mean
-// filter, but the ciphertexts of the 3 x w neighbourhood rows are assembled on the fly from
-// the cached multiples d * Enc(r^k) (L2-resident) instead of being read back from HBM: the
-// block first writes every pixel's multiple-table rows for the three image rows into shared
-// memory (signed digits with the pixel's randomness bits), then walks the row with the window
-// column sums in registers. The centre row's ciphertexts are the encryption output (each
-// written once); the filtered row is the second output. Residues equal those of the radix
-// combine kernel followed by the mean filter.
+// item is a strip of columns of one image for one polynomial, channel and 32 coefficient
+// pairs: lane = coefficient pair (coalesced 512-byte accesses), warp = column. Every warp walks
+// its column from top to bottom, rebuilding each pixel's ciphertext once from the
+// L2-resident cached multiples d * Enc(r^k) (signed digits with the pixel's randomness bits,
+// as in the radix combine) and writing it as the encryption output. The vertical 3-sums come
+// from two running sums in registers (S1 = row y, S2 = rows y-1 + y); the horizontal 3-sum from
+// the neighbouring warps through shared memory (double-buffered: one barrier per row). The
+// strip's first and last warps are halo columns (clamped at the image border) whose outputs
+// belong to the neighbouring strips. Sums stay unreduced (at most 9 residues below 2^60) up to
+// the fused multiply + rescale, as in the mean filter. Residues equal those of the radix
+// combine followed by the mean filter.
 template <int LIMBS>
-__global__ void __launch_bounds__(512) k_radix_meanfilter3_batch(const __grid_constant__ RadixArgs ra,
-                                                                 const __grid_constant__ OpsArgs a,
-                                                                 const __grid_constant__ SegTable t)
+__global__ void __launch_bounds__(1024) k_radix_meanfilter3_batch(const __grid_constant__ RadixArgs ra,
+                                                                  const __grid_constant__ OpsArgs a,
+                                                                  const __grid_constant__ SegTable t)
 {
-    extern __shared__ int8_t sdig[];   // [3][w][n_pow]: d' + r per cached power (r = digit 0)
-    const int n = 1 << a.logn;
-    const int chunks = (n / 2) / blockDim.x;
-    const int npow = ra.n_pow, r = ra.r, width = 2 * r + 1;
-    const size_t ct_words_in = (size_t)2 * LIMBS * n;
+    extern __shared__ ulonglong2 vbuf[];   // [2][cols][LIMBS][32]: vertical sums of one row
+    const int half = (1 << a.logn) / 2;
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const int cols = blockDim.x >> 5;
+    const int pchunks = half / 32;
+    const int width = 2 * ra.r + 1;
+    const size_t ct_u2 = (size_t)2 * LIMBS * half;          // one ciphertext, in coefficient pairs
+    const size_t out_u2 = (size_t)2 * (LIMBS - 1) * half;
+    const ulonglong2* mult = reinterpret_cast<const ulonglong2*>(ra.mult);
     const u64 total = t.start[t.n];
     for (u64 g = blockIdx.x; g < total; g += gridDim.x) {
         const int s = seg_of(t, g);
         u64 i = g - t.start[s];
         const int h = (int)t.h[s], w = (int)t.w[s], C = (int)t.c[s];
-        const int y = (int)(i % h); i /= h;
-        const int chunk = (int)(i % chunks); i /= chunks;
+        const int strips = (w + cols - 3) / (cols - 2);
+        const int strip = (int)(i % strips); i /= strips;
+        const int pc = (int)(i % pchunks); i /= pchunks;
         const int b = (int)(i % 2); i /= 2;
         const int ch = (int)i;
-        const int rows[3] = {y > 0 ? y - 1 : 0, y, y + 1 < h ? y + 1 : h - 1};
-        __syncthreads();  // previous item done with the digit rows
-        for (int idx = threadIdx.x; idx < 3 * w; idx += blockDim.x) {
-            const int rr = idx / w, x = idx % w;
-            const u64 k = ((u64)rows[rr] * w + x) * C + ch;
-            int p = t.px[s][k];
-            u32 bits = 0;
-            if (ra.randomize) bits = philox(t.seed[s], kStreamRadixBits, k, 0).w[0];
-            for (int kk = 0; kk < npow; ++kk) {
-                const int dk = p % r;
-                p /= r;
-                const int bk = (ra.randomize && kk >= 1) ? (int)((bits >> kk) & 1u) : 0;
-                const int bk1 = (ra.randomize && kk + 1 < npow) ? (int)((bits >> (kk + 1)) & 1u) : 0;
-                sdig[(rr * w + x) * npow + kk] = (int8_t)(dk + bk - r * bk1 + r);
+        const int xr = strip * (cols - 2) - 1 + wi;
+        const int x = xr < 0 ? 0 : (xr >= w ? w - 1 : xr);
+        const bool owned = wi >= 1 && wi <= cols - 2 && xr < w;
+        const int c2 = pc * 32 + lane;
+        const uint8_t* px = t.px[s];
+        const u64 seed = t.seed[s];
+        ulonglong2* enc = reinterpret_cast<ulonglong2*>(t.out[s]) + (size_t)b * LIMBS * half + c2;
+        ulonglong2* flt = reinterpret_cast<ulonglong2*>(t.out2[s]) + (size_t)b * (LIMBS - 1) * half + c2;
+        // digit codes of this column, 32 rows at a time: lane j holds row code_base + j, one
+        // byte per cached power (signed digit + r)
+        u64 code = 0;
+        int code_base = -64;
+        auto code_of = [&](int yy) -> u64 {
+            if (yy >= code_base + 32) {   // warp-uniform
+                code_base = yy;
+                code = 0;
+                const int yl = yy + lane;
+                if (yl < h) {
+                    const u64 k = ((u64)yl * w + x) * C + ch;
+                    int p = px[k];
+                    const u32 bits = ra.randomize ? philox(seed, kStreamRadixBits, k, 0).w[0] : 0u;
+                    for (int kk = 0; kk < ra.n_pow; ++kk) {
+                        const int dk = p % ra.r;
+                        p /= ra.r;
+                        const int bk = (ra.randomize && kk >= 1) ? (int)((bits >> kk) & 1u) : 0;
+                        const int bk1 = (ra.randomize && kk + 1 < ra.n_pow) ? (int)((bits >> (kk + 1)) & 1u) : 0;
+                        code |= (u64)(dk + bk - ra.r * bk1 + ra.r) << (8 * kk);
+                    }
+                }
             }
-        }
-        __syncthreads();
-        const int c2 = chunk * blockDim.x + threadIdx.x;
-        // value of pixel (row rr, column x) at (poly b, limb l, coefficient pair c2)
-        auto enc_val = [&](int rr, int x, int l) {
-            const u64 q = a.q[l];
-            ulonglong2 acc = make_ulonglong2(0, 0);
-            const int8_t* dg = sdig + (rr * w + x) * npow;
-            for (int kk = 0; kk < npow; ++kk) {
-                const int di = dg[kk];
-                if (di == r) continue;
-                const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(
-                    ra.mult + ((size_t)kk * width + di) * ct_words_in + ((size_t)b * LIMBS + l) * n) + c2);
-                acc.x = add_mod(acc.x, v.x, q);
-                acc.y = add_mod(acc.y, v.y, q);
-            }
-            return acc;
+            return __shfl_sync(0xffffffffu, code, yy - code_base);
         };
-        ulonglong2* enc_row = reinterpret_cast<ulonglong2*>(t.out[s]);
-        const u64 ct_len2 = (u64)2 * LIMBS * (n / 2);
-        const u64 out_len2 = (u64)2 * (LIMBS - 1) * (n / 2);
-        int written = 0;  // next column of the centre row whose encryption is still to be stored
-        ulonglong2 col[3][LIMBS];
-        auto column = [&](int xx, ulonglong2 (&dst)[LIMBS]) {
+        auto rebuild = [&](int yy, ulonglong2 (&v)[LIMBS]) {
+            const u64 cd = code_of(yy);
+#pragma unroll
+            for (int l = 0; l < LIMBS; ++l) v[l] = make_ulonglong2(0, 0);
+            for (int kk = 0; kk < ra.n_pow; ++kk) {
+                const int dr = (int)((cd >> (8 * kk)) & 0xffu);
+                if (dr == ra.r) continue;
+                const ulonglong2* src = mult + (size_t)(kk * width + dr) * ct_u2 + (size_t)b * LIMBS * half + c2;
+                ulonglong2 m[LIMBS];
+#pragma unroll
+                for (int l = 0; l < LIMBS; ++l) m[l] = __ldg(src + (size_t)l * half);
+#pragma unroll
+                for (int l = 0; l < LIMBS; ++l) {
+                    v[l].x = add_mod(v[l].x, m[l].x, a.q[l]);
+                    v[l].y = add_mod(v[l].y, m[l].y, a.q[l]);
+                }
+            }
+        };
+        auto store_enc = [&](int yy, const ulonglong2 (&v)[LIMBS]) {
+            ulonglong2* o = enc + (((size_t)yy * w + x) * C + ch) * ct_u2;
+#pragma unroll
+            for (int l = 0; l < LIMBS; ++l) __stcs(o + (size_t)l * half, v[l]);
+        };
+        ulonglong2 S1[LIMBS], S2[LIMBS], nv[LIMBS];
+        rebuild(0, S1);
+        if (owned) store_enc(0, S1);
+#pragma unroll
+        for (int l = 0; l < LIMBS; ++l) S2[l] = make_ulonglong2(S1[l].x + S1[l].x, S1[l].y + S1[l].y);  // row -1 = row 0
+        const u64 qt = a.q[LIMBS - 1];
+        for (int y = 0; y < h; ++y) {
+            const int yn = y + 1 < h ? y + 1 : h - 1;
+            rebuild(yn, nv);
+            if (owned && y + 1 < h) store_enc(y + 1, nv);
+            ulonglong2* vb = vbuf + ((size_t)(y & 1) * cols + wi) * LIMBS * 32 + lane;
 #pragma unroll
             for (int l = 0; l < LIMBS; ++l) {
-                const ulonglong2 v0 = enc_val(0, xx, l), v1 = enc_val(1, xx, l), v2 = enc_val(2, xx, l);
-                if (xx == written)
-                    __stcs(enc_row + (((u64)y * w + xx) * C + ch) * ct_len2 + ((u64)b * LIMBS + l) * (n / 2) + c2, v1);
-                dst[l].x = v0.x + v1.x + v2.x;
-                dst[l].y = v0.y + v1.y + v2.y;
+                vb[l * 32] = make_ulonglong2(S2[l].x + nv[l].x, S2[l].y + nv[l].y);
+                S2[l] = make_ulonglong2(S1[l].x + nv[l].x, S1[l].y + nv[l].y);
+                S1[l] = nv[l];
             }
-            if (xx == written) ++written;
-        };
-        column(0, col[0]);
+            __syncthreads();
+            if (owned) {
+                const ulonglong2* vl = vb - LIMBS * 32;
+                const ulonglong2* vr = vb + LIMBS * 32;
+                const ulonglong2 ht0 = vl[(LIMBS - 1) * 32], ht1 = vb[(LIMBS - 1) * 32], ht2 = vr[(LIMBS - 1) * 32];
+                const u64 tx = shoup(ht0.x + ht1.x + ht2.x, a.k0[LIMBS - 1], a.k0p[LIMBS - 1], qt);
+                const u64 ty = shoup(ht0.y + ht1.y + ht2.y, a.k0[LIMBS - 1], a.k0p[LIMBS - 1], qt);
+                ulonglong2* o = flt + (((size_t)y * w + x) * C + ch) * out_u2;
 #pragma unroll
-        for (int l = 0; l < LIMBS; ++l) col[1][l] = col[0][l];
-        column(w > 1 ? 1 : 0, col[2]);
-        const u64 qt = a.q[LIMBS - 1];
-        ulonglong2* out = reinterpret_cast<ulonglong2*>(t.out2[s]) + (u64)b * (LIMBS - 1) * (n / 2) + c2;
-        for (int x = 0; x < w; ++x) {
-            const u64 sx = col[0][LIMBS - 1].x + col[1][LIMBS - 1].x + col[2][LIMBS - 1].x;
-            const u64 sy = col[0][LIMBS - 1].y + col[1][LIMBS - 1].y + col[2][LIMBS - 1].y;
-            const u64 tx = shoup(sx, a.k0[LIMBS - 1], a.k0p[LIMBS - 1], qt);
-            const u64 ty = shoup(sy, a.k0[LIMBS - 1], a.k0p[LIMBS - 1], qt);
-            ulonglong2* o = out + (((u64)y * w + x) * C + ch) * out_len2;
-#pragma unroll
-            for (int j = 0; j < LIMBS - 1; ++j) {
-                const u64 qj = a.q[j];
-                ulonglong2 v;
-                v.x = rescale_fold(shoup_lazy(col[0][j].x + col[1][j].x + col[2][j].x, a.k0r[j], a.k0rp[j], qj), tx, j, a);
-                v.y = rescale_fold(shoup_lazy(col[0][j].y + col[1][j].y + col[2][j].y, a.k0r[j], a.k0rp[j], qj), ty, j, a);
-                __stcs(o + j * (n / 2), v);
-            }
-            if (x + 1 < w) {
-#pragma unroll
-                for (int l = 0; l < LIMBS; ++l) { col[0][l] = col[1][l]; col[1][l] = col[2][l]; }
-                column(x + 2 < w ? x + 2 : w - 1, col[2]);
+                for (int j = 0; j < LIMBS - 1; ++j) {
+                    const u64 qj = a.q[j];
+                    const ulonglong2 h0 = vl[j * 32], h1 = vb[j * 32], h2 = vr[j * 32];
+                    ulonglong2 v;
+                    v.x = rescale_fold(shoup_lazy(h0.x + h1.x + h2.x, a.k0r[j], a.k0rp[j], qj), tx, j, a);
+                    v.y = rescale_fold(shoup_lazy(h0.y + h1.y + h2.y, a.k0r[j], a.k0rp[j], qj), ty, j, a);
+                    __stcs(o + (size_t)j * half, v);
+                }
             }
         }
+        __syncthreads();   // the next item rewrites both buffers
     }
 }
 
@@ -640,22 +665,48 @@ cudaError_t launch_meanfilter3_batch(const OpsArgs& a, const SegTable& t, Launch
     return cudaGetLastError();
 }
 
-cudaError_t launch_radix_meanfilter3_batch(const RadixArgs& ra, const OpsArgs& a, const SegTable& t, int max_w,
-                                           LaunchShape ls, int num_sms, cudaStream_t st)
+// Threads per block of the fused kernel for a launch shape: 32 x columns per strip (at least 4
+// columns), halved until the two row buffers fit in shared memory.
+int fused_threads(int limbs, int threads)
+{
+    int th = threads < 128 ? 128 : (threads > 1024 ? 1024 : threads);
+    while (th > 128 && (size_t)2 * (th / 32) * limbs * 32 * 16 > 200 * 1024) th /= 2;
+    return th;
+}
+
+u64 fused_items(int logn, int limbs, int threads, u32 w, u32 c)
+{
+    const u64 cols = (u64)fused_threads(limbs, threads) / 32;
+    const u64 strips = ((u64)w + cols - 3) / (cols - 2);
+    return (u64)c * 2 * (((u64)1 << logn) / 2 / 32) * strips;
+}
+
+cudaError_t launch_radix_meanfilter3_batch(const RadixArgs& ra, const OpsArgs& a, const SegTable& t, LaunchShape ls,
+                                           int num_sms, cudaStream_t st)
 {
     const u64 total = t.n > 0 ? t.start[t.n] : 0;
     if (total == 0) return cudaSuccess;
+    if ((1 << a.logn) / 2 < 32) return cudaErrorInvalidValue;
+    const int th = fused_threads(a.limbs, ls.threads);
+    const size_t smem = (size_t)2 * (th / 32) * a.limbs * 32 * sizeof(ulonglong2);
     const unsigned g = persistent_grid(total, ls, num_sms);
-    const size_t smem = (size_t)3 * max_w * ra.n_pow;
-    if (smem > 48 * 1024) return cudaErrorInvalidValue;
+    cudaError_t e = cudaSuccess;
     switch (a.limbs) {
-    case 2: k_radix_meanfilter3_batch<2><<<g, ls.threads, smem, st>>>(ra, a, t); break;
-    case 3: k_radix_meanfilter3_batch<3><<<g, ls.threads, smem, st>>>(ra, a, t); break;
-    case 4: k_radix_meanfilter3_batch<4><<<g, ls.threads, smem, st>>>(ra, a, t); break;
-    case 5: k_radix_meanfilter3_batch<5><<<g, ls.threads, smem, st>>>(ra, a, t); break;
-    case 6: k_radix_meanfilter3_batch<6><<<g, ls.threads, smem, st>>>(ra, a, t); break;
-    case 7: k_radix_meanfilter3_batch<7><<<g, ls.threads, smem, st>>>(ra, a, t); break;
-    case 8: k_radix_meanfilter3_batch<8><<<g, ls.threads, smem, st>>>(ra, a, t); break;
+#define ICHEE_FUSED_CASE(LB)                                                                                   \
+    case LB:                                                                                                   \
+        e = cudaFuncSetAttribute(k_radix_meanfilter3_batch<LB>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                 (int)smem);                                                                   \
+        if (e != cudaSuccess) return e;                                                                        \
+        k_radix_meanfilter3_batch<LB><<<g, th, smem, st>>>(ra, a, t);                                          \
+        break;
+    ICHEE_FUSED_CASE(2)
+    ICHEE_FUSED_CASE(3)
+    ICHEE_FUSED_CASE(4)
+    ICHEE_FUSED_CASE(5)
+    ICHEE_FUSED_CASE(6)
+    ICHEE_FUSED_CASE(7)
+    ICHEE_FUSED_CASE(8)
+#undef ICHEE_FUSED_CASE
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -64,11 +64,14 @@ cudaError_t launch_meanfilter3_batch(const OpsArgs& a, const SegTable& t, Launch
 cudaError_t launch_blend_batch(const OpsArgs& a, const SegTable& t, LaunchShape ls, int num_sms, cudaStream_t st);
 cudaError_t launch_ptadd_batch(const OpsArgs& a, const SegTable& t, LaunchShape ls, int num_sms, cudaStream_t st);
 cudaError_t launch_decrypt_batch(const DecArgs& a, const SegTable& t, LaunchShape ls, int num_sms, cudaStream_t st);
-// Fused radix encryption + 3x3 mean filter over a ragged batch: items as in the batched mean
-// filter; segment s reads pixels px[s] (seed[s]) and writes the encryption to out[s] and the
-// filtered image to out2[s]. max_w bounds the image widths (shared-memory digit rows).
-cudaError_t launch_radix_meanfilter3_batch(const RadixArgs& ra, const OpsArgs& a, const SegTable& t, int max_w,
-                                           LaunchShape ls, int num_sms, cudaStream_t st);
+// Fused radix encryption + 3x3 mean filter over a ragged batch: segment s has
+// fused_items(logn, limbs, ls.threads, w, c) items (c * 2 * (N/64) strips of
+// fused_threads(limbs, ls.threads) / 32 - 2 columns); it reads pixels px[s] (seed[s]) and writes
+// the encryption to out[s] and the filtered image to out2[s].
+int fused_threads(int limbs, int threads);
+u64 fused_items(int logn, int limbs, int threads, u32 w, u32 c);
+cudaError_t launch_radix_meanfilter3_batch(const RadixArgs& ra, const OpsArgs& a, const SegTable& t, LaunchShape ls,
+                                           int num_sms, cudaStream_t st);
 
 // Matching: sum over ciphertexts of (a - b)^2 as a degree-2 ciphertext in the NTT domain.
 struct SqDiffArgs {

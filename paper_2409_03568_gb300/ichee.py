@@ -130,6 +130,7 @@ _SIGS = {
                                    ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(TuneEntry),
                                    ctypes.POINTER(_u32), _vp]),
     "ichee_tuned_shape": (_st, [_vp, _u32, ctypes.POINTER(_u32), ctypes.POINTER(_u32)]),
+    "ichee_set_tuned_shape": (_st, [_vp, _u32, _u32, _u32]),
     "ichee_graph_begin": (_st, [_vp, _vp]),
     "ichee_graph_end": (_st, [_vp, _vp, ctypes.POINTER(_vp)]),
     "ichee_graph_launch": (_st, [_vp, _vp]),
@@ -338,6 +339,10 @@ def ichee_tuned_shape(ctx, kind):
     t, b = _u32(), _u32()
     _check(_lib.ichee_tuned_shape(ctx, kind, ctypes.byref(t), ctypes.byref(b)))
     return int(t.value), int(b.value)
+
+
+def ichee_set_tuned_shape(ctx, kind, threads, blocks_per_sm=0):
+    _check(_lib.ichee_set_tuned_shape(ctx, kind, threads, blocks_per_sm))
 
 
 def ichee_graph_begin(ctx, stream):

@@ -195,26 +195,58 @@ def test_graph_replay_and_autotune(ichee, ctx8192):
     ichee.ichee_graph_destroy(graph)
 
 
-@pytest.mark.parametrize("base,randomize", [(16, 1), (10, 1), (16, 0)])
-def test_fused_encrypt_meanfilter_equals_two_steps(ichee, ctx8192, base, randomize):
+@pytest.mark.parametrize("base,randomize,threads", [(16, 1, 1024), (10, 1, 256), (16, 0, 128), (2, 1, 512)])
+def test_fused_encrypt_meanfilter_equals_two_steps(ichee, ctx8192, base, randomize, threads):
+    """Both schedules of ichee_encrypt_meanfilter_batch against single-image encryption + mean
+    filter; the fused kernel with strips of 30, 6, 2 and 14 columns (widths up to 67: several
+    strips, halo columns at both image borders), 1- and 3-channel images, 1-wide and 1-high
+    images, radix bases 2, 10, 16 with and without randomness."""
     ctx = ctx8192
     shapes, imgs = ragged_images(6, seed=20 + base + randomize, lo=1, hi=11)
     shapes[1] = (1, 7, 3)
     imgs[1] = inputs.random_field_image(1, 7, seed=5, channels=3).reshape(-1).copy()
     shapes[2] = (6, 1, 1)
     imgs[2] = inputs.random_field_image(6, 1, seed=6).reshape(-1).copy()
+    shapes[3] = (5, 67, 1)
+    imgs[3] = inputs.random_field_image(5, 67, seed=7).reshape(-1).copy()
+    shapes[4] = (3, 31, 3)
+    imgs[4] = inputs.random_field_image(3, 31, seed=8, channels=3).reshape(-1).copy()
     seeds = [5000 + i for i in range(len(shapes))]
     cache = ctx.build_cache(ichee.CACHE_RADIX, 51 + base, radix_base=base, randomize=randomize)
     d_px = [torch.from_numpy(im).cuda() for im in imgs]
-    enc = [ctx.empty_cts(h * w * c, 2) for (h, w, c) in shapes]
-    filt = [ctx.empty_cts(h * w * c, 1) for (h, w, c) in shapes]
-    mc, mf = ichee.ichee_encrypt_meanfilter_batch(ctx.handle, cache, d_px, shapes, seeds, enc, filt, ctx.stream())
+    ref = []
     for i, (h, w, c) in enumerate(shapes):
         e, m = ctx.encrypt(d_px[i], h, w, c, seeds[i], cache=cache)
         f, fm = ctx.eval(ichee.OP_MEANFILTER3, e, m, out_level=1)
-        assert torch.equal(enc[i], e), i
-        assert torch.equal(filt[i], f), i
-        assert mf[i].scale == fm.scale and mf[i].level == fm.level and mc[i].level == m.level
+        ref.append((e, m, f, fm))
+    saved = ichee.ichee_tuned_shape(ctx.handle, ichee.TUNE_SCHEDULE)[0]
+    ichee.ichee_set_tuned_shape(ctx.handle, ichee.TUNE_FUSED, threads, 2)
+    try:
+        for schedule in (1, 0):
+            ichee.ichee_set_tuned_shape(ctx.handle, ichee.TUNE_SCHEDULE, schedule)
+            enc = [ctx.empty_cts(h * w * c, 2) for (h, w, c) in shapes]
+            filt = [ctx.empty_cts(h * w * c, 1) for (h, w, c) in shapes]
+            mc, mf = ichee.ichee_encrypt_meanfilter_batch(ctx.handle, cache, d_px, shapes, seeds, enc, filt,
+                                                          ctx.stream())
+            for i, (e, m, f, fm) in enumerate(ref):
+                assert torch.equal(enc[i], e), (schedule, i)
+                assert torch.equal(filt[i], f), (schedule, i)
+                assert mf[i].scale == fm.scale and mf[i].level == fm.level and mc[i].level == m.level
+    finally:
+        ichee.ichee_set_tuned_shape(ctx.handle, ichee.TUNE_SCHEDULE, saved)
+
+
+def test_set_tuned_shape_checks(ichee, ctx8192):
+    ctx = ctx8192
+    for args in ((ichee.TUNE_RADIX, 1024, 2), (ichee.TUNE_FUSED, 2048, 1), (ichee.TUNE_RADIX, 256, 0),
+                 (ichee.TUNE_SCHEDULE, 2, 0), (99, 256, 2)):
+        with pytest.raises(ichee.IcheeError) as e:
+            ichee.ichee_set_tuned_shape(ctx.handle, *args)
+        assert e.value.status == ichee.EINVAL
+    old = ichee.ichee_tuned_shape(ctx.handle, ichee.TUNE_RADIX)
+    ichee.ichee_set_tuned_shape(ctx.handle, ichee.TUNE_RADIX, 256, 3)
+    assert ichee.ichee_tuned_shape(ctx.handle, ichee.TUNE_RADIX) == (256, 3)
+    ichee.ichee_set_tuned_shape(ctx.handle, ichee.TUNE_RADIX, *old)
 
 
 def test_batch_errors(ichee, ctx8192):
