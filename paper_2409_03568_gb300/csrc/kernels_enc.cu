@@ -236,12 +236,12 @@ cudaError_t launch_axpy_const(u64* out, const u64* x, const u64* y, u64 c, int n
 
 // Shared memory of one encryption block: the transform buffer (N words) followed by v, e0, e1
 // as int8 (3N bytes).
-template <int LOGN, bool KEEP_VHAT>
+template <int LOGN, bool KEEP_VHAT, int E>
 __device__ __forceinline__ void encrypt_ct(const EncArgs& a, int p, u64 seed, u64 id, u64* ct, u64* smem)
 {
     constexpr int N = 1 << LOGN;
-    constexpr int T = NttShape<LOGN>::T;
-    constexpr int LAST = NttShape<LOGN>::LAST;
+    constexpr int T = NttShape<LOGN, E>::T;
+    constexpr int LAST = NttShape<LOGN, E>::LAST;
     u64* buf = smem;
     int8_t* sv = reinterpret_cast<int8_t*>(smem + N);
     int8_t* se0 = sv + N;
@@ -271,36 +271,36 @@ __device__ __forceinline__ void encrypt_ct(const EncArgs& a, int p, u64 seed, u6
     for (int l = 0; l < L; ++l) {
         const u64 q = a.rns.q[l];
         const ModTables t = a.rns.tab[l];
-        u64 r[1][16];
-        u64 vh[KEEP_VHAT ? 16 : 1];
+        u64 r[1][E];
+        u64 vh[KEEP_VHAT ? E : 1];
         for (int pb = 0; pb < 2; ++pb) {
             if (KEEP_VHAT && pb == 1) {
 #pragma unroll
-                for (int e = 0; e < 16; ++e) r[0][e] = vh[KEEP_VHAT ? e : 0];
+                for (int e = 0; e < E; ++e) r[0][e] = vh[KEEP_VHAT ? e : 0];
             } else {
 #pragma unroll
-                for (int e = 0; e < 16; ++e) r[0][e] = small_mod(sv[elem_index<LOGN, 0>(tid, e)], q);
+                for (int e = 0; e < E; ++e) r[0][e] = small_mod(sv[elem_index<LOGN, 0, E>(tid, e)], q);
                 __syncthreads();
-                ntt_fwd_regs<LOGN, 1, true>(buf, r, tid, t, q);
+                ntt_fwd_regs<LOGN, 1, true, false, E>(buf, r, tid, t, q);
                 if constexpr (KEEP_VHAT) {
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) vh[e] = r[0][e];
+                    for (int e = 0; e < E; ++e) vh[e] = r[0][e];
                 }
             }
             const u64* pk = a.pk_hat + ((size_t)pb * L + l) * N;
             const u64* pkp = a.pk_hat_p + ((size_t)pb * L + l) * N;
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const int x = elem_index<LOGN, LAST>(tid, e);
+            for (int e = 0; e < E; ++e) {
+                const int x = elem_index<LOGN, LAST, E>(tid, e);
                 r[0][e] = shoup_lazy(r[0][e], __ldg(pk + x), __ldg(pkp + x), q);
             }
             __syncthreads();
-            ntt_inv_regs<LOGN, 1>(buf, r, tid, t, q);
+            ntt_inv_regs<LOGN, 1, false, E>(buf, r, tid, t, q);
             const int8_t* noise = pb == 0 ? se0 : se1;
             u64* dst = ct + ((u64)pb * L + l) * N;
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const int x = elem_index<LOGN, 0>(tid, e);
+            for (int e = 0; e < E; ++e) {
+                const int x = elem_index<LOGN, 0, E>(tid, e);
                 u64 v = add_mod(csub(r[0][e], q), small_mod(noise[x], q), q);
                 if (pb == 0 && x == 0) v = add_mod(v, a.dm[l * 256 + p], q);
                 __stcs(dst + x, v);
@@ -309,20 +309,20 @@ __device__ __forceinline__ void encrypt_ct(const EncArgs& a, int p, u64 seed, u6
     }
 }
 
-template <int LOGN, bool KEEP_VHAT>
-__global__ void __launch_bounds__(NttShape<LOGN>::T, 1) k_encrypt_fresh(const __grid_constant__ EncArgs a)
+template <int LOGN, bool KEEP_VHAT, int E>
+__global__ void __launch_bounds__(NttShape<LOGN, E>::T, 1) k_encrypt_fresh(const __grid_constant__ EncArgs a)
 {
     extern __shared__ u64 smem[];
     const u64 ct_len = (u64)2 * a.L << LOGN;
     for (u64 k = blockIdx.x; k < a.n_ct; k += gridDim.x) {
         const int p = a.pixels[k];
         if (a.skip_lut != nullptr && a.skip_lut[p] >= 0) continue;  // uniform across the block
-        encrypt_ct<LOGN, KEEP_VHAT>(a, p, a.seed, a.id_base + k, a.out + k * ct_len, smem);
+        encrypt_ct<LOGN, KEEP_VHAT, E>(a, p, a.seed, a.id_base + k, a.out + k * ct_len, smem);
     }
 }
 
-template <int LOGN, bool KEEP_VHAT>
-__global__ void __launch_bounds__(NttShape<LOGN>::T, 1) k_encrypt_fresh_batch(const __grid_constant__ EncArgs a,
+template <int LOGN, bool KEEP_VHAT, int E>
+__global__ void __launch_bounds__(NttShape<LOGN, E>::T, 1) k_encrypt_fresh_batch(const __grid_constant__ EncArgs a,
                                                                               const __grid_constant__ SegTable t)
 {
     extern __shared__ u64 smem[];
@@ -333,21 +333,27 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T, 1) k_encrypt_fresh_batch(co
         const u64 k = g - t.start[s];
         const int p = t.px[s][k];
         if (a.skip_lut != nullptr && a.skip_lut[p] >= 0) continue;
-        encrypt_ct<LOGN, KEEP_VHAT>(a, p, t.seed[s], k, t.out[s] + k * ct_len, smem);
+        encrypt_ct<LOGN, KEEP_VHAT, E>(a, p, t.seed[s], k, t.out[s] + k * ct_len, smem);
     }
 }
+
+// Residues per thread of the encryption transforms: 8 at N = 2^13 (1024 threads, twice the
+// warps per SM of the 16-residue layout), else 16.
+template <int LOGN>
+static constexpr int kEncE = LOGN == 13 ? 8 : 16;
 
 template <int LOGN>
 static cudaError_t enc_launch(const EncArgs& a, cudaStream_t st)
 {
     constexpr bool keep = LOGN <= 13;
-    const int T = NttShape<LOGN>::T;
+    constexpr int E = kEncE<LOGN>;
+    const int T = NttShape<LOGN, E>::T;
     const size_t smem = (sizeof(u64) + 3) << LOGN;
-    cudaError_t e = cudaFuncSetAttribute(k_encrypt_fresh<LOGN, keep>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_encrypt_fresh<LOGN, keep, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     u64 grid = a.n_ct < (u64)(1u << 30) ? a.n_ct : (u64)(1u << 30);
-    k_encrypt_fresh<LOGN, keep><<<(unsigned)grid, T, smem, st>>>(a);
+    k_encrypt_fresh<LOGN, keep, E><<<(unsigned)grid, T, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -355,15 +361,16 @@ template <int LOGN>
 static cudaError_t enc_batch_launch(const EncArgs& a, const SegTable& t, int num_sms, cudaStream_t st)
 {
     constexpr bool keep = LOGN <= 13;
-    const int T = NttShape<LOGN>::T;
+    constexpr int E = kEncE<LOGN>;
+    const int T = NttShape<LOGN, E>::T;
     const size_t smem = (sizeof(u64) + 3) << LOGN;
-    cudaError_t e = cudaFuncSetAttribute(k_encrypt_fresh_batch<LOGN, keep>,
+    cudaError_t e = cudaFuncSetAttribute(k_encrypt_fresh_batch<LOGN, keep, E>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const u64 total = t.start[t.n];
     const u64 cap = (u64)num_sms * 4;   // persistent: a few resident blocks per SM
     const unsigned grid = (unsigned)(total < cap ? total : cap);
-    k_encrypt_fresh_batch<LOGN, keep><<<grid, T, smem, st>>>(a, t);
+    k_encrypt_fresh_batch<LOGN, keep, E><<<grid, T, smem, st>>>(a, t);
     return cudaGetLastError();
 }
 

@@ -12,11 +12,11 @@ namespace ichee {
 // the scratch buffer (each position is owned by one thread, so no atomics are needed). The
 // transform of d0 waits in a second shared-memory buffer (SMEM_D0) or, for the 2^14 ring whose
 // buffers do not both fit, in the fourth scratch row; d1's waits in the transform buffer.
-template <int LOGN, bool SMEM_D0>
-__global__ void __launch_bounds__(NttShape<LOGN>::T, 1) k_sqdiff_accumulate(const __grid_constant__ SqDiffArgs a)
+template <int LOGN, bool SMEM_D0, int E>
+__global__ void __launch_bounds__(NttShape<LOGN, E>::T, 1) k_sqdiff_accumulate(const __grid_constant__ SqDiffArgs a)
 {
     constexpr int N = 1 << LOGN;
-    constexpr int LAST = NttShape<LOGN>::LAST;
+    constexpr int LAST = NttShape<LOGN, E>::LAST;
     extern __shared__ u64 buf[];
     u64* acc = a.partial + (size_t)blockIdx.x * 4 * N;
     u64* d0buf = SMEM_D0 ? buf + N : acc + 3 * N;
@@ -29,8 +29,8 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T, 1) k_sqdiff_accumulate(cons
     const u64 qinv = a.rns.qinv[l];
     const ModTables t = a.rns.tab[l];
 #pragma unroll
-    for (int e = 0; e < 16; ++e) {
-        const int x = elem_index<LOGN, LAST>(tid, e);
+    for (int e = 0; e < E; ++e) {
+        const int x = elem_index<LOGN, LAST, E>(tid, e);
         acc[x] = 0;
         acc[N + x] = 0;
         acc[2 * N + x] = 0;
@@ -42,27 +42,27 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T, 1) k_sqdiff_accumulate(cons
         for (int pb = 0; pb < 2; ++pb) {
             const u64* pa = A + ((u64)pb * limbs + l) * N;
             const u64* pbb = B + ((u64)pb * limbs + l) * N;
-            u64 r[1][16];
+            u64 r[1][E];
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const int x = elem_index<LOGN, 0>(tid, e);
+            for (int e = 0; e < E; ++e) {
+                const int x = elem_index<LOGN, 0, E>(tid, e);
                 r[0][e] = sub_mod(__ldcs(pa + x), __ldcs(pbb + x), q);
             }
             __syncthreads();
-            ntt_fwd_regs<LOGN, 1>(buf, r, tid, t, q);
+            ntt_fwd_regs<LOGN, 1, false, false, E>(buf, r, tid, t, q);
             __syncthreads();
             u64* dst = pb == 0 ? d0buf : buf;
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const int x = elem_index<LOGN, LAST>(tid, e);
-                dst[SMEM_D0 || pb ? swz(x) : x] = csub(csub(r[0][e], 2 * q), q);
+            for (int e = 0; e < E; ++e) {
+                const int x = elem_index<LOGN, LAST, E>(tid, e);
+                dst[SMEM_D0 || pb ? swz<E>(x) : x] = csub(csub(r[0][e], 2 * q), q);
             }
         }
 #pragma unroll 1
-        for (int e = 0; e < 16; ++e) {
-            const int x = elem_index<LOGN, LAST>(tid, e);
-            const u64 d1 = buf[swz(x)];
-            const u64 d0 = SMEM_D0 ? d0buf[swz(x)] : d0buf[x];
+        for (int e = 0; e < E; ++e) {
+            const int x = elem_index<LOGN, LAST, E>(tid, e);
+            const u64 d1 = buf[swz<E>(x)];
+            const u64 d0 = SMEM_D0 ? d0buf[swz<E>(x)] : d0buf[x];
             const u64 t0 = mont_mul(d0, d0, q, qinv);   // every term carries 2^{-64}, undone after the INTT
             u64 t1 = mont_mul(d0, d1, q, qinv);
             t1 = add_mod(t1, t1, q);
@@ -74,15 +74,20 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T, 1) k_sqdiff_accumulate(cons
     }
 }
 
+// Residues per thread: 8 at N = 2^13 (1024 threads), else 16.
+template <int LOGN>
+static constexpr int kSqE = LOGN == 13 ? 8 : 16;
+
 template <int LOGN>
 static cudaError_t sqdiff_launch(const SqDiffArgs& a, cudaStream_t st)
 {
     constexpr bool keep = LOGN <= 13;
+    constexpr int E = kSqE<LOGN>;
     const size_t smem = (keep ? 2 : 1) * (sizeof(u64) << LOGN);
-    cudaError_t e = cudaFuncSetAttribute(k_sqdiff_accumulate<LOGN, keep>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_sqdiff_accumulate<LOGN, keep, E>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_sqdiff_accumulate<LOGN, keep><<<a.n_blocks, NttShape<LOGN>::T, smem, st>>>(a);
+    k_sqdiff_accumulate<LOGN, keep, E><<<a.n_blocks, NttShape<LOGN, E>::T, smem, st>>>(a);
     return cudaGetLastError();
 }
 

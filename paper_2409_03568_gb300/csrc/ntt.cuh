@@ -2,11 +2,14 @@
 // R_q = Z_q[X]/(X^N + 1) that CKKS encryption, key generation and ct x ct multiplication
 // need (Sec. 2.2, 2.2.2, 2.2.3).
 //
-// Layout: N = 2^LOGN residues, one thread block of N/16 threads, every thread holding 16
-// residues per polynomial in registers. The log2(N) butterfly stages run in passes of up to 4
-// stages (a radix-16 step entirely in registers); between passes the block exchanges data
-// through one shared-memory buffer of N words per polynomial, XOR-swizzled
-// (x ^ ((x >> 4) & 15)) so that every pass reads and writes without bank conflicts.
+// Layout: N = 2^LOGN residues, one thread block of N/E threads, every thread holding E
+// residues (E = 16 or 8) per polynomial in registers. The log2(N) butterfly stages run in
+// passes of up to log2(E) stages (a radix-E step entirely in registers); between passes the
+// block exchanges data through one shared-memory buffer of N words per polynomial,
+// XOR-swizzled so that every pass reads and writes without bank conflicts (checked by
+// simulating every pass of N = 2^10 .. 2^14): x ^ ((x >> 4) & 15) for E = 16,
+// x ^ ((x >> 2) & 7) ^ ((x >> 3) & 15) for E = 8. E = 8 halves the registers a polynomial
+// takes, so twice the threads fit on an SM, at the price of one more exchange per transform.
 // NP polynomials over the same modulus can be transformed in lockstep: each twiddle pair is
 // loaded once for all of them and the block barriers are shared.
 //
@@ -21,29 +24,42 @@
 
 namespace ichee {
 
-__device__ __forceinline__ int swz(int x) { return x ^ ((x >> 4) & 15); }
-
-template <int LOGN, int S0>
-struct Pass {
-    static constexpr int N = 1 << LOGN;
-    static constexpr int T = N / 16;
-    static constexpr int S = (LOGN - S0) < 4 ? (LOGN - S0) : 4;  // stages in this pass
-    static constexpr int G = 16 >> S;                               // groups per thread
-    static constexpr int LO = LOGN - S0 - S;                        // lowest varying index bit
+template <int E>
+struct Radix {
+    static_assert(E == 8 || E == 16, "8 or 16 residues per thread");
+    static constexpr int LE = E == 16 ? 4 : 3;   // stages of a full pass
 };
 
-template <int LOGN>
-struct NttShape {
+template <int E = 16>
+__device__ __forceinline__ int swz(int x)
+{
+    if constexpr (E == 16) return x ^ ((x >> 4) & 15);
+    else return x ^ ((x >> 2) & 7) ^ ((x >> 3) & 15);
+}
+
+template <int LOGN, int S0, int E = 16>
+struct Pass {
+    static constexpr int LE = Radix<E>::LE;
     static constexpr int N = 1 << LOGN;
-    static constexpr int T = N / 16;
-    static constexpr int LAST = ((LOGN - 1) / 4) * 4;  // first stage of the last pass
+    static constexpr int T = N / E;
+    static constexpr int S = (LOGN - S0) < LE ? (LOGN - S0) : LE;  // stages in this pass
+    static constexpr int G = E >> S;                                 // groups per thread
+    static constexpr int LO = LOGN - S0 - S;                         // lowest varying index bit
+};
+
+template <int LOGN, int E = 16>
+struct NttShape {
+    static constexpr int LE = Radix<E>::LE;
+    static constexpr int N = 1 << LOGN;
+    static constexpr int T = N / E;
+    static constexpr int LAST = ((LOGN - 1) / LE) * LE;  // first stage of the last pass
 };
 
 // Natural index of register e of thread tid in the pass starting at stage S0.
-template <int LOGN, int S0>
+template <int LOGN, int S0, int E = 16>
 __device__ __forceinline__ int elem_index(int tid, int e)
 {
-    using P = Pass<LOGN, S0>;
+    using P = Pass<LOGN, S0, E>;
     const int g = e >> P::S, j = e & ((1 << P::S) - 1);
     const int gid = g * P::T + tid;
     const int l = gid & ((1 << P::LO) - 1);
@@ -51,32 +67,32 @@ __device__ __forceinline__ int elem_index(int tid, int e)
     return (h << (P::LO + P::S)) | (j << P::LO) | l;
 }
 
-template <int LOGN, int S0, int NP>
-__device__ __forceinline__ void load_sm(const u64* sm, u64 (&r)[NP][16], int tid)
+template <int LOGN, int S0, int NP, int E = 16>
+__device__ __forceinline__ void load_sm(const u64* sm, u64 (&r)[NP][E], int tid)
 {
 #pragma unroll
     for (int p = 0; p < NP; ++p)
 #pragma unroll
-        for (int e = 0; e < 16; ++e) r[p][e] = sm[p * (1 << LOGN) + swz(elem_index<LOGN, S0>(tid, e))];
+        for (int e = 0; e < E; ++e) r[p][e] = sm[p * (1 << LOGN) + swz<E>(elem_index<LOGN, S0, E>(tid, e))];
 }
 
-template <int LOGN, int S0, int NP>
-__device__ __forceinline__ void store_sm(u64* sm, const u64 (&r)[NP][16], int tid)
+template <int LOGN, int S0, int NP, int E = 16>
+__device__ __forceinline__ void store_sm(u64* sm, const u64 (&r)[NP][E], int tid)
 {
 #pragma unroll
     for (int p = 0; p < NP; ++p)
 #pragma unroll
-        for (int e = 0; e < 16; ++e) sm[p * (1 << LOGN) + swz(elem_index<LOGN, S0>(tid, e))] = r[p][e];
+        for (int e = 0; e < E; ++e) sm[p * (1 << LOGN) + swz<E>(elem_index<LOGN, S0, E>(tid, e))] = r[p][e];
 }
 
 // Forward stages S0 .. S0+S-1 on the registers. Stage s pairs x with x + N/2^{s+1} and uses
 // twiddle index 2^s + (x >> (LOGN - s)). With TERNARY0 the first stage of pass 0 takes the
 // odd operands as ternary residues {0, 1, q-1}, whose products with the twiddle are 0, W and
 // q - W: no multiplication.
-template <int LOGN, int S0, int NP, bool TERNARY0 = false>
-__device__ __forceinline__ void fwd_regs(u64 (&r)[NP][16], int tid, const ulonglong2* __restrict__ tw, u64 q)
+template <int LOGN, int S0, int NP, bool TERNARY0 = false, int E = 16>
+__device__ __forceinline__ void fwd_regs(u64 (&r)[NP][E], int tid, const ulonglong2* __restrict__ tw, u64 q)
 {
-    using P = Pass<LOGN, S0>;
+    using P = Pass<LOGN, S0, E>;
     const u64 q2 = 2 * q;
 #pragma unroll
     for (int g = 0; g < P::G; ++g) {
@@ -114,10 +130,10 @@ __device__ __forceinline__ void fwd_regs(u64 (&r)[NP][16], int tid, const ulongl
 }
 
 // Inverse stages S0+S-1 .. S0 (reverse order) on the registers.
-template <int LOGN, int S0, int NP>
-__device__ __forceinline__ void inv_regs(u64 (&r)[NP][16], int tid, const ulonglong2* __restrict__ itw, u64 q)
+template <int LOGN, int S0, int NP, int E = 16>
+__device__ __forceinline__ void inv_regs(u64 (&r)[NP][E], int tid, const ulonglong2* __restrict__ itw, u64 q)
 {
-    using P = Pass<LOGN, S0>;
+    using P = Pass<LOGN, S0, E>;
     const u64 q2 = 2 * q;
 #pragma unroll
     for (int g = 0; g < P::G; ++g) {
@@ -148,80 +164,85 @@ __device__ __forceinline__ void inv_regs(u64 (&r)[NP][16], int tid, const ulongl
     }
 }
 
-// Forward passes after the first: on entry r holds the output of pass S0-4 (its layout), on
+// Forward passes after the first: on entry r holds the output of pass S0-LE (its layout), on
 // exit the output of the last pass in the last pass's layout.
-template <int LOGN, int S0, int NP>
-__device__ __forceinline__ void fwd_rest(u64* sm, u64 (&r)[NP][16], int tid, const ulonglong2* __restrict__ tw, u64 q)
+template <int LOGN, int S0, int NP, int E = 16>
+__device__ __forceinline__ void fwd_rest(u64* sm, u64 (&r)[NP][E], int tid, const ulonglong2* __restrict__ tw, u64 q)
 {
-    if constexpr (S0 <= NttShape<LOGN>::LAST) {
-        store_sm<LOGN, S0 - 4, NP>(sm, r, tid);
+    constexpr int LE = Radix<E>::LE;
+    if constexpr (S0 <= NttShape<LOGN, E>::LAST) {
+        store_sm<LOGN, S0 - LE, NP, E>(sm, r, tid);
         __syncthreads();
-        load_sm<LOGN, S0, NP>(sm, r, tid);
-        fwd_regs<LOGN, S0, NP>(r, tid, tw, q);
-        fwd_rest<LOGN, S0 + 4, NP>(sm, r, tid, tw, q);
+        load_sm<LOGN, S0, NP, E>(sm, r, tid);
+        fwd_regs<LOGN, S0, NP, false, E>(r, tid, tw, q);
+        fwd_rest<LOGN, S0 + LE, NP, E>(sm, r, tid, tw, q);
     }
 }
 
-// Inverse passes S0, S0-4, ..., 0: on entry r holds bit-reversed data in the layout of pass
+// Inverse passes S0, S0-LE, ..., 0: on entry r holds bit-reversed data in the layout of pass
 // S0 (no inverse stage applied yet), on exit natural-order data in the layout of pass 0.
-template <int LOGN, int S0, int NP>
-__device__ __forceinline__ void inv_rest(u64* sm, u64 (&r)[NP][16], int tid, const ulonglong2* __restrict__ itw, u64 q)
+template <int LOGN, int S0, int NP, int E = 16>
+__device__ __forceinline__ void inv_rest(u64* sm, u64 (&r)[NP][E], int tid, const ulonglong2* __restrict__ itw, u64 q)
 {
-    inv_regs<LOGN, S0, NP>(r, tid, itw, q);
+    constexpr int LE = Radix<E>::LE;
+    inv_regs<LOGN, S0, NP, E>(r, tid, itw, q);
     if constexpr (S0 > 0) {
-        store_sm<LOGN, S0, NP>(sm, r, tid);
+        store_sm<LOGN, S0, NP, E>(sm, r, tid);
         __syncthreads();
-        load_sm<LOGN, S0 - 4, NP>(sm, r, tid);
-        inv_rest<LOGN, S0 - 4, NP>(sm, r, tid, itw, q);
+        load_sm<LOGN, S0 - LE, NP, E>(sm, r, tid);
+        inv_rest<LOGN, S0 - LE, NP, E>(sm, r, tid, itw, q);
     }
 }
 
 // ---------------------------------------------------------------------------------------
-// Full radix-16 passes with the pass position as a runtime value. The register indexing is
-// the same as in the compile-time form (S = 4, one group per thread); only the index bits of
-// the shared-memory and twiddle addresses depend on the pass. Every full pass of a transform
-// runs through one copy of this code, which keeps a kernel that chains many transforms
-// small enough for the instruction cache.
+// Full passes with the pass position as a runtime value. The register indexing is the same as
+// in the compile-time form (S = LE, one group per thread); only the index bits of the
+// shared-memory and twiddle addresses depend on the pass. Every full pass of a transform runs
+// through one copy of this code, which keeps a kernel that chains many transforms small
+// enough for the instruction cache.
 // ---------------------------------------------------------------------------------------
 
 // Natural index of register e of thread tid in the full pass whose lowest varying index bit
-// is lo (= LOGN - S0 - 4): (tid >> lo) << (lo + 4) | e << lo | (tid & (2^lo - 1)).
-__device__ __forceinline__ int pass_base(int tid, int lo) { return ((tid >> lo) << (lo + 4)) | (tid & ((1 << lo) - 1)); }
+// is lo (= LOGN - S0 - LE): (tid >> lo) << (lo + LE) | e << lo | (tid & (2^lo - 1)).
+template <int LE>
+__device__ __forceinline__ int pass_base(int tid, int lo) { return ((tid >> lo) << (lo + LE)) | (tid & ((1 << lo) - 1)); }
 
-template <int LOGN, int NP>
-__device__ __forceinline__ void store_sm_rt(u64* sm, const u64 (&r)[NP][16], int tid, int lo)
+template <int LOGN, int NP, int E = 16>
+__device__ __forceinline__ void store_sm_rt(u64* sm, const u64 (&r)[NP][E], int tid, int lo)
 {
-    const int base = pass_base(tid, lo);
+    const int base = pass_base<Radix<E>::LE>(tid, lo);
 #pragma unroll
     for (int p = 0; p < NP; ++p)
 #pragma unroll
-        for (int e = 0; e < 16; ++e) sm[p * (1 << LOGN) + swz(base | (e << lo))] = r[p][e];
+        for (int e = 0; e < E; ++e) sm[p * (1 << LOGN) + swz<E>(base | (e << lo))] = r[p][e];
 }
 
-template <int LOGN, int NP>
-__device__ __forceinline__ void load_sm_rt(const u64* sm, u64 (&r)[NP][16], int tid, int lo)
+template <int LOGN, int NP, int E = 16>
+__device__ __forceinline__ void load_sm_rt(const u64* sm, u64 (&r)[NP][E], int tid, int lo)
 {
-    const int base = pass_base(tid, lo);
+    const int base = pass_base<Radix<E>::LE>(tid, lo);
 #pragma unroll
     for (int p = 0; p < NP; ++p)
 #pragma unroll
-        for (int e = 0; e < 16; ++e) r[p][e] = sm[p * (1 << LOGN) + swz(base | (e << lo))];
+        for (int e = 0; e < E; ++e) r[p][e] = sm[p * (1 << LOGN) + swz<E>(base | (e << lo))];
 }
 
-// Forward stages S0 .. S0+3 (lo = LOGN - S0 - 4).
-template <int NP>
-__device__ __forceinline__ void fwd_regs_rt(u64 (&r)[NP][16], int tid, int S0, int lo, const ulonglong2* __restrict__ tw, u64 q)
+// Forward stages S0 .. S0+LE-1 (lo = LOGN - S0 - LE).
+template <int NP, int E = 16>
+__device__ __forceinline__ void fwd_regs_rt(u64 (&r)[NP][E], int tid, int S0, int lo, const ulonglong2* __restrict__ tw,
+                                            u64 q)
 {
+    constexpr int LE = Radix<E>::LE;
     const u64 q2 = 2 * q;
     const int h = tid >> lo;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int half = 1 << (3 - k);
+    for (int k = 0; k < LE; ++k) {
+        const int half = 1 << (LE - 1 - k);
 #pragma unroll
         for (int b = 0; b < (1 << k); ++b) {
             const int widx = (1 << (S0 + k)) + (h << k) + b;
             const ulonglong2 w2 = __ldg(tw + widx);
-                const u64 W = w2.x, Wp = w2.y;
+            const u64 W = w2.x, Wp = w2.y;
 #pragma unroll
             for (int jj = b * 2 * half; jj < b * 2 * half + half; ++jj) {
 #pragma unroll
@@ -237,20 +258,22 @@ __device__ __forceinline__ void fwd_regs_rt(u64 (&r)[NP][16], int tid, int S0, i
     }
 }
 
-// Inverse stages S0+3 .. S0 (lo = LOGN - S0 - 4).
-template <int NP>
-__device__ __forceinline__ void inv_regs_rt(u64 (&r)[NP][16], int tid, int S0, int lo, const ulonglong2* __restrict__ itw, u64 q)
+// Inverse stages S0+LE-1 .. S0 (lo = LOGN - S0 - LE).
+template <int NP, int E = 16>
+__device__ __forceinline__ void inv_regs_rt(u64 (&r)[NP][E], int tid, int S0, int lo, const ulonglong2* __restrict__ itw,
+                                            u64 q)
 {
+    constexpr int LE = Radix<E>::LE;
     const u64 q2 = 2 * q;
     const int h = tid >> lo;
 #pragma unroll
-    for (int k = 3; k >= 0; --k) {
-        const int half = 1 << (3 - k);
+    for (int k = LE - 1; k >= 0; --k) {
+        const int half = 1 << (LE - 1 - k);
 #pragma unroll
         for (int b = 0; b < (1 << k); ++b) {
             const int widx = (1 << (S0 + k)) + (h << k) + b;
             const ulonglong2 w2 = __ldg(itw + widx);
-                const u64 W = w2.x, Wp = w2.y;
+            const u64 W = w2.x, Wp = w2.y;
 #pragma unroll
             for (int jj = b * 2 * half; jj < b * 2 * half + half; ++jj) {
 #pragma unroll
@@ -270,67 +293,69 @@ __device__ __forceinline__ void inv_regs_rt(u64 (&r)[NP][16], int tid, int S0, i
 // pass 0 (values in [0, 4q); with TERNARY0, residues of a ternary polynomial); output in
 // registers in the layout of the last pass. `sm` holds NP buffers of N words. The caller must
 // make sure no thread still reads `sm` from an earlier use (a __syncthreads before the call).
-// Passes: LOGN / 4 full radix-16 passes, then one pass of the remaining LOGN % 4 stages.
+// Passes: LOGN / LE full passes, then one pass of the remaining LOGN % LE stages.
 // COMPACT runs the full passes through one runtime loop (one copy of the pass code); otherwise
 // every pass is unrolled with its position known at compile time, which needs fewer address
-// instructions but about LOGN / 4 times the code.
-template <int LOGN, int NP, bool TERNARY0 = false, bool COMPACT = false>
-__device__ __forceinline__ void ntt_fwd_regs(u64* sm, u64 (&r)[NP][16], int tid, const ModTables& t, u64 q)
+// instructions but about LOGN / LE times the code.
+template <int LOGN, int NP, bool TERNARY0 = false, bool COMPACT = false, int E = 16>
+__device__ __forceinline__ void ntt_fwd_regs(u64* sm, u64 (&r)[NP][E], int tid, const ModTables& t, u64 q)
 {
+    constexpr int LE = Radix<E>::LE;
     if constexpr (!COMPACT) {
-        fwd_regs<LOGN, 0, NP, TERNARY0>(r, tid, t.tw, q);
-        fwd_rest<LOGN, 4, NP>(sm, r, tid, t.tw, q);
+        fwd_regs<LOGN, 0, NP, TERNARY0, E>(r, tid, t.tw, q);
+        fwd_rest<LOGN, LE, NP, E>(sm, r, tid, t.tw, q);
         return;
     }
-    constexpr int NFULL = LOGN / 4, TAIL = LOGN % 4;
+    constexpr int NFULL = LOGN / LE, TAIL = LOGN % LE;
     int p0 = 0;
     if constexpr (TERNARY0) {
-        fwd_regs<LOGN, 0, NP, true>(r, tid, t.tw, q);
+        fwd_regs<LOGN, 0, NP, true, E>(r, tid, t.tw, q);
         p0 = 1;
     }
 #pragma unroll 1
     for (int p = p0; p < NFULL; ++p) {
-        const int lo = LOGN - 4 * p - 4;
+        const int lo = LOGN - LE * p - LE;
         if (p > 0) {
-            store_sm_rt<LOGN, NP>(sm, r, tid, lo + 4);
+            store_sm_rt<LOGN, NP, E>(sm, r, tid, lo + LE);
             __syncthreads();
-            load_sm_rt<LOGN, NP>(sm, r, tid, lo);
+            load_sm_rt<LOGN, NP, E>(sm, r, tid, lo);
         }
-        fwd_regs_rt<NP>(r, tid, 4 * p, lo, t.tw, q);
+        fwd_regs_rt<NP, E>(r, tid, LE * p, lo, t.tw, q);
     }
     if constexpr (TAIL > 0) {
-        store_sm_rt<LOGN, NP>(sm, r, tid, LOGN - 4 * NFULL);
+        store_sm_rt<LOGN, NP, E>(sm, r, tid, LOGN - LE * NFULL);
         __syncthreads();
-        load_sm<LOGN, 4 * NFULL, NP>(sm, r, tid);
-        fwd_regs<LOGN, 4 * NFULL, NP>(r, tid, t.tw, q);
+        load_sm<LOGN, LE * NFULL, NP, E>(sm, r, tid);
+        fwd_regs<LOGN, LE * NFULL, NP, false, E>(r, tid, t.tw, q);
     }
 }
 
 // Whole inverse transform of NP polynomials, input in registers in the layout of the last
 // pass (values in [0, 2q)); output in registers in the layout of pass 0, natural order, in
 // [0, 2q).
-template <int LOGN, int NP, bool COMPACT = false>
-__device__ __forceinline__ void ntt_inv_regs(u64* sm, u64 (&r)[NP][16], int tid, const ModTables& t, u64 q)
+template <int LOGN, int NP, bool COMPACT = false, int E = 16>
+__device__ __forceinline__ void ntt_inv_regs(u64* sm, u64 (&r)[NP][E], int tid, const ModTables& t, u64 q)
 {
+    constexpr int LE = Radix<E>::LE;
     if constexpr (!COMPACT) {
-        inv_rest<LOGN, NttShape<LOGN>::LAST, NP>(sm, r, tid, t.itw, q);
+        inv_rest<LOGN, NttShape<LOGN, E>::LAST, NP, E>(sm, r, tid, t.itw, q);
         return;
     }
-    constexpr int NFULL = LOGN / 4, TAIL = LOGN % 4;
+    constexpr int NFULL = LOGN / LE, TAIL = LOGN % LE;
     if constexpr (TAIL > 0) {
-        inv_regs<LOGN, 4 * NFULL, NP>(r, tid, t.itw, q);
-        store_sm<LOGN, 4 * NFULL, NP>(sm, r, tid);
+        inv_regs<LOGN, LE * NFULL, NP, E>(r, tid, t.itw, q);
+        store_sm<LOGN, LE * NFULL, NP, E>(sm, r, tid);
         __syncthreads();
-        load_sm_rt<LOGN, NP>(sm, r, tid, LOGN - 4 * NFULL);
+        load_sm_rt<LOGN, NP, E>(sm, r, tid, LOGN - LE * NFULL);
     }
 #pragma unroll 1
     for (int p = NFULL - 1; p >= 0; --p) {
-        const int lo = LOGN - 4 * p - 4;
-        inv_regs_rt<NP>(r, tid, 4 * p, lo, t.itw, q);
+        const int lo = LOGN - LE * p - LE;
+        inv_regs_rt<NP, E>(r, tid, LE * p, lo, t.itw, q);
         if (p > 0) {
-            store_sm_rt<LOGN, NP>(sm, r, tid, lo);
+            store_sm_rt<LOGN, NP, E>(sm, r, tid, lo);
             __syncthreads();
-            load_sm_rt<LOGN, NP>(sm, r, tid, lo + 4);
+            load_sm_rt<LOGN, NP, E>(sm, r, tid, lo + LE);
         }
     }
 }
