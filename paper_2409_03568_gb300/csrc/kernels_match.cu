@@ -28,12 +28,14 @@ __global__ void __launch_bounds__(NttShape<LOGN, E>::T, 1) k_sqdiff_accumulate(c
     const u64 q = a.rns.q[l];
     const u64 qinv = a.rns.qinv[l];
     const ModTables t = a.rns.tab[l];
+    // In the last pass registers e and e + 1 (e even) hold positions x and x + 1 (its lowest
+    // index bit is the stage bit), so the accumulators are read and written in 16-byte pairs.
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
+    for (int e = 0; e < E; e += 2) {
         const int x = elem_index<LOGN, LAST, E>(tid, e);
-        acc[x] = 0;
-        acc[N + x] = 0;
-        acc[2 * N + x] = 0;
+        *reinterpret_cast<ulonglong2*>(acc + x) = make_ulonglong2(0, 0);
+        *reinterpret_cast<ulonglong2*>(acc + N + x) = make_ulonglong2(0, 0);
+        *reinterpret_cast<ulonglong2*>(acc + 2 * N + x) = make_ulonglong2(0, 0);
     }
     for (u64 k = start; k < a.n_ct; k += stride) {
         const u64* A = a.a + k * 2 * (u64)limbs * N;
@@ -59,17 +61,28 @@ __global__ void __launch_bounds__(NttShape<LOGN, E>::T, 1) k_sqdiff_accumulate(c
             }
         }
 #pragma unroll 1
-        for (int e = 0; e < E; ++e) {
+        for (int e = 0; e < E; e += 2) {
             const int x = elem_index<LOGN, LAST, E>(tid, e);
-            const u64 d1 = buf[swz<E>(x)];
-            const u64 d0 = SMEM_D0 ? d0buf[swz<E>(x)] : d0buf[x];
-            const u64 t0 = mont_mul(d0, d0, q, qinv);   // every term carries 2^{-64}, undone after the INTT
-            u64 t1 = mont_mul(d0, d1, q, qinv);
-            t1 = add_mod(t1, t1, q);
-            const u64 t2 = mont_mul(d1, d1, q, qinv);
-            acc[x] = add_mod(acc[x], t0, q);
-            acc[N + x] = add_mod(acc[N + x], t1, q);
-            acc[2 * N + x] = add_mod(acc[2 * N + x], t2, q);
+            ulonglong2* p0 = reinterpret_cast<ulonglong2*>(acc + x);
+            ulonglong2* p1 = reinterpret_cast<ulonglong2*>(acc + N + x);
+            ulonglong2* p2 = reinterpret_cast<ulonglong2*>(acc + 2 * N + x);
+            ulonglong2 s0 = *p0, s1 = *p1, s2 = *p2;
+            u64 t[2][3];
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const u64 d1 = buf[swz<E>(x + hh)];
+                const u64 d0 = SMEM_D0 ? d0buf[swz<E>(x + hh)] : d0buf[x + hh];
+                t[hh][0] = mont_mul(d0, d0, q, qinv);   // every term carries 2^{-64}, undone after the INTT
+                const u64 c = mont_mul(d0, d1, q, qinv);
+                t[hh][1] = add_mod(c, c, q);
+                t[hh][2] = mont_mul(d1, d1, q, qinv);
+            }
+            s0 = make_ulonglong2(add_mod(s0.x, t[0][0], q), add_mod(s0.y, t[1][0], q));
+            s1 = make_ulonglong2(add_mod(s1.x, t[0][1], q), add_mod(s1.y, t[1][1], q));
+            s2 = make_ulonglong2(add_mod(s2.x, t[0][2], q), add_mod(s2.y, t[1][2], q));
+            *p0 = s0;
+            *p1 = s1;
+            *p2 = s2;
         }
     }
 }
