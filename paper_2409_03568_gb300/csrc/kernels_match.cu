@@ -161,12 +161,12 @@ cudaError_t launch_sqdiff_reduce(const RnsArgs& rns, int limbs, const u64* parti
 // them in shared memory instead was slower, because the larger carve-out leaves too little
 // L1 for the twiddle tables.
 // ---------------------------------------------------------------------------------------
-template <int LOGN>
-__global__ void __launch_bounds__(NttShape<LOGN>::T) k_sqdiff_image(const __grid_constant__ SqImgArgs a)
+template <int LOGN, int E>
+__global__ void __launch_bounds__(NttShape<LOGN, E>::T) k_sqdiff_image(const __grid_constant__ SqImgArgs a)
 {
     constexpr int N = 1 << LOGN;
-    constexpr int T = NttShape<LOGN>::T;
-    constexpr int LAST = NttShape<LOGN>::LAST;
+    constexpr int T = NttShape<LOGN, E>::T;
+    constexpr int LAST = NttShape<LOGN, E>::LAST;
     extern __shared__ u64 sm[];
     const int tid = threadIdx.x;
     const int limbs = a.limbs, L = a.L;
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_sqdiff_image(const __grid
     for (u64 k = blockIdx.x; k < a.n_ct; k += gridDim.x) {
         const u64* A = a.a + k * 2 * (u64)limbs * N;
         const u64* B = a.b + k * 2 * (u64)limbs * N;
-        u64 r[1][16];
+        u64 r[1][E];
 #pragma unroll 1
         for (int l = 0; l < limbs; ++l) {
             const u64 q = a.rns.q[l];
@@ -193,19 +193,19 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_sqdiff_image(const __grid
                 const u64* pa = A + ((u64)pb * limbs + l) * N;
                 const u64* pq = B + ((u64)pb * limbs + l) * N;
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    const int x = elem_index<LOGN, 0>(tid, e);
+                for (int e = 0; e < E; ++e) {
+                    const int x = elem_index<LOGN, 0, E>(tid, e);
                     r[0][e] = sub_mod(__ldcs(pa + x), __ldcs(pq + x), q);
                 }
                 __syncthreads();
-                ntt_fwd_regs<LOGN, 1, false, true>(sm, r, tid, a.rns.tab[l], q);
+                ntt_fwd_regs<LOGN, 1, false, true, E>(sm, r, tid, a.rns.tab[l], q);
                 u64* dst = pb == 0 ? t0 : t2;
 #pragma unroll
-                for (int e = 0; e < 16; ++e) dst[e * T] = csub(csub(r[0][e], 2 * q), q);
+                for (int e = 0; e < E; ++e) dst[e * T] = csub(csub(r[0][e], 2 * q), q);
             }
             const u64 qinv = a.rns.qinv[l];   // Montgomery products: 2^64 is folded into ninv and pn
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
+            for (int e = 0; e < E; ++e) {
                 const u64 d0 = t0[e * T], d1 = t2[e * T];
                 t0[e * T] = mont_mul(d0, d0, q, qinv);
                 const u64 c = mont_mul(d0, d1, q, qinv);
@@ -213,9 +213,9 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_sqdiff_image(const __grid
                 r[0][e] = shoup(mont_mul(d1, d1, q, qinv), a.ninv[l], a.ninv_p[l], q);
             }
             __syncthreads();
-            ntt_inv_regs<LOGN, 1, true>(sm, r, tid, a.rns.tab[l], q);
+            ntt_inv_regs<LOGN, 1, true, E>(sm, r, tid, a.rns.tab[l], q);
 #pragma unroll
-            for (int e = 0; e < 16; ++e) t2[e * T] = csub(r[0][e], q);
+            for (int e = 0; e < E; ++e) t2[e * T] = csub(r[0][e], q);
         }
 #pragma unroll 1
         for (int step = 0; step <= limbs; ++step) {
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_sqdiff_image(const __grid
                 const u64 half = (qj - 1) / 2;
                 const u64* t2 = T2 + (size_t)j * N;
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
+                for (int e = 0; e < E; ++e) {
                     const u64 v = t2[e * T];
                     if (v <= half) {
                         r[0][e] = reduce64(v, q, mu);
@@ -240,14 +240,14 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_sqdiff_image(const __grid
                     }
                 }
                 __syncthreads();
-                ntt_fwd_regs<LOGN, 1, false, true>(sm, r, tid, a.rns.tab[mod], q);
+                ntt_fwd_regs<LOGN, 1, false, true, E>(sm, r, tid, a.rns.tab[mod], q);
                 const u64* e0 = a.evk_hat + (((size_t)j * 2 + 0) * (L + 1) + mod) * N;
                 const u64* e0p = a.evk_hat_p + (((size_t)j * 2 + 0) * (L + 1) + mod) * N;
                 const u64* e1 = a.evk_hat + (((size_t)j * 2 + 1) * (L + 1) + mod) * N;
                 const u64* e1p = a.evk_hat_p + (((size_t)j * 2 + 1) * (L + 1) + mod) * N;
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    const int x = elem_index<LOGN, LAST>(tid, e);
+                for (int e = 0; e < E; ++e) {
+                    const int x = elem_index<LOGN, LAST, E>(tid, e);
                     const u64 d = csub(csub(r[0][e], 2 * q), q);
                     const u64 p0 = shoup(d, __ldg(e0 + x), __ldg(e0p + x), q);
                     const u64 p1 = shoup(d, __ldg(e1 + x), __ldg(e1p + x), q);
@@ -269,18 +269,18 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_sqdiff_image(const __grid
             for (int pb = 0; pb < 2; ++pb) {
                 u64* acc = pb == 0 ? acc0 : acc1;
 #pragma unroll
-                for (int e = 0; e < 16; ++e) r[0][e] = acc[e * T];
+                for (int e = 0; e < E; ++e) r[0][e] = acc[e * T];
                 __syncthreads();
-                ntt_inv_regs<LOGN, 1, true>(sm, r, tid, a.rns.tab[mod], q);
+                ntt_inv_regs<LOGN, 1, true, E>(sm, r, tid, a.rns.tab[mod], q);
                 if (m < 0) {
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) acc[e * T] = csub(r[0][e], q);
+                    for (int e = 0; e < E; ++e) acc[e * T] = csub(r[0][e], q);
                     continue;
                 }
                 const u64* last = (pb == 0 ? T0 : T1) + (size_t)t * N;
                 u64* o = a.out + ((k * 2 + pb) * (u64)t + m) * N;
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
+                for (int e = 0; e < E; ++e) {
                     const u64 ap = AP[(size_t)pb * N + e * T];
                     u64 lp = reduce64(ap, q, mu);
                     if (ap > halfP) lp = add_mod(lp, a.neg_p_mod[m], q);   // (ap - P) mod q_m
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_sqdiff_image(const __grid
                         const u64 w = shoup_lazy(ct, a.qt_inv[m], a.qt_inv_p[m], q);
                         u64 v = csub(csub(u + 2 * q - w, 2 * q), q);
                         if (ct > a.half_qt) v = add_mod(v, 1, q);
-                        __stcs(o + elem_index<LOGN, 0>(tid, e), v);
+                        __stcs(o + elem_index<LOGN, 0, E>(tid, e), v);
                     }
                 }
             }
@@ -303,17 +303,23 @@ __global__ void __launch_bounds__(NttShape<LOGN>::T) k_sqdiff_image(const __grid
 
 size_t sqdiff_image_scratch_words(int logn, int limbs) { return (size_t)(3 * limbs + 2) << logn; }
 
+// Residues per thread: 8 up to N = 2^13 (twice the warps of the 16-residue layout hide the
+// latency of the scratch and key loads), 16 at N = 2^14 (thread limit).
+template <int LOGN>
+static constexpr int kSqImgE = LOGN <= 13 ? 8 : 16;
+
 template <int LOGN>
 static size_t sqimg_smem() { return sizeof(u64) << LOGN; }
 
 template <int LOGN>
 static cudaError_t sqimg_prepare(int* blocks_per_sm)
 {
-    auto kern = k_sqdiff_image<LOGN>;
+    auto kern = k_sqdiff_image<LOGN, kSqImgE<LOGN>>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sqimg_smem<LOGN>());
     if (e != cudaSuccess) return e;
     if (blocks_per_sm)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, NttShape<LOGN>::T, sqimg_smem<LOGN>());
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, NttShape<LOGN, kSqImgE<LOGN>>::T,
+                                                          sqimg_smem<LOGN>());
     return e;
 }
 
@@ -340,7 +346,7 @@ int sqdiff_image_grid(int logn, u64 n_ct, int num_sms)
 template <int LOGN>
 static void sqimg_launch(const SqImgArgs& a, int grid, cudaStream_t st)
 {
-    k_sqdiff_image<LOGN><<<grid, NttShape<LOGN>::T, sqimg_smem<LOGN>(), st>>>(a);
+    k_sqdiff_image<LOGN, kSqImgE<LOGN>><<<grid, NttShape<LOGN, kSqImgE<LOGN>>::T, sqimg_smem<LOGN>(), st>>>(a);
 }
 
 cudaError_t launch_sqdiff_image(const SqImgArgs& a, int grid, cudaStream_t st)
