@@ -152,6 +152,23 @@ ichee_status ichee_ctx_primes(const ichee_ctx* ctx, uint64_t* q_out, uint64_t* p
 ichee_status ichee_keygen(ichee_ctx* ctx, uint64_t seed, uint32_t flags, void* stream);
 
 /*
+ * Working-memory allocator. By default the library takes the device memory it needs during a
+ * call (scratch of matching and of the per-pixel squared difference, staging of host buffers,
+ * per-ciphertext constant tables) from cudaMalloc and keeps it for later calls. After
+ * ichee_set_allocator those buffers come from alloc(bytes, stream, user), which must return
+ * device memory of the context's device usable by work on `stream` (NULL: out of memory, the
+ * call fails with ICHEE_ENOMEM), and go back through free_fn(ptr, stream, user), after which the
+ * allocator may hand the memory out again only once the work already enqueued on that stream
+ * has finished (a stream-ordered caching allocator such as PyTorch's qualifies). alloc = NULL
+ * restores cudaMalloc. Buffers held from before are released first (the call synchronises the
+ * device). Keys, tables and caches are not affected. Callbacks may be called from any library
+ * call on the context, on the calling thread. Errors: EINVAL (free_fn missing).
+ */
+typedef void* (*ichee_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*ichee_free_fn)(void* ptr, void* stream, void* user);
+ichee_status ichee_set_allocator(ichee_ctx* ctx, ichee_alloc_fn alloc, ichee_free_fn free_fn, void* user);
+
+/*
  * Copy a key to host memory for inspection. which: 0 = secret key s as int8[N];
  * 1 = public key as uint64[2][L][N]; 2 = evaluation key as uint64[L][2][L+1][N]
  * (coefficient domain, limb L = the special prime). `bytes` must equal that size.

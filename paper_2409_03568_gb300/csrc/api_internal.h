@@ -18,7 +18,9 @@ ichee_status fail(ichee_status st, const char* fmt, ...);
 #define CK(call)                                                                           \
     do {                                                                                   \
         cudaError_t _e = (call);                                                           \
-        if (_e != cudaSuccess) return ::ichee::fail(ICHEE_ECUDA, "%s failed: %s", #call, cudaGetErrorString(_e)); \
+        if (_e != cudaSuccess)                                                             \
+            return ::ichee::fail(_e == cudaErrorMemoryAllocation ? ICHEE_ENOMEM : ICHEE_ECUDA, "%s failed: %s", \
+                                 #call, cudaGetErrorString(_e));                           \
     } while (0)
 
 }  // namespace ichee
@@ -32,24 +34,43 @@ using ichee::LaunchShape;
 using ichee::kMaxModuli;
 using ichee::kMaxPrimes;
 
+// Working buffer of a context: grows on demand, from cudaMalloc or from the allocator the
+// caller installed (ichee_set_allocator). It remembers which allocator made its block, so the
+// block goes back to the same one.
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
-    cudaError_t ensure(size_t want)
+    ichee_free_fn freer = nullptr;
+    void* freer_user = nullptr;
+    cudaError_t ensure(size_t want, ichee_alloc_fn alloc, ichee_free_fn free_fn, void* user, cudaStream_t st)
     {
         if (want <= bytes) return cudaSuccess;
-        if (p) cudaFree(p);
-        p = nullptr;
-        bytes = 0;
-        cudaError_t e = cudaMalloc(&p, want);
-        if (e == cudaSuccess) bytes = want;
-        return e;
+        release(st);
+        if (alloc) {
+            p = alloc(want, (void*)st, user);
+            if (!p) return cudaErrorMemoryAllocation;
+            freer = free_fn;
+            freer_user = user;
+        } else {
+            cudaError_t e = cudaMalloc(&p, want);
+            if (e != cudaSuccess) {
+                p = nullptr;
+                return e;
+            }
+        }
+        bytes = want;
+        return cudaSuccess;
     }
-    void release()
+    void release(cudaStream_t st = nullptr)
     {
-        if (p) cudaFree(p);
+        if (p) {
+            if (freer) freer(p, (void*)st, freer_user);
+            else cudaFree(p);
+        }
         p = nullptr;
         bytes = 0;
+        freer = nullptr;
+        freer_user = nullptr;
     }
 };
 
@@ -78,6 +99,9 @@ struct ichee_ctx {
     u64* d_evk_hat = nullptr;
     u64* d_evk_hat_p = nullptr;
     DevBuf stage_in, stage_out, stage_res, scratch, kadd;
+    ichee_alloc_fn user_alloc = nullptr;   // working-memory allocator (ichee_set_allocator), else cudaMalloc
+    ichee_free_fn user_free = nullptr;
+    void* user_alloc_ctx = nullptr;
     int* d_status = nullptr;
     int num_sms = 0;
     // launch shapes of the persistent batched kernels (defaults; ichee_autotune_batch refines)

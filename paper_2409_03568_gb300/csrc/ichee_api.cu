@@ -613,7 +613,7 @@ extern "C" ichee_status ichee_cache_export(const ichee_cache* k, int part, void*
 static ichee_status device_pixels(ichee_ctx* c, const uint8_t* px, u64 n, cudaStream_t st, const uint8_t** d_px)
 {
     if (is_device_ptr(px)) { *d_px = px; return ICHEE_OK; }
-    CK(c->stage_in.ensure(n));
+    CK(c->stage_in.ensure(n, c->user_alloc, c->user_free, c->user_alloc_ctx, st));
     CK(cudaMemcpyAsync(c->stage_in.p, px, n, cudaMemcpyHostToDevice, st));
     *d_px = (const uint8_t*)c->stage_in.p;
     return ICHEE_OK;
@@ -795,7 +795,7 @@ extern "C" ichee_status ichee_eval(ichee_ctx* c, ichee_op op, const uint64_t* d_
             a.kadd_per_ct = 1;
         } else return fail(ICHEE_EINVAL, "ptadd needs 1 or n_ct arguments, got %u", n_args);
         if (a.kadd_per_ct) {
-            CK(c->kadd.ensure(kadd.size() * 8));
+            CK(c->kadd.ensure(kadd.size() * 8, c->user_alloc, c->user_free, c->user_alloc_ctx, st));
             CK(cudaMemcpyAsync(c->kadd.p, kadd.data(), kadd.size() * 8, cudaMemcpyHostToDevice, st));
             a.kadd = (const u64*)c->kadd.p;
         } else {
@@ -870,7 +870,7 @@ static ichee_status op_sqdiff(ichee_ctx* c, const uint64_t* d_a, const ichee_cti
     const size_t digits_w = (size_t)limbs * (limbs + 1) * n;
     const size_t acc_w = (size_t)2 * (limbs + 1) * n;
     const size_t rel_w = (size_t)2 * limbs * n;
-    CK(c->scratch.ensure((partial_w + tensor_w + digits_w + acc_w + rel_w) * 8));
+    CK(c->scratch.ensure((partial_w + tensor_w + digits_w + acc_w + rel_w) * 8, c->user_alloc, c->user_free, c->user_alloc_ctx, st));
     u64* partial = (u64*)c->scratch.p;
     u64* tensor = partial + partial_w;
     u64* digits = tensor + tensor_w;
@@ -939,7 +939,7 @@ static ichee_status op_sqdiff_image(ichee_ctx* c, const uint64_t* d_a, const ich
     const int t = limbs - 1;
     const u64 n_ct = (u64)ma->h * ma->w * ma->c;
     const int grid = sqdiff_image_grid(c->logn, n_ct, c->num_sms);
-    CK(c->scratch.ensure((size_t)grid * sqdiff_image_scratch_words(c->logn, limbs) * 8));
+    CK(c->scratch.ensure((size_t)grid * sqdiff_image_scratch_words(c->logn, limbs) * 8, c->user_alloc, c->user_free, c->user_alloc_ctx, st));
     SqImgArgs a;
     std::memset(&a, 0, sizeof(a));
     a.rns = c->rns;
@@ -977,6 +977,19 @@ static ichee_status op_sqdiff_image(ichee_ctx* c, const uint64_t* d_a, const ich
     return ICHEE_OK;
 }
 
+extern "C" ichee_status ichee_set_allocator(ichee_ctx* c, ichee_alloc_fn alloc, ichee_free_fn free_fn, void* user)
+{
+    if (!c) return fail(ICHEE_EINVAL, "null context");
+    if (alloc && !free_fn) return fail(ICHEE_EINVAL, "an allocator needs its free function");
+    CK(cudaSetDevice(c->device));
+    CK(cudaDeviceSynchronize());
+    for (DevBuf* b : {&c->stage_in, &c->stage_out, &c->stage_res, &c->scratch, &c->kadd}) b->release();
+    c->user_alloc = alloc;
+    c->user_free = alloc ? free_fn : nullptr;
+    c->user_alloc_ctx = alloc ? user : nullptr;
+    return ICHEE_OK;
+}
+
 // ---------------------------------------------------------------------------------------
 // Decryption
 // ---------------------------------------------------------------------------------------
@@ -1004,13 +1017,13 @@ static ichee_status decrypt_impl(ichee_ctx* c, const uint64_t* d_ct, const ichee
     a.scale = m->scale;
     if (out_dev) a.out = out;
     else {
-        CK(c->stage_out.ensure(n_ct * 8));
+        CK(c->stage_out.ensure(n_ct * 8, c->user_alloc, c->user_free, c->user_alloc_ctx, st));
         a.out = (double*)c->stage_out.p;
     }
     if (residues) {
         if (res_dev) a.residues_out = residues;
         else {
-            CK(c->stage_res.ensure(n_ct * nl * 8));
+            CK(c->stage_res.ensure(n_ct * nl * 8, c->user_alloc, c->user_free, c->user_alloc_ctx, st));
             a.residues_out = (u64*)c->stage_res.p;
         }
     }

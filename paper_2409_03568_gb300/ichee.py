@@ -104,6 +104,7 @@ _SIGS = {
     "ichee_ctx_primes": (_st, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     "ichee_keygen": (_st, [_vp, _u64, _u32, _vp]),
     "ichee_export_key": (_st, [_vp, ctypes.c_int, _vp, _sz, _vp]),
+    "ichee_set_allocator": (_st, [_vp, _vp, _vp, _vp]),
     "ichee_build_cache": (_st, [_vp, ctypes.POINTER(CacheDesc), _vp, _sz, _u64, ctypes.POINTER(_vp), _vp]),
     "ichee_cache_free": (None, [_vp]),
     "ichee_cache_info": (_st, [_vp, ctypes.POINTER(_u32), _vp, ctypes.POINTER(_u32)]),
@@ -211,6 +212,20 @@ def ichee_ctx_primes(ctx, n_primes):
 
 def ichee_keygen(ctx, seed, flags=0, stream=None):
     _check(_lib.ichee_keygen(ctx, seed, flags, stream))
+
+
+# Working-memory allocator callbacks: alloc(bytes, stream, user) -> device pointer (0 = out
+# of memory); free(ptr, stream, user).
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+def ichee_set_allocator(ctx, alloc=None, free=None):
+    """alloc, free: ALLOC_FN / FREE_FN instances (the caller keeps them alive), or None for
+    cudaMalloc."""
+    a = ctypes.cast(alloc, ctypes.c_void_p) if alloc is not None else None
+    f = ctypes.cast(free, ctypes.c_void_p) if free is not None else None
+    _check(_lib.ichee_set_allocator(ctx, a, f, None))
 
 
 def ichee_export_key(ctx, which, host_array, stream=None):
@@ -422,8 +437,33 @@ class Context:
             ichee_cache_free(c)
         self.caches = []
         if self.handle:
+            if getattr(self, "_alloc_cbs", None):
+                ichee_set_allocator(self.handle, None, None)   # hand the buffers back while torch is alive
+                self._alloc_cbs = None
             ichee_ctx_destroy(self.handle)
             self.handle = None
+
+    def use_torch_allocator(self):
+        """Take the library's working memory from PyTorch's caching allocator on this device.
+        Returns the list of (bytes, pointer) allocations made through it (for inspection)."""
+        import torch
+        log = []
+
+        def _alloc(n, stream, _user):
+            try:
+                p = torch.cuda.caching_allocator_alloc(int(n), self.device, stream or 0)
+            except RuntimeError:
+                return 0
+            log.append((int(n), int(p)))
+            return p
+
+        def _free(ptr, _stream, _user):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        cbs = (ALLOC_FN(_alloc), FREE_FN(_free))
+        ichee_set_allocator(self.handle, *cbs)
+        self._alloc_cbs = cbs
+        return log
 
     def __del__(self):
         try:

@@ -389,6 +389,41 @@ def test_ring16384_keys_encryption_and_matching(ichee):
     ctx.close()
 
 
+# ------------------------------------------------------------- working-memory allocator
+def test_torch_allocator_serves_working_memory(ichee):
+    """Host-buffer encryption and decryption (staging) and matching (scratch) through PyTorch's
+    caching allocator give the same bits as with cudaMalloc; an allocator that fails makes the
+    call fail with ENOMEM and leaves the context usable."""
+    wl = SMALL_OPS
+    h, w, c = 4, 5, 1
+    a = inputs.random_field_image(h, w, seed=41).reshape(-1).copy()
+    b = inputs.noisy_copy(a, seed=42)
+    res = []
+    for use_torch in (False, True):
+        ctx = gpu_for(ichee, wl, with_evk=True)
+        log = ctx.use_torch_allocator() if use_torch else None
+        ga, ma = ctx.encrypt(torch.from_numpy(a), h, w, c, 11)      # host pixels: staged
+        gb, mb = ctx.encrypt(torch.from_numpy(b), h, w, c, 12)
+        m_out, mm = ctx.eval(ichee.OP_SQDIFF_SUM, ga, ma, gb, mb, out_n_ct=1, out_level=2)
+        dec = torch.empty(h * w * c, dtype=torch.float64)                # host output: staged
+        ichee.ichee_decrypt_image(ctx.handle, ga, ma, dec, ctx.stream())
+        torch.cuda.synchronize()
+        res.append((ga.cpu(), m_out.cpu(), dec.clone()))
+        if use_torch:
+            assert len(log) >= 3 and all(n > 0 and p != 0 for n, p in log)
+            failing = ichee.ALLOC_FN(lambda n, s_, u: 0)
+            keep = ichee.FREE_FN(lambda p, s_, u: None)
+            ichee.ichee_set_allocator(ctx.handle, failing, keep)
+            with pytest.raises(ichee.IcheeError) as e:
+                ctx.eval(ichee.OP_SQDIFF_SUM, ga, ma, gb, mb, out_n_ct=1, out_level=2)
+            assert e.value.status == ichee.ENOMEM
+            ichee.ichee_set_allocator(ctx.handle, None, None)
+            again, _ = ctx.eval(ichee.OP_SQDIFF_SUM, ga, ma, gb, mb, out_n_ct=1, out_level=2)
+            assert torch.equal(again.cpu(), res[0][1])
+        ctx.close()
+    assert all(torch.equal(x, y) for x, y in zip(res[0], res[1]))
+
+
 # ------------------------------------------------------------------------ errors
 def test_error_paths(ichee):
     wl = W.TOY
