@@ -314,7 +314,7 @@ ichee_status ichee_encrypt_meanfilter_batch(ichee_ctx* ctx, const ichee_cache* c
 typedef struct {
     uint32_t kind;            /* ICHEE_TUNE_* */
     uint32_t threads;         /* threads per block */
-    uint32_t blocks_per_sm;   /* persistent grid = blocks_per_sm x SM count */
+    uint32_t blocks_per_sm;   /* persistent grid = blocks_per_sm x SM count; 0 = one block per work item */
     float ms;                 /* best of two timed runs */
 } ichee_tune_entry;
 
@@ -340,7 +340,8 @@ ichee_status ichee_tuned_shape(const ichee_ctx* ctx, uint32_t kind, uint32_t* th
  * Set the launch shape of a kernel kind (e.g. tuning results saved from an earlier run), or with
  * ICHEE_TUNE_SCHEDULE the encrypt + mean-filter schedule (threads = 1: fused kernel, 0: two
  * kernels; blocks_per_sm ignored). threads: 128, 256 or 512 (the fused kernel also 1024);
- * blocks_per_sm: 1..32. Results do not depend on shapes or schedule. Errors: EINVAL.
+ * blocks_per_sm: 1..32 resident blocks per SM striding over the work, or 0 for one block per
+ * work item. Results do not depend on shapes or schedule. Errors: EINVAL.
  */
 ichee_status ichee_set_tuned_shape(ichee_ctx* ctx, uint32_t kind, uint32_t threads, uint32_t blocks_per_sm);
 

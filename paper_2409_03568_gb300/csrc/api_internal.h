@@ -105,8 +105,9 @@ struct ichee_ctx {
     int* d_status = nullptr;
     int num_sms = 0;
     // launch shapes of the persistent batched kernels (defaults; ichee_autotune_batch refines)
-    LaunchShape shape_radix = {256, 8}, shape_lookup = {256, 8}, shape_meanfilter = {256, 6};
-    LaunchShape shape_blend = {256, 8}, shape_ptadd = {256, 8}, shape_decrypt = {256, 8};
+    // one block per work item by default (the autotuner's choice for the 32-image batch)
+    LaunchShape shape_radix = {256, 0}, shape_lookup = {256, 0}, shape_meanfilter = {256, 0};
+    LaunchShape shape_blend = {256, 0}, shape_ptadd = {256, 0}, shape_decrypt = {256, 0};
     LaunchShape shape_fused = {1024, 1};
     int fused_schedule = 0;   // ichee_encrypt_meanfilter_batch: 0 = two batched kernels, 1 = fused kernel
 };

@@ -368,8 +368,9 @@ extern "C" ichee_status ichee_autotune_batch(ichee_ctx* c, const ichee_cache* k,
         metas[i].level = (u32)(c->L - 1);
         metas[i].scale = c->delta;
     }
+    // blocks_per_sm = 0: one block per work item, the launch shape of the single-image kernels
     const LaunchShape cands[] = {{128, 4}, {128, 8}, {128, 16}, {256, 2}, {256, 4}, {256, 8},
-                                 {512, 1}, {512, 2}, {512, 4}};
+                                 {512, 1}, {512, 2}, {512, 4}, {256, 0}, {512, 0}};
     uint32_t nrep = 0;
     const uint32_t cap = n_report ? *n_report : 0;
     auto time_it = [&](auto&& run, float* best) -> ichee_status {
@@ -536,7 +537,7 @@ extern "C" ichee_status ichee_set_tuned_shape(ichee_ctx* c, uint32_t kind, uint3
     const bool fused = kind == ICHEE_TUNE_FUSED;
     if (!(threads == 128 || threads == 256 || threads == 512 || (fused && threads == 1024)))
         return fail(ICHEE_EINVAL, "threads %u not supported for kind %u", threads, kind);
-    if (blocks_per_sm < 1 || blocks_per_sm > 32) return fail(ICHEE_EINVAL, "blocks_per_sm %u outside [1, 32]", blocks_per_sm);
+    if (blocks_per_sm > 32) return fail(ICHEE_EINVAL, "blocks_per_sm %u above 32", blocks_per_sm);
     if ((kind == ICHEE_TUNE_MEANFILTER) && (uint32_t)(c->n / 2) < threads)
         return fail(ICHEE_EINVAL, "threads %u above N/2 for the mean filter", threads);
     const LaunchShape ls = {(int)threads, (int)blocks_per_sm};

@@ -519,73 +519,83 @@ cudaError_t launch_radix_combine(const RadixArgs& a, cudaStream_t st)
 
 // Value lookup with the randomness pool: c = C[lut[p]] (+) Z[idx], idx = floor(w*M / 2^32)
 // from stream 4. Pixels whose value is not cached are left to another kernel.
-__device__ __forceinline__ void lookup_ct(const LookupArgs& a, int slot, u64 seed, u64 id, u64* ct)
+// One row (polynomial b, limb l: row = b L + l) of one pixel's ciphertext. The work is
+// ordered row-major -- row 0 of every pixel, then row 1, ... -- so that while a row is being
+// written only that row of the cached ciphertexts and of the pool is read: 256 x N x 8 bytes
+// (16 MB at N = 8192) plus the pool's, which stays in L2 even when the whole cache does not.
+__device__ __forceinline__ void lookup_row(const LookupArgs& a, int slot, u64 seed, u64 id, u64* ct, int row)
 {
     const int n = 1 << a.logn;
+    const int half = n / 2;
     const size_t ct_len = (size_t)2 * a.L * n;
-    const ulonglong2* c = reinterpret_cast<const ulonglong2*>(a.value_cts + (size_t)slot * ct_len);
+    const size_t base = (size_t)row * half;
+    const ulonglong2* c = reinterpret_cast<const ulonglong2*>(a.value_cts + (size_t)slot * ct_len) + base;
     const ulonglong2* z = nullptr;
     if (a.pool_size > 0) {
         u32 w = philox(seed, kStreamPool, id, 0).w[0];
         u32 idx = (u32)(((u64)w * a.pool_size) >> 32);
-        z = reinterpret_cast<const ulonglong2*>(a.pool + (size_t)idx * ct_len);
+        z = reinterpret_cast<const ulonglong2*>(a.pool + (size_t)idx * ct_len) + base;
     }
-    // Row by row (one modulus per row); four coefficient pairs per thread and round, their
-    // loads issued together.
-    ulonglong2* dst = reinterpret_cast<ulonglong2*>(ct);
-    const int half = n / 2;
-    for (int row = 0; row < 2 * a.L; ++row) {
-        const u64 q = a.q[row % a.L];
-        const size_t base = (size_t)row * half;
-        for (int i0 = threadIdx.x; i0 < half; i0 += 4 * blockDim.x) {
-            ulonglong2 v[4], w[4];
+    ulonglong2* dst = reinterpret_cast<ulonglong2*>(ct) + base;
+    const u64 q = a.q[row % a.L];
+    // four coefficient pairs per thread and round, their loads issued together
+    for (int i0 = threadIdx.x; i0 < half; i0 += 4 * blockDim.x) {
+        ulonglong2 v[4], w[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int i = i0 + u * blockDim.x;
-                v[u] = i < half ? __ldg(c + base + i) : make_ulonglong2(0, 0);
-                w[u] = (i < half && z != nullptr) ? __ldg(z + base + i) : make_ulonglong2(0, 0);
-            }
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * blockDim.x;
+            v[u] = i < half ? __ldg(c + i) : make_ulonglong2(0, 0);
+            w[u] = (i < half && z != nullptr) ? __ldg(z + i) : make_ulonglong2(0, 0);
+        }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int i = i0 + u * blockDim.x;
-                if (i >= half) continue;
-                if (z != nullptr) {
-                    v[u].x = add_mod(v[u].x, w[u].x, q);
-                    v[u].y = add_mod(v[u].y, w[u].y, q);
-                }
-                __stcs(dst + base + i, v[u]);
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i >= half) continue;
+            if (z != nullptr) {
+                v[u].x = add_mod(v[u].x, w[u].x, q);
+                v[u].y = add_mod(v[u].y, w[u].y, q);
             }
+            __stcs(dst + i, v[u]);
         }
     }
 }
 
+// Work item g = row * n_ct + pixel.
 __global__ void __launch_bounds__(256) k_lookup_combine(const __grid_constant__ LookupArgs a)
 {
     const size_t ct_len = (size_t)2 * a.L << a.logn;
-    for (u64 k = blockIdx.x; k < a.n_ct; k += gridDim.x) {
+    const u64 items = a.n_ct * 2 * a.L;
+    for (u64 g = blockIdx.x; g < items; g += gridDim.x) {
+        const int row = (int)(g / a.n_ct);
+        const u64 k = g % a.n_ct;
         const int slot = a.lut[a.pixels[k]];
         if (slot < 0) continue;
-        lookup_ct(a, slot, a.seed, a.id_base + k, a.out + k * ct_len);
+        lookup_row(a, slot, a.seed, a.id_base + k, a.out + k * ct_len, row);
     }
 }
 
+// Work item g = row * total + (pixel item of the batch), rows outermost across all segments.
 __global__ void __launch_bounds__(1024) k_lookup_combine_batch(const __grid_constant__ LookupArgs a,
                                                                const __grid_constant__ SegTable t)
 {
     const size_t ct_len = (size_t)2 * a.L << a.logn;
     const u64 total = t.start[t.n];
-    for (u64 g = blockIdx.x; g < total; g += gridDim.x) {
+    const u64 items = total * 2 * a.L;
+    for (u64 gg = blockIdx.x; gg < items; gg += gridDim.x) {
+        const int row = (int)(gg / total);
+        const u64 g = gg % total;
         const int s = seg_of(t, g);
         const u64 k = g - t.start[s];
         const int slot = a.lut[t.px[s][k]];
         if (slot < 0) continue;
-        lookup_ct(a, slot, t.seed[s], k, t.out[s] + k * ct_len);
+        lookup_row(a, slot, t.seed[s], k, t.out[s] + k * ct_len, row);
     }
 }
 
 static unsigned persistent_grid(u64 total, LaunchShape ls, int num_sms)
 {
-    const u64 cap = (u64)num_sms * (ls.blocks_per_sm > 0 ? ls.blocks_per_sm : 1);
+    // blocks_per_sm = 0: one block per work item (no grid-stride loop), capped at 2^31 - 1
+    const u64 cap = ls.blocks_per_sm > 0 ? (u64)num_sms * ls.blocks_per_sm : 0x7fffffffull;
     return (unsigned)(total < cap ? total : cap);
 }
 
@@ -603,14 +613,15 @@ cudaError_t launch_lookup_combine_batch(const LookupArgs& a, const SegTable& t, 
 {
     const u64 total = t.n > 0 ? t.start[t.n] : 0;
     if (total == 0) return cudaSuccess;
-    k_lookup_combine_batch<<<persistent_grid(total, ls, num_sms), ls.threads, 0, st>>>(a, t);
+    k_lookup_combine_batch<<<persistent_grid(total * 2 * a.L, ls, num_sms), ls.threads, 0, st>>>(a, t);
     return cudaGetLastError();
 }
 
 cudaError_t launch_lookup_combine(const LookupArgs& a, cudaStream_t st)
 {
     if (a.n_ct == 0) return cudaSuccess;
-    unsigned grid = (unsigned)(a.n_ct < (1u << 30) ? a.n_ct : (1u << 30));
+    const u64 items = a.n_ct * 2 * a.L;
+    unsigned grid = (unsigned)(items < (1u << 30) ? items : (1u << 30));
     k_lookup_combine<<<grid, 256, 0, st>>>(a);
     return cudaGetLastError();
 }

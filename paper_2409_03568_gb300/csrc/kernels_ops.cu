@@ -652,7 +652,8 @@ cudaError_t launch_blend(const OpsArgs& a, cudaStream_t st)
 
 static unsigned persistent_grid(u64 total, LaunchShape ls, int num_sms)
 {
-    const u64 cap = (u64)num_sms * (ls.blocks_per_sm > 0 ? ls.blocks_per_sm : 1);
+    // blocks_per_sm = 0: one block per work item (no grid-stride loop), capped at 2^31 - 1
+    const u64 cap = ls.blocks_per_sm > 0 ? (u64)num_sms * ls.blocks_per_sm : 0x7fffffffull;
     return (unsigned)(total < cap ? total : cap);
 }
 

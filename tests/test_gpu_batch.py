@@ -238,7 +238,7 @@ def test_fused_encrypt_meanfilter_equals_two_steps(ichee, ctx8192, base, randomi
 
 def test_set_tuned_shape_checks(ichee, ctx8192):
     ctx = ctx8192
-    for args in ((ichee.TUNE_RADIX, 1024, 2), (ichee.TUNE_FUSED, 2048, 1), (ichee.TUNE_RADIX, 256, 0),
+    for args in ((ichee.TUNE_RADIX, 1024, 2), (ichee.TUNE_FUSED, 2048, 1), (ichee.TUNE_RADIX, 256, 33),
                  (ichee.TUNE_SCHEDULE, 2, 0), (99, 256, 2)):
         with pytest.raises(ichee.IcheeError) as e:
             ichee.ichee_set_tuned_shape(ctx.handle, *args)
