@@ -275,7 +275,8 @@ ichee_status ichee_encrypt_batch(ichee_ctx* ctx, const ichee_cache* cache, const
  * ICHEE_OP_MEANFILTER3 (Sec. 4.4.1), ICHEE_OP_BRIGHTNESS / ICHEE_OP_PTADD (Sec. 4.4.2; args:
  * one constant per image) and ICHEE_OP_BLEND (args: alpha; d_b[i] the pattern of image i with
  * c or 1 channels). Results equal the single-image ichee_eval per image. Outputs must not
- * alias inputs. Other operations return ICHEE_EUNSUPPORTED.
+ * alias inputs, except that brightness / plaintext add may run in place (d_out[i] == d_a[i]:
+ * only coefficient 0 of c0 is rewritten). Other operations return ICHEE_EUNSUPPORTED.
  */
 ichee_status ichee_eval_batch(ichee_ctx* ctx, ichee_op op, const uint64_t* const* d_a, const ichee_ctimg_meta* ma,
                               const uint64_t* const* d_b, const ichee_ctimg_meta* mb, const double* op_args,

@@ -249,7 +249,8 @@ extern "C" ichee_status ichee_eval_batch(ichee_ctx* c, ichee_op op, const uint64
     if (s != ICHEE_OK) return s;
     for (uint32_t i = 0; i < n_images; ++i) {
         if (!d_out[i]) return fail(ICHEE_EINVAL, "null output for image %u", i);
-        if (d_out[i] == d_a[i]) return fail(ICHEE_EINVAL, "batched operations do not run in place");
+        if (d_out[i] == d_a[i] && op != ICHEE_OP_BRIGHTNESS && op != ICHEE_OP_PTADD)
+            return fail(ICHEE_EINVAL, "only brightness / plaintext add run in place");
         if (!same_scale(ma[i].scale, ma[0].scale)) return fail(ICHEE_ESCALE, "image %u has another scale", i);
     }
     CK(cudaSetDevice(c->device));

@@ -412,6 +412,11 @@ __global__ void __launch_bounds__(1024) k_ptadd_batch(const __grid_constant__ Op
     for (u64 g = blockIdx.x; g < total; g += gridDim.x) {
         const int s = seg_of(t, g);
         const u64 k = g - t.start[s];
+        if (t.in0[s] == t.out[s]) {   // in place: only coefficient 0 of c0 changes, per limb
+            u64* c0 = t.out[s] + k * 2 * (u64)limbs * n;
+            for (int l = threadIdx.x; l < limbs; l += blockDim.x) c0[(u64)l * n] = add_mod(c0[(u64)l * n], t.kadd[s][l], a.q[l]);
+            continue;
+        }
         const ulonglong2* src = reinterpret_cast<const ulonglong2*>(t.in0[s] + k * 2 * (u64)limbs * n);
         ulonglong2* dst = reinterpret_cast<ulonglong2*>(t.out[s] + k * 2 * (u64)limbs * n);
         for (int i = threadIdx.x; i < limbs * n; i += blockDim.x) {

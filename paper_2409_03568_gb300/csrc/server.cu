@@ -153,9 +153,8 @@ void sizes(const ichee_server* s, const ichee_request& r, size_t* dev, size_t* h
     switch (r.kind) {
     case ICHEE_REQ_MEANFILTER:
     case ICHEE_REQ_WATERMARK: d += Arena::round(n_ct * ctb(c, L - 2)); break;
-    case ICHEE_REQ_BRIGHTNESS: d += Arena::round(n_ct * ctb(c, L - 1)); break;
     case ICHEE_REQ_MATCH: d += Arena::round(ctb(c, L - 2)); break;
-    default: break;
+    default: break;   // brightness runs in place on the encrypted image
     }
     const u64 n_res = r.kind == ICHEE_REQ_MATCH ? 1 : n_ct;
     d += Arena::round(n_res * 8);
@@ -179,7 +178,7 @@ void carve(ichee_server* s, Req* q)
     switch (r.kind) {
     case ICHEE_REQ_MEANFILTER:
     case ICHEE_REQ_WATERMARK: q->ct_op = reinterpret_cast<u64*>(p); p += Arena::round(n_ct * ctb(c, L - 2)); break;
-    case ICHEE_REQ_BRIGHTNESS: q->ct_op = reinterpret_cast<u64*>(p); p += Arena::round(n_ct * ctb(c, L - 1)); break;
+    case ICHEE_REQ_BRIGHTNESS: q->ct_op = q->ct_a; break;   // in place
     case ICHEE_REQ_MATCH: q->ct_op = reinterpret_cast<u64*>(p); p += Arena::round(ctb(c, L - 2)); break;
     default: break;
     }

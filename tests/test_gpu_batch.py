@@ -103,6 +103,12 @@ def test_batch_ops_and_decrypt_equal_single(ichee, ctx8192):
     for i, m in enumerate(metas):
         single, _ = ctx.eval(ichee.OP_BRIGHTNESS, enc[i], m, args=(betas[i],))
         assert torch.equal(br[i], single), i
+    # the same in place on copies (every second image), the others out of place
+    cp = [e.clone() for e in enc]
+    outs = [cp[i] if i % 2 == 0 else ctx.empty_cts(m.n_ct, 2) for i, m in enumerate(metas)]
+    ichee.ichee_eval_batch(ctx.handle, ichee.OP_BRIGHTNESS, cp, metas, args=betas, outs=outs, stream=ctx.stream())
+    for i in range(len(metas)):
+        assert torch.equal(outs[i], br[i]), i
     # blend with a one-channel pattern per image
     pats = [inputs.binary_pattern(h, w, seed=70 + i).reshape(-1).copy() for i, (h, w, c) in enumerate(shapes)]
     pshapes = [(h, w, 1) for (h, w, c) in shapes]
