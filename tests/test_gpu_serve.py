@@ -144,4 +144,17 @@ def test_server_refuses_bad_requests(ichee, rings):
     with pytest.raises(ichee.IcheeError) as e:   # collected already
         ichee.ichee_server_wait(srv, t, timeout_ms=10)
     assert e.value.status == ichee.ETIMEOUT
+    # a request held back by the host: bounded waits time out, then it completes normally
+    r4, _, _, res4, _ = make_request(ichee, ctxs, ichee.REQ_ENCRYPT, 0, 3, 3, 1, 8, keep)
+    ichee.ichee_server_hold(srv, True)
+    t4 = ichee.ichee_server_submit(srv, r4)
+    for _ in range(2):
+        with pytest.raises(ichee.IcheeError) as e:
+            ichee.ichee_server_wait(srv, t4, timeout_ms=20)
+        assert e.value.status == ichee.ETIMEOUT
+    assert ichee.ichee_server_stats_get(srv)["pending"] == 1
+    ichee.ichee_server_hold(srv, False)
+    d = ichee.ichee_server_wait(srv, t4)
+    assert d.status == ichee.OK and d.t_done >= d.t_admit >= d.t_submit
+    assert np.max(np.abs(res4 - keep[-1][0].astype(np.float64))) < 1e-3
     ichee.ichee_server_destroy(srv)
