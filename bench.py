@@ -335,6 +335,13 @@ def run_ours(args):
         "clocks": clk,
     }
     out["extras"] = extras_ours(args, ctx, ichee, enc_out["fresh"], metas["fresh"], nz_ct, nz_meta, flush, alu_peak)
+    # measured integer throughput (outside the timed region): the rate behind the derived peak,
+    # and what the library's butterfly reaches alone in registers
+    imad_s, bfly_s = ichee.ichee_probe_int_throughput(local)
+    out["alu_probe"] = {"imad_per_sm_per_clk": round(imad_s / SM_COUNT / (sm_mhz * 1e6), 2),
+                        "butterfly_g_per_s": round(bfly_s / 1e9, 1),
+                        "dominant_frac_of_butterfly_rate": round(kernels[dominant]["achieved"] / (bfly_s / 1e9), 4)
+                        if kernels[dominant]["bound"] == "alu" else None}
     # launches of our kernels per step: 1 per encryption (2 for the frequent-value cache),
     # 1 per mean filter / brightness / blend, matching: 1 accumulate + 1 reduce + 2 inverse
     # transform/scale + digits + transform + MAC + transform + mod-down + rescale, 1 per decrypt

@@ -456,6 +456,16 @@ ichee_status ichee_sqdiff_sum_noalloc(ichee_ctx* ctx, const uint64_t* d_a, const
                                       ichee_ctimg_meta* mout, void* stream);
 
 /*
+ * Measurement utility (not part of the method): integer throughput of CUDA device `device`,
+ * the context of the rooflines of the transform kernels. Runs two register-only kernels for a
+ * few tens of milliseconds: 32-bit multiply-adds (*imad_per_s, operations per second over the
+ * whole GPU) and the library's forward butterfly with its Shoup product on 60-bit residues
+ * (*butterflies_per_s). Synchronous; allocates and frees a small output buffer. Errors: EINVAL,
+ * ECUDA.
+ */
+ichee_status ichee_probe_int_throughput(int device, double* imad_per_s, double* butterflies_per_s);
+
+/*
  * Wait for `stream` and collect errors of work enqueued on it (CUDA launch or execution
  * errors, the context's device-side status word). Returns ICHEE_OK, ICHEE_ECUDA or
  * ICHEE_ETIMEOUT and clears the status word.

@@ -105,6 +105,7 @@ _SIGS = {
     "ichee_keygen": (_st, [_vp, _u64, _u32, _vp]),
     "ichee_export_key": (_st, [_vp, ctypes.c_int, _vp, _sz, _vp]),
     "ichee_set_allocator": (_st, [_vp, _vp, _vp, _vp]),
+    "ichee_probe_int_throughput": (_st, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "ichee_build_cache": (_st, [_vp, ctypes.POINTER(CacheDesc), _vp, _sz, _u64, ctypes.POINTER(_vp), _vp]),
     "ichee_cache_free": (None, [_vp]),
     "ichee_cache_info": (_st, [_vp, ctypes.POINTER(_u32), _vp, ctypes.POINTER(_u32)]),
@@ -226,6 +227,13 @@ def ichee_set_allocator(ctx, alloc=None, free=None):
     a = ctypes.cast(alloc, ctypes.c_void_p) if alloc is not None else None
     f = ctypes.cast(free, ctypes.c_void_p) if free is not None else None
     _check(_lib.ichee_set_allocator(ctx, a, f, None))
+
+
+def ichee_probe_int_throughput(device=0):
+    """(32-bit multiply-adds per second, library butterflies per second) of the GPU."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.ichee_probe_int_throughput(device, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def ichee_export_key(ctx, which, host_array, stream=None):

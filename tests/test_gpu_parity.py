@@ -461,3 +461,12 @@ def test_error_paths(ichee):
     ctx.status()
     other.close()
     ctx.close()
+
+
+def test_integer_probe_reports_rates(ichee):
+    """The throughput probe runs and reports plausible rates (a measurement utility)."""
+    imad, bfly = ichee.ichee_probe_int_throughput(0)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    per_sm_per_ghz = imad / sms / 1e9
+    assert 8 < per_sm_per_ghz < 512
+    assert 1e9 < bfly < imad
