@@ -29,7 +29,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_2409_03568_gb300 import inputs, workloads as W  # noqa: E402
+from paper_2409_03568_gb300 import inputs, metrics as M, workloads as W  # noqa: E402
 
 METRIC = "pixel ciphertexts/s at N=8192 (fresh + cached encryption, image ops, decryption per step)"
 UNIT = "pixel-ct/s"
@@ -248,11 +248,18 @@ def run_ours(args):
         flush.zero_()
         step()
     torch.cuda.synchronize()
-    # correctness guard on the benchmarked outputs (decoded pixels of every encryption)
+    # correctness guard on the benchmarked outputs (decoded pixels of every encryption), and
+    # the image-quality figures of Sec. 4.3.2 / 4.4.1 on them (rounded decoded pixels)
+    quality = {}
     for m in methods:
-        err = float((dec_out[m].cpu().numpy() - img).__abs__().max())
+        dec = dec_out[m].cpu().numpy()
+        err = float(np.abs(dec - img).max())
         if err > 1e-3:
             raise RuntimeError("decode error %.3g for %s" % (err, m))
+        quality[m] = {"max_abs_error": err, "mse_rounded": M.mse(img, np.rint(dec))}
+    mf = np.clip(np.rint(dec_out["meanfilter3"].cpu().numpy()), 0, 255)
+    mf_mse = M.mse(img, mf)
+    quality["meanfilter3_vs_original"] = {"mse": round(mf_mse, 3), "psnr_db": round(M.psnr(mf_mse), 2)}
     phase_ms = {name: 0.0 for name, _ in phases}
     total_ms = 0.0
     clocks = ClockSampler(local)
@@ -333,6 +340,7 @@ def run_ours(args):
         "roofline": roof,
         "gpu_launches": None,
         "clocks": clk,
+        "quality": quality,
     }
     out["extras"] = extras_ours(args, ctx, ichee, enc_out["fresh"], metas["fresh"], nz_ct, nz_meta, flush, alu_peak)
     # measured integer throughput (outside the timed region): the rate behind the derived peak,

@@ -177,6 +177,17 @@ ichee_status ichee_set_allocator(ichee_ctx* ctx, ichee_alloc_fn alloc, ichee_fre
 ichee_status ichee_export_key(ichee_ctx* ctx, int which, void* host_out, size_t bytes, void* stream);
 
 /*
+ * Load a key exported from a context with the same parameters (same `which` numbering and
+ * layout as ichee_export_key), instead of or after ichee_keygen: for resuming from saved keys,
+ * or for a context that holds only the public and evaluation keys (it encrypts and evaluates;
+ * decryption there fails with EINVAL, as it has no secret key). The transformed forms the
+ * kernels use are derived on `stream`; the call synchronises it. Errors: EINVAL (size, a
+ * residue not below its modulus, a secret-key coefficient outside {-1, 0, 1}, no special prime
+ * for the evaluation key), ENOMEM, ECUDA.
+ */
+ichee_status ichee_import_key(ichee_ctx* ctx, int which, const void* host_in, size_t bytes, void* stream);
+
+/*
  * Build a cache (Sec. 3.2 radix / scanning / full caching, Sec. 3.3 randomness pool).
  * scan_pixels (host or device, n_scan bytes) is read for ICHEE_CACHE_FREQ only (may be NULL
  * otherwise). Cached ciphertexts are fresh encryptions keyed by `seed`: value slot j uses

@@ -6,6 +6,8 @@
 #include <cstring>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/ichee.h"
 #include "host_math.h"
 #include "ops.h"
@@ -22,6 +24,15 @@ ichee_status fail(ichee_status st, const char* fmt, ...);
             return ::ichee::fail(_e == cudaErrorMemoryAllocation ? ICHEE_ENOMEM : ICHEE_ECUDA, "%s failed: %s", \
                                  #call, cudaGetErrorString(_e));                           \
     } while (0)
+
+// NVTX range over a public entry point (shows up in Nsight / ncu timelines; a no-op without
+// a tool attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 }  // namespace ichee
 
@@ -88,7 +99,7 @@ struct ichee_ctx {
     u64* d_ninv = nullptr;       // [nmod] N^{-1} mod modulus, then [nmod] N^{-1} 2^64 (d_ninv_r)
     u64* d_ninv_r = nullptr;     // inside d_ninv: not freed separately
     CrtLevel crt[kMaxPrimes];    // index nl - 1
-    bool have_keys = false, have_evk = false;
+    bool have_pk = false, have_sk = false, have_evk = false;   // public key, secret key, evaluation key
     std::vector<int8_t> h_s;
     int8_t* d_s = nullptr;
     int8_t* d_srev = nullptr;

@@ -174,9 +174,10 @@ extern "C" ichee_status ichee_encrypt_meanfilter_batch(ichee_ctx* c, const ichee
                                                        ichee_ctimg_meta* metas_ct, ichee_ctimg_meta* metas_filtered,
                                                        void* stream)
 {
+    ichee::NvtxRange nvtx_range("ichee_encrypt_meanfilter_batch");
     if (!c || !k || !pixels || !d_ct_out || !d_filtered_out || !metas_ct || !metas_filtered)
         return fail(ICHEE_EINVAL, "null argument");
-    if (!c->have_keys) return fail(ICHEE_EINVAL, "run ichee_keygen first");
+    if (!c->have_pk) return fail(ICHEE_EINVAL, "no public key (ichee_keygen or ichee_import_key)");
     if (k->ctx != c) return fail(ICHEE_EMISMATCH, "cache belongs to another context");
     if (k->desc.kind != ICHEE_CACHE_RADIX) return fail(ICHEE_EUNSUPPORTED, "the fused pipeline needs a radix cache");
     if (c->L < 2) return fail(ICHEE_ELEVEL, "the mean filter needs a limb to drop");
@@ -218,8 +219,9 @@ extern "C" ichee_status ichee_encrypt_batch(ichee_ctx* c, const ichee_cache* k, 
                                             const ichee_image_desc* images, uint32_t n_images,
                                             uint64_t* const* d_ct_out, ichee_ctimg_meta* metas_out, void* stream)
 {
+    ichee::NvtxRange nvtx_range("ichee_encrypt_batch");
     if (!c || !pixels || !d_ct_out || !metas_out) return fail(ICHEE_EINVAL, "null argument");
-    if (!c->have_keys) return fail(ICHEE_EINVAL, "ichee_encrypt_batch: run ichee_keygen first");
+    if (!c->have_pk) return fail(ICHEE_EINVAL, "ichee_encrypt_batch: no public key");
     if (k && k->ctx != c) return fail(ICHEE_EMISMATCH, "cache belongs to another context");
     ichee_status s = check_desc(images, n_images);
     if (s != ICHEE_OK) return s;
@@ -244,6 +246,7 @@ extern "C" ichee_status ichee_eval_batch(ichee_ctx* c, ichee_op op, const uint64
                                          uint64_t* const* d_out, ichee_ctimg_meta* mout, uint32_t n_images,
                                          void* stream)
 {
+    ichee::NvtxRange nvtx_range("ichee_eval_batch");
     if (!c || !d_out || !mout) return fail(ICHEE_EINVAL, "null argument");
     ichee_status s = check_metas(c, d_a, ma, n_images, "a");
     if (s != ICHEE_OK) return s;
@@ -330,8 +333,9 @@ extern "C" ichee_status ichee_eval_batch(ichee_ctx* c, ichee_op op, const uint64
 extern "C" ichee_status ichee_decrypt_batch(ichee_ctx* c, const uint64_t* const* d_ct, const ichee_ctimg_meta* metas,
                                             double* const* d_out, uint32_t n_images, void* stream)
 {
+    ichee::NvtxRange nvtx_range("ichee_decrypt_batch");
     if (!c || !d_out) return fail(ICHEE_EINVAL, "null argument");
-    if (!c->have_keys) return fail(ICHEE_EINVAL, "no secret key");
+    if (!c->have_sk) return fail(ICHEE_EINVAL, "no secret key");
     ichee_status s = check_metas(c, d_ct, metas, n_images, "ciphertexts");
     if (s != ICHEE_OK) return s;
     for (uint32_t i = 0; i < n_images; ++i)
@@ -350,8 +354,9 @@ extern "C" ichee_status ichee_autotune_batch(ichee_ctx* c, const ichee_cache* k,
                                              uint64_t* const* d_ct, uint64_t* const* d_filtered,
                                              ichee_tune_entry* report, uint32_t* n_report, void* stream)
 {
+    ichee::NvtxRange nvtx_range("ichee_autotune_batch");
     if (!c || !pixels || !d_ct || !d_filtered) return fail(ICHEE_EINVAL, "null argument");
-    if (!c->have_keys) return fail(ICHEE_EINVAL, "run ichee_keygen first");
+    if (!c->have_pk) return fail(ICHEE_EINVAL, "no public key (ichee_keygen or ichee_import_key)");
     if (k && k->ctx != c) return fail(ICHEE_EMISMATCH, "cache belongs to another context");
     ichee_status s = check_desc(images, n_images);
     if (s != ICHEE_OK) return s;

@@ -240,8 +240,24 @@ extern "C" ichee_status ichee_ct_bytes(const ichee_ctx* c, uint32_t level, size_
 // ---------------------------------------------------------------------------------------
 // Key generation (Sec. 2.2.2, reading R1 for pk, R11 for evk)
 // ---------------------------------------------------------------------------------------
+// Key buffers of the context (allocated once, by keygen or the first import).
+static cudaError_t alloc_key_buffers(ichee_ctx* c)
+{
+    const size_t polyb = (size_t)c->n * 8;
+    cudaError_t e = cudaSuccess;
+    if (!c->d_s) {
+        if ((e = cudaMalloc(&c->d_s, c->n)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&c->d_srev, c->n)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&c->d_pk, 2 * c->L * polyb)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&c->d_pk_hat, 2 * c->L * polyb)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&c->d_pk_hat_p, 2 * c->L * polyb)) != cudaSuccess) return e;
+    }
+    return e;
+}
+
 extern "C" ichee_status ichee_keygen(ichee_ctx* c, uint64_t seed, uint32_t flags, void* stream)
 {
+    ichee::NvtxRange nvtx_range("ichee_keygen");
     if (!c) return fail(ICHEE_EINVAL, "null context");
     const bool want_evk = (flags & ICHEE_WITH_EVK) != 0;
     if (want_evk && !c->P) return fail(ICHEE_EINVAL, "evaluation key needs special_bits > 0");
@@ -249,13 +265,7 @@ extern "C" ichee_status ichee_keygen(ichee_ctx* c, uint64_t seed, uint32_t flags
     cudaStream_t st = (cudaStream_t)stream;
     const int n = c->n, L = c->L;
     const size_t polyb = (size_t)n * 8;
-    if (!c->d_s) {
-        CK(cudaMalloc(&c->d_s, n));
-        CK(cudaMalloc(&c->d_srev, n));
-        CK(cudaMalloc(&c->d_pk, 2 * L * polyb));
-        CK(cudaMalloc(&c->d_pk_hat, 2 * L * polyb));
-        CK(cudaMalloc(&c->d_pk_hat_p, 2 * L * polyb));
-    }
+    CK(alloc_key_buffers(c));
     const int nm = L + 1;  // moduli of the evaluation key
     const size_t tmp_polys = want_evk ? (size_t)(3 * L * nm + 2 * nm) : (size_t)(3 * L);
     int8_t* d_e = nullptr;
@@ -351,25 +361,29 @@ extern "C" ichee_status ichee_keygen(ichee_ctx* c, uint64_t seed, uint32_t flags
         c->have_evk = true;
     }
 #undef KCK
-    c->have_keys = true;
+    c->have_pk = c->have_sk = true;
     return done(ICHEE_OK);
 }
 
 extern "C" ichee_status ichee_export_key(ichee_ctx* c, int which, void* host_out, size_t bytes, void* stream)
 {
     if (!c || !host_out) return fail(ICHEE_EINVAL, "null argument");
-    if (!c->have_keys) return fail(ICHEE_EINVAL, "no keys");
     CK(cudaSetDevice(c->device));
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n = (size_t)c->n;
     if (which == 0) {
+        if (!c->have_sk) return fail(ICHEE_EINVAL, "no secret key");
         if (bytes != n) return fail(ICHEE_EINVAL, "secret key is %zu bytes", n);
         std::memcpy(host_out, c->h_s.data(), n);
         return ICHEE_OK;
     }
     const void* src = nullptr;
     size_t want = 0;
-    if (which == 1) { src = c->d_pk; want = 2 * (size_t)c->L * n * 8; }
+    if (which == 1) {
+        if (!c->have_pk) return fail(ICHEE_EINVAL, "no public key");
+        src = c->d_pk;
+        want = 2 * (size_t)c->L * n * 8;
+    }
     else if (which == 2) {
         if (!c->have_evk) return fail(ICHEE_EINVAL, "no evaluation key");
         src = c->d_evk;
@@ -379,6 +393,76 @@ extern "C" ichee_status ichee_export_key(ichee_ctx* c, int which, void* host_out
     CK(cudaMemcpyAsync(host_out, src, want, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     return ICHEE_OK;
+}
+
+extern "C" ichee_status ichee_import_key(ichee_ctx* c, int which, const void* host_in, size_t bytes, void* stream)
+{
+    if (!c || !host_in) return fail(ICHEE_EINVAL, "null argument");
+    CK(cudaSetDevice(c->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = c->n, L = c->L, nm = L + 1;
+    const size_t polyb = (size_t)n * 8;
+    std::vector<int> id = iota_idx(kMaxModuli);
+    CK(alloc_key_buffers(c));
+    if (which == 0) {
+        if (bytes != (size_t)n) return fail(ICHEE_EINVAL, "secret key is %d bytes, got %zu", n, bytes);
+        const int8_t* s = static_cast<const int8_t*>(host_in);
+        for (int j = 0; j < n; ++j)
+            if (s[j] < -1 || s[j] > 1) return fail(ICHEE_EINVAL, "secret key coefficient %d is %d, not ternary", j, s[j]);
+        c->h_s.assign(s, s + n);
+        std::vector<int8_t> srev(n);
+        srev[0] = s[0];
+        for (int j = 1; j < n; ++j) srev[j] = (int8_t)(-s[n - j]);
+        CK(cudaMemcpyAsync(c->d_s, s, n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(c->d_srev, srev.data(), n, cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        c->have_sk = true;
+        return ICHEE_OK;
+    }
+    if (which == 1) {
+        if (bytes != 2 * (size_t)L * polyb) return fail(ICHEE_EINVAL, "public key is %zu bytes, got %zu", 2 * L * polyb, bytes);
+        const u64* k = static_cast<const u64*>(host_in);
+        for (int b = 0; b < 2; ++b)
+            for (int l = 0; l < L; ++l)
+                for (int j = 0; j < n; ++j)
+                    if (k[((size_t)b * L + l) * n + j] >= c->q[l]) return fail(ICHEE_EINVAL, "public key residue out of range");
+        const RnsArgs rl = rns_prefix(c, L);
+        CK(cudaMemcpyAsync(c->d_pk, k, 2 * L * polyb, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(c->d_pk_hat, c->d_pk, 2 * L * polyb, cudaMemcpyDeviceToDevice, st));
+        CK(launch_ntt_fwd(rl, batch(c->d_pk_hat, 2 * L, L, id.data()), st));
+        CK(launch_scale_const(rl, batch(c->d_pk_hat, 2 * L, L, id.data()), c->d_ninv, st));
+        CK(launch_shoup_companions(rl, batch(c->d_pk_hat, 2 * L, L, id.data()), c->d_pk_hat_p, st));
+        CK(cudaStreamSynchronize(st));
+        c->have_pk = true;
+        return ICHEE_OK;
+    }
+    if (which == 2) {
+        if (!c->P) return fail(ICHEE_EINVAL, "evaluation key needs special_bits > 0");
+        const size_t want = (size_t)L * 2 * nm * polyb;
+        if (bytes != want) return fail(ICHEE_EINVAL, "evaluation key is %zu bytes, got %zu", want, bytes);
+        const u64* k = static_cast<const u64*>(host_in);
+        for (int j = 0; j < L; ++j)
+            for (int b = 0; b < 2; ++b)
+                for (int i = 0; i < nm; ++i)
+                    for (int x = 0; x < n; ++x)
+                        if (k[(((size_t)j * 2 + b) * nm + i) * n + x] >= c->q[i])
+                            return fail(ICHEE_EINVAL, "evaluation key residue out of range");
+        if (!c->d_evk) {
+            CK(cudaMalloc(&c->d_evk, want));
+            CK(cudaMalloc(&c->d_evk_hat, want));
+            CK(cudaMalloc(&c->d_evk_hat_p, want));
+        }
+        const RnsArgs rm = c->rns;
+        CK(cudaMemcpyAsync(c->d_evk, k, want, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(c->d_evk_hat, c->d_evk, want, cudaMemcpyDeviceToDevice, st));
+        CK(launch_ntt_fwd(rm, batch(c->d_evk_hat, L * 2 * nm, nm, id.data()), st));
+        CK(launch_scale_const(rm, batch(c->d_evk_hat, L * 2 * nm, nm, id.data()), c->d_ninv, st));
+        CK(launch_shoup_companions(rm, batch(c->d_evk_hat, L * 2 * nm, nm, id.data()), c->d_evk_hat_p, st));
+        CK(cudaStreamSynchronize(st));
+        c->have_evk = true;
+        return ICHEE_OK;
+    }
+    return fail(ICHEE_EINVAL, "unknown key %d", which);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -491,9 +575,10 @@ static ichee_status build_radix(ichee_ctx* c, ichee_cache* k, u32 base, u32 rand
 extern "C" ichee_status ichee_build_cache(ichee_ctx* c, const ichee_cache_desc* d, const uint8_t* scan, size_t n_scan,
                                           uint64_t seed, ichee_cache** out, void* stream)
 {
+    ichee::NvtxRange nvtx_range("ichee_build_cache");
     if (!c || !d || !out) return fail(ICHEE_EINVAL, "null argument");
     *out = nullptr;
-    if (!c->have_keys) return fail(ICHEE_EINVAL, "ichee_build_cache: run ichee_keygen first");
+    if (!c->have_pk) return fail(ICHEE_EINVAL, "ichee_build_cache: no public key");
     const bool needs_radix = d->kind == ICHEE_CACHE_RADIX || (d->kind == ICHEE_CACHE_FREQ && d->miss_policy == 1);
     if (needs_radix && (d->radix_base < 2 || d->radix_base > 16))
         return fail(ICHEE_EINVAL, "radix_base %u outside [2, 16]", d->radix_base);
@@ -623,8 +708,9 @@ extern "C" ichee_status ichee_encrypt_image(ichee_ctx* c, const ichee_cache* k, 
                                             uint32_t w, uint32_t ch, uint64_t seed, uint64_t* d_out,
                                             ichee_ctimg_meta* meta, void* stream)
 {
+    ichee::NvtxRange nvtx_range("ichee_encrypt_image");
     if (!c || !pixels || !d_out || !meta) return fail(ICHEE_EINVAL, "null argument");
-    if (!c->have_keys) return fail(ICHEE_EINVAL, "ichee_encrypt_image: run ichee_keygen first");
+    if (!c->have_pk) return fail(ICHEE_EINVAL, "ichee_encrypt_image: no public key (ichee_keygen or ichee_import_key)");
     if (k && k->ctx != c) return fail(ICHEE_EMISMATCH, "cache belongs to another context");
     const u64 n_ct = (u64)h * w * ch;
     if (n_ct == 0) return fail(ICHEE_EINVAL, "empty image %ux%ux%u", h, w, ch);
@@ -740,6 +826,7 @@ extern "C" ichee_status ichee_eval(ichee_ctx* c, ichee_op op, const uint64_t* d_
                                    const uint64_t* d_b, const ichee_ctimg_meta* mb, const double* args, uint32_t n_args,
                                    uint64_t* d_out, ichee_ctimg_meta* mout, void* stream)
 {
+    ichee::NvtxRange nvtx_range("ichee_eval");
     if (!c || !mout) return fail(ICHEE_EINVAL, "null argument");
     CK(cudaSetDevice(c->device));
     ichee_status s = check_img(c, d_a, ma, "a");
@@ -997,7 +1084,7 @@ static ichee_status decrypt_impl(ichee_ctx* c, const uint64_t* d_ct, const ichee
                                  uint64_t* residues, void* stream)
 {
     if (!c || !out) return fail(ICHEE_EINVAL, "null argument");
-    if (!c->have_keys) return fail(ICHEE_EINVAL, "no secret key");
+    if (!c->have_sk) return fail(ICHEE_EINVAL, "no secret key");
     CK(cudaSetDevice(c->device));
     ichee_status s = check_img(c, d_ct, m, "ciphertexts");
     if (s != ICHEE_OK) return s;
@@ -1037,6 +1124,7 @@ static ichee_status decrypt_impl(ichee_ctx* c, const uint64_t* d_ct, const ichee
 extern "C" ichee_status ichee_decrypt_image(ichee_ctx* c, const uint64_t* d_ct, const ichee_ctimg_meta* m, double* out,
                                             void* stream)
 {
+    ichee::NvtxRange nvtx_range("ichee_decrypt_image");
     return decrypt_impl(c, d_ct, m, out, nullptr, stream);
 }
 

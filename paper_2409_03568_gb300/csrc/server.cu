@@ -190,6 +190,7 @@ void carve(ichee_server* s, Req* q)
 // Launch one admission round for the requests of one ring on that ring's stream.
 ichee_status launch_round(ichee_server* s, uint32_t ring, const std::vector<Req*>& reqs, cudaStream_t st)
 {
+    ichee::NvtxRange nvtx_range("ichee_server round");
     ichee_ctx* c = s->rings[ring];
     const ichee_cache* k = s->caches[ring];
     // inputs to the device
@@ -396,7 +397,8 @@ extern "C" ichee_status ichee_server_create(ichee_ctx* const* rings, const ichee
     if (!rings || !caches || !out || n_rings == 0 || n_rings > 8) return fail(ICHEE_EINVAL, "bad ring list");
     *out = nullptr;
     for (uint32_t i = 0; i < n_rings; ++i) {
-        if (!rings[i] || !rings[i]->have_keys) return fail(ICHEE_EINVAL, "ring %u has no keys", i);
+        if (!rings[i] || !rings[i]->have_pk || !rings[i]->have_sk)
+            return fail(ICHEE_EINVAL, "ring %u needs its public and secret keys", i);
         if (rings[i]->device != rings[0]->device) return fail(ICHEE_EINVAL, "all rings must share one device");
         if (rings[i]->L < 2) return fail(ICHEE_EINVAL, "ring %u needs two limbs for its operations", i);
         if (caches[i] && caches[i]->ctx != rings[i]) return fail(ICHEE_EMISMATCH, "cache %u belongs to another ring", i);

@@ -104,6 +104,7 @@ _SIGS = {
     "ichee_ctx_primes": (_st, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     "ichee_keygen": (_st, [_vp, _u64, _u32, _vp]),
     "ichee_export_key": (_st, [_vp, ctypes.c_int, _vp, _sz, _vp]),
+    "ichee_import_key": (_st, [_vp, ctypes.c_int, _vp, _sz, _vp]),
     "ichee_set_allocator": (_st, [_vp, _vp, _vp, _vp]),
     "ichee_probe_int_throughput": (_st, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "ichee_build_cache": (_st, [_vp, ctypes.POINTER(CacheDesc), _vp, _sz, _u64, ctypes.POINTER(_vp), _vp]),
@@ -238,6 +239,14 @@ def ichee_probe_int_throughput(device=0):
 
 def ichee_export_key(ctx, which, host_array, stream=None):
     _check(_lib.ichee_export_key(ctx, which, _ptr(host_array), host_array.nbytes, stream))
+
+
+def ichee_import_key(ctx, which, host_array, stream=None):
+    """which: 0 = secret key int8[N], 1 = public key uint64[2][L][N], 2 = evaluation key
+    uint64[L][2][L+1][N] (numpy arrays, as ichee_export_key writes them)."""
+    import numpy as np
+    arr = np.ascontiguousarray(host_array)
+    _check(_lib.ichee_import_key(ctx, which, arr.ctypes.data, arr.nbytes, stream))
 
 
 def ichee_build_cache(ctx, desc, scan=None, n_scan=0, seed=0, stream=None):
@@ -486,6 +495,38 @@ class Context:
 
     def keygen(self, seed, with_evk=False):
         ichee_keygen(self.handle, seed, WITH_EVK if with_evk else 0, self.stream())
+
+    def save_keys(self, path, secret=True, evk=True):
+        """Write the keys (and the prime chain they belong to) to an .npz file. secret=False
+        leaves the secret key out, e.g. for a server that only encrypts and evaluates."""
+        import numpy as np
+        n, L = self.n, self.L
+        parts = {"primes": np.array(self.q + ([self.P] if self.P else []), dtype=np.uint64)}
+        pk = np.zeros((2, L, n), dtype=np.uint64)
+        ichee_export_key(self.handle, 1, pk, self.stream())
+        parts["pk"] = pk
+        if secret:
+            s = np.zeros(n, dtype=np.int8)
+            ichee_export_key(self.handle, 0, s, self.stream())
+            parts["s"] = s
+        if evk:
+            e = np.zeros((L, 2, L + 1, n), dtype=np.uint64)
+            ichee_export_key(self.handle, 2, e, self.stream())
+            parts["evk"] = e
+        np.savez(path, **parts)
+
+    def load_keys(self, path):
+        """Load keys written by save_keys into this context (same parameters required)."""
+        import numpy as np
+        with np.load(path) as z:
+            primes = [int(x) for x in z["primes"]]
+            if primes != self.q + ([self.P] if self.P else []):
+                raise IcheeError(EINVAL, "keys belong to another prime chain")
+            ichee_import_key(self.handle, 1, z["pk"], self.stream())
+            if "s" in z:
+                ichee_import_key(self.handle, 0, z["s"], self.stream())
+            if "evk" in z:
+                ichee_import_key(self.handle, 2, z["evk"], self.stream())
 
     def ct_words(self, level):
         return ichee_ct_bytes(self.handle, level) // 8

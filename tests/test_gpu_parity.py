@@ -389,6 +389,50 @@ def test_ring16384_keys_encryption_and_matching(ichee):
     ctx.close()
 
 
+# ------------------------------------------------------------- saved keys, key-only contexts
+def test_saved_keys_resume_and_public_only_context(ichee, tmp_path):
+    """Keys saved and loaded into a fresh context give the same ciphertexts; a context holding
+    only the public and evaluation keys encrypts and matches but cannot decrypt, and the
+    secret-key holder decrypts its results; bad imports are refused."""
+    wl = SMALL_OPS
+    a = inputs.random_field_image(3, 4, seed=81).reshape(-1).copy()
+    b = inputs.noisy_copy(a, seed=82)
+    src = gpu_for(ichee, wl, with_evk=True)
+    src.save_keys(str(tmp_path / "all.npz"))
+    src.save_keys(str(tmp_path / "public.npz"), secret=False)
+    ra, ma = src.encrypt(torch.from_numpy(a).cuda(), 3, 4, 1, 5)
+    rb, mb = src.encrypt(torch.from_numpy(b).cuda(), 3, 4, 1, 6)
+    rm, mm = src.eval(ichee.OP_SQDIFF_SUM, ra, ma, rb, mb, out_n_ct=1, out_level=2)
+    resumed = ichee.Context(**W.ctx_kwargs(wl))
+    resumed.load_keys(str(tmp_path / "all.npz"))
+    ga, _ = resumed.encrypt(torch.from_numpy(a).cuda(), 3, 4, 1, 5)
+    assert torch.equal(ga, ra)
+    np.testing.assert_array_equal(resumed.decrypt(ga, ma).cpu().numpy(), src.decrypt(ra, ma).cpu().numpy())
+    server = ichee.Context(**W.ctx_kwargs(wl))
+    server.load_keys(str(tmp_path / "public.npz"))
+    sa, sma = server.encrypt(torch.from_numpy(a).cuda(), 3, 4, 1, 5)
+    sb, smb = server.encrypt(torch.from_numpy(b).cuda(), 3, 4, 1, 6)
+    sm_, smm = server.eval(ichee.OP_SQDIFF_SUM, sa, sma, sb, smb, out_n_ct=1, out_level=2)
+    assert torch.equal(sa, ra) and torch.equal(sm_, rm)
+    with pytest.raises(ichee.IcheeError) as e:
+        server.decrypt(sm_, smm)
+    assert e.value.status == ichee.EINVAL
+    assert abs(float(src.decrypt(sm_, smm).cpu()[0]) - float(((a.astype(float) - b) ** 2).sum())) < 1e-2
+    bad = np.zeros(server.n, dtype=np.int8)
+    bad[3] = 2
+    with pytest.raises(ichee.IcheeError) as e:
+        ichee.ichee_import_key(server.handle, 0, bad)
+    assert e.value.status == ichee.EINVAL
+    with pytest.raises(ichee.IcheeError) as e:
+        ichee.ichee_import_key(server.handle, 1, np.zeros(7, dtype=np.uint64))
+    assert e.value.status == ichee.EINVAL
+    other = ichee.Context(**W.ctx_kwargs(W.TOY))
+    with pytest.raises(ichee.IcheeError):
+        other.load_keys(str(tmp_path / "all.npz"))
+    for c in (src, resumed, server, other):
+        c.close()
+
+
 # ------------------------------------------------------------- working-memory allocator
 def test_torch_allocator_serves_working_memory(ichee):
     """Host-buffer encryption and decryption (staging) and matching (scratch) through PyTorch's
