@@ -17,7 +17,12 @@
  * known-answer vectors, closed-form noise bounds, the paper's worked radix example
  * (Sec. 3.3) and its MSE/PSNR table (Sec. 4.3.2).
  *
- * Readings of the paper that this file fixes are listed in DESIGN.md ("Readings").
+ * Where the paper is silent this file fixes one reading and states it next to the code:
+ * the key / encryption sign convention, the constant-polynomial pixel encoding, the prime
+ * chain (largest primes = 1 mod 2N below each bit size), Philox4x32-10 with counters
+ * (block, stream, ciphertext id), the CDT Gaussian and ternary samplers, the signed-digit
+ * form of the radix randomness, the pool index rule, centered rounding in rescale and
+ * hybrid key switching with one special prime.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -312,7 +317,7 @@ static void small_to_residues(u32 n, const int8_t *x, u64 q, u64 *out)
 
 /* ------------------------------------------------------------------------- */
 /* CKKS (Sec. 2.2.2, with the sign convention of the paper's library: the      */
-/* printed formulas do not cancel as written, reading R1).       */
+/* printed KeyGen / Enc / Dec do not cancel as written -- r*a*(1 - s^2) stays). */
 /*   pk = (pk0, pk1) = (-a*s + e, a)                                           */
 /*   Enc(m) = (v*pk0 + e0 + m, v*pk1 + e1),  Dec(c) = c0 + c1*s                 */
 /* Layouts: polynomial [n]; ciphertext [2][limbs][n] (coefficient domain).      */
