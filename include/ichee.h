@@ -146,8 +146,9 @@ ichee_status ichee_ctx_primes(const ichee_ctx* ctx, uint64_t* q_out, uint64_t* p
  * pk = (-a*s + e, a), and with flags & ICHEE_WITH_EVK the evaluation key used by
  * ICHEE_OP_SQDIFF_SUM and ICHEE_OP_SQDIFF (hybrid key switching with the special prime; needs
  * special_bits > 0).
- * Deterministic in `seed`. Keys stay in the context. Enqueued on `stream`; the call waits for
- * its own set-up copies. Errors: EINVAL (evk without a special prime), ECUDA.
+ * Deterministic in `seed`. Keys stay in the context (ichee_export_key / ichee_import_key move
+ * them out and in). Enqueued on `stream`; the call waits for its own set-up copies. Errors:
+ * EINVAL (evk without a special prime), ECUDA.
  */
 ichee_status ichee_keygen(ichee_ctx* ctx, uint64_t seed, uint32_t flags, void* stream);
 
@@ -232,7 +233,8 @@ ichee_status ichee_encrypt_image(ichee_ctx* ctx, const ichee_cache* cache, const
 
 /*
  * Apply an image operation (see ichee_op). d_a / d_b / d_out are device ciphertext images
- * described by ma / mb / mout; d_b and mb are used by ADD, SUB, BLEND and SQDIFF_SUM only.
+ * described by ma / mb / mout; d_b and mb are used by ADD, SUB, BLEND, SQDIFF_SUM and SQDIFF
+ * only.
  * op_args holds the operation's real-valued arguments (host). d_out must not overlap the
  * inputs, except that PTADD, BRIGHTNESS and WATERMARK_PIXEL may run in place (d_out == d_a).
  * *mout receives the result's shape, level and scale. Errors: EINVAL, ELEVEL (no limb to
@@ -245,7 +247,8 @@ ichee_status ichee_eval(ichee_ctx* ctx, ichee_op op, const uint64_t* d_a, const 
 /*
  * Decrypt and decode (Sec. 2.2.2 decryption; a pixel is read from coefficient 0 of
  * c0 + c1*s): exact CRT of the residues to the centered integer, divided by meta->scale, one
- * double per ciphertext. out: host or device, n_ct doubles. Errors: EINVAL, ECUDA.
+ * double per ciphertext. out: host or device, n_ct doubles. Needs the secret key. Errors:
+ * EINVAL (no secret key, arguments), ECUDA.
  */
 ichee_status ichee_decrypt_image(ichee_ctx* ctx, const uint64_t* d_ct, const ichee_ctimg_meta* meta, double* out,
                                  void* stream);
