@@ -444,17 +444,15 @@ extern "C" ichee_status ichee_server_submit(ichee_server* s, const ichee_request
         return fail(ICHEE_EUNSUPPORTED, "ring %u has no evaluation key for matching", r->ring);
     if (r->kind == ICHEE_REQ_MEANFILTER && s->rings[r->ring]->n / 2 < s->rings[r->ring]->shape_meanfilter.threads)
         return fail(ICHEE_EUNSUPPORTED, "ring too small for the mean filter");
+    size_t dev_bytes = 0, host_bytes = 0;
+    sizes(s, *r, &dev_bytes, &host_bytes);
+    if (dev_bytes > s->dev.size())
+        return fail(ICHEE_EINVAL, "request needs %zu bytes, more than the %zu-byte budget", dev_bytes, s->dev.size());
+    if (host_bytes > s->host.size()) return fail(ICHEE_EINVAL, "request needs %zu bytes of host staging", host_bytes);
     Req* q = new Req();
     q->r = *r;
-    sizes(s, *r, &q->bytes, &q->hbytes);
-    if (q->bytes > s->dev.size()) {
-        delete q;
-        return fail(ICHEE_EINVAL, "request needs %zu bytes, more than the %zu-byte budget", q->bytes, s->dev.size());
-    }
-    if (q->hbytes > s->host.size()) {
-        delete q;
-        return fail(ICHEE_EINVAL, "request needs %zu bytes of host staging", q->hbytes);
-    }
+    q->bytes = dev_bytes;
+    q->hbytes = host_bytes;
     std::lock_guard<std::mutex> lock(s->mu);
     if (s->stop) {
         delete q;
