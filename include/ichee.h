@@ -422,7 +422,9 @@ typedef struct ichee_server ichee_server;
  * Start a server over n_rings contexts (keys made; matching needs the evaluation key) sharing
  * one device, each with its cache (NULL = fresh encryption). Reserves hbm_budget_bytes of
  * device memory and 512 MiB of pinned host staging; at most max_inflight requests (0 = 256)
- * are admitted at once. Errors: EINVAL, EMISMATCH, ENOMEM, ECUDA.
+ * are admitted at once. While the server runs, its worker thread uses the ring contexts and
+ * caches: the caller must not use them itself until ichee_server_destroy has returned.
+ * Errors: EINVAL, EMISMATCH, ENOMEM, ECUDA.
  */
 ichee_status ichee_server_create(ichee_ctx* const* rings, const ichee_cache* const* caches, uint32_t n_rings,
                                  size_t hbm_budget_bytes, uint32_t max_inflight, ichee_server** out);
