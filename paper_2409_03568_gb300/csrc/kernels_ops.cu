@@ -249,8 +249,15 @@ __global__ void __launch_bounds__(1024) k_radix_meanfilter3_batch(const __grid_c
         const int c2 = pc * 32 + lane;
         const uint8_t* px = t.px[s];
         const u64 seed = t.seed[s];
-        ulonglong2* enc = reinterpret_cast<ulonglong2*>(t.out[s]) + (size_t)b * LIMBS * half + c2;
-        ulonglong2* flt = reinterpret_cast<ulonglong2*>(t.out2[s]) + (size_t)b * (LIMBS - 1) * half + c2;
+        // this thread's coefficient pair in pixel (0, x) of each output; one row further is
+        // a fixed stride (no per-row 64-bit products on the multiply pipe)
+        const size_t row_px = (size_t)w * C;
+        ulonglong2* enc = reinterpret_cast<ulonglong2*>(t.out[s]) + (size_t)b * LIMBS * half + c2 +
+                          ((size_t)x * C + ch) * ct_u2;
+        ulonglong2* flt = reinterpret_cast<ulonglong2*>(t.out2[s]) + (size_t)b * (LIMBS - 1) * half + c2 +
+                          ((size_t)x * C + ch) * out_u2;
+        const size_t enc_row = row_px * ct_u2, flt_row = row_px * out_u2;
+        const ulonglong2* mult_b = mult + (size_t)b * LIMBS * half + c2;
         // digit codes of this column, 32 rows at a time: lane j holds row code_base + j, one
         // byte per cached power (signed digit + r)
         u64 code = 0;
@@ -282,7 +289,8 @@ __global__ void __launch_bounds__(1024) k_radix_meanfilter3_batch(const __grid_c
             for (int kk = 0; kk < ra.n_pow; ++kk) {
                 const int dr = (int)((cd >> (8 * kk)) & 0xffu);
                 if (dr == ra.r) continue;
-                const ulonglong2* src = mult + (size_t)(kk * width + dr) * ct_u2 + (size_t)b * LIMBS * half + c2;
+                // (kk * width + dr) < 8 * 33 and ct_u2 <= 2^17: the offset fits 32 bits
+                const ulonglong2* src = mult_b + (u32)(kk * width + dr) * (u32)ct_u2;
                 ulonglong2 m[LIMBS];
 #pragma unroll
                 for (int l = 0; l < LIMBS; ++l) m[l] = __ldg(src + (size_t)l * half);
@@ -294,7 +302,7 @@ __global__ void __launch_bounds__(1024) k_radix_meanfilter3_batch(const __grid_c
             }
         };
         auto store_enc = [&](int yy, const ulonglong2 (&v)[LIMBS]) {
-            ulonglong2* o = enc + (((size_t)yy * w + x) * C + ch) * ct_u2;
+            ulonglong2* o = enc + (size_t)yy * enc_row;
 #pragma unroll
             for (int l = 0; l < LIMBS; ++l) __stcs(o + (size_t)l * half, v[l]);
         };
@@ -322,7 +330,7 @@ __global__ void __launch_bounds__(1024) k_radix_meanfilter3_batch(const __grid_c
                 const ulonglong2 ht0 = vl[(LIMBS - 1) * 32], ht1 = vb[(LIMBS - 1) * 32], ht2 = vr[(LIMBS - 1) * 32];
                 const u64 tx = shoup(ht0.x + ht1.x + ht2.x, a.k0[LIMBS - 1], a.k0p[LIMBS - 1], qt);
                 const u64 ty = shoup(ht0.y + ht1.y + ht2.y, a.k0[LIMBS - 1], a.k0p[LIMBS - 1], qt);
-                ulonglong2* o = flt + (((size_t)y * w + x) * C + ch) * out_u2;
+                ulonglong2* o = flt + (size_t)y * flt_row;
 #pragma unroll
                 for (int j = 0; j < LIMBS - 1; ++j) {
                     const u64 qj = a.q[j];
