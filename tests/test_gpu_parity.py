@@ -468,6 +468,49 @@ def test_torch_allocator_serves_working_memory(ichee):
     assert all(torch.equal(x, y) for x, y in zip(res[0], res[1]))
 
 
+# ------------------------------------------------- the paper's ring size and N = 2048
+@pytest.mark.parametrize("wl", [
+    dict(name="paper_n4096_q109", log_n=12, prime_bits=[45, 32, 32], log2_scale=32, special_bits=50),
+    dict(name="n2048", log_n=11, prime_bits=[45, 30, 30], log2_scale=30, special_bits=50),
+], ids=lambda w: w["name"])
+def test_other_rings_bit_exact(ichee, wl):
+    """N = 4096 with a 109-bit ciphertext modulus (the paper's parameter set) and N = 2048:
+    keys, fresh and radix encryption, mean filter, matching and the per-pixel squared
+    difference, every ciphertext word against the oracle."""
+    ctx = gpu_for(ichee, wl, with_evk=True)
+    o = oracle_for(wl, with_evk=True)
+    n, L = ctx.n, ctx.L
+    pk = np.zeros((2, L, n), dtype=np.uint64)
+    ichee.ichee_export_key(ctx.handle, 1, pk)
+    assert np.array_equal(pk, o.pk)
+    evk = np.zeros((L, 2, L + 1, n), dtype=np.uint64)
+    ichee.ichee_export_key(ctx.handle, 2, evk)
+    assert np.array_equal(evk, o.evk)
+    h, w = 4, 5
+    a = inputs.random_field_image(h, w, seed=91).reshape(-1).copy()
+    b = inputs.noisy_copy(a, seed=92)
+    ga, ma = ctx.encrypt(torch.from_numpy(a).cuda(), h, w, 1, 31)
+    gb, mb = ctx.encrypt(torch.from_numpy(b).cuda(), h, w, 1, 32)
+    ra, rb = o.encrypt_pixels(a, 31), o.encrypt_pixels(b, 32)
+    assert np.array_equal(as_cts(ga, h * w, L, n), ra)
+    assert np.max(np.abs(ctx.decrypt(ga, ma).cpu().numpy() - a)) < 1e-3
+    cache = ctx.build_cache(ichee.CACHE_RADIX, 33, radix_base=16, randomize=1)
+    gr, _ = ctx.encrypt(torch.from_numpy(a).cuda(), h, w, 1, 34, cache=cache)
+    rr = o.encrypt_radix(a, o.radix_cache(16, 33), 34, randomize=True)
+    assert np.array_equal(as_cts(gr, h * w, L, n), rr)
+    mf, mm = ctx.eval(ichee.OP_MEANFILTER3, ga, ma, out_level=L - 2)
+    rf, _ = o.meanfilter3(ra, o.delta, h, w, 1)
+    assert np.array_equal(as_cts(mf, h * w, L - 1, n), rf)
+    m1, mm1 = ctx.eval(ichee.OP_SQDIFF_SUM, ga, ma, gb, mb, out_n_ct=1, out_level=L - 2)
+    r1, s1 = o.match(ra, rb, o.delta)
+    assert np.array_equal(as_cts(m1, 1, L - 1, n), r1)
+    sq, _ = ctx.eval(ichee.OP_SQDIFF, ga, ma, gb, mb, out_level=L - 2)
+    rs, _ = o.sqdiff_image(ra, rb, o.delta)
+    assert np.array_equal(as_cts(sq, h * w, L - 1, n), rs)
+    np.testing.assert_allclose(ctx.decrypt(m1, mm1).cpu().numpy(), o.decrypt(r1, s1), rtol=1e-9)
+    ctx.close()
+
+
 # ------------------------------------------------------------------------ errors
 def test_error_paths(ichee):
     wl = W.TOY
