@@ -468,6 +468,45 @@ def test_torch_allocator_serves_working_memory(ichee):
     assert all(torch.equal(x, y) for x, y in zip(res[0], res[1]))
 
 
+# ------------------------------------------------------------- degenerate pixel values
+def test_degenerate_pixel_values(ichee):
+    """Pixels 0 and 255 and values with a single nonzero radix digit, through every cache kind
+    (radix 2 / 10 / 16 with and without randomness, full cache with the pool): bit for bit
+    against the oracle. Without randomness pixel 0 has no nonzero digit and encrypts to the
+    all-zero ciphertext -- the paper's method as stated; its randomness removes that. A
+    constant 255 image keeps its value through the mean filter."""
+    wl = W.TOY
+    ctx = gpu_for(ichee, wl)
+    o = oracle_for(wl)
+    pix = np.array([0, 255, 1, 16, 240, 128, 2, 100, 0, 255, 10, 15], dtype=np.uint8)
+    dp = torch.from_numpy(pix).cuda()
+    for base in (2, 10, 16):
+        for rnd in (0, 1):
+            cache = ctx.build_cache(ichee.CACHE_RADIX, CACHE_SEED + base, radix_base=base, randomize=rnd)
+            ct, meta = ctx.encrypt(dp, 3, 4, 1, IMG_SEED, cache=cache)
+            ref = o.encrypt_radix(pix, o.radix_cache(base, CACHE_SEED + base), IMG_SEED, randomize=bool(rnd))
+            got = as_cts(ct, 12, 2, ctx.n)
+            assert np.array_equal(got, ref), (base, rnd)
+            assert np.max(np.abs(ctx.decrypt(ct, meta).cpu().numpy() - pix)) < 1e-3
+            if not rnd:
+                assert not got[0].any() and not got[8].any()   # pixel 0: the zero ciphertext
+    full = ctx.build_cache(ichee.CACHE_FULL, CACHE_SEED, pool_size=8)
+    ct, meta = ctx.encrypt(dp, 3, 4, 1, IMG_SEED, cache=full)
+    ref = o.encrypt_lookup(pix, o.full_cache(8, CACHE_SEED), IMG_SEED)
+    assert np.array_equal(as_cts(ct, 12, 2, ctx.n), ref)
+    ctx.close()
+    # constant image through the mean filter (four-prime ring: a limb to drop)
+    ctx = gpu_for(ichee, SMALL_OPS)
+    o = oracle_for(SMALL_OPS)
+    const = np.full(5 * 6, 255, dtype=np.uint8)
+    ct, meta = ctx.encrypt(torch.from_numpy(const).cuda(), 5, 6, 1, IMG_SEED)
+    mf, mm = ctx.eval(ichee.OP_MEANFILTER3, ct, meta, out_level=2)
+    ref, sc = o.meanfilter3(o.encrypt_pixels(const, IMG_SEED), o.delta, 5, 6, 1)
+    assert np.array_equal(as_cts(mf, 30, 3, ctx.n), ref)
+    assert np.max(np.abs(ctx.decrypt(mf, mm).cpu().numpy() - 255.0)) < 0.05
+    ctx.close()
+
+
 # ------------------------------------------------- the paper's ring size and N = 2048
 @pytest.mark.parametrize("wl", [
     dict(name="paper_n4096_q109", log_n=12, prime_bits=[45, 32, 32], log2_scale=32, special_bits=50),
