@@ -11,6 +11,10 @@
  *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = the default stream). All GPU
  *    work is enqueued asynchronously on it; results are ready when the stream is.
  *  - Memory: ciphertext buffers are caller-owned DEVICE memory (size from ichee_ct_bytes).
+ *    Every device buffer a call reads or writes is checked, before any launch, against the
+ *    allocation that holds it (the driver's pointer attributes; for virtual-memory mappings the
+ *    reserved address range): a buffer that ends before the bytes the call needs gives
+ *    ICHEE_EINVAL. Memory the driver does not describe is trusted.
  *    Pixel inputs and decrypted outputs may be host or device memory; host buffers are staged
  *    through library-owned device memory (and the call then waits for its own copies).
  *    Library-owned state (keys, tables, caches) lives in opaque handles freed by the
@@ -487,6 +491,15 @@ ichee_status ichee_probe_int_throughput(int device, double* imad_per_s, double* 
  * ICHEE_ETIMEOUT and clears the status word.
  */
 ichee_status ichee_stream_status(ichee_ctx* ctx, void* stream);
+
+/*
+ * Bytes from `ptr` to the end of the device allocation that holds it (for a caching
+ * allocator's block: to the end of its segment; for virtual-memory mappings: to the end of the
+ * reserved address range), the bound the entry points check device buffers against.
+ * Errors: EINVAL (null argument), EUNSUPPORTED (not device memory, or the driver does not
+ * describe the allocation; calls then trust the buffer).
+ */
+ichee_status ichee_buffer_bytes_left(const void* ptr, size_t* bytes_left);
 
 /* Message of the last failing call on this host thread ("" if none). */
 const char* ichee_last_error(void);

@@ -143,6 +143,10 @@ constexpr u64 kIdRadixBase = 1ull << 33;
 namespace ichee {
 size_t ct_words(const ichee_ctx* c, int limbs);
 bool is_device_ptr(const void* p);
+// Bytes from p to the end of the device allocation holding it; false if unknown.
+bool device_bytes_left(const void* p, u64* left);
+// EINVAL if [p, p + bytes) is known to run past the end of p's device allocation.
+ichee_status check_span(const void* p, u64 bytes, const char* what);
 RnsArgs rns_prefix(const ichee_ctx* c, int limbs);
 PolyBatch batch(u64* data, int n_poly, int nl, const int* midx);
 void encode_const(const ichee_ctx* c, double value, double scale, int limbs, u64* out);
@@ -156,5 +160,6 @@ void set_k1(const ichee_ctx* c, OpsArgs& a, double v, double scale);
 void fold_constants(const ichee_ctx* c, OpsArgs& a);
 bool same_scale(double a, double b);
 ichee_status check_img(const ichee_ctx* c, const uint64_t* d, const ichee_ctimg_meta* m, const char* what);
+ichee_status check_out(const ichee_ctx* c, const uint64_t* d, u64 n_ct, int limbs, const char* what);
 DecArgs dec_args(const ichee_ctx* c, int nl);
 }  // namespace ichee

@@ -31,12 +31,39 @@ ichee_status check_metas(const ichee_ctx* c, const uint64_t* const* d, const ich
                          const char* what)
 {
     if (!d || !m || n == 0) return fail(ICHEE_EINVAL, "%s: empty batch", what);
+    char name[64];
     for (uint32_t i = 0; i < n; ++i) {
-        if (!d[i]) return fail(ICHEE_EINVAL, "%s: null image %u", what, i);
         if (m[i].level != m[0].level) return fail(ICHEE_ELEVEL, "%s: image %u has another level", what, i);
-        if ((int)m[i].level >= c->L) return fail(ICHEE_ELEVEL, "%s: level %u >= %d", what, m[i].level, c->L);
-        if ((u64)m[i].h * m[i].w * m[i].c == 0) return fail(ICHEE_EINVAL, "%s: image %u is empty", what, i);
-        if (!(m[i].scale > 0.0)) return fail(ICHEE_ESCALE, "%s: image %u has no scale", what, i);
+        std::snprintf(name, sizeof(name), "%s, image %u", what, i);
+        const ichee_status s = check_img(c, d[i], &m[i], name);
+        if (s != ICHEE_OK) return s;
+    }
+    return ICHEE_OK;
+}
+
+// Pixels of every image: device memory of h*w*c bytes.
+ichee_status check_pixels(const uint8_t* const* px, const ichee_image_desc* images, uint32_t n)
+{
+    char name[48];
+    for (uint32_t i = 0; i < n; ++i) {
+        if (!is_device_ptr(px[i])) return fail(ICHEE_EINVAL, "pixels of image %u must be device memory", i);
+        std::snprintf(name, sizeof(name), "pixels of image %u", i);
+        const ichee_status s = check_span(px[i], n_ct_of(images[i]), name);
+        if (s != ICHEE_OK) return s;
+    }
+    return ICHEE_OK;
+}
+
+// Output images: device memory for h*w*c ciphertexts of `limbs` limbs each.
+template <class Shape>
+ichee_status check_outs(const ichee_ctx* c, uint64_t* const* out, const Shape* shapes, uint32_t n, int limbs,
+                        const char* what)
+{
+    char name[64];
+    for (uint32_t i = 0; i < n; ++i) {
+        std::snprintf(name, sizeof(name), "%s, image %u", what, i);
+        const ichee_status s = check_out(c, out[i], (u64)shapes[i].h * shapes[i].w * shapes[i].c, limbs, name);
+        if (s != ICHEE_OK) return s;
     }
     return ICHEE_OK;
 }
@@ -186,6 +213,9 @@ extern "C" ichee_status ichee_encrypt_meanfilter_batch(ichee_ctx* c, const ichee
     for (uint32_t i = 0; i < n_images; ++i)
         if (!pixels[i] || !d_ct_out[i] || !d_filtered_out[i]) return fail(ICHEE_EINVAL, "null buffer for image %u", i);
     CK(cudaSetDevice(c->device));
+    if ((s = check_pixels(pixels, images, n_images)) != ICHEE_OK) return s;
+    if ((s = check_outs(c, d_ct_out, images, n_images, c->L, "ciphertext output")) != ICHEE_OK) return s;
+    if ((s = check_outs(c, d_filtered_out, images, n_images, c->L - 1, "filtered output")) != ICHEE_OK) return s;
     if (c->fused_schedule == 1) {
         s = fused_chunked(c, k, pixels, images, n_images, d_ct_out, d_filtered_out, c->shape_fused, (cudaStream_t)stream);
     } else {
@@ -228,6 +258,8 @@ extern "C" ichee_status ichee_encrypt_batch(ichee_ctx* c, const ichee_cache* k, 
     for (uint32_t i = 0; i < n_images; ++i)
         if (!pixels[i] || !d_ct_out[i]) return fail(ICHEE_EINVAL, "null buffer for image %u", i);
     CK(cudaSetDevice(c->device));
+    if ((s = check_pixels(pixels, images, n_images)) != ICHEE_OK) return s;
+    if ((s = check_outs(c, d_ct_out, images, n_images, c->L, "ciphertext output")) != ICHEE_OK) return s;
     s = encrypt_chunked(c, k, pixels, images, n_images, d_ct_out, (cudaStream_t)stream);
     if (s != ICHEE_OK) return s;
     for (uint32_t i = 0; i < n_images; ++i) {
@@ -248,6 +280,7 @@ extern "C" ichee_status ichee_eval_batch(ichee_ctx* c, ichee_op op, const uint64
 {
     ichee::NvtxRange nvtx_range("ichee_eval_batch");
     if (!c || !d_out || !mout) return fail(ICHEE_EINVAL, "null argument");
+    CK(cudaSetDevice(c->device));
     ichee_status s = check_metas(c, d_a, ma, n_images, "a");
     if (s != ICHEE_OK) return s;
     for (uint32_t i = 0; i < n_images; ++i) {
@@ -256,7 +289,12 @@ extern "C" ichee_status ichee_eval_batch(ichee_ctx* c, ichee_op op, const uint64
             return fail(ICHEE_EINVAL, "only brightness / plaintext add run in place");
         if (!same_scale(ma[i].scale, ma[0].scale)) return fail(ICHEE_ESCALE, "image %u has another scale", i);
     }
-    CK(cudaSetDevice(c->device));
+    {
+        // mean filter and blend drop a limb; brightness / plaintext add keep the level
+        const bool drops = op == ICHEE_OP_MEANFILTER3 || op == ICHEE_OP_BLEND;
+        if ((s = check_outs(c, d_out, ma, n_images, (int)ma[0].level + (drops ? 0 : 1), "output")) != ICHEE_OK)
+            return s;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     if (op == ICHEE_OP_MEANFILTER3) {
         if (ma[0].level == 0) return fail(ICHEE_ELEVEL, "mean filter needs a limb to drop");
@@ -336,11 +374,15 @@ extern "C" ichee_status ichee_decrypt_batch(ichee_ctx* c, const uint64_t* const*
     ichee::NvtxRange nvtx_range("ichee_decrypt_batch");
     if (!c || !d_out) return fail(ICHEE_EINVAL, "null argument");
     if (!c->have_sk) return fail(ICHEE_EINVAL, "no secret key");
+    CK(cudaSetDevice(c->device));
     ichee_status s = check_metas(c, d_ct, metas, n_images, "ciphertexts");
     if (s != ICHEE_OK) return s;
-    for (uint32_t i = 0; i < n_images; ++i)
-        if (!d_out[i]) return fail(ICHEE_EINVAL, "null output for image %u", i);
-    CK(cudaSetDevice(c->device));
+    char name[48];
+    for (uint32_t i = 0; i < n_images; ++i) {
+        if (!is_device_ptr(d_out[i])) return fail(ICHEE_EINVAL, "output of image %u must be device memory", i);
+        std::snprintf(name, sizeof(name), "output of image %u", i);
+        if ((s = check_span(d_out[i], (u64)metas[i].h * metas[i].w * metas[i].c * 8, name)) != ICHEE_OK) return s;
+    }
     return decrypt_chunked(c, d_ct, metas, d_out, n_images, c->shape_decrypt, (cudaStream_t)stream);
 }
 
@@ -361,7 +403,12 @@ extern "C" ichee_status ichee_autotune_batch(ichee_ctx* c, const ichee_cache* k,
     ichee_status s = check_desc(images, n_images);
     if (s != ICHEE_OK) return s;
     if (c->L < 2) return fail(ICHEE_ELEVEL, "tuning the mean filter needs two limbs");
+    for (uint32_t i = 0; i < n_images; ++i)
+        if (!pixels[i] || !d_ct[i] || !d_filtered[i]) return fail(ICHEE_EINVAL, "null buffer for image %u", i);
     CK(cudaSetDevice(c->device));
+    if ((s = check_pixels(pixels, images, n_images)) != ICHEE_OK) return s;
+    if ((s = check_outs(c, d_ct, images, n_images, c->L, "ciphertext output")) != ICHEE_OK) return s;
+    if ((s = check_outs(c, d_filtered, images, n_images, c->L - 1, "filtered output")) != ICHEE_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));

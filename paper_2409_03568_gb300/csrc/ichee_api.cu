@@ -5,6 +5,8 @@
 #include <cmath>
 #include <string>
 
+#include <cuda.h>
+
 #include "api_internal.h"
 
 using namespace ichee;
@@ -40,6 +42,63 @@ bool ichee::is_device_ptr(const void* p)
         return false;
     }
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// The driver's pointer-attribute query, looked up once through the runtime so that the library
+// links no driver library. Of an address it gives the range of the allocation holding it: for
+// cudaMalloc memory the allocation itself; for virtual-memory mappings (cuMemMap, as in pool
+// allocators with expandable segments) the whole reserved address range, so a buffer that spans
+// several mappings is never refused.
+typedef CUresult (*PtrAttrsFn)(unsigned int n, CUpointer_attribute* attrs, void** data, CUdeviceptr p);
+
+static PtrAttrsFn ptr_attrs_fn()
+{
+    static const PtrAttrsFn fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult qr = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuPointerGetAttributes", &f, 12000, cudaEnableDefault, &qr) != cudaSuccess ||
+            qr != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            f = nullptr;
+        }
+        return reinterpret_cast<PtrAttrsFn>(f);
+    }();
+    return fn;
+}
+
+bool ichee::device_bytes_left(const void* p, u64* left)
+{
+    if (!is_device_ptr(p)) return false;
+    const PtrAttrsFn fn = ptr_attrs_fn();
+    if (!fn) return false;
+    CUdeviceptr base = 0;
+    size_t size = 0;
+    CUpointer_attribute attrs[2] = {CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, CU_POINTER_ATTRIBUTE_RANGE_SIZE};
+    void* data[2] = {&base, &size};
+    if (fn(2, attrs, data, (CUdeviceptr)(uintptr_t)p) != CUDA_SUCCESS) return false;
+    const u64 at = (u64)(uintptr_t)p;
+    if (size == 0 || at < base || at - base >= size) return false;
+    *left = size - (at - base);
+    return true;
+}
+
+// Memory the query does not know (another process's, an unusual allocator's) is taken on trust.
+ichee_status ichee::check_span(const void* p, u64 bytes, const char* what)
+{
+    u64 left = 0;
+    if (bytes > 0 && device_bytes_left(p, &left) && bytes > left)
+        return fail(ICHEE_EINVAL, "%s: needs %llu bytes but its allocation ends %llu bytes after the pointer", what,
+                    (unsigned long long)bytes, (unsigned long long)left);
+    return ICHEE_OK;
+}
+
+extern "C" ichee_status ichee_buffer_bytes_left(const void* p, size_t* bytes_left)
+{
+    if (!p || !bytes_left) return fail(ICHEE_EINVAL, "null argument");
+    u64 left = 0;
+    if (!device_bytes_left(p, &left)) return fail(ICHEE_EUNSUPPORTED, "extent of %p unknown", p);
+    *bytes_left = (size_t)left;
+    return ICHEE_OK;
 }
 
 RnsArgs ichee::rns_prefix(const ichee_ctx* c, int limbs)
@@ -609,6 +668,10 @@ extern "C" ichee_status ichee_build_cache(ichee_ctx* c, const ichee_cache_desc* 
             for (int v = 0; v < 256; ++v) k->values.push_back(v);
         } else {
             // scanning step: histogram on the device, top-k on the host (count desc, value asc)
+            if (is_device_ptr(scan)) {
+                ichee_status s = check_span(scan, n_scan, "scan pixels");
+                if (s != ICHEE_OK) return bail(s);
+            }
             const uint8_t* d_scan = scan;
             uint8_t* tmp = nullptr;
             u32* d_counts = nullptr;
@@ -697,7 +760,10 @@ extern "C" ichee_status ichee_cache_export(const ichee_cache* k, int part, void*
 // Pixels as a device pointer: staged through the context when they live on the host.
 static ichee_status device_pixels(ichee_ctx* c, const uint8_t* px, u64 n, cudaStream_t st, const uint8_t** d_px)
 {
-    if (is_device_ptr(px)) { *d_px = px; return ICHEE_OK; }
+    if (is_device_ptr(px)) {
+        *d_px = px;
+        return check_span(px, n, "pixels");
+    }
     CK(c->stage_in.ensure(n, c->user_alloc, c->user_free, c->user_alloc_ctx, st));
     CK(cudaMemcpyAsync(c->stage_in.p, px, n, cudaMemcpyHostToDevice, st));
     *d_px = (const uint8_t*)c->stage_in.p;
@@ -715,10 +781,11 @@ extern "C" ichee_status ichee_encrypt_image(ichee_ctx* c, const ichee_cache* k, 
     const u64 n_ct = (u64)h * w * ch;
     if (n_ct == 0) return fail(ICHEE_EINVAL, "empty image %ux%ux%u", h, w, ch);
     CK(cudaSetDevice(c->device));
-    if (!is_device_ptr(d_out)) return fail(ICHEE_EINVAL, "ciphertext output must be device memory");
+    ichee_status s = check_out(c, d_out, n_ct, c->L, "ciphertext output");
+    if (s != ICHEE_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     const uint8_t* d_px = nullptr;
-    ichee_status s = device_pixels(c, pixels, n_ct, st, &d_px);
+    s = device_pixels(c, pixels, n_ct, st, &d_px);
     if (s != ICHEE_OK) return s;
     if (!k) {
         CK(launch_encrypt_fresh(enc_args(c, d_px, n_ct, seed, 0, d_out), st));
@@ -814,7 +881,13 @@ ichee_status ichee::check_img(const ichee_ctx* c, const uint64_t* d, const ichee
     if ((u64)m->h * m->w * m->c == 0) return fail(ICHEE_EINVAL, "%s: empty image", what);
     if (!(m->scale > 0.0)) return fail(ICHEE_ESCALE, "%s: scale must be positive", what);
     if (!is_device_ptr(d)) return fail(ICHEE_EINVAL, "%s: ciphertexts must be device memory", what);
-    return ICHEE_OK;
+    return check_span(d, (u64)m->h * m->w * m->c * ct_words(c, (int)m->level + 1) * 8, what);
+}
+
+ichee_status ichee::check_out(const ichee_ctx* c, const uint64_t* d, u64 n_ct, int limbs, const char* what)
+{
+    if (!d || !is_device_ptr(d)) return fail(ICHEE_EINVAL, "%s must be device memory", what);
+    return check_span(d, n_ct * ct_words(c, limbs) * 8, what);
 }
 
 static ichee_status op_sqdiff(ichee_ctx* c, const uint64_t* d_a, const ichee_ctimg_meta* ma, const uint64_t* d_b,
@@ -831,7 +904,14 @@ extern "C" ichee_status ichee_eval(ichee_ctx* c, ichee_op op, const uint64_t* d_
     CK(cudaSetDevice(c->device));
     ichee_status s = check_img(c, d_a, ma, "a");
     if (s != ICHEE_OK) return s;
-    if (!d_out || !is_device_ptr(d_out)) return fail(ICHEE_EINVAL, "output must be device memory");
+    {
+        // the output holds n_ct ciphertexts (one for the matching sum), one limb fewer after a rescale
+        const bool drops = op == ICHEE_OP_RESCALE || op == ICHEE_OP_MEANFILTER3 || op == ICHEE_OP_BLEND ||
+                           op == ICHEE_OP_SQDIFF_SUM || op == ICHEE_OP_SQDIFF;
+        const u64 out_n = op == ICHEE_OP_SQDIFF_SUM ? 1 : (u64)ma->h * ma->w * ma->c;
+        s = check_out(c, d_out, out_n, (int)ma->level + (drops ? 0 : 1), "output");
+        if (s != ICHEE_OK) return s;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     const bool binary = op == ICHEE_OP_ADD || op == ICHEE_OP_SUB || op == ICHEE_OP_BLEND || op == ICHEE_OP_SQDIFF_SUM ||
                         op == ICHEE_OP_SQDIFF;
@@ -1093,6 +1173,8 @@ static ichee_status decrypt_impl(ichee_ctx* c, const uint64_t* d_ct, const ichee
     const int nl = (int)m->level + 1;
     const bool out_dev = is_device_ptr(out);
     const bool res_dev = residues == nullptr || is_device_ptr(residues);
+    if (out_dev && (s = check_span(out, n_ct * 8, "output")) != ICHEE_OK) return s;
+    if (residues && res_dev && (s = check_span(residues, n_ct * nl * 8, "residues")) != ICHEE_OK) return s;
     DecArgs a;
     std::memset(&a, 0, sizeof(a));
     a.logn = c->logn;
@@ -1194,7 +1276,8 @@ extern "C" ichee_status ichee_sqdiff_sum_noalloc(ichee_ctx* c, const uint64_t* d
     if (s != ICHEE_OK) return s;
     s = check_img(c, d_b, mb, "b");
     if (s != ICHEE_OK) return s;
-    if (!d_out || !is_device_ptr(d_out)) return fail(ICHEE_EINVAL, "output must be device memory");
+    s = check_out(c, d_out, 1, (int)ma->level, "output");
+    if (s != ICHEE_OK) return s;
     if (mb->level != ma->level) return fail(ICHEE_ELEVEL, "levels differ (%u vs %u)", ma->level, mb->level);
     if (!same_scale(ma->scale, mb->scale)) return fail(ICHEE_ESCALE, "scales differ (%g vs %g)", ma->scale, mb->scale);
     if (mb->h != ma->h || mb->w != ma->w || mb->c != ma->c) return fail(ICHEE_EMISMATCH, "shapes differ");

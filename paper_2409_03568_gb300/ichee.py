@@ -145,6 +145,7 @@ _SIGS = {
     "ichee_server_hold": (_st, [_vp, ctypes.c_int]),
     "ichee_server_destroy": (None, [_vp]),
     "ichee_stream_status": (_st, [_vp, _vp]),
+    "ichee_buffer_bytes_left": (_st, [_vp, ctypes.POINTER(_sz)]),
     "ichee_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -433,6 +434,14 @@ def ichee_server_destroy(server):
 
 def ichee_stream_status(ctx, stream=None):
     _check(_lib.ichee_stream_status(ctx, stream))
+
+
+def ichee_buffer_bytes_left(buf):
+    """Bytes from the buffer's address to the end of its device allocation (the bound every
+    entry point checks device buffers against)."""
+    n = _sz(0)
+    _check(_lib.ichee_buffer_bytes_left(_ptr(buf), ctypes.byref(n)))
+    return n.value
 
 
 class Context:

@@ -589,6 +589,41 @@ def test_error_paths(ichee):
     ctx.close()
 
 
+def test_short_device_buffers_are_refused(ichee):
+    """A device buffer that ends before the bytes a call needs is refused before any launch (the
+    bound is the allocation holding it, from the driver's address-range query); the context
+    stays usable."""
+    ctx = gpu_for(ichee, W.TOY)
+    h = w = 32
+    gen = torch.Generator().manual_seed(5)
+    pix = torch.randint(0, 256, (h * w,), dtype=torch.uint8, generator=gen).cuda()
+    one = ctx.empty_cts(1, ctx.L - 1)                  # room for one ciphertext only
+    need = h * w * ctx.ct_words(ctx.L - 1) * 8
+    try:
+        left = ichee.ichee_buffer_bytes_left(one)
+    except ichee.IcheeError:
+        pytest.skip("the driver reports no allocation extents here")
+    if not 0 < left < need:  # every call below must be refused on the host, never launched
+        pytest.skip("the allocator's segment is larger than the image (virtual-memory segments)")
+    with pytest.raises(ichee.IcheeError) as e:
+        ctx.encrypt(pix, h, w, 1, 1, out=one)
+    assert e.value.status == ichee.EINVAL and "allocation" in str(e.value)
+    ct, m = ctx.encrypt(pix, h, w, 1, 1)
+    with pytest.raises(ichee.IcheeError) as e:
+        ctx.eval(ichee.OP_ADD, ct, m, ct, m, out=one)
+    assert e.value.status == ichee.EINVAL
+    with pytest.raises(ichee.IcheeError) as e:
+        ctx.decrypt(one, m)                            # metadata promises 1024 ciphertexts
+    assert e.value.status == ichee.EINVAL
+    with pytest.raises(ichee.IcheeError) as e:
+        ichee.ichee_encrypt_batch(ctx.handle, None, [pix, pix], [(h, w, 1), (h, w, 1)], [1, 2],
+                                  [ctx.empty_cts(h * w, ctx.L - 1), one], ctx.stream())
+    assert e.value.status == ichee.EINVAL and "image 1" in str(e.value)
+    ctx.status()
+    np.testing.assert_array_equal(np.rint(ctx.decrypt(ct, m).cpu().numpy()), pix.cpu().numpy())
+    ctx.close()
+
+
 def test_integer_probe_reports_rates(ichee):
     """The throughput probe runs and reports plausible rates (a measurement utility)."""
     imad, bfly = ichee.ichee_probe_int_throughput(0)
