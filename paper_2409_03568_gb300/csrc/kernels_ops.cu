@@ -189,9 +189,15 @@ __global__ void __launch_bounds__(256) k_meanfilter3(const __grid_constant__ Ops
     meanfilter_row<LIMBS>(a, a.in0, a.out, a.h, a.w, a.c, y, chunk, b, (int)bid);
 }
 
-// Ragged batch: segment s has h*chunks*2*c items, in the order of the single-image kernel.
+// Largest block of the batched mean-filter kernels for a limb count: the column sums of more
+// than three limbs need more than the 64 registers a thread gets at 1024 threads.
 template <int LIMBS>
-__global__ void __launch_bounds__(1024) k_meanfilter3_batch(const __grid_constant__ OpsArgs a,
+static constexpr int kMfMaxThreads = LIMBS <= 3 ? 1024 : 512;
+
+// Ragged batch: segment s has h*chunks*2*c items, in the order of the single-image kernel.
+// Launched with at most 512 threads (the tunable shapes).
+template <int LIMBS>
+__global__ void __launch_bounds__(kMfMaxThreads<LIMBS>) k_meanfilter3_batch(const __grid_constant__ OpsArgs a,
                                                             const __grid_constant__ SegTable t)
 {
     const int chunks = ((1 << a.logn) / 2) / blockDim.x;
@@ -220,7 +226,7 @@ __global__ void __launch_bounds__(1024) k_meanfilter3_batch(const __grid_constan
 // the fused multiply + rescale, as in the mean filter. Residues equal those of the radix
 // combine followed by the mean filter.
 template <int LIMBS>
-__global__ void __launch_bounds__(1024) k_radix_meanfilter3_batch(const __grid_constant__ RadixArgs ra,
+__global__ void __launch_bounds__(kMfMaxThreads<LIMBS>) k_radix_meanfilter3_batch(const __grid_constant__ RadixArgs ra,
                                                                   const __grid_constant__ OpsArgs a,
                                                                   const __grid_constant__ SegTable t)
 {
@@ -680,10 +686,12 @@ cudaError_t launch_meanfilter3_batch(const OpsArgs& a, const SegTable& t, Launch
 }
 
 // Threads per block of the fused kernel for a launch shape: 32 x columns per strip (at least 4
-// columns), halved until the two row buffers fit in shared memory.
+// columns), at most 512 above three limbs (the kernel's register bound), halved until the two
+// row buffers fit in shared memory.
 int fused_threads(int limbs, int threads)
 {
-    int th = threads < 128 ? 128 : (threads > 1024 ? 1024 : threads);
+    const int cap = limbs <= 3 ? 1024 : 512;
+    int th = threads < 128 ? 128 : (threads > cap ? cap : threads);
     while (th > 128 && (size_t)2 * (th / 32) * limbs * 32 * 16 > 200 * 1024) th /= 2;
     return th;
 }

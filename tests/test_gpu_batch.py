@@ -271,3 +271,45 @@ def test_batch_errors(ichee, ctx8192):
         ichee.ichee_eval_batch(ctx.handle, ichee.OP_BRIGHTNESS, [out], metas, args=(1.0, 2.0), outs=[ctx.empty_cts(4, 2)],
                                stream=ctx.stream())
     assert e.value.status == ichee.EINVAL
+
+
+def test_batched_mean_filter_five_limbs(ichee):
+    """The N = 16384 ring with five limbs (half of the serving requests): batched radix
+    encryption and batched mean filter against the oracle, and the fused encrypt + mean-filter
+    kernel (asked for 1024 threads, run at its five-limb bound of 512) against both."""
+    wl = W.RING16384
+    ctx = ichee.Context(**W.ctx_kwargs(wl))
+    ctx.keygen(KEY)
+    o = Oracle(Params(wl["log_n"], wl["prime_bits"], wl["log2_scale"])).keygen(KEY)
+    n, L = ctx.n, ctx.L
+    shapes = [(3, 5, 1), (2, 4, 3), (1, 1, 1)]
+    imgs = [inputs.random_field_image(h, w, seed=90 + i, channels=c).reshape(-1).copy()
+            for i, (h, w, c) in enumerate(shapes)]
+    seeds = [700 + i for i in range(len(shapes))]
+    cache = ctx.build_cache(ichee.CACHE_RADIX, 71, radix_base=16)
+    ocache = o.radix_cache(16, 71)
+    d_px = [torch.from_numpy(im).cuda() for im in imgs]
+    enc = [ctx.empty_cts(h * w * c, L - 1) for (h, w, c) in shapes]
+    metas = ichee.ichee_encrypt_batch(ctx.handle, cache, d_px, shapes, seeds, enc, ctx.stream())
+    filt = [ctx.empty_cts(h * w * c, L - 2) for (h, w, c) in shapes]
+    ichee.ichee_eval_batch(ctx.handle, ichee.OP_MEANFILTER3, enc, metas, outs=filt, stream=ctx.stream())
+    torch.cuda.synchronize()
+    for i, (h, w, c) in enumerate(shapes):
+        ref = o.encrypt_radix(imgs[i], ocache, seeds[i])
+        assert np.array_equal(as_cts(enc[i], h * w * c, L, n), ref), i
+        rf, _ = o.meanfilter3(ref, o.delta, h, w, c)
+        assert np.array_equal(as_cts(filt[i], h * w * c, L - 1, n), rf), i
+    saved = ichee.ichee_tuned_shape(ctx.handle, ichee.TUNE_SCHEDULE)[0]
+    ichee.ichee_set_tuned_shape(ctx.handle, ichee.TUNE_FUSED, 1024, 1)
+    ichee.ichee_set_tuned_shape(ctx.handle, ichee.TUNE_SCHEDULE, 1)
+    try:
+        enc2 = [ctx.empty_cts(h * w * c, L - 1) for (h, w, c) in shapes]
+        filt2 = [ctx.empty_cts(h * w * c, L - 2) for (h, w, c) in shapes]
+        ichee.ichee_encrypt_meanfilter_batch(ctx.handle, cache, d_px, shapes, seeds, enc2, filt2, ctx.stream())
+        torch.cuda.synchronize()
+        for i in range(len(shapes)):
+            assert torch.equal(enc2[i], enc[i]) and torch.equal(filt2[i], filt[i]), i
+    finally:
+        ichee.ichee_set_tuned_shape(ctx.handle, ichee.TUNE_SCHEDULE, saved)
+    ctx.status()
+    ctx.close()
