@@ -129,6 +129,28 @@ __device__ __forceinline__ int gauss_of(u64 u, const CdtTable& cdt)
     return (u >> 63) ? -mag : mag;
 }
 
+// The same magnitude by a branch-free binary search: t holds the table's first kCdtSearch
+// entries, those from `bound` on replaced by 2^63 (which no 63-bit value reaches), in memory
+// that lanes may index independently (shared memory). Five probes count the entries the value
+// reaches instead of one comparison per entry.
+constexpr int kCdtSearch = 31;
+static_assert(kMaxGaussBound <= kCdtSearch, "a 31-entry search covers every table");
+
+__device__ __forceinline__ int gauss_of_sorted(u64 u, const u64* t)
+{
+    const u64 r = u & 0x7FFFFFFFFFFFFFFFull;
+    int pos = 0;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) pos += r >= t[pos + s - 1] ? s : 0;
+    return (u >> 63) ? -pos : pos;
+}
+
+// Fill the search copy of the table (every thread of the block calls it).
+__device__ __forceinline__ void cdt_for_search(const CdtTable& cdt, u64* t)
+{
+    for (int k = threadIdx.x; k < kCdtSearch; k += blockDim.x) t[k] = k < (int)cdt.bound ? cdt.t[k] : (1ull << 63);
+}
+
 // Residue of a small signed integer.
 __device__ __forceinline__ u64 small_mod(int x, u64 q) { return x < 0 ? q - (u64)(-x) : (u64)x; }
 

@@ -234,8 +234,14 @@ cudaError_t launch_axpy_const(u64* out, const u64* x, const u64* y, u64 c, int n
 // ternary operand and needs no product.
 // ---------------------------------------------------------------------------------------
 
-// Shared memory of one encryption block: the transform buffer (N words) followed by v, e0, e1
-// as int8 (3N bytes).
+// Shared memory of one encryption block: the transform buffer (N words), v, e0, e1 as int8
+// (3N bytes), then the search copy of the Gaussian table (32 words).
+template <int LOGN>
+__device__ __forceinline__ u64* enc_cdt_smem(u64* smem) { return smem + (1 << LOGN) + (3 << LOGN) / 8; }
+
+template <int LOGN>
+static constexpr size_t kEncSmem = ((sizeof(u64) + 3) << LOGN) + 32 * sizeof(u64);
+
 template <int LOGN, bool KEEP_VHAT, int E>
 __device__ __forceinline__ void encrypt_ct(const EncArgs& a, int p, u64 seed, u64 id, u64* ct, u64* smem)
 {
@@ -246,6 +252,7 @@ __device__ __forceinline__ void encrypt_ct(const EncArgs& a, int p, u64 seed, u6
     int8_t* sv = reinterpret_cast<int8_t*>(smem + N);
     int8_t* se0 = sv + N;
     int8_t* se1 = se0 + N;
+    const u64* tcdt = enc_cdt_smem<LOGN>(smem);   // filled by the kernel before its first ciphertext
     const int tid = threadIdx.x;
     const int L = a.L;
     __syncthreads();  // smem of the previous ciphertext no longer read
@@ -259,10 +266,10 @@ __device__ __forceinline__ void encrypt_ct(const EncArgs& a, int p, u64 seed, u6
     for (int b = tid; b < N / 2; b += T) {
         Words4 w0 = philox(seed, kStreamE0, id, (u32)b);
         Words4 w1 = philox(seed, kStreamE1, id, (u32)b);
-        int g00 = gauss_of((u64)w0.w[0] | ((u64)w0.w[1] << 32), a.cdt);
-        int g01 = gauss_of((u64)w0.w[2] | ((u64)w0.w[3] << 32), a.cdt);
-        int g10 = gauss_of((u64)w1.w[0] | ((u64)w1.w[1] << 32), a.cdt);
-        int g11 = gauss_of((u64)w1.w[2] | ((u64)w1.w[3] << 32), a.cdt);
+        int g00 = gauss_of_sorted((u64)w0.w[0] | ((u64)w0.w[1] << 32), tcdt);
+        int g01 = gauss_of_sorted((u64)w0.w[2] | ((u64)w0.w[3] << 32), tcdt);
+        int g10 = gauss_of_sorted((u64)w1.w[0] | ((u64)w1.w[1] << 32), tcdt);
+        int g11 = gauss_of_sorted((u64)w1.w[2] | ((u64)w1.w[3] << 32), tcdt);
         reinterpret_cast<uint16_t*>(se0)[b] = (uint16_t)((uint8_t)g00 | ((uint16_t)(uint8_t)g01 << 8));
         reinterpret_cast<uint16_t*>(se1)[b] = (uint16_t)((uint8_t)g10 | ((uint16_t)(uint8_t)g11 << 8));
     }
@@ -313,6 +320,7 @@ template <int LOGN, bool KEEP_VHAT, int E>
 __global__ void __launch_bounds__(NttShape<LOGN, E>::T, 1) k_encrypt_fresh(const __grid_constant__ EncArgs a)
 {
     extern __shared__ u64 smem[];
+    cdt_for_search(a.cdt, enc_cdt_smem<LOGN>(smem));   // ordered by encrypt_ct's first barrier
     const u64 ct_len = (u64)2 * a.L << LOGN;
     for (u64 k = blockIdx.x; k < a.n_ct; k += gridDim.x) {
         const int p = a.pixels[k];
@@ -326,6 +334,7 @@ __global__ void __launch_bounds__(NttShape<LOGN, E>::T, 1) k_encrypt_fresh_batch
                                                                               const __grid_constant__ SegTable t)
 {
     extern __shared__ u64 smem[];
+    cdt_for_search(a.cdt, enc_cdt_smem<LOGN>(smem));   // ordered by encrypt_ct's first barrier
     const u64 ct_len = (u64)2 * a.L << LOGN;
     const u64 total = t.start[t.n];
     for (u64 g = blockIdx.x; g < total; g += gridDim.x) {
@@ -348,7 +357,7 @@ static cudaError_t enc_launch(const EncArgs& a, cudaStream_t st)
     constexpr bool keep = LOGN <= 13;
     constexpr int E = kEncE<LOGN>;
     const int T = NttShape<LOGN, E>::T;
-    const size_t smem = (sizeof(u64) + 3) << LOGN;
+    const size_t smem = kEncSmem<LOGN>;
     cudaError_t e = cudaFuncSetAttribute(k_encrypt_fresh<LOGN, keep, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -363,7 +372,7 @@ static cudaError_t enc_batch_launch(const EncArgs& a, const SegTable& t, int num
     constexpr bool keep = LOGN <= 13;
     constexpr int E = kEncE<LOGN>;
     const int T = NttShape<LOGN, E>::T;
-    const size_t smem = (sizeof(u64) + 3) << LOGN;
+    const size_t smem = kEncSmem<LOGN>;
     cudaError_t e = cudaFuncSetAttribute(k_encrypt_fresh_batch<LOGN, keep, E>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
