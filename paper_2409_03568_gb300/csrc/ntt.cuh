@@ -67,22 +67,34 @@ __device__ __forceinline__ int elem_index(int tid, int e)
     return (h << (P::LO + P::S)) | (j << P::LO) | l;
 }
 
+// Shared-memory slot of register e of thread tid in the pass starting at S0. elem_index is a
+// permutation of the bits of (tid, e) and the swizzle is linear over GF(2), so the slot is
+// swz(elem_index(tid, 0)) ^ swz(elem_index(0, e)): a per-thread base XOR a compile-time
+// constant, one instruction per access (checked for every pass of N = 2^10 .. 2^14).
+template <int LOGN, int S0, int E = 16>
+__device__ __forceinline__ int slot_base(int tid) { return swz<E>(elem_index<LOGN, S0, E>(tid, 0)); }
+
+template <int LOGN, int S0, int E = 16>
+__device__ __forceinline__ int slot_of(int base, int e) { return base ^ swz<E>(elem_index<LOGN, S0, E>(0, e)); }
+
 template <int LOGN, int S0, int NP, int E = 16>
 __device__ __forceinline__ void load_sm(const u64* sm, u64 (&r)[NP][E], int tid)
 {
+    const int base = slot_base<LOGN, S0, E>(tid);
 #pragma unroll
     for (int p = 0; p < NP; ++p)
 #pragma unroll
-        for (int e = 0; e < E; ++e) r[p][e] = sm[p * (1 << LOGN) + swz<E>(elem_index<LOGN, S0, E>(tid, e))];
+        for (int e = 0; e < E; ++e) r[p][e] = sm[p * (1 << LOGN) + slot_of<LOGN, S0, E>(base, e)];
 }
 
 template <int LOGN, int S0, int NP, int E = 16>
 __device__ __forceinline__ void store_sm(u64* sm, const u64 (&r)[NP][E], int tid)
 {
+    const int base = slot_base<LOGN, S0, E>(tid);
 #pragma unroll
     for (int p = 0; p < NP; ++p)
 #pragma unroll
-        for (int e = 0; e < E; ++e) sm[p * (1 << LOGN) + swz<E>(elem_index<LOGN, S0, E>(tid, e))] = r[p][e];
+        for (int e = 0; e < E; ++e) sm[p * (1 << LOGN) + slot_of<LOGN, S0, E>(base, e)] = r[p][e];
 }
 
 // Forward stages S0 .. S0+S-1 on the registers. Stage s pairs x with x + N/2^{s+1} and uses
