@@ -275,6 +275,8 @@ __device__ __forceinline__ void encrypt_ct(const EncArgs& a, int p, u64 seed, u6
     }
     __syncthreads();
 
+    const int x0 = elem_index<LOGN, 0, E>(tid, 0);       // first-pass layout: x0 + elem_offset(e)
+    const int xl = elem_index<LOGN, LAST, E>(tid, 0);    // last-pass layout
     for (int l = 0; l < L; ++l) {
         const u64 q = a.rns.q[l];
         const ModTables t = a.rns.tab[l];
@@ -286,7 +288,7 @@ __device__ __forceinline__ void encrypt_ct(const EncArgs& a, int p, u64 seed, u6
                 for (int e = 0; e < E; ++e) r[0][e] = vh[KEEP_VHAT ? e : 0];
             } else {
 #pragma unroll
-                for (int e = 0; e < E; ++e) r[0][e] = small_mod(sv[elem_index<LOGN, 0, E>(tid, e)], q);
+                for (int e = 0; e < E; ++e) r[0][e] = small_mod(sv[x0 + elem_offset<LOGN, 0, E>(e)], q);
                 __syncthreads();
                 ntt_fwd_regs<LOGN, 1, true, false, E>(buf, r, tid, t, q);
                 if constexpr (KEEP_VHAT) {
@@ -294,22 +296,22 @@ __device__ __forceinline__ void encrypt_ct(const EncArgs& a, int p, u64 seed, u6
                     for (int e = 0; e < E; ++e) vh[e] = r[0][e];
                 }
             }
-            const u64* pk = a.pk_hat + ((size_t)pb * L + l) * N;
-            const u64* pkp = a.pk_hat_p + ((size_t)pb * L + l) * N;
+            const u64* pk = a.pk_hat + ((size_t)pb * L + l) * N + xl;
+            const u64* pkp = a.pk_hat_p + ((size_t)pb * L + l) * N + xl;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                const int x = elem_index<LOGN, LAST, E>(tid, e);
+                const int x = elem_offset<LOGN, LAST, E>(e);
                 r[0][e] = shoup_lazy(r[0][e], __ldg(pk + x), __ldg(pkp + x), q);
             }
             __syncthreads();
             ntt_inv_regs<LOGN, 1, false, E>(buf, r, tid, t, q);
-            const int8_t* noise = pb == 0 ? se0 : se1;
-            u64* dst = ct + ((u64)pb * L + l) * N;
+            const int8_t* noise = (pb == 0 ? se0 : se1) + x0;
+            u64* dst = ct + ((u64)pb * L + l) * N + x0;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                const int x = elem_index<LOGN, 0, E>(tid, e);
+                const int x = elem_offset<LOGN, 0, E>(e);
                 u64 v = add_mod(csub(r[0][e], q), small_mod(noise[x], q), q);
-                if (pb == 0 && x == 0) v = add_mod(v, a.dm[l * 256 + p], q);
+                if (pb == 0 && x == 0 && x0 == 0) v = add_mod(v, a.dm[l * 256 + p], q);   // coefficient 0
                 __stcs(dst + x, v);
             }
         }

@@ -42,22 +42,25 @@ __global__ void __launch_bounds__(NttShape<LOGN, E>::T, 1) k_sqdiff_accumulate(c
         const u64* B = a.b + k * 2 * (u64)limbs * N;
 #pragma unroll 1
         for (int pb = 0; pb < 2; ++pb) {
-            const u64* pa = A + ((u64)pb * limbs + l) * N;
-            const u64* pbb = B + ((u64)pb * limbs + l) * N;
+            const int x0 = elem_index<LOGN, 0, E>(tid, 0);   // first-pass layout: x0 + elem_offset(e)
+            const u64* pa = A + ((u64)pb * limbs + l) * N + x0;
+            const u64* pbb = B + ((u64)pb * limbs + l) * N + x0;
             u64 r[1][E];
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                const int x = elem_index<LOGN, 0, E>(tid, e);
+                const int x = elem_offset<LOGN, 0, E>(e);
                 r[0][e] = sub_mod(__ldcs(pa + x), __ldcs(pbb + x), q);
             }
             __syncthreads();
             ntt_fwd_regs<LOGN, 1, false, false, E>(buf, r, tid, t, q);
             __syncthreads();
             u64* dst = pb == 0 ? d0buf : buf;
+            const int sb = slot_base<LOGN, LAST, E>(tid);
+            const int xl = elem_index<LOGN, LAST, E>(tid, 0);
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                const int x = elem_index<LOGN, LAST, E>(tid, e);
-                dst[SMEM_D0 || pb ? swz<E>(x) : x] = csub(csub(r[0][e], 2 * q), q);
+                const int at = SMEM_D0 || pb ? slot_of<LOGN, LAST, E>(sb, e) : xl + elem_offset<LOGN, LAST, E>(e);
+                dst[at] = csub(csub(r[0][e], 2 * q), q);
             }
         }
 #pragma unroll 1

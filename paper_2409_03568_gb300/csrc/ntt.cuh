@@ -67,6 +67,12 @@ __device__ __forceinline__ int elem_index(int tid, int e)
     return (h << (P::LO + P::S)) | (j << P::LO) | l;
 }
 
+// Without the swizzle the split is additive: elem_index(tid, e) = elem_index(tid, 0) +
+// elem_index(0, e) (disjoint bits), so global accesses take a per-thread base pointer and
+// compile-time offsets.
+template <int LOGN, int S0, int E = 16>
+__device__ __forceinline__ int elem_offset(int e) { return elem_index<LOGN, S0, E>(0, e); }
+
 // Shared-memory slot of register e of thread tid in the pass starting at S0. elem_index is a
 // permutation of the bits of (tid, e) and the swizzle is linear over GF(2), so the slot is
 // swz(elem_index(tid, 0)) ^ swz(elem_index(0, e)): a per-thread base XOR a compile-time
