@@ -380,19 +380,20 @@ __device__ __forceinline__ void blend_pair(const OpsArgs& a, const u64* ci, cons
     }
 }
 
+// A block takes whole rows (ciphertext k, polynomial b): the pattern index of k (a division
+// by the channel count) is worked out once per row, not once per coefficient pair.
 template <int LIMBS>
 __global__ void k_blend(const __grid_constant__ OpsArgs a)
 {
     const int n = 1 << a.logn;
-    const u64 total = a.n_ct * 2 * (u64)(n / 2);
-    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < total; i += (u64)gridDim.x * blockDim.x) {
-        const u64 kb = i / (n / 2);
-        const int c = (int)(i % (n / 2));
-        const u64 k = kb / 2;
-        const int b = (int)(kb % 2);
+    for (u64 kb = blockIdx.x; kb < 2 * a.n_ct; kb += gridDim.x) {
+        const u64 k = kb >> 1;
+        const int b = (int)(kb & 1);
         const u64 kw = (k / a.c) * a.c_w + (a.c_w == 1 ? 0 : k % a.c);
-        blend_pair<LIMBS>(a, a.in0 + k * 2 * LIMBS * (u64)n, a.in1 + kw * 2 * LIMBS * (u64)n,
-                          a.out + k * 2 * (LIMBS - 1) * (u64)n, b, c);
+        const u64* ci = a.in0 + k * 2 * LIMBS * (u64)n;
+        const u64* cw = a.in1 + kw * 2 * LIMBS * (u64)n;
+        u64* co = a.out + k * 2 * (LIMBS - 1) * (u64)n;
+        for (int c = threadIdx.x; c < n / 2; c += blockDim.x) blend_pair<LIMBS>(a, ci, cw, co, b, c);
     }
 }
 
@@ -411,7 +412,8 @@ __global__ void __launch_bounds__(1024) k_blend_batch(const __grid_constant__ Op
         const u64* ci = t.in0[s] + k * 2 * LIMBS * (u64)n;
         const u64* cw = t.in1[s] + kw * 2 * LIMBS * (u64)n;
         u64* co = t.out[s] + k * 2 * (LIMBS - 1) * (u64)n;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) blend_pair<LIMBS>(a, ci, cw, co, i / (n / 2), i % (n / 2));
+        const int lh = a.logn - 1;   // n / 2 = 2^lh coefficient pairs per polynomial
+        for (int i = threadIdx.x; i < n; i += blockDim.x) blend_pair<LIMBS>(a, ci, cw, co, i >> lh, i & ((1 << lh) - 1));
     }
 }
 
@@ -663,8 +665,7 @@ cudaError_t launch_meanfilter3(const OpsArgs& a, cudaStream_t st)
 
 cudaError_t launch_blend(const OpsArgs& a, cudaStream_t st)
 {
-    const u64 work = a.n_ct * 2 * (u64)((1u << a.logn) / 2);
-    const unsigned g = grid_for(work, 256);
+    const unsigned g = grid_for(2 * a.n_ct, 1);   // rows (ciphertext, polynomial)
     ICHEE_LIMB_SWITCH(k_blend, g, 256, a)
     return cudaGetLastError();
 }
