@@ -329,6 +329,7 @@ ichee_status ichee_encrypt_meanfilter_batch(ichee_ctx* ctx, const ichee_cache* c
 #define ICHEE_TUNE_MEANFILTER 3u
 #define ICHEE_TUNE_FUSED 4u
 #define ICHEE_TUNE_SCHEDULE 5u   /* ichee_tuned_shape: *threads = 1 if the fused kernel runs, 0 for two kernels */
+#define ICHEE_TUNE_DECRYPT 6u    /* decryption, single-image and batched (one block per ciphertext) */
 
 typedef struct {
     uint32_t kind;            /* ICHEE_TUNE_* */
@@ -358,7 +359,8 @@ ichee_status ichee_tuned_shape(const ichee_ctx* ctx, uint32_t kind, uint32_t* th
 /*
  * Set the launch shape of a kernel kind (e.g. tuning results saved from an earlier run), or with
  * ICHEE_TUNE_SCHEDULE the encrypt + mean-filter schedule (threads = 1: fused kernel, 0: two
- * kernels; blocks_per_sm ignored). threads: 128, 256 or 512 (the fused kernel also 1024);
+ * kernels; blocks_per_sm ignored). threads: 128, 256 or 512 (the fused kernel also 1024, decryption
+ * 32 to 1024 in powers of two);
  * blocks_per_sm: 1..32 resident blocks per SM striding over the work, or 0 for one block per
  * work item. Results do not depend on shapes or schedule. Errors: EINVAL.
  */

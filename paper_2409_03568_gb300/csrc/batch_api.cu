@@ -520,6 +520,7 @@ extern "C" ichee_status ichee_tuned_shape(const ichee_ctx* c, uint32_t kind, uin
     case ICHEE_TUNE_LOOKUP: ls = c->shape_lookup; break;
     case ICHEE_TUNE_MEANFILTER: ls = c->shape_meanfilter; break;
     case ICHEE_TUNE_FUSED: ls = c->shape_fused; break;
+    case ICHEE_TUNE_DECRYPT: ls = c->shape_decrypt; break;
     case ICHEE_TUNE_SCHEDULE: *threads = (uint32_t)c->fused_schedule; *blocks_per_sm = 0; return ICHEE_OK;
     default: return fail(ICHEE_EINVAL, "unknown kernel kind %u", kind);
     }
@@ -587,8 +588,10 @@ extern "C" ichee_status ichee_set_tuned_shape(ichee_ctx* c, uint32_t kind, uint3
         c->fused_schedule = (int)threads;
         return ICHEE_OK;
     }
-    const bool fused = kind == ICHEE_TUNE_FUSED;
-    if (!(threads == 128 || threads == 256 || threads == 512 || (fused && threads == 1024)))
+    const bool wide = kind == ICHEE_TUNE_FUSED || kind == ICHEE_TUNE_DECRYPT;   // 1024 threads allowed
+    const bool narrow = kind == ICHEE_TUNE_DECRYPT;                            // 32 and 64 too
+    if (!(threads == 128 || threads == 256 || threads == 512 || (wide && threads == 1024) ||
+          (narrow && (threads == 32 || threads == 64))))
         return fail(ICHEE_EINVAL, "threads %u not supported for kind %u", threads, kind);
     if (blocks_per_sm > 32) return fail(ICHEE_EINVAL, "blocks_per_sm %u above 32", blocks_per_sm);
     if ((kind == ICHEE_TUNE_MEANFILTER) && (uint32_t)(c->n / 2) < threads)
@@ -599,6 +602,7 @@ extern "C" ichee_status ichee_set_tuned_shape(ichee_ctx* c, uint32_t kind, uint3
     case ICHEE_TUNE_LOOKUP: c->shape_lookup = ls; break;
     case ICHEE_TUNE_MEANFILTER: c->shape_meanfilter = ls; break;
     case ICHEE_TUNE_FUSED: c->shape_fused = ls; break;
+    case ICHEE_TUNE_DECRYPT: c->shape_decrypt = ls; break;
     default: return fail(ICHEE_EINVAL, "unknown kernel kind %u", kind);
     }
     return ICHEE_OK;

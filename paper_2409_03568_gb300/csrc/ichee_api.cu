@@ -1196,7 +1196,7 @@ static ichee_status decrypt_impl(ichee_ctx* c, const uint64_t* d_ct, const ichee
             a.residues_out = (u64*)c->stage_res.p;
         }
     }
-    CK(launch_decrypt(a, st));
+    CK(launch_decrypt(a, c->shape_decrypt.threads, st));
     if (!out_dev) CK(cudaMemcpyAsync(out, a.out, n_ct * 8, cudaMemcpyDeviceToHost, st));
     if (residues && !res_dev) CK(cudaMemcpyAsync(residues, a.residues_out, n_ct * nl * 8, cudaMemcpyDeviceToHost, st));
     if (!out_dev || (residues && !res_dev)) CK(cudaStreamSynchronize(st));

@@ -559,7 +559,12 @@ __device__ __forceinline__ void decrypt_ct(const DecArgs& a, const u64* ct, doub
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(256) k_decrypt(const __grid_constant__ DecArgs a)
+// Two register budgets: blocks of up to 256 threads at 8 resident blocks per SM (32 registers:
+// twice the loads in flight of the unconstrained build, the shape for whole images), and
+// blocks of up to 1024 threads for a handful of ciphertexts, where one block's bandwidth is
+// what counts.
+template <int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_decrypt(const __grid_constant__ DecArgs a)
 {
     __shared__ u64 red[32][2][kMaxPrimes];
     const int nl = a.crt.nl;
@@ -569,8 +574,9 @@ __global__ void __launch_bounds__(256) k_decrypt(const __grid_constant__ DecArgs
 }
 
 // Ragged batch: segment s decrypts in0[s] (at the level of `a`) into dout[s] with scale[s].
-__global__ void __launch_bounds__(1024) k_decrypt_batch(const __grid_constant__ DecArgs a,
-                                                        const __grid_constant__ SegTable t)
+template <int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_decrypt_batch(const __grid_constant__ DecArgs a,
+                                                              const __grid_constant__ SegTable t)
 {
     __shared__ u64 red[32][2][kMaxPrimes];
     const int nl = a.crt.nl;
@@ -756,15 +762,19 @@ cudaError_t launch_decrypt_batch(const DecArgs& a, const SegTable& t, LaunchShap
 {
     const u64 total = t.n > 0 ? t.start[t.n] : 0;
     if (total == 0) return cudaSuccess;
-    k_decrypt_batch<<<persistent_grid(total, ls, num_sms), ls.threads, 0, st>>>(a, t);
+    if (ls.threads <= 256) k_decrypt_batch<256, 8><<<persistent_grid(total, ls, num_sms), ls.threads, 0, st>>>(a, t);
+    else k_decrypt_batch<1024, 1><<<persistent_grid(total, ls, num_sms), ls.threads, 0, st>>>(a, t);
     return cudaGetLastError();
 }
 
-cudaError_t launch_decrypt(const DecArgs& a, cudaStream_t st)
+cudaError_t launch_decrypt(const DecArgs& a, int threads, cudaStream_t st)
 {
     if (a.n_ct == 0) return cudaSuccess;
+    if (threads < 32 || threads > 1024 || threads % 32 != 0) return cudaErrorInvalidValue;
     unsigned grid = (unsigned)(a.n_ct < (1u << 30) ? a.n_ct : (1u << 30));
-    k_decrypt<<<grid, 256, 0, st>>>(a);
+    if (a.n_ct < 64) threads = 1024;   // a few ciphertexts: one wide block each
+    if (threads <= 256) k_decrypt<256, 8><<<grid, threads, 0, st>>>(a);
+    else k_decrypt<1024, 1><<<grid, threads, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -56,7 +56,7 @@ cudaError_t launch_ptmul(const OpsArgs& a, cudaStream_t st);
 cudaError_t launch_rescale(const OpsArgs& a, cudaStream_t st);
 cudaError_t launch_meanfilter3(const OpsArgs& a, cudaStream_t st);
 cudaError_t launch_blend(const OpsArgs& a, cudaStream_t st);
-cudaError_t launch_decrypt(const DecArgs& a, cudaStream_t st);
+cudaError_t launch_decrypt(const DecArgs& a, int threads, cudaStream_t st);
 
 // Ragged batches (SegTable items: ciphertexts, or mean-filter rows x chunks x polys x channels).
 // All segments share the level, the scale class and the constants of `a`.

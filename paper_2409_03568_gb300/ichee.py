@@ -72,7 +72,7 @@ class TuneEntry(ctypes.Structure):
                 ("ms", ctypes.c_float)]
 
 
-TUNE_RADIX, TUNE_LOOKUP, TUNE_MEANFILTER, TUNE_FUSED, TUNE_SCHEDULE = 1, 2, 3, 4, 5
+TUNE_RADIX, TUNE_LOOKUP, TUNE_MEANFILTER, TUNE_FUSED, TUNE_SCHEDULE, TUNE_DECRYPT = 1, 2, 3, 4, 5, 6
 REQ_ENCRYPT, REQ_MEANFILTER, REQ_BRIGHTNESS, REQ_WATERMARK, REQ_MATCH = range(5)
 
 

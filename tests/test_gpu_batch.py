@@ -253,6 +253,37 @@ def test_set_tuned_shape_checks(ichee, ctx8192):
     ichee.ichee_set_tuned_shape(ctx.handle, ichee.TUNE_RADIX, 256, 3)
     assert ichee.ichee_tuned_shape(ctx.handle, ichee.TUNE_RADIX) == (256, 3)
     ichee.ichee_set_tuned_shape(ctx.handle, ichee.TUNE_RADIX, *old)
+    with pytest.raises(ichee.IcheeError):
+        ichee.ichee_set_tuned_shape(ctx.handle, ichee.TUNE_RADIX, 64, 0)   # 32 / 64 only for decryption
+
+
+def test_decrypt_shapes_give_identical_values(ichee, ctx8192):
+    """Decryption (single-image and batched) at every block size it accepts gives the same
+    doubles, bit for bit; the default is 256 threads."""
+    ctx = ctx8192
+    assert ichee.ichee_tuned_shape(ctx.handle, ichee.TUNE_DECRYPT) == (256, 0)
+    shapes, imgs = ragged_images(3, seed=41, hi=12)
+    d_px = [torch.from_numpy(im).cuda() for im in imgs]
+    enc = [ctx.empty_cts(h * w * c, 2) for (h, w, c) in shapes]
+    metas = ichee.ichee_encrypt_batch(ctx.handle, None, d_px, shapes, [9, 10, 11], enc, ctx.stream())
+    ref = None
+    try:
+        for th in (32, 64, 128, 256, 512, 1024):
+            ichee.ichee_set_tuned_shape(ctx.handle, ichee.TUNE_DECRYPT, th, 0 if th != 256 else 2)
+            single = [ctx.decrypt(enc[i], metas[i]) for i in range(len(shapes))]
+            outs = [torch.empty(m.n_ct, dtype=torch.float64, device="cuda") for m in metas]
+            ichee.ichee_decrypt_batch(ctx.handle, enc, metas, outs, ctx.stream())
+            torch.cuda.synchronize()
+            for i in range(len(shapes)):
+                assert torch.equal(single[i], outs[i]), (th, i)
+            if ref is None:
+                ref = single
+                for i in range(len(shapes)):
+                    assert np.max(np.abs(single[i].cpu().numpy() - imgs[i])) < 1e-3
+            for i in range(len(shapes)):
+                assert torch.equal(single[i], ref[i]), (th, i)
+    finally:
+        ichee.ichee_set_tuned_shape(ctx.handle, ichee.TUNE_DECRYPT, 256, 0)
 
 
 def test_batch_errors(ichee, ctx8192):
