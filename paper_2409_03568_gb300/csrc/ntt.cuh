@@ -225,24 +225,47 @@ __device__ __forceinline__ void inv_rest(u64* sm, u64 (&r)[NP][E], int tid, cons
 template <int LE>
 __device__ __forceinline__ int pass_base(int tid, int lo) { return ((tid >> lo) << (lo + LE)) | (tid & ((1 << lo) - 1)); }
 
+// As in the compile-time form, slot = swz(base) ^ swz(e << lo); with lo known only at run time
+// the E offsets swz(e << lo) are XOR combinations of the LE basis values swz(2^k << lo).
+template <int E = 16>
+__device__ __forceinline__ void rt_offsets(int lo, int (&c)[E])
+{
+    constexpr int LE = Radix<E>::LE;
+    int b[LE];
+#pragma unroll
+    for (int k = 0; k < LE; ++k) b[k] = swz<E>(1 << (k + lo));
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        int v = 0;
+#pragma unroll
+        for (int k = 0; k < LE; ++k)
+            if (e & (1 << k)) v ^= b[k];
+        c[e] = v;
+    }
+}
+
 template <int LOGN, int NP, int E = 16>
 __device__ __forceinline__ void store_sm_rt(u64* sm, const u64 (&r)[NP][E], int tid, int lo)
 {
-    const int base = pass_base<Radix<E>::LE>(tid, lo);
+    const int base = swz<E>(pass_base<Radix<E>::LE>(tid, lo));
+    int c[E];
+    rt_offsets<E>(lo, c);
 #pragma unroll
     for (int p = 0; p < NP; ++p)
 #pragma unroll
-        for (int e = 0; e < E; ++e) sm[p * (1 << LOGN) + swz<E>(base | (e << lo))] = r[p][e];
+        for (int e = 0; e < E; ++e) sm[p * (1 << LOGN) + (base ^ c[e])] = r[p][e];
 }
 
 template <int LOGN, int NP, int E = 16>
 __device__ __forceinline__ void load_sm_rt(const u64* sm, u64 (&r)[NP][E], int tid, int lo)
 {
-    const int base = pass_base<Radix<E>::LE>(tid, lo);
+    const int base = swz<E>(pass_base<Radix<E>::LE>(tid, lo));
+    int c[E];
+    rt_offsets<E>(lo, c);
 #pragma unroll
     for (int p = 0; p < NP; ++p)
 #pragma unroll
-        for (int e = 0; e < E; ++e) r[p][e] = sm[p * (1 << LOGN) + swz<E>(base | (e << lo))];
+        for (int e = 0; e < E; ++e) r[p][e] = sm[p * (1 << LOGN) + (base ^ c[e])];
 }
 
 // Forward stages S0 .. S0+LE-1 (lo = LOGN - S0 - LE).
