@@ -137,15 +137,24 @@ __device__ __forceinline__ void meanfilter_row(const OpsArgs& a, const u64* in0,
     const ulonglong2* in = reinterpret_cast<const ulonglong2*>(in0) + (u64)b * LIMBS * (n / 2) + c2;
     ulonglong2* out = reinterpret_cast<ulonglong2*>(out0) + (u64)b * (LIMBS - 1) * (n / 2) + c2;
     const int ym = y > 0 ? y - 1 : 0, yp = y + 1 < h ? y + 1 : h - 1;
+    const int half = n / 2;
+    // the three input rows at column 0 and the output row at column 0; one column further is a
+    // fixed stride of C ciphertexts (pointer adds, no per-column 64-bit products)
+    const ulonglong2* r0 = in + ((u64)ym * w * C + ch) * ct_len2;
+    const ulonglong2* r1 = in + ((u64)y * w * C + ch) * ct_len2;
+    const ulonglong2* r2 = in + ((u64)yp * w * C + ch) * ct_len2;
+    const u64 in_step = (u64)C * ct_len2;
+    ulonglong2* o = out + ((u64)y * w * C + ch) * out_len2;
+    const u64 out_step = (u64)C * out_len2;
 
     ulonglong2 col[3][LIMBS];
     auto column = [&](int xx, ulonglong2 (&dst)[LIMBS]) {
-        const u64 k0 = ((u64)ym * w + xx) * C + ch, k1 = ((u64)y * w + xx) * C + ch, k2 = ((u64)yp * w + xx) * C + ch;
+        const u64 off = (u64)xx * in_step;
 #pragma unroll
         for (int l = 0; l < LIMBS; ++l) {
-            ulonglong2 v0 = __ldg(in + k0 * ct_len2 + l * (n / 2));
-            ulonglong2 v1 = __ldg(in + k1 * ct_len2 + l * (n / 2));
-            ulonglong2 v2 = __ldg(in + k2 * ct_len2 + l * (n / 2));
+            ulonglong2 v0 = __ldg(r0 + off + l * half);
+            ulonglong2 v1 = __ldg(r1 + off + l * half);
+            ulonglong2 v2 = __ldg(r2 + off + l * half);
             dst[l].x = v0.x + v1.x + v2.x;
             dst[l].y = v0.y + v1.y + v2.y;
         }
@@ -155,19 +164,18 @@ __device__ __forceinline__ void meanfilter_row(const OpsArgs& a, const u64* in0,
     for (int l = 0; l < LIMBS; ++l) col[1][l] = col[0][l];
     column(w > 1 ? 1 : 0, col[2]);
     const u64 qt = a.q[LIMBS - 1];
-    for (int x = 0; x < w; ++x) {
+    for (int x = 0; x < w; ++x, o += out_step) {
         const u64 sx = col[0][LIMBS - 1].x + col[1][LIMBS - 1].x + col[2][LIMBS - 1].x;
         const u64 sy = col[0][LIMBS - 1].y + col[1][LIMBS - 1].y + col[2][LIMBS - 1].y;
         const u64 tx = shoup(sx, a.k0[LIMBS - 1], a.k0p[LIMBS - 1], qt);
         const u64 ty = shoup(sy, a.k0[LIMBS - 1], a.k0p[LIMBS - 1], qt);
-        ulonglong2* o = out + (((u64)y * w + x) * C + ch) * out_len2;
 #pragma unroll
         for (int j = 0; j < LIMBS - 1; ++j) {
             const u64 qj = a.q[j];
             ulonglong2 v;
             v.x = rescale_fold(shoup_lazy(col[0][j].x + col[1][j].x + col[2][j].x, a.k0r[j], a.k0rp[j], qj), tx, j, a);
             v.y = rescale_fold(shoup_lazy(col[0][j].y + col[1][j].y + col[2][j].y, a.k0r[j], a.k0rp[j], qj), ty, j, a);
-            __stcs(o + j * (n / 2), v);
+            __stcs(o + j * half, v);
         }
         if (x + 1 < w) {
 #pragma unroll
