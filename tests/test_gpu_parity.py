@@ -511,11 +511,14 @@ def test_degenerate_pixel_values(ichee):
 @pytest.mark.parametrize("wl", [
     dict(name="paper_n4096_q109", log_n=12, prime_bits=[45, 32, 32], log2_scale=32, special_bits=50),
     dict(name="n2048", log_n=11, prime_bits=[45, 30, 30], log2_scale=30, special_bits=50),
+    dict(name="n1024_8primes", log_n=10, prime_bits=[50, 40, 40, 40, 40, 40, 40, 40], log2_scale=40,
+         special_bits=58),
 ], ids=lambda w: w["name"])
 def test_other_rings_bit_exact(ichee, wl):
-    """N = 4096 with a 109-bit ciphertext modulus (the paper's parameter set) and N = 2048:
-    keys, fresh and radix encryption, mean filter, matching and the per-pixel squared
-    difference, every ciphertext word against the oracle."""
+    """N = 4096 with a 109-bit ciphertext modulus (the paper's parameter set), N = 2048, and
+    the largest limb count the library takes (8 primes): keys, fresh and radix encryption, mean
+    filter, matching and the per-pixel squared difference, every ciphertext word against the
+    oracle."""
     ctx = gpu_for(ichee, wl, with_evk=True)
     o = oracle_for(wl, with_evk=True)
     n, L = ctx.n, ctx.L
