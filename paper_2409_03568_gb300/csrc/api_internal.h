@@ -141,6 +141,14 @@ constexpr u64 kIdRadixBase = 1ull << 33;
 
 
 namespace ichee {
+// Ciphertexts of an h x w x c image; 0 if the image is empty or holds more than 2^40 of them (no
+// device stores that many, and every size computed from the count then fits 64 bits).
+inline u64 image_cts(uint32_t h, uint32_t w, uint32_t c)
+{
+    const u64 hw = (u64)h * w;
+    if (hw == 0 || c == 0 || hw > (1ull << 40) / c) return 0;
+    return hw * c;
+}
 size_t ct_words(const ichee_ctx* c, int limbs);
 bool is_device_ptr(const void* p);
 // Bytes from p to the end of the device allocation holding it; false if unknown.

@@ -16,13 +16,13 @@ namespace hm = ichee::host;
 
 namespace {
 
-u64 n_ct_of(const ichee_image_desc& d) { return (u64)d.h * d.w * d.c; }
+u64 n_ct_of(const ichee_image_desc& d) { return image_cts(d.h, d.w, d.c); }
 
 ichee_status check_desc(const ichee_image_desc* images, uint32_t n)
 {
     if (!images || n == 0) return fail(ICHEE_EINVAL, "empty batch");
     for (uint32_t i = 0; i < n; ++i)
-        if (n_ct_of(images[i]) == 0) return fail(ICHEE_EINVAL, "image %u is empty", i);
+        if (n_ct_of(images[i]) == 0) return fail(ICHEE_EINVAL, "image %u is empty or oversized", i);
     return ICHEE_OK;
 }
 

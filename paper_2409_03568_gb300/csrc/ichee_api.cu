@@ -778,8 +778,8 @@ extern "C" ichee_status ichee_encrypt_image(ichee_ctx* c, const ichee_cache* k, 
     if (!c || !pixels || !d_out || !meta) return fail(ICHEE_EINVAL, "null argument");
     if (!c->have_pk) return fail(ICHEE_EINVAL, "ichee_encrypt_image: no public key (ichee_keygen or ichee_import_key)");
     if (k && k->ctx != c) return fail(ICHEE_EMISMATCH, "cache belongs to another context");
-    const u64 n_ct = (u64)h * w * ch;
-    if (n_ct == 0) return fail(ICHEE_EINVAL, "empty image %ux%ux%u", h, w, ch);
+    const u64 n_ct = image_cts(h, w, ch);
+    if (n_ct == 0) return fail(ICHEE_EINVAL, "empty or oversized image %ux%ux%u", h, w, ch);
     CK(cudaSetDevice(c->device));
     ichee_status s = check_out(c, d_out, n_ct, c->L, "ciphertext output");
     if (s != ICHEE_OK) return s;
@@ -878,7 +878,7 @@ ichee_status ichee::check_img(const ichee_ctx* c, const uint64_t* d, const ichee
 {
     if (!d || !m) return fail(ICHEE_EINVAL, "%s: null operand", what);
     if ((int)m->level >= c->L) return fail(ICHEE_ELEVEL, "%s: level %u >= %d", what, m->level, c->L);
-    if ((u64)m->h * m->w * m->c == 0) return fail(ICHEE_EINVAL, "%s: empty image", what);
+    if (image_cts(m->h, m->w, m->c) == 0) return fail(ICHEE_EINVAL, "%s: empty or oversized image", what);
     if (!(m->scale > 0.0)) return fail(ICHEE_ESCALE, "%s: scale must be positive", what);
     if (!is_device_ptr(d)) return fail(ICHEE_EINVAL, "%s: ciphertexts must be device memory", what);
     return check_span(d, (u64)m->h * m->w * m->c * ct_words(c, (int)m->level + 1) * 8, what);

@@ -436,7 +436,7 @@ extern "C" ichee_status ichee_server_submit(ichee_server* s, const ichee_request
     if (!s || !r || !ticket) return fail(ICHEE_EINVAL, "null argument");
     if (r->ring >= s->rings.size()) return fail(ICHEE_EINVAL, "ring %u out of range", r->ring);
     if (r->kind > ICHEE_REQ_MATCH) return fail(ICHEE_EINVAL, "unknown request kind %u", r->kind);
-    if ((u64)r->h * r->w * r->c == 0) return fail(ICHEE_EINVAL, "empty image");
+    if (image_cts(r->h, r->w, r->c) == 0) return fail(ICHEE_EINVAL, "empty or oversized image");
     if (!r->pixels || !r->result) return fail(ICHEE_EINVAL, "request needs pixels and a result buffer");
     if ((r->kind == ICHEE_REQ_WATERMARK || r->kind == ICHEE_REQ_MATCH) && !r->pixels2)
         return fail(ICHEE_EINVAL, "watermark and match need a second image");

@@ -565,6 +565,14 @@ def test_error_paths(ichee):
     with pytest.raises(ichee.IcheeError) as e:
         ichee.ichee_encrypt_image(ctx.handle, None, pix, 2, 2, 1, 1, host_out, ctx.stream())
     assert e.value.status == ichee.EINVAL
+    small = ctx.empty_cts(4, ctx.L - 1)
+    for shape in ((1 << 31, 1 << 31, 1), (1 << 20, 1 << 20, 2)):   # products beyond 2^40 ciphertexts
+        with pytest.raises(ichee.IcheeError) as e:
+            ichee.ichee_encrypt_image(ctx.handle, None, pix, *shape, 1, small, ctx.stream())
+        assert e.value.status == ichee.EINVAL and "oversized" in str(e.value)
+        with pytest.raises(ichee.IcheeError) as e:
+            ichee.ichee_encrypt_batch(ctx.handle, None, [pix], [shape], [1], [small], ctx.stream())
+        assert e.value.status == ichee.EINVAL
     ct, m = ctx.encrypt(pix, 2, 2, 1, 1)
     r1, m1 = ctx.eval(ichee.OP_RESCALE, ct, m, out_level=0)
     with pytest.raises(ichee.IcheeError) as e:
