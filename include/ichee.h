@@ -258,6 +258,15 @@ ichee_status ichee_decrypt_image(ichee_ctx* ctx, const uint64_t* d_ct, const ich
                                  void* stream);
 
 /*
+ * ichee_decrypt_image without waiting: out is device memory or page-locked host memory (from
+ * cudaHostAlloc / cudaHostRegister, or a pinned tensor), which the decryption kernel writes
+ * directly; the values are ready once `stream` is. Pageable host memory is refused (EINVAL).
+ * Errors otherwise as ichee_decrypt_image.
+ */
+ichee_status ichee_decrypt_image_async(ichee_ctx* ctx, const uint64_t* d_ct, const ichee_ctimg_meta* meta,
+                                       double* out, void* stream);
+
+/*
  * Like ichee_decrypt_image, and also writes the residues of coefficient 0 of c0 + c1*s per
  * limb to residues_out (host or device, n_ct * (level+1) uint64).
  */

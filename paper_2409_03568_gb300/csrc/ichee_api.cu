@@ -1160,8 +1160,22 @@ extern "C" ichee_status ichee_set_allocator(ichee_ctx* c, ichee_alloc_fn alloc, 
 // ---------------------------------------------------------------------------------------
 // Decryption
 // ---------------------------------------------------------------------------------------
+// Device address of page-locked host memory the GPU can write directly (null for pageable
+// host memory or device memory).
+static void* mapped_host_ptr(const void* p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+// async_out: the output is device memory or page-locked host memory written by the kernel
+// itself; nothing is staged and the call does not wait.
 static ichee_status decrypt_impl(ichee_ctx* c, const uint64_t* d_ct, const ichee_ctimg_meta* m, double* out,
-                                 uint64_t* residues, void* stream)
+                                 uint64_t* residues, void* stream, bool async_out)
 {
     if (!c || !out) return fail(ICHEE_EINVAL, "null argument");
     if (!c->have_sk) return fail(ICHEE_EINVAL, "no secret key");
@@ -1175,6 +1189,11 @@ static ichee_status decrypt_impl(ichee_ctx* c, const uint64_t* d_ct, const ichee
     const bool res_dev = residues == nullptr || is_device_ptr(residues);
     if (out_dev && (s = check_span(out, n_ct * 8, "output")) != ICHEE_OK) return s;
     if (residues && res_dev && (s = check_span(residues, n_ct * nl * 8, "residues")) != ICHEE_OK) return s;
+    double* direct = out_dev ? out : nullptr;   // written by the kernel in place
+    if (async_out && !out_dev) {
+        direct = static_cast<double*>(mapped_host_ptr(out));
+        if (!direct) return fail(ICHEE_EINVAL, "output must be device or page-locked host memory");
+    }
     DecArgs a;
     std::memset(&a, 0, sizeof(a));
     a.logn = c->logn;
@@ -1184,7 +1203,7 @@ static ichee_status decrypt_impl(ichee_ctx* c, const uint64_t* d_ct, const ichee
     a.srev = c->d_srev;
     a.ct = d_ct;
     a.scale = m->scale;
-    if (out_dev) a.out = out;
+    if (direct) a.out = direct;
     else {
         CK(c->stage_out.ensure(n_ct * 8, c->user_alloc, c->user_free, c->user_alloc_ctx, st));
         a.out = (double*)c->stage_out.p;
@@ -1197,9 +1216,9 @@ static ichee_status decrypt_impl(ichee_ctx* c, const uint64_t* d_ct, const ichee
         }
     }
     CK(launch_decrypt(a, c->shape_decrypt.threads, st));
-    if (!out_dev) CK(cudaMemcpyAsync(out, a.out, n_ct * 8, cudaMemcpyDeviceToHost, st));
+    if (!direct) CK(cudaMemcpyAsync(out, a.out, n_ct * 8, cudaMemcpyDeviceToHost, st));
     if (residues && !res_dev) CK(cudaMemcpyAsync(residues, a.residues_out, n_ct * nl * 8, cudaMemcpyDeviceToHost, st));
-    if (!out_dev || (residues && !res_dev)) CK(cudaStreamSynchronize(st));
+    if (!direct || (residues && !res_dev)) CK(cudaStreamSynchronize(st));
     return ICHEE_OK;
 }
 
@@ -1207,14 +1226,21 @@ extern "C" ichee_status ichee_decrypt_image(ichee_ctx* c, const uint64_t* d_ct, 
                                             void* stream)
 {
     ichee::NvtxRange nvtx_range("ichee_decrypt_image");
-    return decrypt_impl(c, d_ct, m, out, nullptr, stream);
+    return decrypt_impl(c, d_ct, m, out, nullptr, stream, false);
+}
+
+extern "C" ichee_status ichee_decrypt_image_async(ichee_ctx* c, const uint64_t* d_ct, const ichee_ctimg_meta* m,
+                                                  double* out, void* stream)
+{
+    ichee::NvtxRange nvtx_range("ichee_decrypt_image_async");
+    return decrypt_impl(c, d_ct, m, out, nullptr, stream, true);
 }
 
 extern "C" ichee_status ichee_decrypt_residues(ichee_ctx* c, const uint64_t* d_ct, const ichee_ctimg_meta* m,
                                                double* out, uint64_t* residues, void* stream)
 {
     if (!residues) return fail(ICHEE_EINVAL, "null residues");
-    return decrypt_impl(c, d_ct, m, out, residues, stream);
+    return decrypt_impl(c, d_ct, m, out, residues, stream, false);
 }
 
 extern "C" ichee_status ichee_stream_status(ichee_ctx* c, void* stream)

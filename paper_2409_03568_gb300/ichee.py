@@ -117,6 +117,7 @@ _SIGS = {
                          _vp, _u32, _vp, ctypes.POINTER(CtImgMeta), _vp]),
     "ichee_decrypt_image": (_st, [_vp, _vp, ctypes.POINTER(CtImgMeta), _vp, _vp]),
     "ichee_decrypt_residues": (_st, [_vp, _vp, ctypes.POINTER(CtImgMeta), _vp, _vp, _vp]),
+    "ichee_decrypt_image_async": (_st, [_vp, _vp, ctypes.POINTER(CtImgMeta), _vp, _vp]),
     "ichee_sqdiff_sum_noalloc": (_st, [_vp, _vp, ctypes.POINTER(CtImgMeta), _vp, ctypes.POINTER(CtImgMeta), _vp,
                                        ctypes.POINTER(CtImgMeta), _vp]),
     "ichee_encrypt_batch": (_st, [_vp, _vp, ctypes.POINTER(_vp), ctypes.POINTER(ImageDesc), _u32,
@@ -295,6 +296,11 @@ def ichee_eval(ctx, op, a, ma, b=None, mb=None, args=(), out=None, stream=None):
 
 def ichee_decrypt_image(ctx, ct, meta, out, stream=None):
     _check(_lib.ichee_decrypt_image(ctx, _ptr(ct), ctypes.byref(meta), _ptr(out), stream))
+
+
+def ichee_decrypt_image_async(ctx, ct, meta, out, stream=None):
+    """Decrypt into device or page-locked host memory without waiting for the stream."""
+    _check(_lib.ichee_decrypt_image_async(ctx, _ptr(ct), ctypes.byref(meta), _ptr(out), stream))
 
 
 def ichee_decrypt_residues(ctx, ct, meta, out, residues, stream=None):

@@ -95,6 +95,28 @@ def test_fresh_toy_bit_exact_and_decodes(ichee):
     ctx.close()
 
 
+def test_decrypt_async_into_pinned_memory(ichee):
+    """ichee_decrypt_image_async writes page-locked host memory (or device memory) from the
+    kernel and returns without waiting; after the stream the values equal the synchronous
+    call's. Pageable host memory is refused."""
+    wl = W.TOY
+    ctx = gpu_for(ichee, wl)
+    pix = W.image_for(wl).reshape(-1)
+    ct, meta = ctx.encrypt(torch.from_numpy(pix).cuda(), wl["h"], wl["w"], wl["c"], IMG_SEED)
+    ref = ctx.decrypt(ct, meta).cpu()
+    pinned = torch.full((64,), -1.0, dtype=torch.float64).pin_memory()
+    ichee.ichee_decrypt_image_async(ctx.handle, ct, meta, pinned, ctx.stream())
+    torch.cuda.synchronize()
+    assert torch.equal(pinned, ref)
+    dev = torch.empty(64, dtype=torch.float64, device="cuda")
+    ichee.ichee_decrypt_image_async(ctx.handle, ct, meta, dev, ctx.stream())
+    assert torch.equal(dev.cpu(), ref)
+    with pytest.raises(ichee.IcheeError) as e:
+        ichee.ichee_decrypt_image_async(ctx.handle, ct, meta, np.zeros(64), ctx.stream())
+    assert e.value.status == ichee.EINVAL
+    ctx.close()
+
+
 def test_fresh_enc8192_full_image_sampled(ichee):
     wl = W.ENC8192
     ctx = gpu_for(ichee, wl)
