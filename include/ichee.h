@@ -241,6 +241,9 @@ ichee_status ichee_encrypt_image(ichee_ctx* ctx, const ichee_cache* cache, const
  * only.
  * op_args holds the operation's real-valued arguments (host). d_out must not overlap the
  * inputs, except that PTADD, BRIGHTNESS and WATERMARK_PIXEL may run in place (d_out == d_a).
+ * d_out holds h*w*c ciphertexts (one for SQDIFF_SUM) at level ma->level, or ma->level - 1 for
+ * RESCALE, MEANFILTER3, BLEND, SQDIFF_SUM and SQDIFF (ichee_ct_bytes); a shorter allocation
+ * gives EINVAL before any launch.
  * *mout receives the result's shape, level and scale. Errors: EINVAL, ELEVEL (no limb to
  * drop), ESCALE, EMISMATCH (shapes), EUNSUPPORTED (no evaluation key), ENOMEM, ECUDA.
  */
