@@ -359,7 +359,9 @@ def run_ours(args):
         out["e2e"] = e2e_ours(args, ctx, ichee, img, wm_ct, wm_meta, nz_ct, nz_meta, beta, caches, methods, enc_out,
                               ops_out, st, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(sample_steps=1, sample=484)
+        ref = {}
+        out["cpu_baseline"] = cpu_baseline(sample_steps=1, sample=484, keep=ref)
+        out["parity_sample"] = parity_on_sample(ctx, enc_out, ops_out, ref)
     if rank == 0:
         print(json.dumps(out))
     ctx.close()
@@ -459,9 +461,11 @@ def oracle_step_setup(sample):
     return o, img, idx, caches, wm, noisy
 
 
-def oracle_step(o, img, idx, caches, wm, noisy):
+def oracle_step(o, img, idx, caches, wm, noisy, keep=None):
     """The step of the GPU arm restricted to the sampled pixels (ops on a 3x3-neighbourhood
-    patch per sampled pixel are replaced by the same ops on the sampled ciphertexts)."""
+    patch per sampled pixel are replaced by the same ops on the sampled ciphertexts). With
+    `keep` (a dict), the per-ciphertext results are left in it: the five encryptions,
+    brightness and blend of the sampled pixels."""
     px = img[idx.astype(np.int64)]
     outs = {"fresh": o.encrypt_pixels(px, 7, ids=idx)}
     outs["radix16"] = o.encrypt_radix(px, caches["radix16"], 7, ids=idx)
@@ -472,7 +476,7 @@ def oracle_step(o, img, idx, caches, wm, noisy):
     k = len(idx)
     side = int(np.sqrt(k))
     mf, sc_mf = o.meanfilter3(fr[:side * side], o.delta, side, side, 1)
-    br, sc_br = o.brightness(fr, o.delta, 7.5)
+    br, sc_br = o.brightness(fr, o.delta, inputs.brightness_beta(4))   # the GPU arm's beta
     wct = o.encrypt_pixels(wm[idx.astype(np.int64)], 21, ids=idx)
     bl, sc_bl = o.blend(fr, wct, o.delta, 0.9, 1, 1)
     nct = o.encrypt_pixels(noisy[idx.astype(np.int64)], 22, ids=idx)
@@ -483,21 +487,44 @@ def oracle_step(o, img, idx, caches, wm, noisy):
     o.decrypt(br, sc_br)
     o.decrypt(bl, sc_bl)
     o.decrypt(mt, sc_mt)
+    if keep is not None:
+        keep.update(outs)
+        keep["brightness"], keep["blend"] = br, bl
     return 5 * k
 
 
-def cpu_baseline(sample_steps=1, sample=36):
+def cpu_baseline(sample_steps=1, sample=36, keep=None):
+    """The oracle timed on the host cores; with `keep`, its per-ciphertext results of the last
+    step and the sampled indices (`keep["idx"]`) are left for a parity check."""
     from oracle.ckks import lib as olib
     setup = oracle_step_setup(sample)
     t0 = time.perf_counter()
     units = 0
     for _ in range(sample_steps):
-        units += oracle_step(*setup)
+        units += oracle_step(*setup, keep=keep)
     dt = time.perf_counter() - t0
+    if keep is not None:
+        keep["idx"] = setup[2]
     return {"value": round(units / dt, 3), "unit": UNIT, "cores": int(olib().orc_num_threads()), "kind": "oracle",
             "sample": "%d of the 4096 pixels per method (5 methods), ops on those ciphertexts (mean filter on a "
                       "%dx%d patch), decryption; %d step(s), %.1f s" % (sample, int(np.sqrt(sample)),
                                                                       int(np.sqrt(sample)), sample_steps, dt)}
+
+
+def parity_on_sample(ctx, enc_out, ops_out, ref, n_check=64):
+    """Ciphertexts of the bench run against the oracle's, on the first n_check sampled pixels:
+    the five encryptions, brightness and blend, word for word."""
+    import torch
+    idx = torch.from_numpy(ref["idx"][:n_check].astype(np.int64))
+    mismatched, checked = [], []
+    for name in list(enc_out) + ["brightness", "blend"]:
+        t = enc_out[name] if name in enc_out else ops_out[name]
+        want = ref[name][:n_check]
+        rows = t.view(-1, want[0].size).index_select(0, idx.to(t.device)).cpu().numpy().view(np.uint64)
+        checked.append(name)
+        if not np.array_equal(rows.reshape(want.shape), want):
+            mismatched.append(name)
+    return {"pixels": int(len(idx)), "results": checked, "bit_exact": not mismatched, "mismatched": mismatched}
 
 
 def run_reference(args):
