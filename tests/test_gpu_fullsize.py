@@ -3,6 +3,8 @@
 * The benchmark's launch configuration: the 64x64 image at N = 8192, primes 60/40/60 (plus the
   61-bit special prime of the evaluation key), every image operation the benchmark step runs.
 * The four-prime operations workload: a 128x128x3 image at N = 8192, primes 60/40/40/40.
+* The 32-image ragged batch (radix-16 encryption + mean filter, 142 GB of ciphertexts) in the
+  batched entry points' default launch shapes.
 
 For a sampled output pixel the oracle encrypts exactly the input pixels that output depends
 on (same seeds, same ciphertext ids) and applies its own operation; the GPU ciphertext must
@@ -206,3 +208,54 @@ def test_ops_128x128x3_blend_and_matching(ichee, ops_full):
     plain = float(((flat.astype(np.float64) - noisy) ** 2).sum())
     dec = float(ctx.decrypt(om, mm).cpu().numpy()[0])
     assert abs(dec - plain) < 1e-7 * plain + 0.01
+
+
+def test_batch32_full_size_sampled(ichee):
+    """The 32-image ragged batch at its full size (216,613 pixels, 142 GB of ciphertexts) through
+    the batched radix-16 encryption and the batched mean filter in their default launch shapes
+    (the autotuner's choice for this batch): sampled ciphertexts and filter outputs of the
+    first, the largest and the last image against the oracle, one by one."""
+    wl = W.BATCH32
+    imgs = inputs.ragged_batch(wl["n_images"], wl["batch_seed"], wl["side_lo"], wl["side_hi"])
+    shapes = [(im.shape[0], im.shape[1], 1) for im in imgs]
+    n_total = sum(h * w for h, w, _ in shapes)
+    need = n_total * (393216 + 262144)
+    free, _ = torch.cuda.mem_get_info()
+    if free < need + (16 << 30):
+        pytest.skip("needs %.0f GB of free device memory" % (need / 1e9))
+    ctx = ichee.Context(**W.ctx_kwargs(wl))
+    ctx.keygen(77)
+    cache = ctx.build_cache(ichee.CACHE_RADIX, 15, radix_base=wl["radix_base"], randomize=1)
+    seeds = [500 + i for i in range(len(imgs))]
+    d_px = [torch.from_numpy(im.reshape(-1).copy()).cuda() for im in imgs]
+    enc = [ctx.empty_cts(h * w, 2) for h, w, _ in shapes]
+    filt = [ctx.empty_cts(h * w, 1) for h, w, _ in shapes]
+    metas = ichee.ichee_encrypt_batch(ctx.handle, cache, d_px, shapes, seeds, enc, ctx.stream())
+    ichee.ichee_eval_batch(ctx.handle, ichee.OP_MEANFILTER3, enc, metas, outs=filt, stream=ctx.stream())
+    torch.cuda.synchronize()
+    ctx.status()
+    o = Oracle(Params(wl["log_n"], wl["prime_bits"], wl["log2_scale"])).keygen(77)
+    oc = o.radix_cache(wl["radix_base"], 15)
+    n = ctx.n
+    largest = int(np.argmax([h * w for h, w, _ in shapes]))
+    try:
+        for i in (0, largest, len(imgs) - 1):
+            h, w, _ = shapes[i]
+            flat = imgs[i].reshape(-1)
+            idx = sample_idx(h * w, 3, seed=i)
+            sel = torch.from_numpy(idx.astype(np.int64)).cuda()
+            got_e = enc[i].view(h * w, -1).index_select(0, sel).cpu().numpy().view(np.uint64).reshape(-1, 2, 3, n)
+            ref_e = o.encrypt_radix(flat[idx], oc, seeds[i], ids=idx.astype(np.uint64))
+            assert np.array_equal(got_e, ref_e), i
+            got_f = filt[i].view(h * w, -1).index_select(0, sel).cpu().numpy().view(np.uint64).reshape(-1, 2, 2, n)
+            for j, k in enumerate(idx):
+                y, x = divmod(int(k), w)
+                nb = np.array([_clamp(y + dy, h) * w + _clamp(x + dx, w) for dy in (-1, 0, 1) for dx in (-1, 0, 1)],
+                              dtype=np.uint64)
+                patch = o.encrypt_radix(flat[nb.astype(np.int64)], oc, seeds[i], ids=nb)
+                out, _ = o.meanfilter3(patch, o.delta, 3, 3, 1)
+                assert np.array_equal(got_f[j], out[4]), (i, int(k))
+    finally:
+        del enc, filt, d_px
+        ctx.close()
+        torch.cuda.empty_cache()
