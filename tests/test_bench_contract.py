@@ -25,3 +25,33 @@ def test_reference_arm_prints_one_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_parity_on_sample_compares_word_for_word():
+    """The bench's parity check (its ciphertexts against the oracle's on the CPU-baseline sample)
+    accepts identical words and names every result that differs in one word."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import torch
+    import bench
+    ref = {}
+    bench.cpu_baseline(sample_steps=1, sample=9, keep=ref)
+    idx = ref["idx"].astype(np.int64)
+    n_px, n = 4096, 8192
+    enc = {}
+    for m in ("fresh", "radix16", "radix10", "freq32_pool64", "full256_pool64"):
+        t = np.zeros((n_px, 2, 3, n), dtype=np.uint64)
+        t[idx] = ref[m]
+        enc[m] = torch.from_numpy(t.view(np.int64).reshape(-1))
+    ops = {}
+    for name, limbs in (("brightness", 3), ("blend", 2)):
+        t = np.zeros((n_px, 2, limbs, n), dtype=np.uint64)
+        t[idx] = ref[name]
+        ops[name] = torch.from_numpy(t.view(np.int64).reshape(-1))
+    ok = bench.parity_on_sample(None, enc, ops, ref, n_check=9)
+    assert ok["bit_exact"] and ok["pixels"] == 9 and len(ok["results"]) == 7
+    flipped = enc["radix10"].view(n_px, -1)
+    flipped[int(idx[4]), 12345] ^= 1
+    bad = bench.parity_on_sample(None, enc, ops, ref, n_check=9)
+    assert not bad["bit_exact"] and bad["mismatched"] == ["radix10"]
