@@ -16,7 +16,10 @@
  *    reserved address range): a buffer that ends before the bytes the call needs gives
  *    ICHEE_EINVAL. Memory the driver does not describe is trusted.
  *    Pixel inputs and decrypted outputs may be host or device memory; host buffers are staged
- *    through library-owned device memory (and the call then waits for its own copies).
+ *    through library-owned device memory. A decryption into host memory waits for its copy
+ *    (ichee_decrypt_image_async does not). Host pixel input follows cudaMemcpyAsync: pageable
+ *    memory may be reused when the call returns, page-locked memory once the stream has passed
+ *    the call.
  *    Library-owned state (keys, tables, caches) lives in opaque handles freed by the
  *    matching destroy/free call.
  *  - Layouts: one ciphertext = uint64[2][limbs][N] residues in the coefficient domain
