@@ -19,7 +19,8 @@
  *    through library-owned device memory. A decryption into host memory waits for its copy
  *    (ichee_decrypt_image_async does not). Host pixel input follows cudaMemcpyAsync: pageable
  *    memory may be reused when the call returns, page-locked memory once the stream has passed
- *    the call.
+ *    the call. The staging buffers belong to the context: calls that stage host buffers on
+ *    different streams must be ordered between those streams by the caller.
  *    Library-owned state (keys, tables, caches) lives in opaque handles freed by the
  *    matching destroy/free call.
  *  - Layouts: one ciphertext = uint64[2][limbs][N] residues in the coefficient domain
