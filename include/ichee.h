@@ -473,6 +473,15 @@ ichee_status ichee_server_hold(ichee_server* server, int hold);
 void ichee_server_destroy(ichee_server* server);
 
 /*
+ * Failure injection for tests (not part of the method), on the host only: the next
+ * launch_errors admission rounds launch nothing and fail as a launch error would, and the next
+ * query_errors round completions report a device error instead of reading the round's event.
+ * Every request of such a round completes with ICHEE_ECUDA; the server keeps serving and
+ * ichee_server_destroy returns. No GPU fault is involved. Errors: EINVAL.
+ */
+ichee_status ichee_server_inject_failure(ichee_server* server, uint32_t launch_errors, uint32_t query_errors);
+
+/*
  * Matching (the ICHEE_OP_SQDIFF_SUM operation) for callers that cannot allocate device
  * memory: processes whose GPU memory is handed out by their own arena or pool, or loops that
  * must not risk the device-wide synchronisation cudaMalloc / cudaFree can cause. The paper

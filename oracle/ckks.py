@@ -9,12 +9,19 @@ The ring arithmetic lives in ckks_oracle.c (scalar C, 128-bit products). This mo
 those steps together in the paper's order, keeps the scale of every ciphertext as an exact
 rational, and decodes with exact big-integer CRT (Python ints):
 
-  * KeyGen / Enc / Dec ............ Sec. 2.2.2 (sign convention: reading R1)
-  * encoding of one pixel ......... Sec. 2.2 encoding, reading R2 (constant polynomial)
-  * add / mult / relin / rescale .. Sec. 2.2.3 (relin: reading R11, rescale: reading R10)
+  * KeyGen / Enc / Dec ............ Sec. 2.2.2, with the library sign convention
+                                    pk = (-a*s + e, a), Dec = ct0 + ct1*s (the printed
+                                    formulas do not cancel)
+  * encoding of one pixel ......... Sec. 2.2 encoding: the pixel fills every slot, so the
+                                    plaintext is the constant polynomial Delta*p
+  * add / mult / relin / rescale .. Sec. 2.2.3; relin by hybrid key switching with one
+                                    special prime P, rescale with centered rounding
   * radix / scanning / full cache . Sec. 3.2
-  * radix randomness, zero pool ... Sec. 3.3 (readings R7, R8)
-  * mean filter, brightness, matching, watermark ... Sec. 4.4 (readings R12-R15)
+  * radix randomness, zero pool ... Sec. 3.3: one Philox bit per radix position decides the
+                                    add/subtract step; the pool index is a Philox draw
+  * mean filter, brightness, matching, watermark ... Sec. 4.4 (clamp-to-edge borders, no clamp
+                                    of the encrypted brightness, squared L2 distance for
+                                    matching, blend alpha*I + (1-alpha)*W)
   * MSE / PSNR .................... Sec. 4.3.2
 """
 import ctypes
@@ -66,7 +73,8 @@ def llround(x):
 
 class Params:
     """CKKS parameters (Sec. 2.2 parameter table): ring dimension N = 2^log_n, ciphertext
-    primes of the given bit sizes (reading R3), scale Delta = 2^log2_scale, special prime bits
+    primes of the given bit sizes (for each size, the largest unused prime q < 2^bits with
+    q = 1 mod 2N), scale Delta = 2^log2_scale, special prime bits
     for the evaluation key (0 = none), Gaussian sigma and tail bound."""
 
     def __init__(self, log_n, prime_bits, log2_scale, special_bits=0, sigma=3.2, bound=19):
@@ -133,7 +141,7 @@ class Oracle:
         return out
 
     def encode_pixels(self, pixels):
-        """Reading R2: pixel p fills every slot, so its plaintext is the constant Delta*p."""
+        """Encoding (Sec. 2.2): pixel p fills every slot, so its plaintext is the constant Delta*p."""
         return np.asarray(pixels, dtype=np.int64).reshape(-1) * self.delta
 
     def encrypt_pixels(self, pixels, seed, ids=None):
@@ -162,7 +170,7 @@ class Oracle:
     @staticmethod
     def top_values(scan_pixels, k):
         """Scanning step of Sec. 3.2: the k most frequent values present, ties to the smaller
-        value (reading R9)."""
+        value; values absent from the scan are never cached."""
         counts = np.bincount(np.asarray(scan_pixels, dtype=np.uint8).reshape(-1), minlength=256)
         order = sorted(range(256), key=lambda v: (-int(counts[v]), v))
         return [v for v in order if counts[v] > 0][:k]
@@ -275,7 +283,8 @@ class Oracle:
         return out
 
     def rescale(self, a):
-        """Rescale by the last prime (Sec. 2.2.3, reading R10)."""
+        """Rescale by the last prime q_t (Sec. 2.2.3): c_j <- (c_j - [c_t]_centered) * q_t^-1 mod q_j,
+        centered in (-q_t/2, q_t/2]."""
         lim = self._limbs(a)
         out = np.zeros(a.shape[:-2] + (lim - 1, self.n), dtype=np.uint64)
         for j in range(a.shape[0]):
@@ -284,10 +293,11 @@ class Oracle:
         return out
 
     def encode_const(self, value, scale):
-        """A real plaintext constant at a given scale: llround(value * scale) (reading R13)."""
+        """A real plaintext constant at a given scale: llround(value * scale) in FP64, halves away
+        from zero."""
         return llround(float(value) * float(scale))
 
-    # brightness, Sec. 4.4.2 (reading R14)
+    # brightness, Sec. 4.4.2: beta added to coefficient 0, no clamp in the encrypted domain
     def brightness(self, a, scale, beta):
         return self.add_int(a, self.encode_const(beta, scale)), Fraction(scale)
 
@@ -302,7 +312,7 @@ class Oracle:
         return self.mul_int(a, k), Fraction(scale) * self.delta
 
     def meanfilter3(self, a, scale, h, w, ch):
-        """3x3 mean filter (Sec. 4.4.1, reading R13): 9-neighbour sum, x encoded 1/9, rescale."""
+        """3x3 mean filter (Sec. 4.4.1): clamp-to-edge 9-neighbour sum, x encoded 1/9, rescale."""
         lim = self._limbs(a)
         k9 = self.encode_const(1.0 / 9.0, self.delta)
         out = np.zeros((h * w * ch, 2, lim - 1, self.n), dtype=np.uint64)
@@ -313,7 +323,8 @@ class Oracle:
         return out, Fraction(scale) * self.delta / int(self.q[lim - 1])
 
     def blend(self, img, wm, scale, alpha, ch, ch_w):
-        """Watermark blend alpha*I + (1-alpha)*W (reading R15)."""
+        """Watermark blend alpha*I + (1-alpha)*W, W an encrypted pattern (the workload's form of
+        Sec. 4.4.4)."""
         lim = self._limbs(img)
         ka = self.encode_const(alpha, self.delta)
         kb = self.encode_const(1.0 - float(alpha), self.delta)
@@ -336,7 +347,8 @@ class Oracle:
         return out
 
     def relin(self, d):
-        """Relinearise a degree-2 ciphertext [3][limbs][n] (Sec. 2.2.3, reading R11)."""
+        """Relinearise a degree-2 ciphertext [3][limbs][n] (Sec. 2.2.3) by hybrid key switching:
+        one digit per ciphertext prime, one special prime P, mod-down with centered rounding."""
         lim = d.shape[1]
         out = np.zeros((2, lim, self.n), dtype=np.uint64)
         d = np.ascontiguousarray(d)
@@ -345,7 +357,8 @@ class Oracle:
         return out
 
     def match(self, a, b, scale):
-        """Image matching (Sec. 4.4.3, reading R12): sum of squared differences, relinearised
+        """Image matching (Sec. 4.4.3; |x| is not a CKKS polynomial, so the squared L2 distance):
+        sum of squared differences, relinearised
         once and rescaled once. Returns ([1][2][limbs-1][n], scale)."""
         lim = self._limbs(a)
         t = self.sqdiff_sum_raw(a, b)
@@ -353,7 +366,7 @@ class Oracle:
         return self.rescale(r), Fraction(scale) * Fraction(scale) / int(self.q[lim - 1])
 
     def sqdiff_image(self, a, b, scale):
-        """Squared difference pixel by pixel (the per-pixel form of Sec. 4.4.3, reading R12):
+        """Squared difference pixel by pixel (the per-pixel form of Sec. 4.4.3, squared):
         for every ciphertext pair d = a - b, d (x) d, relinearised and rescaled on its own.
         Returns ([count][2][limbs-1][n], scale)."""
         lim = self._limbs(a)

@@ -353,7 +353,7 @@ int orc_keygen(u32 n, u32 L, const u64 *q, u64 seed, const u64 *T, u32 bound,
 
 /*
  * Evaluation key for relinearisation (Sec. 2.2.3: Relin(ct, evk); Sec. 2.2.2
- * step 3).  The paper gives no construction; reading R11: hybrid RNS key
+ * step 3).  The paper gives no construction; this oracle uses hybrid RNS key
  * switching with one special prime P and one digit per ciphertext prime.
  * Moduli m_0..m_{L-1} = q_0..q_{L-1}, m_L = P.  Digit j (ct id 1+j):
  *   evk_j = (-a_j*s + e_j + P*g_j*s^2, a_j) over Q*P,
@@ -397,7 +397,7 @@ int orc_keygen_evk(u32 n, u32 L, const u64 *q, u64 P, u64 seed, const u64 *T, u3
 
 /*
  * Encrypt one message (Sec. 2.2.2 "To encrypt a plaintext").  The message is the
- * encoded constant polynomial msg (reading R2: a pixel fills every slot, so its
+ * encoded constant polynomial msg (a pixel fills every slot, so its
  * encoding is the constant round(Delta * p)).  v from stream 0, e0 from stream 1,
  * e1 from stream 2, all keyed by (seed, id).
  */
@@ -497,7 +497,7 @@ void orc_ct_add_int(u32 n, u32 limbs, const u64 *q, const u64 *a, i64 k, u64 *c)
 }
 
 /* Rescale (Sec. 2.2.3): divide by the last prime q_t with rounding and drop it.
- * c'_j = (c_j - [c_t]_centered) * q_t^{-1} mod q_j  (reading R10). */
+ * c'_j = (c_j - [c_t]_centered) * q_t^{-1} mod q_j, [x]_centered in (-q_t/2, q_t/2]. */
 void orc_rescale(u32 n, u32 limbs, const u64 *q, const u64 *a, u64 *c)
 {
     u32 t = limbs - 1;
@@ -533,7 +533,8 @@ void orc_ct_square(u32 n, u32 limbs, const u64 *q, const u64 *d, u64 *out)
 }
 
 /*
- * Relinearisation (Sec. 2.2.3: ct_rel = Relin(ct_mul, evk)); reading R11.
+ * Relinearisation (Sec. 2.2.3: ct_rel = Relin(ct_mul, evk)) by hybrid key
+ * switching with the special prime P.
  * Input (d0, d1, d2) at `limbs` limbs, [3][limbs][n]; evk as from
  * orc_keygen_evk for L_full limbs.  For each digit j < limbs the centered
  * residue [d2]_{q_j} is lifted to every modulus q_0..q_{limbs-1}, P, multiplied
@@ -579,8 +580,8 @@ void orc_relin(u32 n, u32 limbs, u32 L_full, const u64 *q, u64 P, const u64 *evk
     free(acc); free(dig); free(prod);
 }
 
-/* Decryption, coefficient 0 only (Sec. 2.2.2 "To decrypt"; reading R2 decodes a
- * constant message from coefficient 0).  By the definition of the negacyclic
+/* Decryption, coefficient 0 only (Sec. 2.2.2 "To decrypt"; a constant message is
+ * decoded from coefficient 0).  By the definition of the negacyclic
  * product, (c1*s)_0 = c1_0 s_0 - sum_{j=1}^{N-1} c1_j s_{N-j}.  out[l] is the
  * residue of c0 + c1*s at coefficient 0 modulo q_l. */
 void orc_decrypt_coef0(u32 n, u32 limbs, const u64 *q, const int8_t *s, const u64 *ct, u64 *out)
@@ -731,7 +732,7 @@ int orc_lookup_encrypt_batch(u32 n, u32 limbs, const u64 *q, const u64 *value_ct
 /* ------------------------------------------------------------------------- */
 
 /* 3x3 mean filter (Sec. 4.4.1 formula with n = 3): sum of the 9 neighbours with
- * clamp-to-edge borders (reading R13), times the integer constant k9 (the
+ * clamp-to-edge borders (the paper does not say how borders are treated), times the integer constant k9 (the
  * encoded 1/9), then rescale.  Output has limbs-1 limbs. */
 int orc_meanfilter3(u32 n, u32 limbs, const u64 *q, const u64 *in, u32 h, u32 w, u32 ch,
                     i64 k9, u64 *out)
@@ -765,7 +766,7 @@ int orc_meanfilter3(u32 n, u32 limbs, const u64 *q, const u64 *in, u32 h, u32 w,
     return 0;
 }
 
-/* Watermark blend alpha*I + (1-alpha)*W (reading R15): both scaled by their
+/* Watermark blend alpha*I + (1-alpha)*W with W an encrypted pattern: both scaled by their
  * encoded integer constants, added, rescaled.  wm has c_w channels (1 or c). */
 int orc_blend(u32 n, u32 limbs, const u64 *q, const u64 *img, const u64 *wm, u64 count, u32 ch,
               u32 ch_w, i64 ka, i64 kb, u64 *out)
@@ -791,7 +792,7 @@ int orc_blend(u32 n, u32 limbs, const u64 *q, const u64 *img, const u64 *wm, u64
 }
 
 /*
- * Image matching (Sec. 4.4.3; reading R12: squared differences, since |x| is not
+ * Image matching (Sec. 4.4.3; squared differences, since |x| is not
  * a CKKS operation): sum over all ciphertexts of (a_k - b_k)^2 as a degree-2
  * ciphertext, out is [3][limbs][n].  Relinearisation and rescale follow in the
  * caller (orc_relin, orc_rescale).

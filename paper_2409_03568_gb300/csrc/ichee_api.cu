@@ -297,7 +297,8 @@ extern "C" ichee_status ichee_ct_bytes(const ichee_ctx* c, uint32_t level, size_
 }
 
 // ---------------------------------------------------------------------------------------
-// Key generation (Sec. 2.2.2, reading R1 for pk, R11 for evk)
+// Key generation (Sec. 2.2.2: pk = (-a*s + e, a); evk for hybrid key switching with the
+// special prime P, one digit per ciphertext prime)
 // ---------------------------------------------------------------------------------------
 // Key buffers of the context (allocated once, by keygen or the first import).
 static cudaError_t alloc_key_buffers(ichee_ctx* c)
@@ -1020,7 +1021,7 @@ extern "C" ichee_status ichee_eval(ichee_ctx* c, ichee_op op, const uint64_t* d_
     return ICHEE_OK;
 }
 
-// Matching (Sec. 4.4.3, reading R12): T = sum_k (a_k - b_k)^2 in the NTT domain, INTT,
+// Matching (Sec. 4.4.3, as a squared L2 distance): T = sum_k (a_k - b_k)^2 in the NTT domain, INTT,
 // relinearise, rescale.
 static ichee_status op_sqdiff(ichee_ctx* c, const uint64_t* d_a, const ichee_ctimg_meta* ma, const uint64_t* d_b,
                               uint64_t* d_out, ichee_ctimg_meta* mout, cudaStream_t st)

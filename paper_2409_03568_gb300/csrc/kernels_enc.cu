@@ -225,7 +225,8 @@ cudaError_t launch_axpy_const(u64* out, const u64* x, const u64* y, u64 c, int n
 }
 
 // ---------------------------------------------------------------------------------------
-// Fused fresh encryption (Sec. 2.2.2 with reading R1): one thread block per ciphertext.
+// Fused fresh encryption (Sec. 2.2.2, with the library sign convention pk = (-a*s + e, a),
+// since the printed formulas do not cancel): one thread block per ciphertext.
 //   sample v (ternary), e0, e1 (Gaussian) once into shared memory (int8), then per limb l:
 //   v^ = NTT(v); c_b = INTT(v^ . pk^_b) + e_b (+ Delta*p at coefficient 0 of c0)
 // pk^_b already carries the 1/N of the inverse transform. With KEEP_VHAT the transform of v

@@ -1,6 +1,6 @@
-// kernels_match.cu -- image matching (Sec. 4.4.3, reading R12): the sum over all pixel
+// kernels_match.cu -- image matching (Sec. 4.4.3, as a squared L2 distance): the sum over all pixel
 // ciphertexts of (a - b)^2 with ct x ct multiplication, then relinearisation with the
-// evaluation key (Sec. 2.2.3, reading R11).
+// evaluation key (Sec. 2.2.3; hybrid key switching with one special prime P).
 #include "ops.h"
 #include "ntt.cuh"
 
@@ -143,8 +143,8 @@ cudaError_t launch_sqdiff_reduce(const RnsArgs& rns, int limbs, const u64* parti
 
 // ---------------------------------------------------------------------------------------
 // Per-pixel squared difference: out_k = Rescale(Relin((a_k - b_k) (x) (a_k - b_k))) for every
-// ciphertext pair (the per-pixel form of Sec. 4.4.3; Relin as in reading R11, rescale as in
-// R10). A persistent block takes one pixel at a time and runs the whole chain on it:
+// ciphertext pair (the per-pixel form of Sec. 4.4.3; Relin by hybrid key switching, rescale
+// with centered rounding). A persistent block takes one pixel at a time and runs the whole chain on it:
 //   1. per limb l: d^ = NTT(a - b) for both polynomials; t0^ = d0^2, t1^ = 2 d0 d1 stay in the
 //      NTT domain; t2 = INTT(d1^2) (N^{-1} folded into the product). The squares are
 //      Montgomery products, so each carries 2^{-64}; the constants below carry 2^64;
@@ -369,7 +369,8 @@ cudaError_t launch_sqdiff_image(const SqImgArgs& a, int grid, cudaStream_t st)
 }
 
 // ---------------------------------------------------------------------------------------
-// Relinearisation by hybrid key switching with one special prime P (reading R11).
+// Relinearisation by hybrid key switching with one special prime P, one digit per ciphertext
+// prime, mod-down with centered rounding.
 // ---------------------------------------------------------------------------------------
 
 __global__ void k_relin_digits(const __grid_constant__ RelinArgs a, const u64* d2, u64* digits)

@@ -5,8 +5,9 @@
 namespace ichee {
 
 // ---------------------------------------------------------------------------------------
-// Rescale by the last prime q_t of a ciphertext with t+1 limbs (reading R10):
-//   c'_j = (c_j - [c_t]_centered) * q_t^{-1} mod q_j.
+// Rescale by the last prime q_t of a ciphertext with t+1 limbs (Sec. 2.2.3, rounding to
+// nearest):
+//   c'_j = (c_j - [c_t]_centered) * q_t^{-1} mod q_j, [x]_centered in (-q_t/2, q_t/2].
 // Since q_t * q_t^{-1} = 1 mod q_j this is c_j q_t^{-1} - c_t q_t^{-1} + [c_t > (q_t-1)/2]:
 // two Shoup products (both accept any 64-bit operand, so c_t needs no reduction mod q_j).
 // A constant K multiplied in before the rescale folds into the first product as
@@ -120,7 +121,7 @@ __global__ void k_rescale(const __grid_constant__ OpsArgs a)
     }
 }
 
-// Fused 3x3 mean filter (Sec. 4.4.1, reading R13): out(y,x) = Rescale(K9 * sum of the 9
+// Fused 3x3 mean filter (Sec. 4.4.1; borders clamp to the edge): out(y,x) = Rescale(K9 * sum of the 9
 // clamp-to-edge neighbours). One block per (row y, channel, poly, coefficient chunk); each
 // thread owns one coefficient pair and walks the row left to right keeping the three column
 // sums of the window in registers, so every input row is loaded once per output row. Residues
@@ -360,7 +361,7 @@ __global__ void __launch_bounds__(kMfMaxThreads<LIMBS>) k_radix_meanfilter3_batc
     }
 }
 
-// Fused watermark blend (reading R15): out = Rescale(Ka * I + Kb * W), W broadcast over
+// Fused watermark blend alpha*I + (1-alpha)*W, W an encrypted pattern: out = Rescale(Ka * I + Kb * W), W broadcast over
 // channels when it has one channel. The kept limbs use Ka q_t^{-1}, Kb q_t^{-1}. One call
 // handles coefficient pair c of polynomial b of one ciphertext.
 template <int LIMBS>
@@ -487,7 +488,8 @@ __device__ __forceinline__ U192 mul192(u64 y, const u64 (&w)[3])
 }
 
 // ---------------------------------------------------------------------------------------
-// Decryption of coefficient 0 (Sec. 2.2.2, reading R2) and exact CRT decoding (reading R17).
+// Decryption of coefficient 0 (Sec. 2.2.2; the plaintext of a pixel is a constant polynomial)
+// and exact CRT decoding (x held modulo 2^192, exact for |x| < 2^191).
 // (c0 + c1*s)_0 = c0_0 + sum_j c1_j * srev_j with srev_0 = s_0, srev_j = -s_{N-j}; s is
 // ternary, so the sum is signed additions only. One block per ciphertext.
 // ---------------------------------------------------------------------------------------

@@ -88,7 +88,8 @@ cudaError_t launch_sqdiff_accumulate(const SqDiffArgs& a, cudaStream_t st);
 cudaError_t launch_sqdiff_reduce(const RnsArgs& rns, int limbs, const u64* partial, int n_blocks, u64* tensor,
                                  cudaStream_t st);
 
-// Key switching of a degree-2 ciphertext (reading R11).
+// Key switching of a degree-2 ciphertext (hybrid, one digit per ciphertext prime, one special
+// prime P).
 struct RelinArgs {
     RnsArgs rns;                   // moduli q_0..q_{L-1}, P at index L
     int L;                         // limbs of the key (full chain)

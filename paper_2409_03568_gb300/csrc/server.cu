@@ -9,6 +9,7 @@
 // are on the GPU join the next round and their work runs behind or beside the earlier rounds;
 // memory returns to the arena as each round's completion event fires.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -133,6 +134,7 @@ struct ichee_server {
     uint32_t inflight = 0;
     bool stop = false;
     bool hold = false;
+    std::atomic<uint32_t> inject_launch_errors{0}, inject_query_errors{0};   // ichee_server_inject_failure
     ichee_server_stats stats{};
     std::thread worker;
 };
@@ -322,14 +324,25 @@ void worker_main(ichee_server* s)
     for (;;) {
         // completions, in order per ring stream (a round's event covers all its copies)
         for (auto it = s->rounds.begin(); it != s->rounds.end();) {
-            if (cudaEventQuery(it->done) == cudaSuccess) {
-                for (Req* q : it->reqs) complete(s, q);
-                s->ring_rounds[it->ring]--;
-                cudaEventDestroy(it->done);
-                it = s->rounds.erase(it);
-            } else {
-                ++it;
+            cudaError_t e = it->done ? cudaEventQuery(it->done) : cudaErrorInvalidResourceHandle;
+            if (e != cudaErrorNotReady && s->inject_query_errors.load() > 0) {   // host-side failure injection
+                s->inject_query_errors--;
+                e = cudaErrorLaunchFailure;
             }
+            if (e == cudaErrorNotReady) {
+                ++it;
+                continue;
+            }
+            // Any other answer ends the round: success completes its requests; an error (a
+            // sticky launch or execution error, or no event) fails them with ICHEE_ECUDA, so
+            // clients are answered, the ring admits again and the worker can stop.
+            if (e != cudaSuccess)
+                for (Req* q : it->reqs)
+                    if (q->status == ICHEE_OK) q->status = ICHEE_ECUDA;
+            for (Req* q : it->reqs) complete(s, q);
+            s->ring_rounds[it->ring]--;
+            if (it->done) cudaEventDestroy(it->done);
+            it = s->rounds.erase(it);
         }
         std::vector<Req*> admitted;
         {
@@ -374,12 +387,19 @@ void worker_main(ichee_server* s)
                 if (q->r.ring == ring) mine.push_back(q);
             if (mine.empty()) continue;
             cudaStream_t st = s->streams[ring];
-            ichee_status r = launch_round(s, ring, mine, st);
+            ichee_status r = ICHEE_ECUDA;
+            if (s->inject_launch_errors.load() > 0)   // host-side failure injection: nothing is launched
+                s->inject_launch_errors--;
+            else
+                r = launch_round(s, ring, mine, st);
             if (r != ICHEE_OK)
                 for (Req* q : mine) q->status = r;
             Round rd;
-            cudaEventCreateWithFlags(&rd.done, cudaEventDisableTiming);
-            cudaEventRecord(rd.done, st);
+            if (cudaEventCreateWithFlags(&rd.done, cudaEventDisableTiming) != cudaSuccess) rd.done = nullptr;
+            if (rd.done && cudaEventRecord(rd.done, st) != cudaSuccess) {
+                cudaEventDestroy(rd.done);
+                rd.done = nullptr;
+            }
             rd.ring = ring;
             rd.reqs = mine;
             s->rounds.push_back(rd);
@@ -509,6 +529,14 @@ extern "C" ichee_status ichee_server_hold(ichee_server* s, int hold)
     std::lock_guard<std::mutex> lock(s->mu);
     s->hold = hold != 0;
     s->cv_work.notify_all();
+    return ICHEE_OK;
+}
+
+extern "C" ichee_status ichee_server_inject_failure(ichee_server* s, uint32_t launch_errors, uint32_t query_errors)
+{
+    if (!s) return fail(ICHEE_EINVAL, "null server");
+    s->inject_launch_errors = launch_errors;
+    s->inject_query_errors = query_errors;
     return ICHEE_OK;
 }
 

@@ -145,6 +145,7 @@ _SIGS = {
     "ichee_server_stats_get": (_st, [_vp, ctypes.POINTER(ServerStats)]),
     "ichee_server_hold": (_st, [_vp, ctypes.c_int]),
     "ichee_server_destroy": (None, [_vp]),
+    "ichee_server_inject_failure": (_st, [_vp, _u32, _u32]),
     "ichee_stream_status": (_st, [_vp, _vp]),
     "ichee_buffer_bytes_left": (_st, [_vp, ctypes.POINTER(_sz)]),
     "ichee_last_error": (ctypes.c_char_p, []),
@@ -436,6 +437,11 @@ def ichee_server_hold(server, hold):
 
 def ichee_server_destroy(server):
     _lib.ichee_server_destroy(server)
+
+
+def ichee_server_inject_failure(server, launch_errors=0, query_errors=0):
+    """Host-side failure injection (tests): the next rounds fail as launch / completion errors."""
+    _check(_lib.ichee_server_inject_failure(server, launch_errors, query_errors))
 
 
 def ichee_stream_status(ctx, stream=None):

@@ -158,3 +158,80 @@ def test_server_refuses_bad_requests(ichee, rings):
     assert d.status == ichee.OK and d.t_done >= d.t_admit >= d.t_submit
     assert np.max(np.abs(res4 - keep[-1][0].astype(np.float64))) < 1e-3
     ichee.ichee_server_destroy(srv)
+
+
+_ORACLES = {}
+
+
+def oracle_ring(i):
+    """The CPU oracle with the keys and full cache of test ring i (same seeds as the fixture)."""
+    if i not in _ORACLES:
+        from oracle import Oracle, Params
+        r = RINGS[i]
+        o = Oracle(Params(r["log_n"], r["prime_bits"], r["log2_scale"], r["special_bits"])).keygen(900 + i,
+                                                                                                   with_evk=True)
+        _ORACLES[i] = (o, o.full_cache(8, 60 + i))
+    return _ORACLES[i]
+
+
+def oracle_request(ichee, o, cache, kind, h, w, c, seed, img, two, arg):
+    """The request as the oracle computes it: full-cache encryption with the pool (Sec. 3.2,
+    3.3), then the operation of Sec. 4.4; returns (ciphertexts, exact scale)."""
+    a = o.encrypt_lookup(img, cache, seed)
+    if kind == ichee.REQ_ENCRYPT:
+        return a, o.delta
+    if kind == ichee.REQ_MEANFILTER:
+        return o.meanfilter3(a, o.delta, h, w, c)
+    if kind == ichee.REQ_BRIGHTNESS:
+        return o.brightness(a, o.delta, arg)
+    if kind == ichee.REQ_WATERMARK:
+        return o.blend(a, o.encrypt_lookup(two, cache, seed + 1), o.delta, arg, c, 1)
+    return o.match(a, o.encrypt_lookup(two, cache, seed + 1), o.delta)
+
+
+def test_served_results_equal_the_oracle(ichee, rings):
+    """Every request kind on both rings, served together in one burst: each served ciphertext
+    equals the oracle's word for word and each decoded value its exact decode (rtol 1e-9)."""
+    ctxs, caches = rings
+    keep, built, specs = [], [], []
+    for ring in range(2):
+        for kind in range(5):
+            h, w, c = 3 + kind, 4 + ring, 1 + 2 * ((kind + ring) % 2)
+            seed = 3000 + 31 * (5 * ring + kind)
+            specs.append((kind, ring, h, w, c, seed))
+            built.append(make_request(ichee, ctxs, kind, ring, h, w, c, seed, keep))
+    srv = ichee.ichee_server_create([x.handle for x in ctxs], caches, 256 << 20)
+    ichee.ichee_server_hold(srv, True)
+    tickets = [ichee.ichee_server_submit(srv, r) for (r, *_rest) in built]
+    ichee.ichee_server_hold(srv, False)
+    for t, (r, img, two, res, ct), (kind, ring, h, w, c, seed) in zip(tickets, built, specs):
+        ichee.ichee_server_wait(srv, t)
+        o, cache = oracle_ring(ring)
+        want, scale = oracle_request(ichee, o, cache, kind, h, w, c, seed, img, two, r.arg)
+        got = ct.cpu().numpy().view(np.uint64).reshape(want.shape)
+        assert np.array_equal(got, want), (kind, ring)
+        np.testing.assert_allclose(res, o.decrypt(want, scale), rtol=1e-9, atol=0)
+    ichee.ichee_server_destroy(srv)
+
+
+@pytest.mark.timeout(300)
+def test_failed_rounds_complete_and_server_stops(ichee, rings):
+    """A round that fails to launch, and a round whose completion reports a device error (both
+    injected on the host, no GPU fault), answer their requests with ECUDA; the server keeps
+    serving and destroy returns."""
+    ctxs, caches = rings
+    keep = []
+    srv = ichee.ichee_server_create([x.handle for x in ctxs], caches, 64 << 20)
+    for launch_errors, query_errors in ((1, 0), (0, 1)):
+        ichee.ichee_server_inject_failure(srv, launch_errors, query_errors)
+        r, *_ = make_request(ichee, ctxs, ichee.REQ_ENCRYPT, 0, 2, 3, 1, 77, keep)
+        t = ichee.ichee_server_submit(srv, r)
+        with pytest.raises(ichee.IcheeError) as e:
+            ichee.ichee_server_wait(srv, t, timeout_ms=60000)
+        assert e.value.status == ichee.ECUDA
+    r, img, _, res, _ = make_request(ichee, ctxs, ichee.REQ_ENCRYPT, 1, 2, 3, 1, 78, keep)
+    d = ichee.ichee_server_wait(srv, ichee.ichee_server_submit(srv, r))
+    assert d.status == ichee.OK and np.max(np.abs(res - img)) < 1e-3
+    st = ichee.ichee_server_stats_get(srv)
+    assert st["inflight"] == 0 and st["arena_used_bytes"] == 0
+    ichee.ichee_server_destroy(srv)

@@ -223,7 +223,7 @@ def test_polymul_full_size_ternary_by_shifts():
 
 # ------------------------------------------------------------------- keys and encrypt
 def test_public_key_is_rlwe_sample(toy):
-    """pk0 + pk1*s = e with |e| <= bound (sign of a*s, Sec. 2.2.2 / reading R1)."""
+    """pk0 + pk1*s = e with |e| <= bound (sign of a*s, Sec. 2.2.2 with the library convention pk0 = -a*s + e)."""
     o = toy
     zero_ct = np.ascontiguousarray(o.pk)        # (pk0, pk1) decrypts like a ciphertext
     e = _centered_poly(o, zero_ct)
@@ -385,7 +385,7 @@ def test_relin_matches_three_term_decryption(small4):
 
 
 def test_relin_depends_on_evk_sign(small4):
-    """Flipping the sign of the evk's s^2 term must break decryption (guards reading R11)."""
+    """Flipping the sign of the evk's s^2 term must break decryption (guards the sign of the s^2 term in the key)."""
     o = small4
     a = o.encrypt_pixels(np.array([9], dtype=np.uint8), seed=41)
     b = o.encrypt_pixels(np.array([2], dtype=np.uint8), seed=42)
