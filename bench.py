@@ -71,8 +71,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["enc8192", "batch32", "serve"], default="enc8192",
-                    help="enc8192: the headline step; batch32: ragged batch under a CUDA graph vs per-image "
+    ap.add_argument("--workload", choices=["all", "enc8192", "ops128", "batch32", "serve"], default="all",
+                    help="all (default): the headline step, then the other configurations as sub-records of the "
+                         "same JSON line; enc8192: the headline step alone; ops128: image operations on the "
+                         "128x128x3 four-prime image; batch32: ragged batch under a CUDA graph vs per-image "
                          "launches; serve: Poisson request stream through the continuous-batching server")
     ap.add_argument("--duration", type=float, default=None, help="serve: seconds of arrivals (default 60)")
     ap.add_argument("--op", choices=sorted(SINGLE_OPS), default=None,
@@ -362,9 +364,19 @@ def run_ours(args):
         ref = {}
         out["cpu_baseline"] = cpu_baseline(sample_steps=1, sample=484, keep=ref)
         out["parity_sample"] = parity_on_sample(ctx, enc_out, ops_out, ref)
+    ctx.close()
+    if args.workload == "all" and world == 1:
+        # the other configurations, each in a process of its own (its own device memory), as
+        # sub-records of this line
+        del enc_out, ops_out, dec_out, flush, caches
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        out["configs"] = {name: sub_record(name, extra) for name, extra in
+                          (("ops128", ["--steps", "10", "--warmup", "3"]),
+                           ("batch32", ["--steps", "10", "--warmup", "3"]),
+                           ("serve", []))}
     if rank == 0:
         print(json.dumps(out))
-    ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 
@@ -553,6 +565,140 @@ def run_reference(args):
                       "e2e": {"value": round(v, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def sub_record(workload, extra, timeout=900):
+    """Run `bench.py --workload <workload>` in a child process and return its JSON line (or the
+    failure) as a sub-record."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--workload", workload] + extra
+    t0 = time.perf_counter()
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout)
+    except subprocess.TimeoutExpired:
+        return {"error": "timed out after %d s" % timeout}
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    if r.returncode != 0 or not lines:
+        return {"error": "exit %d" % r.returncode, "stderr_tail": r.stderr[-600:]}
+    rec = json.loads(lines[-1])
+    rec["wall_s"] = round(time.perf_counter() - t0, 1)
+    return rec
+
+
+# ---------------------------------------------------------------------------------------
+# image operations on the 128x128x3 image at N = 8192, four primes
+# ---------------------------------------------------------------------------------------
+def run_ops128(args):
+    """The image operations of Sec. 4.4 on the 128x128x3 random-field image (N = 8192, primes
+    60/40/40/40, Delta = 2^40): 3x3 mean filter, brightness +beta (copy), watermark blend with an
+    encrypted binary 128x128 pattern (alpha 0.9), matching against an encrypted noisy copy (sum of
+    squared differences, relinearised), each result decrypted. One step = the four operations and
+    the four decryptions; every operation is also timed on its own (CUDA events on the library's
+    stream). Inputs (tens of GB) are far larger than L2."""
+    import torch
+    from paper_2409_03568_gb300 import ichee
+    wl = W.OPS8192
+    torch.cuda.set_device(0)
+    hbm_peak, peak_kind = measured_peaks()
+    ctx = ichee.Context(**W.ctx_kwargs(wl))
+    ctx.keygen(2025, with_evk=True)
+    h, w, c = wl["h"], wl["w"], wl["c"]
+    n_px = h * w * c
+    img = W.image_for(wl).reshape(-1)
+    noisy = inputs.noisy_copy(img, seed=wl["noisy_seed"])
+    wm = inputs.binary_pattern(h, w, seed=wl["watermark_seed"]).reshape(-1)
+    beta = inputs.brightness_beta(wl["beta_seed"])
+    a, ma = ctx.encrypt(torch.from_numpy(img).cuda(), h, w, c, 31)
+    b, mb = ctx.encrypt(torch.from_numpy(noisy).cuda(), h, w, c, 32)
+    wct, mw = ctx.encrypt(torch.from_numpy(wm).cuda(), h, w, 1, 33)
+    L = ctx.L
+    outs = {"meanfilter3": ctx.empty_cts(n_px, L - 2), "brightness": ctx.empty_cts(n_px, L - 1),
+            "blend": ctx.empty_cts(n_px, L - 2), "match": ctx.empty_cts(1, L - 2)}
+    dec = {k: torch.empty(1 if k == "match" else n_px, dtype=torch.float64, device="cuda") for k in outs}
+    st, H = ctx.stream(), ctx.handle
+    metas = {}
+    ops = {"meanfilter3": (ichee.OP_MEANFILTER3, None, None, ()),
+           "brightness": (ichee.OP_BRIGHTNESS, None, None, (beta,)),
+           "blend": (ichee.OP_BLEND, wct, mw, (wl["alpha"],)),
+           "match": (ichee.OP_SQDIFF_SUM, b, mb, ())}
+
+    def op(name):
+        o, x, mx, arg = ops[name]
+        metas[name] = ichee.ichee_eval(H, o, a, ma, x, mx, arg, outs[name], st)
+
+    def decrypt_all():
+        for k in outs:
+            ichee.ichee_decrypt_image(H, outs[k], metas[k], dec[k], st)
+
+    names = list(ops)
+    ev = {k: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for k in names + ["decrypt"]}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = {k: 0.0 for k in ev}
+    total = 0.0
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        e0.record()
+        for k in names:
+            ev[k][0].record()
+            op(k)
+            ev[k][1].record()
+        ev["decrypt"][0].record()
+        decrypt_all()
+        ev["decrypt"][1].record()
+        e1.record()
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            total += e0.elapsed_time(e1)
+            for k in ev:
+                ms[k] += ev[k][0].elapsed_time(ev[k][1])
+    ms = {k: v / args.steps for k, v in ms.items()}
+    step_ms = total / args.steps
+    # correctness guard and quality against FP64 plaintext references of the operations
+    f = img.reshape(h, w, c).astype(np.float64)
+    pad = np.pad(f, ((1, 1), (1, 1), (0, 0)), mode="edge")
+    box = sum(pad[dy:dy + h, dx:dx + w] for dy in range(3) for dx in range(3)) / 9.0
+    wmf = wm.reshape(h, w, 1).astype(np.float64)
+    refs = {"meanfilter3": box.reshape(-1), "brightness": img.astype(np.float64) + beta,
+            "blend": (wl["alpha"] * f + (1 - wl["alpha"]) * wmf).reshape(-1),
+            "match": np.array([float(((img.astype(np.float64) - noisy) ** 2).sum())])}
+    errors = {k: float(np.max(np.abs(dec[k].cpu().numpy() - refs[k]))) for k in names}
+    for k, tol in (("meanfilter3", 1e-2), ("brightness", 1e-3), ("blend", 1e-2), ("match", 5.0)):
+        if errors[k] > tol:
+            raise RuntimeError("ops128: %s decodes %.3g away from its plaintext reference" % (k, errors[k]))
+    n, logn = ctx.n, wl["log_n"]
+    ct_in, ct_out = 2 * L * n * 8, 2 * (L - 1) * n * 8
+    alu_peak = SM_COUNT * SM_MAX_MHZ * 1e6 * IMAD_PER_SM_CLK / IMAD_PER_MODMUL / 1e9
+    bytes_of = {"meanfilter3": n_px * (ct_in + ct_out), "brightness": n_px * 2 * ct_in,
+                "blend": n_px * (ct_in + ct_out) + h * w * ct_in}
+    per_op = {}
+    for k in names:
+        t = ms[k] / 1e3
+        rec = {"ms": round(ms[k], 4), "px_per_s": round(n_px / t, 1)}
+        if k in bytes_of:
+            ach = bytes_of[k] / t / 1e9
+            rec.update({"bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
+                        "frac": round(ach / hbm_peak, 4), "bytes": bytes_of[k]})
+        else:
+            mm = n_px * L * (2 * (n // 2) * logn + 3 * n)
+            ach = mm / t / 1e9
+            rec.update({"bound": "alu", "achieved": round(ach, 1), "peak": round(alu_peak, 1), "unit": "Gmodmul/s",
+                        "frac": round(ach / alu_peak, 4)})
+        rec["max_abs_error"] = errors[k]
+        per_op[k] = rec
+    dec_bytes = n_px * (L - 1) * n * 8 * 2 + n_px * L * n * 8 + (L - 1) * n * 8
+    per_op["decrypt"] = {"ms": round(ms["decrypt"], 4), "bound": "hbm",
+                         "frac": round(dec_bytes / (ms["decrypt"] / 1e3) / 1e9 / hbm_peak, 4)}
+    print(json.dumps({
+        "metric": "image-operation pixels/s, N=8192, 4 primes, 128x128x3 (mean filter, brightness, blend, matching "
+                  "and their decryption per step)",
+        "value": round(4 * n_px / (step_ms / 1e3), 1), "unit": "px-op/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64 (RNS residues mod 60/40/40/40-bit primes)",
+        "data": "synthetic (128x128x3 random field seed 3, beta seed 4, pattern seed 5, noisy copy seed 6)",
+        "config": {"workload": wl["name"], "N": n, "primes_bits": wl["prime_bits"], "image": "%dx%dx%d" % (h, w, c),
+                   "l2": "inputs (%.0f GB) far larger than L2" % ((2 * n_px + h * w) * ct_in / 1e9),
+                   "peak_kind": peak_kind},
+        "ops": per_op}))
+    ctx.close()
+
+
 # ---------------------------------------------------------------------------------------
 # ragged batch under one CUDA graph vs per-image launches
 # ---------------------------------------------------------------------------------------
@@ -677,6 +823,31 @@ def serve_requests(wl, duration):
     return reqs
 
 
+def serve_algorithmic_bytes(wl, reqs, served):
+    """HBM bytes the served requests need at least: every encryption written once, every
+    operation's inputs read and output written once (brightness in place touches one word per
+    limb), every decryption reads c1 and coefficient 0 of c0 (half a ciphertext)."""
+    total = 0
+    for q, ok in zip(reqs, served):
+        if not ok:
+            continue
+        ring = wl["rings"][q["ring"]]
+        n, L = 1 << ring["log_n"], len(ring["prime_bits"])
+        ct, ct1 = 2 * L * n * 8, 2 * (L - 1) * n * 8
+        npx = q["h"] * q["w"] * q["c"]
+        nb = q["h"] * q["w"] if q["kind"] == 3 else (npx if q["kind"] == 4 else 0)
+        total += (npx + nb) * ct
+        if q["kind"] == 1:
+            total += npx * (ct + ct1) + npx * ct1 // 2
+        elif q["kind"] == 3:
+            total += npx * (ct + ct1) + nb * ct + npx * ct1 // 2
+        elif q["kind"] == 4:
+            total += 2 * npx * ct
+        else:   # encrypt-only, brightness
+            total += npx * ct // 2
+    return total
+
+
 def run_serve(args):
     import threading
     import torch
@@ -765,6 +936,8 @@ def run_serve(args):
                 if q["kind"] == ichee.REQ_ENCRYPT and t is not None and t >= 0)
     span = last_done - first_sub
     lat = np.array(lat)
+    alg_bytes = serve_algorithmic_bytes(wl, reqs, [t is not None and t >= 0 for t in tickets])
+    hbm_peak, peak_kind = measured_peaks()
 
     # the unbatched plain path: the same arrivals, one request at a time through the
     # single-request entry points, on a prefix of the stream (at most 20 s of arrivals or 60 s)
@@ -804,6 +977,11 @@ def run_serve(args):
            "config": {"workload": wl["name"], "requests": len(reqs), "duration_s": duration, "pixels": px_total,
                       "offered_px_per_s": round(px_total / duration, 1), "budget_gb": wl["budget_gb"],
                       "refused_over_budget": refused},
+           "served_px": served_px, "served_over_offered": round((served_px / span) / (px_total / duration), 4),
+           "roofline": {"bound": "hbm", "achieved": round(alg_bytes / span / 1e9, 1), "peak": hbm_peak, "unit": "GB/s",
+                        "frac": round(alg_bytes / span / 1e9 / hbm_peak, 4), "traffic": None,
+                        "algorithmic_bytes": alg_bytes, "peak_kind": peak_kind,
+                        "kernel": "all kernels of the served mix over the span (first submit to last completion)"},
            "latency_s": {"p50": round(float(np.percentile(lat, 50)), 5), "p99": round(float(np.percentile(lat, 99)), 5),
                          "max": round(float(lat.max()), 5)},
            "round_size": {"mean": round(float(np.mean(rounds)), 2), "max": int(np.max(rounds))},
@@ -896,6 +1074,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch32":
         run_batch(args)
+    elif args.workload == "ops128":
+        run_ops128(args)
     else:
         run_ours(args)
 

@@ -240,6 +240,18 @@ ichee_status ichee_encrypt_image(ichee_ctx* ctx, const ichee_cache* cache, const
                                  ichee_ctimg_meta* meta_out, void* stream);
 
 /*
+ * Pixel-level encryption of a range of an image (Sec. 3.1), for images split into pieces: pixel
+ * tiles streamed through limited memory, or pixel ranges on several GPUs. pixels (host or
+ * device, n bytes) are the image's pixels first_id .. first_id + n - 1 in (y, x, channel)
+ * order; d_ct_out (device, n ciphertexts at level L-1, scale Delta) receives exactly the
+ * ciphertexts first_id .. first_id + n - 1 that ichee_encrypt_image makes for the whole image
+ * with the same seed and cache (every random draw is keyed by the ciphertext's index in its
+ * image). Errors: EINVAL (null, empty or n > 2^40, first_id > 2^40), EMISMATCH, ECUDA.
+ */
+ichee_status ichee_encrypt_pixels(ichee_ctx* ctx, const ichee_cache* cache, const uint8_t* pixels, uint64_t n,
+                                  uint64_t first_id, uint64_t seed, uint64_t* d_ct_out, void* stream);
+
+/*
  * Apply an image operation (see ichee_op). d_a / d_b / d_out are device ciphertext images
  * described by ma / mb / mout; d_b and mb are used by ADD, SUB, BLEND, SQDIFF_SUM and SQDIFF
  * only.
@@ -346,6 +358,8 @@ ichee_status ichee_encrypt_meanfilter_batch(ichee_ctx* ctx, const ichee_cache* c
 #define ICHEE_TUNE_FUSED 4u
 #define ICHEE_TUNE_SCHEDULE 5u   /* ichee_tuned_shape: *threads = 1 if the fused kernel runs, 0 for two kernels */
 #define ICHEE_TUNE_DECRYPT 6u    /* decryption, single-image and batched (one block per ciphertext) */
+#define ICHEE_TUNE_MF_STAGED 7u  /* mean filter form: threads = 0 (default): each thread loads its input
+                                    columns into registers; 1: columns staged in shared memory by bulk copies */
 
 typedef struct {
     uint32_t kind;            /* ICHEE_TUNE_* */
@@ -482,17 +496,67 @@ void ichee_server_destroy(ichee_server* server);
 ichee_status ichee_server_inject_failure(ichee_server* server, uint32_t launch_errors, uint32_t query_errors);
 
 /*
+ * 3x3 mean filter (Sec. 4.4.1, the ICHEE_OP_MEANFILTER3 operation) of a band of rows, for images
+ * split into pieces (row tiles streamed through limited memory, or row ranges on several GPUs).
+ * m_img describes the whole image (h rows of w x c ciphertexts, level >= 1, scale); d_in (device)
+ * holds its rows row0 .. row0 + n_rows - 1, which must include the rows the output needs
+ * (y0 - 1 .. y1, clamped to the image). d_out (device, (y1 - y0) * w * c ciphertexts at level - 1)
+ * receives output rows y0 .. y1 - 1, equal word for word to those rows of the whole-image
+ * operation (borders clamp to the edge of the whole image, not of the band); *mout is their
+ * metadata (h = y1 - y0). Errors: EINVAL (rows outside the image or not held, null, short or
+ * non-device buffers), ELEVEL, ESCALE, EUNSUPPORTED (N < 512), ECUDA.
+ */
+ichee_status ichee_meanfilter_rows(ichee_ctx* ctx, const uint64_t* d_in, const ichee_ctimg_meta* m_img, uint32_t row0,
+                                   uint32_t n_rows, uint32_t y0, uint32_t y1, uint64_t* d_out,
+                                   ichee_ctimg_meta* mout, void* stream);
+
+/*
+ * Matching in pieces (Sec. 4.4.3): the sum over all pixel pairs of (a - b) (x) (a - b) is a sum,
+ * so it can be formed tile by tile (images streamed through limited memory) or range by range
+ * on several GPUs, and relinearised and rescaled once at the end.
+ *
+ * ichee_sqdiff_acc_words: *words = 3 * (level + 1) * N, the uint64 words of one accumulator.
+ *
+ * ichee_sqdiff_accumulate: d_acc (device, caller-owned, ichee_sqdiff_acc_words(ma->level)
+ * words) receives the sum over the n pixel pairs of d_a, d_b (device images of the same shape,
+ * level >= 1 and scale; evaluation key needed) -- overwriting it (accumulate = 0) or adding to the
+ * accumulator it holds (accumulate != 0). The accumulator is an internal representation (the
+ * transform domain of this library, residues below each prime): only ichee_sqdiff_accumulate and
+ * ichee_sqdiff_finish of a context with the same parameters read it. The pixel ranges of the
+ * pieces must together cover each pair once; their order does not matter (exact modular sums).
+ * Working memory: the context's scratch (as ichee_eval).
+ *
+ * ichee_sqdiff_finish: relinearise and rescale an accumulator into d_out (device, one
+ * ciphertext at level m_in->level - 1; *mout its metadata, shape 1x1x1). d_acc may also be the
+ * element-wise uint64 sum, without reduction, of up to 8 accumulators (for example the
+ * all-reduce of per-GPU accumulators): its words are reduced first. m_in gives the level and the
+ * scale of the matched images (its shape is ignored). The result equals ichee_eval with
+ * ICHEE_OP_SQDIFF_SUM over all the pairs, bit for bit.
+ *
+ * Errors: EINVAL (null or non-device buffers, short buffers), ELEVEL, ESCALE, EMISMATCH,
+ * EUNSUPPORTED (no evaluation key), ENOMEM, ECUDA.
+ */
+ichee_status ichee_sqdiff_acc_words(const ichee_ctx* ctx, uint32_t level, size_t* words);
+ichee_status ichee_sqdiff_accumulate(ichee_ctx* ctx, const uint64_t* d_a, const ichee_ctimg_meta* ma,
+                                     const uint64_t* d_b, const ichee_ctimg_meta* mb, uint64_t* d_acc, int accumulate,
+                                     void* stream);
+ichee_status ichee_sqdiff_finish(ichee_ctx* ctx, const uint64_t* d_acc, const ichee_ctimg_meta* m_in,
+                                 uint64_t* d_out, ichee_ctimg_meta* mout, void* stream);
+
+/*
  * Matching (the ICHEE_OP_SQDIFF_SUM operation) for callers that cannot allocate device
  * memory: processes whose GPU memory is handed out by their own arena or pool, or loops that
  * must not risk the device-wide synchronisation cudaMalloc / cudaFree can cause. The paper
- * has no counterpart; this is an interface for such callers. Same arguments, checks and
- * result as ichee_eval with ICHEE_OP_SQDIFF_SUM (d_a, d_b: device inputs; d_out: caller's
- * device output of one ciphertext at level - 1; *mout receives its metadata), but no call to
+ * has no counterpart; this is an interface for such callers. Same arguments and result as
+ * ichee_eval with ICHEE_OP_SQDIFF_SUM, and the same checks (d_out may not be d_a or d_b)
+ * (d_a, d_b: device inputs; d_out: caller's device output of one ciphertext at level - 1;
+ * *mout receives its metadata), but no call to
  * cudaMalloc, cudaFree or any other allocating routine: the working memory is one static
  * device array of ICHEE_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
  * the process exits. The first call on each device looks up that array's device address
  * (cudaGetSymbolAddress) with the device current; make that first call before any stream
- * capture. All calls share the array and it keeps the last call's contents (the kernels
+ * capture. The address is kept for the life of the process, so a device reset
+ * (cudaDeviceReset) after the first call is not supported. All calls share the array and it keeps the last call's contents (the kernels
  * overwrite or zero everything they read), so calls that overlap on the GPU -- on different
  * streams, or from different contexts on one device -- race: order them. A shape whose
  * working set exceeds the array fails with ICHEE_EINVAL and a message giving both sizes.

@@ -118,6 +118,7 @@ struct ichee_ctx {
     // launch shapes of the persistent batched kernels (defaults; ichee_autotune_batch refines)
     // one block per work item by default (the autotuner's choice for the 32-image batch)
     LaunchShape shape_radix = {256, 0}, shape_lookup = {256, 0}, shape_meanfilter = {256, 0};
+    int mf_staged = 0;   // mean filter: 0 = register walk, 1 = bulk-copy staged form (ICHEE_TUNE_MF_STAGED)
     LaunchShape shape_blend = {256, 0}, shape_ptadd = {256, 0}, shape_decrypt = {256, 0};
     LaunchShape shape_fused = {1024, 1};
     int fused_schedule = 0;   // ichee_encrypt_meanfilter_batch: 0 = two batched kernels, 1 = fused kernel

@@ -119,6 +119,7 @@ ichee_status meanfilter_chunked(ichee_ctx* c, const uint64_t* const* a, const ic
     set_k0(c, base, 1.0 / 9.0, c->delta);
     set_rescale(c, base);
     fold_constants(c, base);
+    ls.threads = mf_batch_threads(base.limbs, ls.threads, c->mf_staged != 0);
     const int chunks = (c->n / 2) / ls.threads;
     for (uint32_t first = 0; first < n; first += kMaxSegs) {
         const int cnt = (int)std::min<uint32_t>(kMaxSegs, n - first);
@@ -133,7 +134,7 @@ ichee_status meanfilter_chunked(ichee_ctx* c, const uint64_t* const* a, const ic
             t.w[s] = ma[i].w;
             t.c[s] = ma[i].c;
         }
-        CK(launch_meanfilter3_batch(base, t, ls, c->num_sms, st));
+        CK(launch_meanfilter3_batch(base, t, ls, c->mf_staged != 0, c->num_sms, st));
     }
     return ICHEE_OK;
 }
@@ -522,6 +523,7 @@ extern "C" ichee_status ichee_tuned_shape(const ichee_ctx* c, uint32_t kind, uin
     case ICHEE_TUNE_FUSED: ls = c->shape_fused; break;
     case ICHEE_TUNE_DECRYPT: ls = c->shape_decrypt; break;
     case ICHEE_TUNE_SCHEDULE: *threads = (uint32_t)c->fused_schedule; *blocks_per_sm = 0; return ICHEE_OK;
+    case ICHEE_TUNE_MF_STAGED: *threads = (uint32_t)c->mf_staged; *blocks_per_sm = 0; return ICHEE_OK;
     default: return fail(ICHEE_EINVAL, "unknown kernel kind %u", kind);
     }
     *threads = (uint32_t)ls.threads;
@@ -586,6 +588,11 @@ extern "C" ichee_status ichee_set_tuned_shape(ichee_ctx* c, uint32_t kind, uint3
     if (kind == ICHEE_TUNE_SCHEDULE) {
         if (threads > 1) return fail(ICHEE_EINVAL, "schedule must be 0 (two kernels) or 1 (fused)");
         c->fused_schedule = (int)threads;
+        return ICHEE_OK;
+    }
+    if (kind == ICHEE_TUNE_MF_STAGED) {
+        if (threads > 1) return fail(ICHEE_EINVAL, "mean-filter form must be 0 (register walk) or 1 (staged)");
+        c->mf_staged = (int)threads;
         return ICHEE_OK;
     }
     const bool wide = kind == ICHEE_TUNE_FUSED || kind == ICHEE_TUNE_DECRYPT;   // 1024 threads allowed

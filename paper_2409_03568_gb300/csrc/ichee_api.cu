@@ -771,48 +771,70 @@ static ichee_status device_pixels(ichee_ctx* c, const uint8_t* px, u64 n, cudaSt
     return ICHEE_OK;
 }
 
+// Pixels k = 0..n_ct-1 into ciphertexts with ct ids first_id + k (fresh, radix or lookup).
+static ichee_status encrypt_impl(ichee_ctx* c, const ichee_cache* k, const uint8_t* pixels, u64 n_ct, u64 first_id,
+                                 uint64_t seed, uint64_t* d_out, cudaStream_t st)
+{
+    if (!c->have_pk) return fail(ICHEE_EINVAL, "encryption needs the public key (ichee_keygen or ichee_import_key)");
+    if (k && k->ctx != c) return fail(ICHEE_EMISMATCH, "cache belongs to another context");
+    CK(cudaSetDevice(c->device));
+    ichee_status s = check_out(c, d_out, n_ct, c->L, "ciphertext output");
+    if (s != ICHEE_OK) return s;
+    const uint8_t* d_px = nullptr;
+    s = device_pixels(c, pixels, n_ct, st, &d_px);
+    if (s != ICHEE_OK) return s;
+    if (!k) {
+        CK(launch_encrypt_fresh(enc_args(c, d_px, n_ct, seed, first_id, d_out), st));
+    } else if (k->desc.kind == ICHEE_CACHE_RADIX) {
+        RadixArgs r = radix_args(c, k, d_px, n_ct, seed, d_out);
+        r.id_base = first_id;
+        CK(launch_radix_combine(r, st));
+    } else {
+        LookupArgs a = lookup_args(c, k, d_px, n_ct, seed, d_out);
+        a.id_base = first_id;
+        CK(launch_lookup_combine(a, st));
+        if (k->values.size() < 256) {  // values outside the cache
+            if (k->desc.miss_policy == 0) {
+                EncArgs e = enc_args(c, d_px, n_ct, seed, first_id, d_out);
+                e.skip_lut = k->d_lut;
+                CK(launch_encrypt_fresh(e, st));
+            } else {
+                RadixArgs r = radix_args(c, k, d_px, n_ct, seed, d_out);
+                r.id_base = first_id;
+                r.skip_lut = k->d_lut;
+                CK(launch_radix_combine(r, st));
+            }
+        }
+    }
+    return ICHEE_OK;
+}
+
 extern "C" ichee_status ichee_encrypt_image(ichee_ctx* c, const ichee_cache* k, const uint8_t* pixels, uint32_t h,
                                             uint32_t w, uint32_t ch, uint64_t seed, uint64_t* d_out,
                                             ichee_ctimg_meta* meta, void* stream)
 {
     ichee::NvtxRange nvtx_range("ichee_encrypt_image");
     if (!c || !pixels || !d_out || !meta) return fail(ICHEE_EINVAL, "null argument");
-    if (!c->have_pk) return fail(ICHEE_EINVAL, "ichee_encrypt_image: no public key (ichee_keygen or ichee_import_key)");
-    if (k && k->ctx != c) return fail(ICHEE_EMISMATCH, "cache belongs to another context");
     const u64 n_ct = image_cts(h, w, ch);
     if (n_ct == 0) return fail(ICHEE_EINVAL, "empty or oversized image %ux%ux%u", h, w, ch);
-    CK(cudaSetDevice(c->device));
-    ichee_status s = check_out(c, d_out, n_ct, c->L, "ciphertext output");
+    ichee_status s = encrypt_impl(c, k, pixels, n_ct, 0, seed, d_out, (cudaStream_t)stream);
     if (s != ICHEE_OK) return s;
-    cudaStream_t st = (cudaStream_t)stream;
-    const uint8_t* d_px = nullptr;
-    s = device_pixels(c, pixels, n_ct, st, &d_px);
-    if (s != ICHEE_OK) return s;
-    if (!k) {
-        CK(launch_encrypt_fresh(enc_args(c, d_px, n_ct, seed, 0, d_out), st));
-    } else if (k->desc.kind == ICHEE_CACHE_RADIX) {
-        CK(launch_radix_combine(radix_args(c, k, d_px, n_ct, seed, d_out), st));
-    } else {
-        LookupArgs a = lookup_args(c, k, d_px, n_ct, seed, d_out);
-        CK(launch_lookup_combine(a, st));
-        if (k->values.size() < 256) {  // values outside the cache
-            if (k->desc.miss_policy == 0) {
-                EncArgs e = enc_args(c, d_px, n_ct, seed, 0, d_out);
-                e.skip_lut = k->d_lut;
-                CK(launch_encrypt_fresh(e, st));
-            } else {
-                RadixArgs r = radix_args(c, k, d_px, n_ct, seed, d_out);
-                r.skip_lut = k->d_lut;
-                CK(launch_radix_combine(r, st));
-            }
-        }
-    }
     meta->h = h;
     meta->w = w;
     meta->c = ch;
     meta->level = (u32)(c->L - 1);
     meta->scale = c->delta;
     return ICHEE_OK;
+}
+
+extern "C" ichee_status ichee_encrypt_pixels(ichee_ctx* c, const ichee_cache* k, const uint8_t* pixels, uint64_t n,
+                                             uint64_t first_id, uint64_t seed, uint64_t* d_out, void* stream)
+{
+    ichee::NvtxRange nvtx_range("ichee_encrypt_pixels");
+    if (!c || !pixels || !d_out) return fail(ICHEE_EINVAL, "null argument");
+    if (n == 0 || n > (1ull << 40)) return fail(ICHEE_EINVAL, "pixel count %llu outside [1, 2^40]", (unsigned long long)n);
+    if (first_id > (1ull << 40)) return fail(ICHEE_EINVAL, "first ciphertext id beyond 2^40");
+    return encrypt_impl(c, k, pixels, n, first_id, seed, d_out, (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -832,6 +854,10 @@ OpsArgs ichee::ops_base(const ichee_ctx* c, const ichee_ctimg_meta* m)
     a.h = (int)m->h;
     a.w = (int)m->w;
     a.c = (int)m->c;
+    a.y0 = 0;
+    a.rows = (int)m->h;
+    a.row0 = 0;
+    a.status = c->d_status;
     return a;
 }
 
@@ -864,12 +890,25 @@ void ichee::set_k1(const ichee_ctx* c, OpsArgs& a, double v, double scale)
 // Constants of a fused multiply + rescale: K * q_t^{-1} mod q_j for the kept limbs.
 void ichee::fold_constants(const ichee_ctx* c, OpsArgs& a)
 {
-    for (int j = 0; j < a.limbs - 1; ++j) {
+    const int t = a.limbs - 1;
+    a.k0_same = 1;
+    int k1_same = 1;
+    for (int l = 1; l < a.limbs; ++l) {
+        if (a.k0[l] != a.k0[0]) a.k0_same = 0;   // residues < q_l: equal ones are one integer below every q
+        if (a.k1[l] != a.k1[0]) k1_same = 0;
+    }
+    a.k01_same = a.k0_same && k1_same;
+    for (int j = 0; j < t; ++j) {
+        if (a.k0[0] + a.k1[0] >= 2 * c->q[j]) a.k01_same = 0;
+        if (a.k0[0] >= c->q[j] / 4) a.k0_same = 0;   // the mean filter's quotient reaches 4 K
+    }
+    for (int j = 0; j < t; ++j) {
         const u64 qj = c->q[j];
         a.k0r[j] = hm::mulm(a.k0[j], a.qt_inv[j], qj);
         a.k0rp[j] = hm::shoup_of(a.k0r[j], qj);
         a.k1r[j] = hm::mulm(a.k1[j], a.qt_inv[j], qj);
         a.k1rp[j] = hm::shoup_of(a.k1r[j], qj);
+        a.mq[j] = (4 * c->q[t] + qj - 1) / qj * qj;
     }
 }
 
@@ -993,7 +1032,7 @@ extern "C" ichee_status ichee_eval(ichee_ctx* c, ichee_op op, const uint64_t* d_
         set_k0(c, a, 1.0 / 9.0, c->delta);
         set_rescale(c, a);
         fold_constants(c, a);
-        CK(launch_meanfilter3(a, st));
+        CK(launch_meanfilter3(a, c->mf_staged != 0, c->num_sms, st));
         m.level = ma->level - 1;
         m.scale = ma->scale * c->delta / (double)c->q[ma->level];
         break;
@@ -1021,30 +1060,74 @@ extern "C" ichee_status ichee_eval(ichee_ctx* c, ichee_op op, const uint64_t* d_
     return ICHEE_OK;
 }
 
-// Matching (Sec. 4.4.3, as a squared L2 distance): T = sum_k (a_k - b_k)^2 in the NTT domain, INTT,
-// relinearise, rescale.
-static ichee_status op_sqdiff(ichee_ctx* c, const uint64_t* d_a, const ichee_ctimg_meta* ma, const uint64_t* d_b,
-                              uint64_t* d_out, ichee_ctimg_meta* mout, cudaStream_t st)
+extern "C" ichee_status ichee_meanfilter_rows(ichee_ctx* c, const uint64_t* d_in, const ichee_ctimg_meta* m_img,
+                                              uint32_t row0, uint32_t n_rows, uint32_t y0, uint32_t y1,
+                                              uint64_t* d_out, ichee_ctimg_meta* mout, void* stream)
 {
-    if (!c->have_evk) return fail(ICHEE_EUNSUPPORTED, "matching needs the evaluation key (ICHEE_WITH_EVK)");
-    if (ma->level == 0) return fail(ICHEE_ELEVEL, "matching needs a limb to drop");
-    const int limbs = (int)ma->level + 1;
-    const int n = c->n;
-    const int L = c->L;
-    int n_blocks = (c->num_sms / limbs) * limbs;
-    if (n_blocks < limbs) n_blocks = limbs;
-    const size_t partial_w = (size_t)n_blocks * 4 * n;
-    const size_t tensor_w = (size_t)3 * limbs * n;
-    const size_t digits_w = (size_t)limbs * (limbs + 1) * n;
-    const size_t acc_w = (size_t)2 * (limbs + 1) * n;
-    const size_t rel_w = (size_t)2 * limbs * n;
-    CK(c->scratch.ensure((partial_w + tensor_w + digits_w + acc_w + rel_w) * 8, c->user_alloc, c->user_free, c->user_alloc_ctx, st));
-    u64* partial = (u64*)c->scratch.p;
-    u64* tensor = partial + partial_w;
-    u64* digits = tensor + tensor_w;
-    u64* acc = digits + digits_w;
-    u64* rel = acc + acc_w;
+    ichee::NvtxRange nvtx_range("ichee_meanfilter_rows");
+    if (!c || !d_in || !m_img || !mout) return fail(ICHEE_EINVAL, "null argument");
+    CK(cudaSetDevice(c->device));
+    if ((int)m_img->level >= c->L) return fail(ICHEE_ELEVEL, "level %u >= %d", m_img->level, c->L);
+    if (m_img->level == 0) return fail(ICHEE_ELEVEL, "mean filter needs a limb to drop");
+    if (image_cts(m_img->h, m_img->w, m_img->c) == 0) return fail(ICHEE_EINVAL, "empty or oversized image");
+    if (!(m_img->scale > 0.0)) return fail(ICHEE_ESCALE, "scale must be positive");
+    if (c->n / 2 < 256) return fail(ICHEE_EUNSUPPORTED, "mean filter needs N >= 512");
+    if (!(y0 < y1 && y1 <= m_img->h)) return fail(ICHEE_EINVAL, "output rows [%u, %u) outside the %u-row image", y0, y1, m_img->h);
+    const u32 need0 = y0 > 0 ? y0 - 1 : 0, need1 = y1 < m_img->h ? y1 + 1 : m_img->h;
+    if (n_rows == 0 || row0 > need0 || (u64)row0 + n_rows < need1 || (u64)row0 + n_rows > m_img->h)
+        return fail(ICHEE_EINVAL, "input rows [%u, %u) do not hold rows [%u, %u) the output needs", row0, row0 + n_rows,
+                    need0, need1);
+    const u64 row_cts = (u64)m_img->w * m_img->c;
+    if (!is_device_ptr(d_in)) return fail(ICHEE_EINVAL, "input must be device memory");
+    ichee_status s = check_span(d_in, (u64)n_rows * row_cts * ct_words(c, (int)m_img->level + 1) * 8, "input rows");
+    if (s != ICHEE_OK) return s;
+    s = check_out(c, d_out, (u64)(y1 - y0) * row_cts, (int)m_img->level, "output rows");
+    if (s != ICHEE_OK) return s;
+    OpsArgs a = ops_base(c, m_img);
+    a.in0 = d_in;
+    a.out = d_out;
+    a.y0 = (int)y0;
+    a.rows = (int)(y1 - y0);
+    a.row0 = (int)row0;
+    set_k0(c, a, 1.0 / 9.0, c->delta);
+    set_rescale(c, a);
+    fold_constants(c, a);
+    CK(launch_meanfilter3(a, c->mf_staged != 0, c->num_sms, (cudaStream_t)stream));
+    *mout = *m_img;
+    mout->h = y1 - y0;
+    mout->level = m_img->level - 1;
+    mout->scale = m_img->scale * c->delta / (double)c->q[m_img->level];
+    return ICHEE_OK;
+}
 
+// Matching (Sec. 4.4.3, as a squared L2 distance): T = sum_k (a_k - b_k)^2 in the NTT domain,
+// INTT, relinearise, rescale. The steps are shared by ICHEE_OP_SQDIFF_SUM, the allocation-free
+// entry point and the split form (ichee_sqdiff_accumulate / ichee_sqdiff_finish); they differ
+// only in where the working memory comes from.
+
+// Accumulating blocks of the first step: one per SM, rounded down to a multiple of the limbs.
+static int sqdiff_blocks(const ichee_ctx* c, int limbs)
+{
+    const int nb = (c->num_sms / limbs) * limbs;
+    return nb < limbs ? limbs : nb;
+}
+
+// Words of the relinearisation working set: the tensor [3][limbs][N], the key-switching digits,
+// the accumulators over Q*P and the relinearised pair.
+static size_t relin_words(const ichee_ctx* c, int limbs)
+{
+    const size_t n = (size_t)c->n;
+    return (size_t)3 * limbs * n + (size_t)limbs * (limbs + 1) * n + (size_t)2 * (limbs + 1) * n +
+           (size_t)2 * limbs * n;
+}
+
+// tensor (= or +=) sum over the pixel pairs of (a - b) (x) (a - b), in the NTT domain (every term
+// carries the Montgomery factor 2^-64); partial: n_blocks x 4N words of scratch.
+static ichee_status sqdiff_partial_sum(ichee_ctx* c, const uint64_t* d_a, const ichee_ctimg_meta* ma,
+                                       const uint64_t* d_b, u64* partial, int n_blocks, u64* tensor, bool add,
+                                       cudaStream_t st)
+{
+    const int limbs = (int)ma->level + 1;
     SqDiffArgs sa;
     std::memset(&sa, 0, sizeof(sa));
     sa.rns = rns_prefix(c, limbs);
@@ -1055,10 +1138,25 @@ static ichee_status op_sqdiff(ichee_ctx* c, const uint64_t* d_a, const ichee_cti
     sa.partial = partial;
     sa.n_blocks = n_blocks;
     CK(launch_sqdiff_accumulate(sa, st));
-    CK(launch_sqdiff_reduce(sa.rns, limbs, partial, n_blocks, tensor, st));
-    std::vector<int> id = iota_idx(kMaxModuli);
-    CK(launch_ntt_inv(c->rns, batch(tensor, 3 * limbs, limbs, id.data()), st));
-    CK(launch_scale_const(c->rns, batch(tensor, 3 * limbs, limbs, id.data()), c->d_ninv_r, st));
+    CK(launch_sqdiff_reduce(sa.rns, limbs, partial, n_blocks, tensor, add, st));
+    return ICHEE_OK;
+}
+
+// tensor (reduced residues, NTT domain, overwritten) -> INTT -> relinearise -> rescale into
+// d_out (one ciphertext at level - 1). work: relin_words - 3 limbs N words after the tensor.
+static ichee_status sqdiff_relin_rescale(ichee_ctx* c, u64* tensor, const ichee_ctimg_meta* ma, u64* work,
+                                         uint64_t* d_out, ichee_ctimg_meta* mout, cudaStream_t st)
+{
+    const int limbs = (int)ma->level + 1;
+    const size_t n = (size_t)c->n;
+    const int L = c->L;
+    u64* digits = work;
+    u64* acc = digits + (size_t)limbs * (limbs + 1) * n;
+    u64* rel = acc + (size_t)2 * (limbs + 1) * n;
+    int id[kMaxModuli];
+    for (int m = 0; m < kMaxModuli; ++m) id[m] = m;
+    CK(launch_ntt_inv(c->rns, batch(tensor, 3 * limbs, limbs, id), st));
+    CK(launch_scale_const(c->rns, batch(tensor, 3 * limbs, limbs, id), c->d_ninv_r, st));
 
     RelinArgs ra;
     std::memset(&ra, 0, sizeof(ra));
@@ -1074,13 +1172,13 @@ static ichee_status op_sqdiff(ichee_ctx* c, const uint64_t* d_a, const ichee_cti
         const u64 r = c->P % c->q[j];
         ra.neg_p_mod[j] = r == 0 ? 0 : c->q[j] - r;
     }
-    std::vector<int> midx(limbs + 1);
+    int midx[kMaxModuli];
     for (int m = 0; m < limbs; ++m) midx[m] = m;
     midx[limbs] = L;
     CK(launch_relin_digits(ra, tensor + (size_t)2 * limbs * n, digits, st));
-    CK(launch_ntt_fwd(c->rns, batch(digits, limbs * (limbs + 1), limbs + 1, midx.data()), st));
+    CK(launch_ntt_fwd(c->rns, batch(digits, limbs * (limbs + 1), limbs + 1, midx), st));
     CK(launch_relin_mac(ra, digits, acc, st));
-    CK(launch_ntt_inv(c->rns, batch(acc, 2 * (limbs + 1), limbs + 1, midx.data()), st));
+    CK(launch_ntt_inv(c->rns, batch(acc, 2 * (limbs + 1), limbs + 1, midx), st));
     CK(launch_relin_moddown(ra, tensor, acc, rel, st));
 
     ichee_ctimg_meta one = *ma;
@@ -1094,6 +1192,99 @@ static ichee_status op_sqdiff(ichee_ctx* c, const uint64_t* d_a, const ichee_cti
     mout->level = ma->level - 1;
     mout->scale = ma->scale * ma->scale / (double)c->q[ma->level];
     return ICHEE_OK;
+}
+
+// The whole matching sum in one working block `base`: [tensor | relin work | partial slices].
+static ichee_status sqdiff_in(ichee_ctx* c, const uint64_t* d_a, const ichee_ctimg_meta* ma, const uint64_t* d_b,
+                              u64* base, int n_blocks, uint64_t* d_out, ichee_ctimg_meta* mout, cudaStream_t st)
+{
+    const int limbs = (int)ma->level + 1;
+    u64* tensor = base;
+    u64* work = tensor + (size_t)3 * limbs * c->n;
+    u64* partial = base + relin_words(c, limbs);   // the accumulate kernel zeroes its own slices
+    ichee_status s = sqdiff_partial_sum(c, d_a, ma, d_b, partial, n_blocks, tensor, false, st);
+    if (s != ICHEE_OK) return s;
+    return sqdiff_relin_rescale(c, tensor, ma, work, d_out, mout, st);
+}
+
+static ichee_status op_sqdiff(ichee_ctx* c, const uint64_t* d_a, const ichee_ctimg_meta* ma, const uint64_t* d_b,
+                              uint64_t* d_out, ichee_ctimg_meta* mout, cudaStream_t st)
+{
+    if (!c->have_evk) return fail(ICHEE_EUNSUPPORTED, "matching needs the evaluation key (ICHEE_WITH_EVK)");
+    if (ma->level == 0) return fail(ICHEE_ELEVEL, "matching needs a limb to drop");
+    const int limbs = (int)ma->level + 1;
+    const int n_blocks = sqdiff_blocks(c, limbs);
+    const size_t words = relin_words(c, limbs) + (size_t)n_blocks * 4 * c->n;
+    CK(c->scratch.ensure(words * 8, c->user_alloc, c->user_free, c->user_alloc_ctx, st));
+    return sqdiff_in(c, d_a, ma, d_b, (u64*)c->scratch.p, n_blocks, d_out, mout, st);
+}
+
+// Argument checks of the matching entry points outside ichee_eval.
+static ichee_status check_match(ichee_ctx* c, const uint64_t* d_a, const ichee_ctimg_meta* ma, const uint64_t* d_b,
+                                const ichee_ctimg_meta* mb)
+{
+    ichee_status s = check_img(c, d_a, ma, "a");
+    if (s != ICHEE_OK) return s;
+    s = check_img(c, d_b, mb, "b");
+    if (s != ICHEE_OK) return s;
+    if (mb->level != ma->level) return fail(ICHEE_ELEVEL, "levels differ (%u vs %u)", ma->level, mb->level);
+    if (!same_scale(ma->scale, mb->scale)) return fail(ICHEE_ESCALE, "scales differ (%g vs %g)", ma->scale, mb->scale);
+    if (mb->h != ma->h || mb->w != ma->w || mb->c != ma->c) return fail(ICHEE_EMISMATCH, "shapes differ");
+    if (!c->have_evk) return fail(ICHEE_EUNSUPPORTED, "matching needs the evaluation key (ICHEE_WITH_EVK)");
+    if (ma->level == 0) return fail(ICHEE_ELEVEL, "matching needs a limb to drop");
+    return ICHEE_OK;
+}
+
+extern "C" ichee_status ichee_sqdiff_acc_words(const ichee_ctx* c, uint32_t level, size_t* words)
+{
+    if (!c || !words) return fail(ICHEE_EINVAL, "null argument");
+    if ((int)level >= c->L) return fail(ICHEE_ELEVEL, "level %u >= %d", level, c->L);
+    *words = (size_t)3 * (level + 1) * c->n;
+    return ICHEE_OK;
+}
+
+extern "C" ichee_status ichee_sqdiff_accumulate(ichee_ctx* c, const uint64_t* d_a, const ichee_ctimg_meta* ma,
+                                                const uint64_t* d_b, const ichee_ctimg_meta* mb, uint64_t* d_acc,
+                                                int accumulate, void* stream)
+{
+    ichee::NvtxRange nvtx_range("ichee_sqdiff_accumulate");
+    if (!c) return fail(ICHEE_EINVAL, "null context");
+    CK(cudaSetDevice(c->device));
+    ichee_status s = check_match(c, d_a, ma, d_b, mb);
+    if (s != ICHEE_OK) return s;
+    const int limbs = (int)ma->level + 1;
+    const size_t acc_words = (size_t)3 * limbs * c->n;
+    if (!d_acc || !is_device_ptr(d_acc)) return fail(ICHEE_EINVAL, "accumulator must be device memory");
+    s = check_span(d_acc, acc_words * 8, "accumulator");
+    if (s != ICHEE_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n_blocks = sqdiff_blocks(c, limbs);
+    CK(c->scratch.ensure((size_t)n_blocks * 4 * c->n * 8, c->user_alloc, c->user_free, c->user_alloc_ctx, st));
+    return sqdiff_partial_sum(c, d_a, ma, d_b, (u64*)c->scratch.p, n_blocks, d_acc, accumulate != 0, st);
+}
+
+extern "C" ichee_status ichee_sqdiff_finish(ichee_ctx* c, const uint64_t* d_acc, const ichee_ctimg_meta* m_in,
+                                            uint64_t* d_out, ichee_ctimg_meta* mout, void* stream)
+{
+    ichee::NvtxRange nvtx_range("ichee_sqdiff_finish");
+    if (!c || !m_in || !mout) return fail(ICHEE_EINVAL, "null argument");
+    CK(cudaSetDevice(c->device));
+    if (!c->have_evk) return fail(ICHEE_EUNSUPPORTED, "matching needs the evaluation key (ICHEE_WITH_EVK)");
+    if ((int)m_in->level >= c->L) return fail(ICHEE_ELEVEL, "level %u >= %d", m_in->level, c->L);
+    if (m_in->level == 0) return fail(ICHEE_ELEVEL, "matching needs a limb to drop");
+    if (!(m_in->scale > 0.0)) return fail(ICHEE_ESCALE, "scale must be positive");
+    const int limbs = (int)m_in->level + 1;
+    const size_t acc_words = (size_t)3 * limbs * c->n;
+    if (!d_acc || !is_device_ptr(d_acc)) return fail(ICHEE_EINVAL, "accumulator must be device memory");
+    ichee_status s = check_span(d_acc, acc_words * 8, "accumulator");
+    if (s != ICHEE_OK) return s;
+    s = check_out(c, d_out, 1, limbs - 1, "output");
+    if (s != ICHEE_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(c->scratch.ensure(relin_words(c, limbs) * 8, c->user_alloc, c->user_free, c->user_alloc_ctx, st));
+    u64* tensor = (u64*)c->scratch.p;
+    CK(launch_reduce_rows(c->rns, 3 * limbs, limbs, d_acc, tensor, st));   // sums of accumulators, reduced
+    return sqdiff_relin_rescale(c, tensor, m_in, tensor + acc_words, d_out, mout, st);
 }
 
 // Per-pixel squared difference (per-pixel form of Sec. 4.4.3): one persistent kernel; each
@@ -1299,32 +1490,20 @@ extern "C" ichee_status ichee_sqdiff_sum_noalloc(ichee_ctx* c, const uint64_t* d
 {
     if (!c || !mout) return fail(ICHEE_EINVAL, "null argument");
     CK(cudaSetDevice(c->device));
-    ichee_status s = check_img(c, d_a, ma, "a");
-    if (s != ICHEE_OK) return s;
-    s = check_img(c, d_b, mb, "b");
+    ichee_status s = check_match(c, d_a, ma, d_b, mb);
     if (s != ICHEE_OK) return s;
     s = check_out(c, d_out, 1, (int)ma->level, "output");
     if (s != ICHEE_OK) return s;
-    if (mb->level != ma->level) return fail(ICHEE_ELEVEL, "levels differ (%u vs %u)", ma->level, mb->level);
-    if (!same_scale(ma->scale, mb->scale)) return fail(ICHEE_ESCALE, "scales differ (%g vs %g)", ma->scale, mb->scale);
-    if (mb->h != ma->h || mb->w != ma->w || mb->c != ma->c) return fail(ICHEE_EMISMATCH, "shapes differ");
-    if (!c->have_evk) return fail(ICHEE_EUNSUPPORTED, "matching needs the evaluation key (ICHEE_WITH_EVK)");
-    if (ma->level == 0) return fail(ICHEE_ELEVEL, "matching needs a limb to drop");
+    if (d_out == d_a || d_out == d_b) return fail(ICHEE_EINVAL, "this operation cannot run in place");
     const int limbs = (int)ma->level + 1;
     const size_t n = (size_t)c->n;
-    const int L = c->L;
-    // fixed part: tensor, digits, key-switch accumulators, relinearised result; then one
-    // 4-row slice per accumulating block, as many blocks as fit (a multiple of limbs)
-    const size_t tensor_w = (size_t)3 * limbs * n;
-    const size_t digits_w = (size_t)limbs * (limbs + 1) * n;
-    const size_t acc_w = (size_t)2 * (limbs + 1) * n;
-    const size_t rel_w = (size_t)2 * limbs * n;
-    const size_t fixed_w = tensor_w + digits_w + acc_w + rel_w;
+    // fixed part (tensor and relinearisation working set), then one 4-row slice per
+    // accumulating block, as many blocks as fit (a multiple of limbs)
+    const size_t fixed_w = relin_words(c, limbs);
     const size_t cap_w = ICHEE_NOALLOC_SCRATCH_BYTES / 8;
     const size_t slice_w = 4 * n;
     const size_t fit = fixed_w < cap_w ? (cap_w - fixed_w) / slice_w : 0;
-    int n_blocks = (c->num_sms / limbs) * limbs;
-    if (n_blocks < limbs) n_blocks = limbs;
+    int n_blocks = sqdiff_blocks(c, limbs);
     if ((size_t)n_blocks > fit) n_blocks = (int)((fit / limbs) * limbs);
     if (n_blocks < limbs)
         return fail(ICHEE_EINVAL, "matching at N=%zu with %d limbs needs %zu bytes of scratch; the allocation-free "
@@ -1333,61 +1512,5 @@ extern "C" ichee_status ichee_sqdiff_sum_noalloc(ichee_ctx* c, const uint64_t* d
     u64* base = nullptr;
     s = noalloc_scratch(c->device, &base);
     if (s != ICHEE_OK) return s;
-    u64* tensor = base;
-    u64* digits = tensor + tensor_w;
-    u64* acc = digits + digits_w;
-    u64* rel = acc + acc_w;
-    u64* partial = rel + rel_w;   // the accumulate kernel zeroes its own slices
-    cudaStream_t st = (cudaStream_t)stream;
-
-    SqDiffArgs sa;
-    std::memset(&sa, 0, sizeof(sa));
-    sa.rns = rns_prefix(c, limbs);
-    sa.limbs = limbs;
-    sa.n_ct = (u64)ma->h * ma->w * ma->c;
-    sa.a = d_a;
-    sa.b = d_b;
-    sa.partial = partial;
-    sa.n_blocks = n_blocks;
-    CK(launch_sqdiff_accumulate(sa, st));
-    CK(launch_sqdiff_reduce(sa.rns, limbs, partial, n_blocks, tensor, st));
-    int id[kMaxModuli];
-    for (int m = 0; m < kMaxModuli; ++m) id[m] = m;
-    CK(launch_ntt_inv(c->rns, batch(tensor, 3 * limbs, limbs, id), st));
-    CK(launch_scale_const(c->rns, batch(tensor, 3 * limbs, limbs, id), c->d_ninv_r, st));
-
-    RelinArgs ra;
-    std::memset(&ra, 0, sizeof(ra));
-    ra.rns = c->rns;
-    ra.L = L;
-    ra.limbs = limbs;
-    ra.evk_hat = c->d_evk_hat;
-    ra.evk_hat_p = c->d_evk_hat_p;
-    for (int m = 0; m < c->nmod; ++m) ra.mu[m] = c->rns.mu[m];
-    for (int j = 0; j < limbs; ++j) {
-        ra.p_inv[j] = hm::invm(c->P % c->q[j], c->q[j]);
-        ra.p_inv_p[j] = hm::shoup_of(ra.p_inv[j], c->q[j]);
-        const u64 r = c->P % c->q[j];
-        ra.neg_p_mod[j] = r == 0 ? 0 : c->q[j] - r;
-    }
-    int midx[kMaxModuli];
-    for (int m = 0; m < limbs; ++m) midx[m] = m;
-    midx[limbs] = L;
-    CK(launch_relin_digits(ra, tensor + (size_t)2 * limbs * n, digits, st));
-    CK(launch_ntt_fwd(c->rns, batch(digits, limbs * (limbs + 1), limbs + 1, midx), st));
-    CK(launch_relin_mac(ra, digits, acc, st));
-    CK(launch_ntt_inv(c->rns, batch(acc, 2 * (limbs + 1), limbs + 1, midx), st));
-    CK(launch_relin_moddown(ra, tensor, acc, rel, st));
-
-    ichee_ctimg_meta one = *ma;
-    one.h = one.w = one.c = 1;
-    OpsArgs a = ops_base(c, &one);
-    a.in0 = rel;
-    a.out = d_out;
-    set_rescale(c, a);
-    CK(launch_rescale(a, st));
-    *mout = one;
-    mout->level = ma->level - 1;
-    mout->scale = ma->scale * ma->scale / (double)c->q[ma->level];
-    return ICHEE_OK;
+    return sqdiff_in(c, d_a, ma, d_b, base, n_blocks, d_out, mout, (cudaStream_t)stream);
 }

@@ -120,24 +120,40 @@ cudaError_t launch_sqdiff_accumulate(const SqDiffArgs& a, cudaStream_t st)
     }
 }
 
-__global__ void k_sqdiff_reduce(RnsArgs rns, int limbs, const u64* partial, int n_blocks, u64* tensor)
+__global__ void k_sqdiff_reduce(RnsArgs rns, int limbs, const u64* partial, int n_blocks, u64* tensor, int add)
 {
     const int n = 1 << rns.logn;
     const int pl = blockIdx.y;                 // p * limbs + l
     const int p = pl / limbs, l = pl % limbs;
     const u64 q = rns.q[l];
     for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
-        u64 s = 0;
+        u64 s = add ? reduce64(tensor[(size_t)pl * n + x], q, rns.mu[l]) : 0;
         for (int j = l; j < n_blocks; j += limbs) s = add_mod(s, partial[((size_t)j * 4 + p) * n + x], q);
         tensor[(size_t)pl * n + x] = s;
     }
 }
 
 cudaError_t launch_sqdiff_reduce(const RnsArgs& rns, int limbs, const u64* partial, int n_blocks, u64* tensor,
-                                 cudaStream_t st)
+                                 bool add, cudaStream_t st)
 {
     dim3 grid((1u << rns.logn) / 256, 3 * limbs);
-    k_sqdiff_reduce<<<grid, 256, 0, st>>>(rns, limbs, partial, n_blocks, tensor);
+    k_sqdiff_reduce<<<grid, 256, 0, st>>>(rns, limbs, partial, n_blocks, tensor, add ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// out[r][x] = in[r][x] mod q_{r % limbs} for any 64-bit input word (sums of accumulators).
+__global__ void k_reduce_rows(RnsArgs rns, int limbs, const u64* in, u64* out)
+{
+    const int n = 1 << rns.logn;
+    const int r = blockIdx.y, l = r % limbs;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x)
+        out[(size_t)r * n + x] = reduce64(in[(size_t)r * n + x], rns.q[l], rns.mu[l]);
+}
+
+cudaError_t launch_reduce_rows(const RnsArgs& rns, int rows, int limbs, const u64* in, u64* out, cudaStream_t st)
+{
+    dim3 grid((1u << rns.logn) / 256, rows);
+    k_reduce_rows<<<grid, 256, 0, st>>>(rns, limbs, in, out);
     return cudaGetLastError();
 }
 

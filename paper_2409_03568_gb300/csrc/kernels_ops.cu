@@ -1,6 +1,7 @@
 // kernels_ops.cu -- ciphertext-wise image operations (Sec. 2.2.3, Sec. 4.4) and decryption
 // (Sec. 2.2.2). Ciphertexts are [n_ct][2][limbs][N] residues in the coefficient domain.
 #include "ops.h"
+#include "bulk.cuh"
 
 namespace ichee {
 
@@ -25,6 +26,39 @@ __device__ __forceinline__ u64 rescale_fold(u64 prod_j, u64 ct, int j, const Ops
 __device__ __forceinline__ u64 rescale_one(u64 cj, u64 ct, int j, const OpsArgs& a)
 {
     return rescale_fold(shoup_lazy(cj, a.qt_inv[j], a.qt_inv_p[j], a.q[j]), ct, j, a);
+}
+
+// Fused multiply by K and rescale when K is one integer with 4K below every modulus
+// (a.k0_same). Let S' = S_t - c q_t (S_t a sum of at most nine residues, below 9 q_t; S' below
+// 4 q_t) and K S' = u q_t + m with m centered in (-q_t/2, q_t/2]. Then
+//   (K S_j - m) q_t^{-1} = K q_t^{-1} (S_j - S') + u  (mod q_j),
+// the rescale of K S, with one Shoup product per kept limb instead of two: the quotient u comes
+// with the product on limb t (Shoup's quotient is exact up to one for any 64-bit operand), and
+// u <= 4K < q_j.
+struct RescaleQuot {
+    u64 s;   // S_t reduced below 4 q_t
+    u64 u;   // rounded quotient of K S' by q_t
+};
+
+__device__ __forceinline__ RescaleQuot rescale_quot(u64 st, const OpsArgs& a, int t)
+{
+    const u64 q = a.q[t];
+    st = st >= 8 * q ? st - 8 * q : st;
+    st = st >= 4 * q ? st - 4 * q : st;
+    u64 hi = mulhi(st, a.k0p[t]);
+    u64 r = st * a.k0[t] - hi * q;   // in [0, 2q): K S' = hi q + r
+    if (r >= q) { r -= q; hi += 1; }
+    return {st, hi + (r > a.half_qt ? 1 : 0)};
+}
+
+// Limb j < t of Rescale(K * S) from the unreduced sum S_j (below 9 q_j) and rescale_quot's
+// result; mq[j] is a multiple of q_j of at least 4 q_t, and S_j + mq[j] - S' < 14 * 2^60.
+__device__ __forceinline__ u64 rescale_quot_limb(u64 sj, const RescaleQuot& rq, int j, const OpsArgs& a)
+{
+    const u64 qj = a.q[j];
+    u64 v = shoup_lazy(sj + a.mq[j] - rq.s, a.k0r[j], a.k0rp[j], qj) + rq.u;   // in [0, 3 q_j)
+    v = v >= 2 * qj ? v - 2 * qj : v;
+    return v >= qj ? v - qj : v;
 }
 
 // Elementwise add / sub of two images with the same shape (Sec. 2.2.3, Sec. 3.3).
@@ -121,15 +155,49 @@ __global__ void k_rescale(const __grid_constant__ OpsArgs a)
     }
 }
 
+// One output pair of the mean filter from the three column sums of its window (each the sum of
+// three rows, unreduced): fused multiply by K9 and rescale, stored to o[j * half] per kept limb.
+template <int LIMBS>
+__device__ __forceinline__ void mf_store(const OpsArgs& a, const ulonglong2 (&cl)[LIMBS], const ulonglong2 (&cm)[LIMBS],
+                                         const ulonglong2 (&cr)[LIMBS], ulonglong2* o, int half)
+{
+    const u64 qt = a.q[LIMBS - 1];
+    const u64 sx = cl[LIMBS - 1].x + cm[LIMBS - 1].x + cr[LIMBS - 1].x;
+    const u64 sy = cl[LIMBS - 1].y + cm[LIMBS - 1].y + cr[LIMBS - 1].y;
+    if (a.k0_same) {
+        const RescaleQuot rx = rescale_quot(sx, a, LIMBS - 1), ry = rescale_quot(sy, a, LIMBS - 1);
+#pragma unroll
+        for (int j = 0; j < LIMBS - 1; ++j) {
+            ulonglong2 v;
+            v.x = rescale_quot_limb(cl[j].x + cm[j].x + cr[j].x, rx, j, a);
+            v.y = rescale_quot_limb(cl[j].y + cm[j].y + cr[j].y, ry, j, a);
+            __stcs(o + j * half, v);
+        }
+    } else {
+        const u64 tx = shoup(sx, a.k0[LIMBS - 1], a.k0p[LIMBS - 1], qt);
+        const u64 ty = shoup(sy, a.k0[LIMBS - 1], a.k0p[LIMBS - 1], qt);
+#pragma unroll
+        for (int j = 0; j < LIMBS - 1; ++j) {
+            const u64 qj = a.q[j];
+            ulonglong2 v;
+            v.x = rescale_fold(shoup_lazy(cl[j].x + cm[j].x + cr[j].x, a.k0r[j], a.k0rp[j], qj), tx, j, a);
+            v.y = rescale_fold(shoup_lazy(cl[j].y + cm[j].y + cr[j].y, a.k0r[j], a.k0rp[j], qj), ty, j, a);
+            __stcs(o + j * half, v);
+        }
+    }
+}
+
 // Fused 3x3 mean filter (Sec. 4.4.1; borders clamp to the edge): out(y,x) = Rescale(K9 * sum of the 9
 // clamp-to-edge neighbours). One block per (row y, channel, poly, coefficient chunk); each
 // thread owns one coefficient pair and walks the row left to right keeping the three column
 // sums of the window in registers, so every input row is loaded once per output row. Residues
 // are below 2^60, so the 9-term sums fit 64 bits unreduced and go straight into the Shoup
 // products (K9 for the dropped limb, K9 q_t^{-1} for the kept ones).
+// in0 holds the image's rows from row0 on, out0 its output rows from yout0 on (0 and 0 for a
+// whole image); h is the height of the whole image (the clamping rows).
 template <int LIMBS>
 __device__ __forceinline__ void meanfilter_row(const OpsArgs& a, const u64* in0, u64* out0, int h, int w, int C, int y,
-                                               int chunk, int b, int ch)
+                                               int chunk, int b, int ch, int row0 = 0, int yout0 = 0)
 {
     const int n = 1 << a.logn;
     const int c2 = chunk * blockDim.x + threadIdx.x;  // coefficient-pair index
@@ -141,11 +209,11 @@ __device__ __forceinline__ void meanfilter_row(const OpsArgs& a, const u64* in0,
     const int half = n / 2;
     // the three input rows at column 0 and the output row at column 0; one column further is a
     // fixed stride of C ciphertexts (pointer adds, no per-column 64-bit products)
-    const ulonglong2* r0 = in + ((u64)ym * w * C + ch) * ct_len2;
-    const ulonglong2* r1 = in + ((u64)y * w * C + ch) * ct_len2;
-    const ulonglong2* r2 = in + ((u64)yp * w * C + ch) * ct_len2;
+    const ulonglong2* r0 = in + ((u64)(ym - row0) * w * C + ch) * ct_len2;
+    const ulonglong2* r1 = in + ((u64)(y - row0) * w * C + ch) * ct_len2;
+    const ulonglong2* r2 = in + ((u64)(yp - row0) * w * C + ch) * ct_len2;
     const u64 in_step = (u64)C * ct_len2;
-    ulonglong2* o = out + ((u64)y * w * C + ch) * out_len2;
+    ulonglong2* o = out + ((u64)(y - yout0) * w * C + ch) * out_len2;
     const u64 out_step = (u64)C * out_len2;
 
     ulonglong2 col[3][LIMBS];
@@ -164,25 +232,173 @@ __device__ __forceinline__ void meanfilter_row(const OpsArgs& a, const u64* in0,
 #pragma unroll
     for (int l = 0; l < LIMBS; ++l) col[1][l] = col[0][l];
     column(w > 1 ? 1 : 0, col[2]);
-    const u64 qt = a.q[LIMBS - 1];
     for (int x = 0; x < w; ++x, o += out_step) {
-        const u64 sx = col[0][LIMBS - 1].x + col[1][LIMBS - 1].x + col[2][LIMBS - 1].x;
-        const u64 sy = col[0][LIMBS - 1].y + col[1][LIMBS - 1].y + col[2][LIMBS - 1].y;
-        const u64 tx = shoup(sx, a.k0[LIMBS - 1], a.k0p[LIMBS - 1], qt);
-        const u64 ty = shoup(sy, a.k0[LIMBS - 1], a.k0p[LIMBS - 1], qt);
-#pragma unroll
-        for (int j = 0; j < LIMBS - 1; ++j) {
-            const u64 qj = a.q[j];
-            ulonglong2 v;
-            v.x = rescale_fold(shoup_lazy(col[0][j].x + col[1][j].x + col[2][j].x, a.k0r[j], a.k0rp[j], qj), tx, j, a);
-            v.y = rescale_fold(shoup_lazy(col[0][j].y + col[1][j].y + col[2][j].y, a.k0r[j], a.k0rp[j], qj), ty, j, a);
-            __stcs(o + j * half, v);
-        }
+        mf_store<LIMBS>(a, col[0], col[1], col[2], o, half);
         if (x + 1 < w) {
 #pragma unroll
             for (int l = 0; l < LIMBS; ++l) { col[0][l] = col[1][l]; col[1][l] = col[2][l]; }
             column(x + 2 < w ? x + 2 : w - 1, col[2]);
         }
+    }
+}
+
+// Status word value written when a bounded wait of a kernel gives up.
+constexpr int kStatusWaitTimeout = 0x5701;
+
+// The same row walk with the input columns staged in shared memory by bulk copies: for each
+// column of the row, one thread copies the three input rows' segments of every limb (T
+// coefficient pairs, T x 16 bytes each) into one of two stages, two columns ahead of the
+// threads that sum them, so the block keeps two columns of loads in flight without holding them
+// in registers. `gc` counts the columns the block has consumed (stage = count mod 2, barrier
+// phase = count / 2). Returns false, with every thread, if a wait gave up (the status word is
+// set and the copies still in flight are waited for, within the bound).
+constexpr int kMfStages = 2;
+
+template <int LIMBS>
+__device__ __forceinline__ bool meanfilter_row_staged(const OpsArgs& a, const u64* in0, u64* out0, int h, int w, int C,
+                                                      int y, int chunk, int b, int ch, int row0, int yout0,
+                                                      ulonglong2* stages, u64* bars, u32& gc)
+{
+    const int T = blockDim.x, tid = threadIdx.x;
+    const int half = (1 << a.logn) / 2;
+    const u64 ct_len2 = (u64)2 * LIMBS * half;
+    const u64 out_len2 = (u64)2 * (LIMBS - 1) * half;
+    const int ym = y > 0 ? y - 1 : 0, yp = y + 1 < h ? y + 1 : h - 1;
+    const ulonglong2* in = reinterpret_cast<const ulonglong2*>(in0) + (u64)b * LIMBS * half + (u64)chunk * T;
+    const ulonglong2* src[3] = {in + ((u64)(ym - row0) * w * C + ch) * ct_len2,
+                                in + ((u64)(y - row0) * w * C + ch) * ct_len2,
+                                in + ((u64)(yp - row0) * w * C + ch) * ct_len2};
+    const u64 in_step = (u64)C * ct_len2;
+    const u32 seg_bytes = (u32)T * 16u;
+    const int stage_u2 = 3 * LIMBS * T;
+    ulonglong2* o = reinterpret_cast<ulonglong2*>(out0) + (u64)b * (LIMBS - 1) * half + (u64)chunk * T + tid +
+                    ((u64)(y - yout0) * w * C + ch) * out_len2;
+    const u64 out_step = (u64)C * out_len2;
+
+    auto issue = [&](int j) {   // one thread: column j into its stage
+        const u32 k = gc + (u32)j;
+        u64* bar = bars + (k % kMfStages);
+        ulonglong2* dst = stages + (k % kMfStages) * stage_u2;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar, 3u * LIMBS * seg_bytes);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int l = 0; l < LIMBS; ++l)
+                bulk_g2s(dst + (r * LIMBS + l) * T, src[r] + (u64)j * in_step + (u64)l * half, seg_bytes, bar);
+    };
+    auto give_up = [&](int j) {   // every thread returns; thread 0 drains the copies issued
+        if (tid == 0) {
+            atomicExch(a.status, kStatusWaitTimeout);
+            for (int jj = j; jj < w && jj < j + kMfStages; ++jj) {
+                const u32 k = gc + (u32)jj;
+                mbar_wait(bars + (k % kMfStages), (k / kMfStages) & 1u);
+            }
+        }
+        return false;
+    };
+    // column j's three-row sums for this thread; then the stage is refilled with column j + 2
+    auto take = [&](int j, ulonglong2 (&cs)[LIMBS]) -> bool {
+        const u32 k = gc + (u32)j;
+        const bool ok = mbar_wait(bars + (k % kMfStages), (k / kMfStages) & 1u);
+        if (ok) {
+            const ulonglong2* sp = stages + (k % kMfStages) * stage_u2 + tid;
+#pragma unroll
+            for (int l = 0; l < LIMBS; ++l) {
+                const ulonglong2 v0 = sp[l * T], v1 = sp[(LIMBS + l) * T], v2 = sp[(2 * LIMBS + l) * T];
+                cs[l] = make_ulonglong2(v0.x + v1.x + v2.x, v0.y + v1.y + v2.y);
+            }
+        }
+        if (__syncthreads_or(ok ? 0 : 1)) return false;   // the stage is free again
+        if (tid == 0 && j + kMfStages < w) issue(j + kMfStages);
+        return true;
+    };
+
+    if (tid == 0) {
+        issue(0);
+        if (w > 1) issue(1);
+    }
+    ulonglong2 cl[LIMBS], cm[LIMBS], cr[LIMBS];
+    if (!take(0, cm)) return give_up(0);
+#pragma unroll
+    for (int l = 0; l < LIMBS; ++l) cl[l] = cm[l];   // x = -1 clamps to 0
+    if (w > 1) {
+        if (!take(1, cr)) return give_up(1);
+    } else {
+#pragma unroll
+        for (int l = 0; l < LIMBS; ++l) cr[l] = cm[l];
+    }
+    for (int x = 0; x < w; ++x, o += out_step) {
+        mf_store<LIMBS>(a, cl, cm, cr, o, half);
+#pragma unroll
+        for (int l = 0; l < LIMBS; ++l) { cl[l] = cm[l]; cm[l] = cr[l]; }
+        if (x + 2 < w && !take(x + 2, cr)) return give_up(x + 2);   // else column w-1 stays on the right
+    }
+    gc += (u32)w;
+    return true;
+}
+
+// Shared memory of the staged mean filter: two barriers (padded to 128 bytes), two stages.
+__host__ __device__ constexpr size_t mf_staged_smem(int limbs, int threads)
+{
+    return 128 + (size_t)kMfStages * 3 * limbs * threads * 16;
+}
+
+__device__ __forceinline__ void mf_staged_setup(unsigned char* smraw, u64*& bars, ulonglong2*& stages)
+{
+    bars = reinterpret_cast<u64*>(smraw);
+    stages = reinterpret_cast<ulonglong2*>(smraw + 128);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kMfStages; ++s) mbar_init(bars + s, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+}
+
+// Persistent grid over the items (row, chunk, poly, channel) of one image.
+template <int LIMBS>
+__global__ void __launch_bounds__(256) k_meanfilter3_staged(const __grid_constant__ OpsArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smraw[];
+    u64* bars;
+    ulonglong2* stages;
+    mf_staged_setup(smraw, bars, stages);
+    const int chunks = ((1 << a.logn) / 2) / blockDim.x;
+    const u64 items = (u64)a.rows * chunks * 2 * a.c;
+    u32 gc = 0;
+    for (u64 g = blockIdx.x; g < items; g += gridDim.x) {
+        u64 bid = g;
+        const int y = a.y0 + (int)(bid % a.rows); bid /= a.rows;
+        const int chunk = (int)(bid % chunks); bid /= chunks;
+        const int b = (int)(bid % 2); bid /= 2;
+        if (!meanfilter_row_staged<LIMBS>(a, a.in0, a.out, a.h, a.w, a.c, y, chunk, b, (int)bid, a.row0, a.y0, stages,
+                                          bars, gc))
+            return;
+    }
+}
+
+// Ragged batch, same items as k_meanfilter3_batch.
+template <int LIMBS>
+__global__ void __launch_bounds__(512) k_meanfilter3_staged_batch(const __grid_constant__ OpsArgs a,
+                                                                  const __grid_constant__ SegTable t)
+{
+    extern __shared__ __align__(128) unsigned char smraw[];
+    u64* bars;
+    ulonglong2* stages;
+    mf_staged_setup(smraw, bars, stages);
+    const int chunks = ((1 << a.logn) / 2) / blockDim.x;
+    const u64 total = t.start[t.n];
+    u32 gc = 0;
+    for (u64 g = blockIdx.x; g < total; g += gridDim.x) {
+        const int s = seg_of(t, g);
+        u64 i = g - t.start[s];
+        const int h = (int)t.h[s];
+        const int y = (int)(i % h); i /= h;
+        const int chunk = (int)(i % chunks); i /= chunks;
+        const int b = (int)(i % 2); i /= 2;
+        if (!meanfilter_row_staged<LIMBS>(a, t.in0[s], t.out[s], h, (int)t.w[s], (int)t.c[s], y, chunk, b, (int)i, 0, 0,
+                                          stages, bars, gc))
+            return;
     }
 }
 
@@ -192,10 +408,10 @@ __global__ void __launch_bounds__(256) k_meanfilter3(const __grid_constant__ Ops
 {
     const int chunks = ((1 << a.logn) / 2) / blockDim.x;
     u64 bid = blockIdx.x;
-    const int y = (int)(bid % a.h); bid /= a.h;
+    const int y = a.y0 + (int)(bid % a.rows); bid /= a.rows;
     const int chunk = (int)(bid % chunks); bid /= chunks;
     const int b = (int)(bid % 2); bid /= 2;
-    meanfilter_row<LIMBS>(a, a.in0, a.out, a.h, a.w, a.c, y, chunk, b, (int)bid);
+    meanfilter_row<LIMBS>(a, a.in0, a.out, a.h, a.w, a.c, y, chunk, b, (int)bid, a.row0, a.y0);
 }
 
 // Largest block of the batched mean-filter kernels for a limb count: the column sums of more
@@ -343,17 +559,30 @@ __global__ void __launch_bounds__(kMfMaxThreads<LIMBS>) k_radix_meanfilter3_batc
                 const ulonglong2* vl = vb - LIMBS * 32;
                 const ulonglong2* vr = vb + LIMBS * 32;
                 const ulonglong2 ht0 = vl[(LIMBS - 1) * 32], ht1 = vb[(LIMBS - 1) * 32], ht2 = vr[(LIMBS - 1) * 32];
-                const u64 tx = shoup(ht0.x + ht1.x + ht2.x, a.k0[LIMBS - 1], a.k0p[LIMBS - 1], qt);
-                const u64 ty = shoup(ht0.y + ht1.y + ht2.y, a.k0[LIMBS - 1], a.k0p[LIMBS - 1], qt);
                 ulonglong2* o = flt + (size_t)y * flt_row;
+                if (a.k0_same) {
+                    const RescaleQuot rx = rescale_quot(ht0.x + ht1.x + ht2.x, a, LIMBS - 1);
+                    const RescaleQuot ry = rescale_quot(ht0.y + ht1.y + ht2.y, a, LIMBS - 1);
 #pragma unroll
-                for (int j = 0; j < LIMBS - 1; ++j) {
-                    const u64 qj = a.q[j];
-                    const ulonglong2 h0 = vl[j * 32], h1 = vb[j * 32], h2 = vr[j * 32];
-                    ulonglong2 v;
-                    v.x = rescale_fold(shoup_lazy(h0.x + h1.x + h2.x, a.k0r[j], a.k0rp[j], qj), tx, j, a);
-                    v.y = rescale_fold(shoup_lazy(h0.y + h1.y + h2.y, a.k0r[j], a.k0rp[j], qj), ty, j, a);
-                    __stcs(o + (size_t)j * half, v);
+                    for (int j = 0; j < LIMBS - 1; ++j) {
+                        const ulonglong2 h0 = vl[j * 32], h1 = vb[j * 32], h2 = vr[j * 32];
+                        ulonglong2 v;
+                        v.x = rescale_quot_limb(h0.x + h1.x + h2.x, rx, j, a);
+                        v.y = rescale_quot_limb(h0.y + h1.y + h2.y, ry, j, a);
+                        __stcs(o + (size_t)j * half, v);
+                    }
+                } else {
+                    const u64 tx = shoup(ht0.x + ht1.x + ht2.x, a.k0[LIMBS - 1], a.k0p[LIMBS - 1], qt);
+                    const u64 ty = shoup(ht0.y + ht1.y + ht2.y, a.k0[LIMBS - 1], a.k0p[LIMBS - 1], qt);
+#pragma unroll
+                    for (int j = 0; j < LIMBS - 1; ++j) {
+                        const u64 qj = a.q[j];
+                        const ulonglong2 h0 = vl[j * 32], h1 = vb[j * 32], h2 = vr[j * 32];
+                        ulonglong2 v;
+                        v.x = rescale_fold(shoup_lazy(h0.x + h1.x + h2.x, a.k0r[j], a.k0rp[j], qj), tx, j, a);
+                        v.y = rescale_fold(shoup_lazy(h0.y + h1.y + h2.y, a.k0r[j], a.k0rp[j], qj), ty, j, a);
+                        __stcs(o + (size_t)j * half, v);
+                    }
                 }
             }
         }
@@ -373,6 +602,39 @@ __device__ __forceinline__ void blend_pair(const OpsArgs& a, const u64* ci, cons
     const ulonglong2* s1 = reinterpret_cast<const ulonglong2*>(cw + (u64)b * LIMBS * n) + c;
     const u64 qt = a.q[t];
     const ulonglong2 ut = __ldcs(s0 + t * (n / 2)), wt = __ldg(s1 + t * (n / 2));
+    if (a.k01_same) {
+        // With Ka, Kb one integer each below every modulus, Ka I_t + Kb W_t = u q_t + m (m
+        // centered) and limb j of the result is Ka q_t^{-1}(I_j - I_t) + Kb q_t^{-1}(W_j - W_t) + u:
+        // two Shoup products per kept limb instead of three. u <= Ka + Kb < 2 q_j.
+        ulonglong2* dst = reinterpret_cast<ulonglong2*>(co + (u64)b * (LIMBS - 1) * n) + c;
+        auto quot = [&](u64 i_t, u64 w_t) -> u64 {
+            u64 ha = mulhi(i_t, a.k0p[t]), hb = mulhi(w_t, a.k1p[t]);
+            u64 r = (i_t * a.k0[t] - ha * qt) + (w_t * a.k1[t] - hb * qt);   // in [0, 4 q_t)
+            u64 u = ha + hb;
+            if (r >= 2 * qt) { r -= 2 * qt; u += 2; }
+            if (r >= qt) { r -= qt; u += 1; }
+            return u + (r > a.half_qt ? 1 : 0);
+        };
+        const u64 ux = quot(ut.x, wt.x), uy = quot(ut.y, wt.y);
+#pragma unroll
+        for (int j = 0; j < LIMBS - 1; ++j) {
+            const u64 qj = a.q[j];
+            const ulonglong2 u = __ldcs(s0 + j * (n / 2)), v = __ldg(s1 + j * (n / 2));
+            auto limb = [&](u64 ij, u64 wj, u64 it, u64 wtt, u64 uu) -> u64 {
+                uu = uu >= qj ? uu - qj : uu;
+                u64 r = shoup_lazy(ij + a.mq[j] - it, a.k0r[j], a.k0rp[j], qj) +
+                        shoup_lazy(wj + a.mq[j] - wtt, a.k1r[j], a.k1rp[j], qj) + uu;   // in [0, 5 q_j)
+                r = r >= 4 * qj ? r - 4 * qj : r;
+                r = r >= 2 * qj ? r - 2 * qj : r;
+                return r >= qj ? r - qj : r;
+            };
+            ulonglong2 o;
+            o.x = limb(u.x, v.x, ut.x, wt.x, ux);
+            o.y = limb(u.y, v.y, ut.y, wt.y, uy);
+            __stcs(dst + j * (n / 2), o);
+        }
+        return;
+    }
     const u64 tx = add_mod(shoup(ut.x, a.k0[t], a.k0p[t], qt), shoup(wt.x, a.k1[t], a.k1p[t], qt), qt);
     const u64 ty = add_mod(shoup(ut.y, a.k0[t], a.k0p[t], qt), shoup(wt.y, a.k1[t], a.k1p[t], qt), qt);
     ulonglong2* dst = reinterpret_cast<ulonglong2*>(co + (u64)b * (LIMBS - 1) * n) + c;
@@ -668,13 +930,50 @@ cudaError_t launch_rescale(const OpsArgs& a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_meanfilter3(const OpsArgs& a, cudaStream_t st)
+// Launch of a staged mean-filter kernel: persistent grid of the blocks that fit on the GPU
+// (bounded by blocks_per_sm when it is set), dynamic shared memory for the two stages.
+template <typename K, typename... Args>
+static cudaError_t mf_staged_launch(K kern, int limbs, int threads, u64 items, int blocks_per_sm, int num_sms,
+                                    cudaStream_t st, const Args&... args)
+{
+    const size_t smem = mf_staged_smem(limbs, threads);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int fit = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (fit < 1) return cudaErrorInvalidConfiguration;
+    if (blocks_per_sm > 0 && blocks_per_sm < fit) fit = blocks_per_sm;
+    const u64 cap = (u64)fit * num_sms;
+    kern<<<(unsigned)(items < cap ? items : cap), threads, smem, st>>>(args...);
+    return cudaGetLastError();
+}
+
+// Threads of a staged block: the requested count, halved while its two stages would not fit
+// in 200 KB of shared memory.
+static int mf_staged_threads(int limbs, int threads)
+{
+    while (threads > 128 && mf_staged_smem(limbs, threads) > 200 * 1024) threads /= 2;
+    return threads;
+}
+
+cudaError_t launch_meanfilter3(const OpsArgs& a, bool staged, int num_sms, cudaStream_t st)
 {
     const int n = 1 << a.logn;
     const int threads = 256;
     const int chunks = (n / 2) / threads;
-    const u64 blocks = (u64)a.h * chunks * 2 * a.c;
+    const u64 blocks = (u64)a.rows * chunks * 2 * a.c;
     if (blocks == 0) return cudaSuccess;
+    if (staged) {
+        switch (a.limbs) {
+#define ICHEE_MF_STAGED_CASE(LB) \
+    case LB: return mf_staged_launch(k_meanfilter3_staged<LB>, LB, threads, blocks, 0, num_sms, st, a);
+            ICHEE_MF_STAGED_CASE(2) ICHEE_MF_STAGED_CASE(3) ICHEE_MF_STAGED_CASE(4) ICHEE_MF_STAGED_CASE(5)
+            ICHEE_MF_STAGED_CASE(6) ICHEE_MF_STAGED_CASE(7) ICHEE_MF_STAGED_CASE(8)
+#undef ICHEE_MF_STAGED_CASE
+        default: return cudaErrorInvalidValue;
+        }
+    }
     ICHEE_LIMB_SWITCH(k_meanfilter3, (unsigned)blocks, threads, a)
     return cudaGetLastError();
 }
@@ -693,10 +992,25 @@ static unsigned persistent_grid(u64 total, LaunchShape ls, int num_sms)
     return (unsigned)(total < cap ? total : cap);
 }
 
-cudaError_t launch_meanfilter3_batch(const OpsArgs& a, const SegTable& t, LaunchShape ls, int num_sms, cudaStream_t st)
+cudaError_t launch_meanfilter3_batch(const OpsArgs& a, const SegTable& t, LaunchShape ls, bool staged, int num_sms,
+                                     cudaStream_t st)
 {
     const u64 total = t.n > 0 ? t.start[t.n] : 0;
     if (total == 0) return cudaSuccess;
+    if (staged) {
+        // items were counted by the caller for ls.threads; the staged block keeps that count
+        // unless its stages do not fit, so the caller counts with mf_batch_threads
+        const int th = mf_staged_threads(a.limbs, ls.threads);
+        if (th != ls.threads) return cudaErrorInvalidValue;
+        switch (a.limbs) {
+#define ICHEE_MF_STAGED_CASE(LB) \
+    case LB: return mf_staged_launch(k_meanfilter3_staged_batch<LB>, LB, th, total, ls.blocks_per_sm, num_sms, st, a, t);
+            ICHEE_MF_STAGED_CASE(2) ICHEE_MF_STAGED_CASE(3) ICHEE_MF_STAGED_CASE(4) ICHEE_MF_STAGED_CASE(5)
+            ICHEE_MF_STAGED_CASE(6) ICHEE_MF_STAGED_CASE(7) ICHEE_MF_STAGED_CASE(8)
+#undef ICHEE_MF_STAGED_CASE
+        default: return cudaErrorInvalidValue;
+        }
+    }
     const unsigned g = persistent_grid(total, ls, num_sms);
     ICHEE_LIMB_SWITCH_T(k_meanfilter3_batch, g, ls.threads, a, t)
     return cudaGetLastError();
@@ -788,4 +1102,8 @@ cudaError_t launch_decrypt(const DecArgs& a, int threads, cudaStream_t st)
     return cudaGetLastError();
 }
 
+}  // namespace ichee
+
+namespace ichee {
+int mf_batch_threads(int limbs, int threads, bool staged) { return staged ? mf_staged_threads(limbs, threads) : threads; }
 }  // namespace ichee

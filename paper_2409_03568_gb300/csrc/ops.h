@@ -16,12 +16,22 @@ struct OpsArgs {
     u64 qt_inv[kMaxPrimes], qt_inv_p[kMaxPrimes], neg_qt_mod[kMaxPrimes], half_qt;
     // constants already multiplied by q_t^{-1} mod q_j (Shoup pairs), for fused multiply + rescale
     u64 k0r[kMaxPrimes], k0rp[kMaxPrimes], k1r[kMaxPrimes], k1rp[kMaxPrimes];
+    // k0_same: k0 is one integer below every modulus (equal residues in every limb), which lets a
+    // fused multiply + rescale take one product per kept limb; mq[j] = ceil(4 q_t / q_j) * q_j
+    int k0_same;
+    u64 mq[kMaxPrimes];
+    // k01_same: k0 and k1 are both such integers and k0 + k1 < 2 q_j for every kept limb j
+    int k01_same;
     // plaintext add to ciphertexts [k_lo, k_hi): kadd[k * limbs + l] if kadd_per_ct, else k0[l]
     const u64* kadd;
     int kadd_per_ct;
     u64 k_lo, k_hi;
     // image shape (mean filter), channels of the second operand (blend)
     int h, w, c, c_w;
+    // mean filter over a band of rows: output rows [y0, y0 + rows) of the h-row image, in0
+    // holding its rows from row0 on (0, h, 0 for the whole image)
+    int y0, rows, row0;
+    int* status;                    // device status word (bounded waits that give up)
     const u64* in0;
     const u64* in1;
     u64* out;
@@ -54,13 +64,18 @@ cudaError_t launch_addsub(const OpsArgs& a, bool subtract, cudaStream_t st);
 cudaError_t launch_ptadd(const OpsArgs& a, cudaStream_t st);
 cudaError_t launch_ptmul(const OpsArgs& a, cudaStream_t st);
 cudaError_t launch_rescale(const OpsArgs& a, cudaStream_t st);
-cudaError_t launch_meanfilter3(const OpsArgs& a, cudaStream_t st);
+// staged: the bulk-copy form (input columns staged in shared memory), else the register walk
+cudaError_t launch_meanfilter3(const OpsArgs& a, bool staged, int num_sms, cudaStream_t st);
 cudaError_t launch_blend(const OpsArgs& a, cudaStream_t st);
 cudaError_t launch_decrypt(const DecArgs& a, int threads, cudaStream_t st);
 
 // Ragged batches (SegTable items: ciphertexts, or mean-filter rows x chunks x polys x channels).
 // All segments share the level, the scale class and the constants of `a`.
-cudaError_t launch_meanfilter3_batch(const OpsArgs& a, const SegTable& t, LaunchShape ls, int num_sms, cudaStream_t st);
+cudaError_t launch_meanfilter3_batch(const OpsArgs& a, const SegTable& t, LaunchShape ls, bool staged, int num_sms,
+                                     cudaStream_t st);
+// Threads per block the batched mean filter runs with for a requested count (the staged form
+// halves it while its stages would not fit); items are counted with it.
+int mf_batch_threads(int limbs, int threads, bool staged);
 cudaError_t launch_blend_batch(const OpsArgs& a, const SegTable& t, LaunchShape ls, int num_sms, cudaStream_t st);
 cudaError_t launch_ptadd_batch(const OpsArgs& a, const SegTable& t, LaunchShape ls, int num_sms, cudaStream_t st);
 cudaError_t launch_decrypt_batch(const DecArgs& a, const SegTable& t, LaunchShape ls, int num_sms, cudaStream_t st);
@@ -84,9 +99,12 @@ struct SqDiffArgs {
     int n_blocks;
 };
 cudaError_t launch_sqdiff_accumulate(const SqDiffArgs& a, cudaStream_t st);
-// tensor[p][l][x] = sum over blocks j = l (mod limbs) of partial[j][p][x]
+// tensor[p][l][x] = (add ? tensor[p][l][x] mod q_l : 0) + sum over blocks j = l (mod limbs) of
+// partial[j][p][x], mod q_l
 cudaError_t launch_sqdiff_reduce(const RnsArgs& rns, int limbs, const u64* partial, int n_blocks, u64* tensor,
-                                 cudaStream_t st);
+                                 bool add, cudaStream_t st);
+// out[r][x] = in[r][x] mod q_{r % limbs}, rows of N words, any 64-bit input
+cudaError_t launch_reduce_rows(const RnsArgs& rns, int rows, int limbs, const u64* in, u64* out, cudaStream_t st);
 
 // Key switching of a degree-2 ciphertext (hybrid, one digit per ciphertext prime, one special
 // prime P).

@@ -72,7 +72,7 @@ class TuneEntry(ctypes.Structure):
                 ("ms", ctypes.c_float)]
 
 
-TUNE_RADIX, TUNE_LOOKUP, TUNE_MEANFILTER, TUNE_FUSED, TUNE_SCHEDULE, TUNE_DECRYPT = 1, 2, 3, 4, 5, 6
+TUNE_RADIX, TUNE_LOOKUP, TUNE_MEANFILTER, TUNE_FUSED, TUNE_SCHEDULE, TUNE_DECRYPT, TUNE_MF_STAGED = 1, 2, 3, 4, 5, 6, 7
 REQ_ENCRYPT, REQ_MEANFILTER, REQ_BRIGHTNESS, REQ_WATERMARK, REQ_MATCH = range(5)
 
 
@@ -118,6 +118,13 @@ _SIGS = {
     "ichee_decrypt_image": (_st, [_vp, _vp, ctypes.POINTER(CtImgMeta), _vp, _vp]),
     "ichee_decrypt_residues": (_st, [_vp, _vp, ctypes.POINTER(CtImgMeta), _vp, _vp, _vp]),
     "ichee_decrypt_image_async": (_st, [_vp, _vp, ctypes.POINTER(CtImgMeta), _vp, _vp]),
+    "ichee_encrypt_pixels": (_st, [_vp, _vp, _vp, _u64, _u64, _u64, _vp, _vp]),
+    "ichee_meanfilter_rows": (_st, [_vp, _vp, ctypes.POINTER(CtImgMeta), _u32, _u32, _u32, _u32, _vp,
+                                    ctypes.POINTER(CtImgMeta), _vp]),
+    "ichee_sqdiff_acc_words": (_st, [_vp, _u32, ctypes.POINTER(_sz)]),
+    "ichee_sqdiff_accumulate": (_st, [_vp, _vp, ctypes.POINTER(CtImgMeta), _vp, ctypes.POINTER(CtImgMeta), _vp,
+                                      ctypes.c_int, _vp]),
+    "ichee_sqdiff_finish": (_st, [_vp, _vp, ctypes.POINTER(CtImgMeta), _vp, ctypes.POINTER(CtImgMeta), _vp]),
     "ichee_sqdiff_sum_noalloc": (_st, [_vp, _vp, ctypes.POINTER(CtImgMeta), _vp, ctypes.POINTER(CtImgMeta), _vp,
                                        ctypes.POINTER(CtImgMeta), _vp]),
     "ichee_encrypt_batch": (_st, [_vp, _vp, ctypes.POINTER(_vp), ctypes.POINTER(ImageDesc), _u32,
@@ -313,6 +320,39 @@ def ichee_sqdiff_sum_noalloc(ctx, a, ma, b, mb, out, stream=None):
     m = CtImgMeta()
     _check(_lib.ichee_sqdiff_sum_noalloc(ctx, _ptr(a), ctypes.byref(ma), _ptr(b), ctypes.byref(mb), _ptr(out),
                                          ctypes.byref(m), stream))
+    return m
+
+
+def ichee_encrypt_pixels(ctx, cache, pixels, n, first_id, seed, out, stream=None):
+    """Ciphertexts first_id .. first_id + n - 1 of the whole-image encryption (see ichee.h)."""
+    _check(_lib.ichee_encrypt_pixels(ctx, cache, _ptr(pixels), n, first_id, seed, _ptr(out), stream))
+
+
+def ichee_meanfilter_rows(ctx, ct_rows, m_img, row0, n_rows, y0, y1, out, stream=None):
+    """Output rows [y0, y1) of the 3x3 mean filter of the image m_img describes, from its rows
+    [row0, row0 + n_rows) (see ichee.h)."""
+    m = CtImgMeta()
+    _check(_lib.ichee_meanfilter_rows(ctx, _ptr(ct_rows), ctypes.byref(m_img), row0, n_rows, y0, y1, _ptr(out),
+                                      ctypes.byref(m), stream))
+    return m
+
+
+def ichee_sqdiff_acc_words(ctx, level):
+    w = _sz()
+    _check(_lib.ichee_sqdiff_acc_words(ctx, level, ctypes.byref(w)))
+    return int(w.value)
+
+
+def ichee_sqdiff_accumulate(ctx, a, ma, b, mb, acc, accumulate=False, stream=None):
+    """acc (device, ichee_sqdiff_acc_words words) = or += the matching sum of the pairs (see ichee.h)."""
+    _check(_lib.ichee_sqdiff_accumulate(ctx, _ptr(a), ctypes.byref(ma), _ptr(b), ctypes.byref(mb), _ptr(acc),
+                                        1 if accumulate else 0, stream))
+
+
+def ichee_sqdiff_finish(ctx, acc, m_in, out, stream=None):
+    """Relinearise and rescale a matching accumulator (or a sum of up to 8) into one ciphertext."""
+    m = CtImgMeta()
+    _check(_lib.ichee_sqdiff_finish(ctx, _ptr(acc), ctypes.byref(m_in), _ptr(out), ctypes.byref(m), stream))
     return m
 
 
