@@ -71,11 +71,13 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["all", "enc8192", "ops128", "batch32", "serve"], default="all",
+    ap.add_argument("--workload", choices=["all", "enc8192", "ops128", "batch32", "serve", "shard"], default="all",
                     help="all (default): the headline step, then the other configurations as sub-records of the "
                          "same JSON line; enc8192: the headline step alone; ops128: image operations on the "
                          "128x128x3 four-prime image; batch32: ragged batch under a CUDA graph vs per-image "
-                         "launches; serve: Poisson request stream through the continuous-batching server")
+                         "launches; serve: Poisson request stream through the continuous-batching server; "
+                         "shard: the step with the image's rows sharded over the ranks (the form every N > 1 "
+                         "run takes)")
     ap.add_argument("--duration", type=float, default=None, help="serve: seconds of arrivals (default 60)")
     ap.add_argument("--op", choices=sorted(SINGLE_OPS), default=None,
                     help="time one operation of the enc8192 workload on its own (for kernel profiles)")
@@ -377,6 +379,187 @@ def run_ours(args):
                            ("serve", []))}
     if rank == 0:
         print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_sharded(args):
+    """The step of run_ours with one image sharded over the ranks (weak scaling: rank r holds
+    rows 64r .. 64r + 63 of a (64 x world) x 64 random-field image, the same per-GPU work as the
+    one-GPU step). Each rank encrypts its band five ways with ichee_encrypt_pixels (ciphertext
+    ids = whole-image pixel indices), runs the mean filter on its band with one halo row on each
+    side (encrypted by the rank itself), brightness and blend on its band, matching as its partial
+    sum + one int64 all-reduce (NCCL) + relinearisation on every rank, and decrypts its results.
+    Keys and caches come from the same seeds on every rank (the same bits a broadcast would give).
+    `value` = pixel ciphertexts encrypted per second by all ranks together (slowest rank's time)."""
+    import torch
+    from paper_2409_03568_gb300 import ichee, shard
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    wl = W.ENC8192
+    hbm_peak, peak_kind = measured_peaks()
+    ctx = ichee.Context(**W.ctx_kwargs(wl), device=local)
+    ctx.keygen(2024, with_evk=True)
+    h_img, w, c = 64 * world, wl["w"], wl["c"]
+    img = inputs.random_field_image(h_img, w, seed=wl["image_seed"], channels=c).reshape(-1)
+    wm = inputs.binary_pattern(h_img, w, seed=5).reshape(-1)
+    noisy = inputs.noisy_copy(img, seed=6)
+    beta = inputs.brightness_beta(4)
+    y0, y1 = shard.row_bands(h_img, world)[rank]
+    r0, r1 = shard.halo_rows(h_img, y0, y1)
+    row = w * c
+    n_band, n_halo = (y1 - y0) * row, (r1 - r0) * row
+    d_band = torch.from_numpy(img[y0 * row:y1 * row].copy()).cuda()
+    d_halo = torch.from_numpy(img[r0 * row:r1 * row].copy()).cuda()
+    caches = {
+        "radix16": ctx.build_cache(ichee.CACHE_RADIX, 11, radix_base=16, randomize=1),
+        "radix10": ctx.build_cache(ichee.CACHE_RADIX, 12, radix_base=10, randomize=1),
+        "freq32_pool64": ctx.build_cache(ichee.CACHE_FREQ, 13, top_k=32, pool_size=64,
+                                         scan=torch.from_numpy(img).cuda()),
+        "full256_pool64": ctx.build_cache(ichee.CACHE_FULL, 14, pool_size=64),
+    }
+    L, H, st = ctx.L, ctx.handle, ctx.stream()
+    ctw = ctx.ct_words(L - 1)
+    halo_ct = ctx.empty_cts(n_halo, L - 1)              # the fresh encryption, with the halo rows
+    band_fresh = halo_ct[(y0 - r0) * row * ctw:(y1 - r0) * row * ctw]
+    m_img = ichee.CtImgMeta(h_img, w, c, L - 1, float(1 << wl["log2_scale"]))
+    m_band = ichee.CtImgMeta(y1 - y0, w, c, L - 1, float(1 << wl["log2_scale"]))
+    wm_ct = ctx.empty_cts((y1 - y0) * w, L - 1)
+    ichee.ichee_encrypt_pixels(H, None, torch.from_numpy(wm[y0 * w:y1 * w].copy()).cuda(), (y1 - y0) * w, y0 * w, 21,
+                               wm_ct, st)
+    m_wm = ichee.CtImgMeta(y1 - y0, w, 1, L - 1, float(1 << wl["log2_scale"]))
+    nz_ct = ctx.empty_cts(n_band, L - 1)
+    ichee.ichee_encrypt_pixels(H, None, torch.from_numpy(noisy[y0 * row:y1 * row].copy()).cuda(), n_band, y0 * row, 22,
+                               nz_ct, st)
+    methods = ["fresh"] + list(caches)
+    enc_out = {m: ctx.empty_cts(n_band, L - 1) for m in caches}
+    enc_out["fresh"] = band_fresh
+    ops_out = {"meanfilter3": ctx.empty_cts(n_band, L - 2), "brightness": ctx.empty_cts(n_band, L - 1),
+               "blend": ctx.empty_cts(n_band, L - 2), "match": ctx.empty_cts(1, L - 2)}
+    acc = torch.empty(ichee.ichee_sqdiff_acc_words(H, L - 1), dtype=torch.int64, device="cuda")
+    dec_out = {k: torch.empty(1 if k == "match" else n_band, dtype=torch.float64, device="cuda")
+               for k in methods + list(ops_out)}
+    metas = {m: m_band for m in methods}
+
+    def p_encrypt(m):
+        def f():
+            if m == "fresh":
+                ichee.ichee_encrypt_pixels(H, None, d_halo, n_halo, r0 * row, 7, halo_ct, st)
+            else:
+                ichee.ichee_encrypt_pixels(H, caches[m], d_band, n_band, y0 * row, 7, enc_out[m], st)
+        return f
+
+    def p_meanfilter():
+        metas["meanfilter3"] = ichee.ichee_meanfilter_rows(H, halo_ct, m_img, r0, r1 - r0, y0, y1,
+                                                           ops_out["meanfilter3"], st)
+
+    def p_op(name, op, b=None, mb=None, op_args=()):
+        def f():
+            metas[name] = ichee.ichee_eval(H, op, band_fresh, m_band, b, mb, op_args, ops_out[name], st)
+        return f
+
+    def p_match():
+        metas["match"] = shard.sharded_match(ichee, ctx, band_fresh, m_band, nz_ct, m_band, acc, ops_out["match"],
+                                             stream=st)
+
+    def p_decrypt():
+        for k in methods:
+            ichee.ichee_decrypt_image(H, enc_out[k], metas[k], dec_out[k], st)
+        for k in ops_out:
+            ichee.ichee_decrypt_image(H, ops_out[k], metas[k], dec_out[k], st)
+
+    phases = [(m, p_encrypt(m)) for m in methods] + [
+        ("meanfilter3", p_meanfilter), ("brightness", p_op("brightness", ichee.OP_BRIGHTNESS, op_args=(beta,))),
+        ("blend", p_op("blend", ichee.OP_BLEND, wm_ct, m_wm, (0.9,))), ("match", p_match), ("decrypt", p_decrypt)]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        for _, fn in phases:
+            fn()
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    band_px = img[y0 * row:y1 * row]
+    for m in methods:
+        err = float(np.abs(dec_out[m].cpu().numpy() - band_px).max())
+        if err > 1e-3:
+            raise RuntimeError("rank %d: decode error %.3g for %s" % (rank, err, m))
+    plain = float(((img.astype(np.float64) - noisy) ** 2).sum())
+    match_err = abs(float(dec_out["match"].cpu().numpy()[0]) - plain)
+    if match_err > 1.0:
+        raise RuntimeError("rank %d: sharded matching decodes %.3g away from the plaintext distance" % (rank, match_err))
+    clocks = ClockSampler(local)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    total_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        ev0.record()
+        step()
+        ev1.record()
+        torch.cuda.synchronize()
+        total_ms += ev0.elapsed_time(ev1)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms, units_all = reduce_over_ranks(total_ms, len(methods) * n_band * args.steps)
+    # end to end: the same step with the band's pixels in pinned host memory (the library copies
+    # them in) and every decoded result written to pinned host memory; host wall clock
+    h_band = torch.from_numpy(band_px.copy()).pin_memory()
+    h_halo = torch.from_numpy(img[r0 * row:r1 * row].copy()).pin_memory()
+    h_out = {k: torch.empty(1 if k == "match" else n_band, dtype=torch.float64).pin_memory() for k in dec_out}
+
+    def step_host():
+        ichee.ichee_encrypt_pixels(H, None, h_halo, n_halo, r0 * row, 7, halo_ct, st)
+        for m in caches:
+            ichee.ichee_encrypt_pixels(H, caches[m], h_band, n_band, y0 * row, 7, enc_out[m], st)
+        for name, fn in phases[len(methods):-1]:
+            fn()
+        for k in methods:
+            ichee.ichee_decrypt_image_async(H, enc_out[k], metas[k], h_out[k], st)
+        for k in ops_out:
+            ichee.ichee_decrypt_image_async(H, ops_out[k], metas[k], h_out[k], st)
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step_host()
+    tot = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step_host()
+        tot += time.perf_counter() - t0
+    e2e_ms, e2e_units = reduce_over_ranks(tot * 1e3, len(methods) * n_band * args.steps)
+    e2e = {"value": round(e2e_units / (e2e_ms / 1e3), 1), "unit": UNIT,
+           "h2d_bytes_per_step": n_halo + len(caches) * n_band,
+           "d2h_bytes_per_step": (len(methods) + 3) * n_band * 8 + 8,
+           "timing": "host wall clock around each step, slowest rank"}
+    out = {
+        "metric": METRIC, "value": round(units_all / (total_ms / 1e3), 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64 (RNS residues mod 60/40/60-bit primes)",
+        "data": "synthetic (Gaussian random field %dx%d, correlation 6 px, seed 2; stands in for USC-SIPI)" % (h_img, w),
+        "config": {"workload": "enc_n8192_l3_64x64_per_gpu_sharded", "N": ctx.n, "primes_bits": wl["prime_bits"],
+                   "image": "%dx%dx%d" % (h_img, w, c), "band_rows_per_gpu": y1 - y0, "methods": methods,
+                   "ops": list(ops_out), "l2": "flushed (512 MB write) before every step",
+                   "parallelism": "pixel rows sharded over %d GPUs; matching all-reduce (int64, NCCL)" % world},
+        "gpu_launches": args.steps * (len(methods) + 1 + 3 + 10 + len(methods) + len(ops_out)),
+        "match_abs_error": match_err, "clocks": clk, "e2e": e2e}
+    if rank == 0:
+        print(json.dumps(out))
+    ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 
@@ -950,7 +1133,7 @@ def run_serve(args):
         if wait > 0:
             time.sleep(wait)
         if q["kind"] == ichee.REQ_MATCH and q["ring"] == 1 and q["h"] * q["w"] * q["c"] > 45000:
-            continue   # refused by the server's budget as well
+            continue   # one unbatched call would hold both images (over 110 GB); the server tiles it
         img, two, _ = bank[id(q)]
         ctx, cache = ctxs[q["ring"]], caches[q["ring"]]
         a, ma = ctx.encrypt(torch.from_numpy(img).cuda(), q["h"], q["w"], q["c"], q["seed"], cache=cache)
@@ -1076,6 +1259,8 @@ def main():
         run_batch(args)
     elif args.workload == "ops128":
         run_ops128(args)
+    elif args.workload == "shard" or dist_env()[1] > 1:
+        run_sharded(args)
     else:
         run_ours(args)
 

@@ -460,13 +460,16 @@ typedef struct ichee_server ichee_server;
  * device memory and 512 MiB of pinned host staging; at most max_inflight requests (0 = 256)
  * are admitted at once. While the server runs, its worker thread uses the ring contexts and
  * caches: the caller must not use them itself until ichee_server_destroy has returned.
+ * Requests whose buffers take more than 1/4 of the budget are served in row tiles, so a request
+ * is refused only if one image row (with its halo rows) does not fit the whole budget.
  * Errors: EINVAL, EMISMATCH, ENOMEM, ECUDA.
  */
 ichee_status ichee_server_create(ichee_ctx* const* rings, const ichee_cache* const* caches, uint32_t n_rings,
                                  size_t hbm_budget_bytes, uint32_t max_inflight, ichee_server** out);
 
 /* Queue a request (copied; its buffers must stay valid until done). *ticket identifies it.
- * Errors: EINVAL (bad request, larger than the budget), EUNSUPPORTED. Never blocks on the GPU. */
+ * Errors: EINVAL (bad request, or one row of it larger than the budget), EUNSUPPORTED. Never
+ * blocks on the GPU. */
 ichee_status ichee_server_submit(ichee_server* server, const ichee_request* request, uint64_t* ticket);
 
 /* Wait up to timeout_ms for a request; *out receives its timestamps and status. Returns
@@ -475,7 +478,10 @@ ichee_status ichee_server_submit(ichee_server* server, const ichee_request* requ
 ichee_status ichee_server_wait(ichee_server* server, uint64_t ticket, uint32_t timeout_ms, ichee_request_done* out);
 
 /* Counters: submitted, served, served pixels, admission rounds, peak concurrency, queue and
- * arena occupancy. */
+ * arena occupancy. A request larger than 1/4 of the budget is served as row tiles (pixel
+ * ranges, mean-filter bands with halo rows, matching accumulated tile by tile, results as of
+ * the whole request): pending counts requests none of whose tiles has been admitted,
+ * max_inflight and inflight count admitted pieces (tiles or whole requests). */
 ichee_status ichee_server_stats_get(ichee_server* server, ichee_server_stats* out);
 
 /* Pause (hold != 0) or resume admission. While held, submitted requests queue and nothing new

@@ -106,6 +106,7 @@ struct ichee_ctx {
     u64* d_pk = nullptr;         // [2][L][N]
     u64* d_pk_hat = nullptr;
     u64* d_pk_hat_p = nullptr;
+    ulonglong2* d_pk_pair = nullptr;   // (pk_hat, pk_hat_p) interleaved: the encryption kernel's operand
     u64* d_evk = nullptr;        // [L][2][L+1][N]
     u64* d_evk_hat = nullptr;
     u64* d_evk_hat_p = nullptr;

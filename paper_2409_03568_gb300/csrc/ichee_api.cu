@@ -267,7 +267,7 @@ extern "C" void ichee_ctx_destroy(ichee_ctx* c)
     if (!c) return;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
-    void* ptrs[] = {c->d_tables, c->d_dm, c->d_ninv, c->d_s, c->d_srev, c->d_pk, c->d_pk_hat, c->d_pk_hat_p,
+    void* ptrs[] = {c->d_tables, c->d_dm, c->d_ninv, c->d_s, c->d_srev, c->d_pk, c->d_pk_hat, c->d_pk_hat_p, c->d_pk_pair,
                     c->d_evk, c->d_evk_hat, c->d_evk_hat_p, c->d_status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -311,6 +311,7 @@ static cudaError_t alloc_key_buffers(ichee_ctx* c)
         if ((e = cudaMalloc(&c->d_pk, 2 * c->L * polyb)) != cudaSuccess) return e;
         if ((e = cudaMalloc(&c->d_pk_hat, 2 * c->L * polyb)) != cudaSuccess) return e;
         if ((e = cudaMalloc(&c->d_pk_hat_p, 2 * c->L * polyb)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&c->d_pk_pair, 4 * c->L * polyb)) != cudaSuccess) return e;
     }
     return e;
 }
@@ -368,6 +369,7 @@ extern "C" ichee_status ichee_keygen(ichee_ctx* c, uint64_t seed, uint32_t flags
     KCK(launch_ntt_fwd(rl, batch(c->d_pk_hat, 2 * L, L, id.data()), st));
     KCK(launch_scale_const(rl, batch(c->d_pk_hat, 2 * L, L, id.data()), c->d_ninv, st));
     KCK(launch_shoup_companions(rl, batch(c->d_pk_hat, 2 * L, L, id.data()), c->d_pk_hat_p, st));
+    KCK(launch_interleave(c->d_pk_hat, c->d_pk_hat_p, (u64)2 * L * c->n, c->d_pk_pair, st));
 
     // s on the host: export copy and the reversed-negated form used by decryption
     c->h_s.resize(n);
@@ -492,6 +494,7 @@ extern "C" ichee_status ichee_import_key(ichee_ctx* c, int which, const void* ho
         CK(launch_ntt_fwd(rl, batch(c->d_pk_hat, 2 * L, L, id.data()), st));
         CK(launch_scale_const(rl, batch(c->d_pk_hat, 2 * L, L, id.data()), c->d_ninv, st));
         CK(launch_shoup_companions(rl, batch(c->d_pk_hat, 2 * L, L, id.data()), c->d_pk_hat_p, st));
+        CK(launch_interleave(c->d_pk_hat, c->d_pk_hat_p, (u64)2 * L * c->n, c->d_pk_pair, st));
         CK(cudaStreamSynchronize(st));
         c->have_pk = true;
         return ICHEE_OK;
@@ -537,8 +540,7 @@ EncArgs ichee::enc_args(const ichee_ctx* c, const uint8_t* d_pix, u64 n_ct, u64 
     a.n_ct = n_ct;
     a.pixels = d_pix;
     a.dm = c->d_dm;
-    a.pk_hat = c->d_pk_hat;
-    a.pk_hat_p = c->d_pk_hat_p;
+    a.pk_pair = c->d_pk_pair;
     a.skip_lut = nullptr;
     a.seed = seed;
     a.id_base = id_base;

@@ -15,14 +15,16 @@ struct EncArgs {
     u64 n_ct;                  // ciphertexts
     const uint8_t* pixels;     // [n_ct] device
     const u64* dm;             // [L][256] (Delta * p) mod q_l
-    const u64* pk_hat;         // [2][L][N] NTT(pk_b) * N^{-1}, bit-reversed order
-    const u64* pk_hat_p;       // [2][L][N] Shoup companions
+    const ulonglong2* pk_pair; // [2][L][N] (NTT(pk_b) * N^{-1}, its Shoup companion), bit-reversed order
     const int32_t* skip_lut;   // optional [256]: skip pixel p when skip_lut[p] >= 0
     u64 seed;
     u64 id_base;               // ct id of ciphertext k is id_base + k
     CdtTable cdt;
     u64* out;                  // [n_ct][2][L][N]
 };
+
+// pair[i] = (a[i], b[i]) for i < n
+cudaError_t launch_interleave(const u64* a, const u64* b, u64 n, ulonglong2* pair, cudaStream_t st);
 
 // Radix-cached encryption: c = sum_k M[k][d'_k], M[k][d] = d * Enc(r^k) (Sec. 3.2, 3.3).
 struct RadixArgs {

@@ -217,6 +217,19 @@ __global__ void k_axpy_const(u64* out, const u64* x, const u64* y, u64 c, int n,
     if (i < n) out[i] = add_mod(x[i], mul_mod(c, y[i], q, m0, m1), q);
 }
 
+__global__ void k_interleave(const u64* a, const u64* b, u64 n, ulonglong2* pair)
+{
+    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x)
+        pair[i] = make_ulonglong2(a[i], b[i]);
+}
+
+cudaError_t launch_interleave(const u64* a, const u64* b, u64 n, ulonglong2* pair, cudaStream_t st)
+{
+    const u64 blocks = (n + 255) / 256;
+    k_interleave<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(a, b, n, pair);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_axpy_const(u64* out, const u64* x, const u64* y, u64 c, int n, u64 q, u64 m0, u64 m1,
                               cudaStream_t st)
 {
@@ -238,10 +251,13 @@ cudaError_t launch_axpy_const(u64* out, const u64* x, const u64* y, u64 c, int n
 // Shared memory of one encryption block: the transform buffer (N words), v, e0, e1 as int8
 // (3N bytes), then the search copy of the Gaussian table (32 words).
 template <int LOGN>
-__device__ __forceinline__ u64* enc_cdt_smem(u64* smem) { return smem + (1 << LOGN) + (3 << LOGN) / 8; }
+static constexpr int kEncBufs = 1;
 
 template <int LOGN>
-static constexpr size_t kEncSmem = ((sizeof(u64) + 3) << LOGN) + 32 * sizeof(u64);
+__device__ __forceinline__ u64* enc_cdt_smem(u64* smem) { return smem + kEncBufs<LOGN> * (1 << LOGN) + (3 << LOGN) / 8; }
+
+template <int LOGN>
+static constexpr size_t kEncSmem = ((sizeof(u64) * kEncBufs<LOGN> + 3) << LOGN) + 32 * sizeof(u64);
 
 template <int LOGN, bool KEEP_VHAT, int E>
 __device__ __forceinline__ void encrypt_ct(const EncArgs& a, int p, u64 seed, u64 id, u64* ct, u64* smem)
@@ -249,8 +265,8 @@ __device__ __forceinline__ void encrypt_ct(const EncArgs& a, int p, u64 seed, u6
     constexpr int N = 1 << LOGN;
     constexpr int T = NttShape<LOGN, E>::T;
     constexpr int LAST = NttShape<LOGN, E>::LAST;
-    u64* buf = smem;
-    int8_t* sv = reinterpret_cast<int8_t*>(smem + N);
+    constexpr int NB = kEncBufs<LOGN>;
+    int8_t* sv = reinterpret_cast<int8_t*>(smem + NB * N);
     int8_t* se0 = sv + N;
     int8_t* se1 = se0 + N;
     const u64* tcdt = enc_cdt_smem<LOGN>(smem);   // filled by the kernel before its first ciphertext
@@ -291,21 +307,20 @@ __device__ __forceinline__ void encrypt_ct(const EncArgs& a, int p, u64 seed, u6
 #pragma unroll
                 for (int e = 0; e < E; ++e) r[0][e] = small_mod(sv[x0 + elem_offset<LOGN, 0, E>(e)], q);
                 __syncthreads();
-                ntt_fwd_regs<LOGN, 1, true, false, E>(buf, r, tid, t, q);
+                ntt_fwd_regs<LOGN, 1, true, false, E>(smem, r, tid, t, q);
                 if constexpr (KEEP_VHAT) {
 #pragma unroll
                     for (int e = 0; e < E; ++e) vh[e] = r[0][e];
                 }
             }
-            const u64* pk = a.pk_hat + ((size_t)pb * L + l) * N + xl;
-            const u64* pkp = a.pk_hat_p + ((size_t)pb * L + l) * N + xl;
+            const ulonglong2* pk = a.pk_pair + ((size_t)pb * L + l) * N + xl;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                const int x = elem_offset<LOGN, LAST, E>(e);
-                r[0][e] = shoup_lazy(r[0][e], __ldg(pk + x), __ldg(pkp + x), q);
+                const ulonglong2 w = __ldg(pk + elem_offset<LOGN, LAST, E>(e));
+                r[0][e] = shoup_lazy(r[0][e], w.x, w.y, q);
             }
             __syncthreads();
-            ntt_inv_regs<LOGN, 1, false, E>(buf, r, tid, t, q);
+            ntt_inv_regs<LOGN, 1, false, E>(smem, r, tid, t, q);
             const int8_t* noise = (pb == 0 ? se0 : se1) + x0;
             u64* dst = ct + ((u64)pb * L + l) * N + x0;
 #pragma unroll

@@ -402,9 +402,13 @@ __global__ void __launch_bounds__(512) k_meanfilter3_staged_batch(const __grid_c
     }
 }
 
-// One block per (row y, coefficient chunk, poly, channel).
+// One block per (row y, coefficient chunk, poly, channel); registers bounded so that three
+// blocks (up to three limbs) or two share an SM.
 template <int LIMBS>
-__global__ void __launch_bounds__(256) k_meanfilter3(const __grid_constant__ OpsArgs a)
+static constexpr int kMfMinBlocks = LIMBS <= 3 ? 3 : 2;
+
+template <int LIMBS>
+__global__ void __launch_bounds__(256, kMfMinBlocks<LIMBS>) k_meanfilter3(const __grid_constant__ OpsArgs a)
 {
     const int chunks = ((1 << a.logn) / 2) / blockDim.x;
     u64 bid = blockIdx.x;

@@ -84,9 +84,31 @@ private:
     size_t size_ = 0, used_ = 0, peak_ = 0;
 };
 
+// A request too large for one piece of the arena, served as row bands ("tiles") that are
+// admitted one by one: pixel ranges encrypted with their whole-image ciphertext ids, the mean
+// filter of a band from its rows plus one halo row on each side, matching accumulated tile by
+// tile into one accumulator and relinearised once (ichee_encrypt_pixels, ichee_meanfilter_rows,
+// ichee_sqdiff_accumulate / ichee_sqdiff_finish): the same result as the one-piece request.
+struct Job {
+    ichee_request r;
+    uint64_t ticket = 0;
+    double t_submit = 0, t_admit = 0;
+    uint32_t n_tiles = 0, tiles_done = 0;
+    int32_t status = ICHEE_OK;
+    size_t off = 0, bytes = 0;       // arena block of the whole request (match: accumulator, result)
+    u64* acc = nullptr;              // matching accumulator
+    u64* fin = nullptr;              // matching result ciphertext
+    double* res = nullptr;           // matching decoded value
+    ichee_ctimg_meta m_img{};        // the encrypted image: whole shape, level, scale
+};
+
 struct Req {
     uint64_t ticket = 0;
     ichee_request r;
+    Job* job = nullptr;              // set for the tiles of a tiled request
+    uint32_t tile = 0;               // tile index, output rows [y0, y1), encrypted rows [r0, r1)
+    uint32_t y0 = 0, y1 = 0, r0 = 0, r1 = 0;
+    size_t job_off = 0;              // first tile: where the job's block starts inside its block
     double t_submit = 0, t_admit = 0, t_done = 0;
     // device block and its parts
     size_t off = 0, bytes = 0, hoff = 0, hbytes = 0;
@@ -132,6 +154,7 @@ struct ichee_server {
     std::vector<uint32_t> ring_rounds;   // rounds in flight per ring
     uint64_t next_ticket = 1;
     uint32_t inflight = 0;
+    size_t tile_bytes = 0;           // requests above this footprint are served in row tiles
     bool stop = false;
     bool hold = false;
     std::atomic<uint32_t> inject_launch_errors{0}, inject_query_errors{0};   // ichee_server_inject_failure
@@ -164,8 +187,79 @@ void sizes(const ichee_server* s, const ichee_request& r, size_t* dev, size_t* h
     *host = Arena::round(n_ct + n_b) + Arena::round(n_res * 8);
 }
 
+// Device and host bytes of one tile of request r: output rows [y0, y1), encrypted rows
+// [r0, r1) (the mean filter's band plus halo).
+void tile_sizes(const ichee_server* s, const ichee_request& r, uint32_t y0, uint32_t y1, uint32_t r0, uint32_t r1,
+                size_t* dev, size_t* host)
+{
+    const ichee_ctx* c = s->rings[r.ring];
+    const int L = c->L;
+    const u64 row = (u64)r.w * r.c;
+    const u64 n_in = (u64)(r1 - r0) * row, n_out = (u64)(y1 - y0) * row;
+    const u64 n_b = r.kind == ICHEE_REQ_WATERMARK ? (u64)(r1 - r0) * r.w : (r.kind == ICHEE_REQ_MATCH ? n_in : 0);
+    size_t d = Arena::round(n_in) + Arena::round(n_b) + Arena::round(n_in * ctb(c, L - 1)) +
+               Arena::round(n_b * ctb(c, L - 1));
+    if (r.kind == ICHEE_REQ_MEANFILTER || r.kind == ICHEE_REQ_WATERMARK) d += Arena::round(n_out * ctb(c, L - 2));
+    const u64 n_res = r.kind == ICHEE_REQ_MATCH ? 1 : n_out;
+    d += Arena::round(n_res * 8);
+    *dev = d;
+    *host = Arena::round(n_in + n_b) + Arena::round(n_res * 8);
+}
+
+// Arena bytes a tiled request holds from its first tile to its last (matching: accumulator,
+// result ciphertext and decoded value).
+size_t job_bytes(const ichee_server* s, const ichee_request& r)
+{
+    if (r.kind != ICHEE_REQ_MATCH) return 0;
+    const ichee_ctx* c = s->rings[r.ring];
+    return Arena::round((size_t)3 * c->L * c->n * 8) + Arena::round(ctb(c, c->L - 2)) + Arena::round(8);
+}
+
+// Encrypted rows of the tile with output rows [y0, y1).
+void tile_rows(const ichee_request& r, uint32_t y0, uint32_t y1, uint32_t* r0, uint32_t* r1)
+{
+    const bool halo = r.kind == ICHEE_REQ_MEANFILTER;
+    *r0 = halo && y0 > 0 ? y0 - 1 : y0;
+    *r1 = halo && y1 < r.h ? y1 + 1 : y1;
+}
+
+void carve_tile(ichee_server* s, Req* q)
+{
+    const ichee_ctx* c = s->rings[q->r.ring];
+    const ichee_request& r = q->r;
+    const int L = c->L;
+    const u64 row = (u64)r.w * r.c;
+    const u64 n_in = (u64)(q->r1 - q->r0) * row, n_out = (u64)(q->y1 - q->y0) * row;
+    const u64 n_b = r.kind == ICHEE_REQ_WATERMARK ? (u64)(q->r1 - q->r0) * r.w : (r.kind == ICHEE_REQ_MATCH ? n_in : 0);
+    uint8_t* p = reinterpret_cast<uint8_t*>(s->d_base) + q->off;
+    q->pix_a = p; p += Arena::round(n_in);
+    q->pix_b = n_b ? p : nullptr; p += Arena::round(n_b);
+    q->ct_a = reinterpret_cast<u64*>(p); p += Arena::round(n_in * ctb(c, L - 1));
+    q->ct_b = n_b ? reinterpret_cast<u64*>(p) : nullptr; p += Arena::round(n_b * ctb(c, L - 1));
+    q->ct_op = r.kind == ICHEE_REQ_BRIGHTNESS ? q->ct_a : nullptr;
+    if (r.kind == ICHEE_REQ_MEANFILTER || r.kind == ICHEE_REQ_WATERMARK) {
+        q->ct_op = reinterpret_cast<u64*>(p);
+        p += Arena::round(n_out * ctb(c, L - 2));
+    }
+    q->res = reinterpret_cast<double*>(p);
+    q->h_pix = s->h_base + q->hoff;
+    q->h_res = reinterpret_cast<double*>(s->h_base + q->hoff + Arena::round(n_in + n_b));
+    if (q->tile == 0 && q->job->bytes) {   // the job's block follows the first tile's
+        Job* j = q->job;
+        j->off = q->off + q->job_off;
+        uint8_t* jp = reinterpret_cast<uint8_t*>(s->d_base) + j->off;
+        j->acc = reinterpret_cast<u64*>(jp); jp += Arena::round((size_t)3 * c->L * c->n * 8);
+        j->fin = reinterpret_cast<u64*>(jp); jp += Arena::round(ctb(c, L - 2));
+        j->res = reinterpret_cast<double*>(jp);
+    }
+}
+
 void carve(ichee_server* s, Req* q)
 {
+    if (q->job) {
+        carve_tile(s, q);
+        return;
+    }
     const ichee_ctx* c = s->rings[q->r.ring];
     const ichee_request& r = q->r;
     const u64 n_ct = (u64)r.h * r.w * r.c;
@@ -189,12 +283,83 @@ void carve(ichee_server* s, Req* q)
     q->h_res = reinterpret_cast<double*>(s->h_base + q->hoff + Arena::round(n_ct + n_b));
 }
 
-// Launch one admission round for the requests of one ring on that ring's stream.
-ichee_status launch_round(ichee_server* s, uint32_t ring, const std::vector<Req*>& reqs, cudaStream_t st)
+// One tile of a tiled request, by the single-image entry points on the ring's stream.
+ichee_status launch_tile(ichee_server* s, ichee_ctx* c, const ichee_cache* k, Req* q, cudaStream_t st)
+{
+    const ichee_request& r = q->r;
+    Job* j = q->job;
+    const u64 row = (u64)r.w * r.c;
+    const u64 n_in = (u64)(q->r1 - q->r0) * row, n_out = (u64)(q->y1 - q->y0) * row;
+    const u64 n_b = q->pix_b ? (r.kind == ICHEE_REQ_WATERMARK ? (u64)(q->r1 - q->r0) * r.w : n_in) : 0;
+    const u64 b_first = r.kind == ICHEE_REQ_WATERMARK ? (u64)q->r0 * r.w : (u64)q->r0 * row;
+    std::memcpy(q->h_pix, r.pixels + (u64)q->r0 * row, n_in);
+    if (n_b) std::memcpy(q->h_pix + n_in, r.pixels2 + b_first, n_b);
+    CK(cudaMemcpyAsync(q->pix_a, q->h_pix, n_in, cudaMemcpyHostToDevice, st));
+    if (n_b) CK(cudaMemcpyAsync(q->pix_b, q->h_pix + n_in, n_b, cudaMemcpyHostToDevice, st));
+    ichee_status e = ichee_encrypt_pixels(c, k, q->pix_a, n_in, (u64)q->r0 * row, r.seed, q->ct_a, st);
+    if (e != ICHEE_OK) return e;
+    if (n_b) {
+        e = ichee_encrypt_pixels(c, k, q->pix_b, n_b, b_first, r.seed + 1, q->ct_b, st);
+        if (e != ICHEE_OK) return e;
+    }
+    ichee_ctimg_meta band = j->m_img;   // the encrypted rows as an image
+    band.h = q->r1 - q->r0;
+    const u64* out = q->ct_a;
+    ichee_ctimg_meta mo = band;
+    switch (r.kind) {
+    case ICHEE_REQ_MEANFILTER:
+        e = ichee_meanfilter_rows(c, q->ct_a, &j->m_img, q->r0, q->r1 - q->r0, q->y0, q->y1, q->ct_op, &mo, st);
+        out = q->ct_op;
+        break;
+    case ICHEE_REQ_BRIGHTNESS:
+        e = ichee_eval(c, ICHEE_OP_BRIGHTNESS, q->ct_a, &band, nullptr, nullptr, &r.arg, 1, q->ct_a, &mo, st);
+        break;
+    case ICHEE_REQ_WATERMARK: {
+        ichee_ctimg_meta mb = band;
+        mb.c = 1;
+        e = ichee_eval(c, ICHEE_OP_BLEND, q->ct_a, &band, q->ct_b, &mb, &r.arg, 1, q->ct_op, &mo, st);
+        out = q->ct_op;
+        break;
+    }
+    case ICHEE_REQ_MATCH:
+        e = ichee_sqdiff_accumulate(c, q->ct_a, &band, q->ct_b, &band, j->acc, q->tile > 0 ? 1 : 0, st);
+        if (e == ICHEE_OK && q->tile + 1 == j->n_tiles) {
+            e = ichee_sqdiff_finish(c, j->acc, &j->m_img, j->fin, &mo, st);
+            if (e == ICHEE_OK) e = ichee_decrypt_image(c, j->fin, &mo, j->res, st);
+            if (e == ICHEE_OK && r.ct_out) CK(cudaMemcpyAsync(r.ct_out, j->fin, ctb(c, (int)mo.level), cudaMemcpyDeviceToDevice, st));
+            if (e == ICHEE_OK) CK(cudaMemcpyAsync(q->h_res, j->res, 8, cudaMemcpyDeviceToHost, st));
+        }
+        return e;
+    default:
+        break;
+    }
+    if (e != ICHEE_OK) return e;
+    e = ichee_decrypt_image(c, out, &mo, q->res, st);
+    if (e != ICHEE_OK) return e;
+    if (r.ct_out)
+        CK(cudaMemcpyAsync(r.ct_out + (u64)q->y0 * row * ct_words(c, (int)mo.level + 1), out,
+                           n_out * ctb(c, (int)mo.level), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(q->h_res, q->res, n_out * 8, cudaMemcpyDeviceToHost, st));
+    return ICHEE_OK;
+}
+
+// Launch one admission round for the requests of one ring on that ring's stream: tiles one by
+// one, the other requests as batched kernels.
+ichee_status launch_round(ichee_server* s, uint32_t ring, const std::vector<Req*>& all, cudaStream_t st)
 {
     ichee::NvtxRange nvtx_range("ichee_server round");
     ichee_ctx* c = s->rings[ring];
     const ichee_cache* k = s->caches[ring];
+    std::vector<Req*> reqs;
+    for (Req* q : all) {
+        if (!q->job) {
+            reqs.push_back(q);
+            continue;
+        }
+        const ichee_status e = launch_tile(s, c, k, q, st);
+        if (e != ICHEE_OK) q->status = e;
+    }
+    if (reqs.empty()) return ICHEE_OK;
     // inputs to the device
     for (Req* q : reqs) {
         const u64 n_ct = (u64)q->r.h * q->r.w * q->r.c;
@@ -302,8 +467,50 @@ ichee_status launch_round(ichee_server* s, uint32_t ring, const std::vector<Req*
     return ICHEE_OK;
 }
 
+// A tile is done: its results go to the request's buffer, its memory back to the arena; the
+// last tile completes the request (and frees the request's own block).
+void complete_tile(ichee_server* s, Req* q)
+{
+    Job* j = q->job;
+    const ichee_request& r = q->r;
+    const bool last_index = q->tile + 1 == j->n_tiles;
+    if (q->status == ICHEE_OK) {
+        if (r.kind != ICHEE_REQ_MATCH)
+            std::memcpy(r.result + (u64)q->y0 * r.w * r.c, q->h_res, (u64)(q->y1 - q->y0) * r.w * r.c * 8);
+        else if (last_index)
+            std::memcpy(r.result, q->h_res, 8);
+    }
+    bool finished = false;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        if (q->status != ICHEE_OK && j->status == ICHEE_OK) j->status = q->status;
+        s->dev.release(q->off, q->tile == 0 && j->bytes ? q->job_off : q->bytes);
+        s->host.release(q->hoff, q->hbytes);
+        s->inflight--;
+        if (++j->tiles_done == j->n_tiles) {
+            finished = true;
+            if (j->bytes) s->dev.release(j->off, j->bytes);
+            s->stats.served++;
+            s->stats.pixels += (u64)r.h * r.w * r.c;
+            q->ticket = j->ticket;
+            q->t_submit = j->t_submit;
+            q->t_admit = j->t_admit;
+            q->t_done = now_s();
+            q->status = j->status;
+            s->done[q->ticket] = q;   // the request's record; freed with its job when collected
+            s->cv_done.notify_all();
+        }
+        s->cv_work.notify_all();
+    }
+    if (!finished) delete q;
+}
+
 void complete(ichee_server* s, Req* q)
 {
+    if (q->job) {
+        complete_tile(s, q);
+        return;
+    }
     const u64 n_res = q->r.kind == ICHEE_REQ_MATCH ? 1 : (u64)q->r.h * q->r.w * q->r.c;
     if (q->status == ICHEE_OK) std::memcpy(q->r.result, q->h_res, n_res * 8);
     q->t_done = now_s();
@@ -378,6 +585,7 @@ void worker_main(ichee_server* s)
         const double t = now_s();
         for (Req* q : admitted) {
             q->t_admit = t;
+            if (q->job && q->tile == 0) q->job->t_admit = t;
             q->round_size = (uint32_t)admitted.size();
             carve(s, q);
         }
@@ -437,6 +645,7 @@ extern "C" ichee_status ichee_server_create(ichee_ctx* const* rings, const ichee
     if (cudaMalloc(&s->d_base, hbm_budget_bytes) != cudaSuccess)
         return bail(fail(ICHEE_ENOMEM, "cannot reserve the %zu-byte HBM budget", hbm_budget_bytes));
     s->dev.reset(hbm_budget_bytes);
+    s->tile_bytes = hbm_budget_bytes / 4;
     const size_t host_bytes = 512ull << 20;
     if (cudaHostAlloc((void**)&s->h_base, host_bytes, cudaHostAllocDefault) != cudaSuccess)
         return bail(fail(ICHEE_ENOMEM, "pinned staging"));
@@ -448,6 +657,77 @@ extern "C" ichee_status ichee_server_create(ichee_ctx* const* rings, const ichee
     s->stats.arena_bytes = hbm_budget_bytes;
     s->worker = std::thread(worker_main, s);
     *out = s;
+    return ICHEE_OK;
+}
+
+// Queue a request as row tiles of at most the server's tile bytes (the first tile also holds
+// the request's own block). Refused if even a one-row tile does not fit the budget.
+static ichee_status submit_tiled(ichee_server* s, const ichee_request* r, uint64_t* ticket)
+{
+    const size_t jb = job_bytes(s, *r);
+    // bytes of a middle tile with `rows` output rows (the mean filter reads a halo row on each side)
+    auto cost = [&](uint32_t rows, size_t* dev, size_t* host) {
+        tile_sizes(s, *r, 0, rows, 0, rows + (r->kind == ICHEE_REQ_MEANFILTER ? 2 : 0), dev, host);
+        *dev += jb;
+    };
+    auto fits = [&](uint32_t rows) {
+        size_t dev, host;
+        cost(rows, &dev, &host);
+        return dev <= s->tile_bytes && host <= s->host.size() / 16;
+    };
+    uint32_t rows = 1;
+    if (!fits(1)) {   // one row is above the tile size: still served if it fits the whole budget
+        size_t dev, host;
+        cost(1, &dev, &host);
+        if (dev > s->dev.size() || host > s->host.size())
+            return fail(ICHEE_EINVAL, "request needs %zu bytes for one image row, more than the %zu-byte budget", dev,
+                        s->dev.size());
+    } else {
+        for (uint32_t step = 1u << 16; step > 0; step >>= 1)   // the largest row count that fits
+            if (rows + step <= r->h && fits(rows + step)) rows += step;
+    }
+    const uint32_t n_tiles = (r->h + rows - 1) / rows;
+    const ichee_ctx* c = s->rings[r->ring];
+    Job* j = new Job();
+    j->r = *r;
+    j->n_tiles = n_tiles;
+    j->bytes = jb;
+    j->m_img.h = r->h;
+    j->m_img.w = r->w;
+    j->m_img.c = r->c;
+    j->m_img.level = (uint32_t)(c->L - 1);
+    j->m_img.scale = c->delta;
+    std::vector<Req*> tiles;
+    for (uint32_t t = 0; t < n_tiles; ++t) {
+        Req* q = new Req();
+        q->r = *r;
+        q->job = j;
+        q->tile = t;
+        q->y0 = t * rows;
+        q->y1 = std::min<uint32_t>(r->h, (t + 1) * rows);
+        tile_rows(*r, q->y0, q->y1, &q->r0, &q->r1);
+        tile_sizes(s, *r, q->y0, q->y1, q->r0, q->r1, &q->bytes, &q->hbytes);
+        if (t == 0 && jb) {
+            q->job_off = q->bytes;
+            q->bytes += jb;
+        }
+        tiles.push_back(q);
+    }
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (s->stop) {
+        for (Req* q : tiles) delete q;
+        delete j;
+        return fail(ICHEE_EINVAL, "server is stopping");
+    }
+    j->ticket = s->next_ticket++;
+    j->t_submit = now_s();
+    for (Req* q : tiles) {
+        q->t_submit = j->t_submit;
+        s->pending.push_back(q);
+    }
+    s->stats.submitted++;
+    *ticket = j->ticket;
+    s->cv_work.notify_all();
     return ICHEE_OK;
 }
 
@@ -466,9 +746,7 @@ extern "C" ichee_status ichee_server_submit(ichee_server* s, const ichee_request
         return fail(ICHEE_EUNSUPPORTED, "ring too small for the mean filter");
     size_t dev_bytes = 0, host_bytes = 0;
     sizes(s, *r, &dev_bytes, &host_bytes);
-    if (dev_bytes > s->dev.size())
-        return fail(ICHEE_EINVAL, "request needs %zu bytes, more than the %zu-byte budget", dev_bytes, s->dev.size());
-    if (host_bytes > s->host.size()) return fail(ICHEE_EINVAL, "request needs %zu bytes of host staging", host_bytes);
+    if (dev_bytes > s->tile_bytes || host_bytes > s->host.size() / 16) return submit_tiled(s, r, ticket);
     Req* q = new Req();
     q->r = *r;
     q->bytes = dev_bytes;
@@ -503,6 +781,7 @@ extern "C" ichee_status ichee_server_wait(ichee_server* s, uint64_t ticket, uint
             out->t_done = q->t_done;
             out->round_size = q->round_size;
             s->done.erase(it);
+            delete q->job;
             delete q;
             return out->status == ICHEE_OK ? ICHEE_OK : fail((ichee_status)out->status, "request %llu failed",
                                                              (unsigned long long)ticket);
@@ -517,7 +796,9 @@ extern "C" ichee_status ichee_server_stats_get(ichee_server* s, ichee_server_sta
     if (!s || !out) return fail(ICHEE_EINVAL, "null argument");
     std::lock_guard<std::mutex> lock(s->mu);
     *out = s->stats;
-    out->pending = s->pending.size();
+    out->pending = 0;   // requests none of whose pieces has been admitted yet
+    for (const Req* q : s->pending)
+        if (!q->job || q->tile == 0) out->pending++;
     out->inflight = s->inflight;
     out->arena_used_bytes = s->dev.used();
     return ICHEE_OK;
@@ -553,8 +834,11 @@ extern "C" void ichee_server_destroy(ichee_server* s)
     cudaSetDevice(s->device);
     for (auto& st : s->streams)
         if (st) cudaStreamSynchronize(st), cudaStreamDestroy(st);
-    for (auto& kv : s->done) delete kv.second;
-    for (Req* q : s->pending) delete q;
+    for (auto& kv : s->done) {
+        delete kv.second->job;
+        delete kv.second;
+    }
+    for (Req* q : s->pending) delete q;   // (empty: the worker finishes every queued request)
     if (s->d_base) cudaFree(s->d_base);
     if (s->h_base) cudaFreeHost(s->h_base);
     delete s;

@@ -189,9 +189,12 @@ def oracle_request(ichee, o, cache, kind, h, w, c, seed, img, two, arg):
     return o.match(a, o.encrypt_lookup(two, cache, seed + 1), o.delta)
 
 
-def test_served_results_equal_the_oracle(ichee, rings):
+@pytest.mark.parametrize("budget", [256 << 20, 6 << 20], ids=["whole", "tiled"])
+def test_served_results_equal_the_oracle(ichee, rings, budget):
     """Every request kind on both rings, served together in one burst: each served ciphertext
-    equals the oracle's word for word and each decoded value its exact decode (rtol 1e-9)."""
+    equals the oracle's word for word and each decoded value its exact decode (rtol 1e-9). With
+    the small budget every request is served as row tiles (pixel ranges, mean-filter bands with
+    halo rows, matching accumulated tile by tile)."""
     ctxs, caches = rings
     keep, built, specs = [], [], []
     for ring in range(2):
@@ -200,7 +203,7 @@ def test_served_results_equal_the_oracle(ichee, rings):
             seed = 3000 + 31 * (5 * ring + kind)
             specs.append((kind, ring, h, w, c, seed))
             built.append(make_request(ichee, ctxs, kind, ring, h, w, c, seed, keep))
-    srv = ichee.ichee_server_create([x.handle for x in ctxs], caches, 256 << 20)
+    srv = ichee.ichee_server_create([x.handle for x in ctxs], caches, budget)
     ichee.ichee_server_hold(srv, True)
     tickets = [ichee.ichee_server_submit(srv, r) for (r, *_rest) in built]
     ichee.ichee_server_hold(srv, False)
@@ -211,6 +214,8 @@ def test_served_results_equal_the_oracle(ichee, rings):
         got = ct.cpu().numpy().view(np.uint64).reshape(want.shape)
         assert np.array_equal(got, want), (kind, ring)
         np.testing.assert_allclose(res, o.decrypt(want, scale), rtol=1e-9, atol=0)
+    st = ichee.ichee_server_stats_get(srv)
+    assert st["served"] == len(built) and st["arena_used_bytes"] == 0 and st["peak_arena_bytes"] <= budget
     ichee.ichee_server_destroy(srv)
 
 
