@@ -95,6 +95,8 @@ struct ichee_ctx {
     RnsArgs rns;                 // all moduli (q_0..q_{L-1}, then P), device tables
     CdtTable cdt;
     u64* d_tables = nullptr;     // [nmod][2][N][2]: (twiddle, Shoup companion), forward then inverse
+    u64* d_half_tw = nullptr;    // N = 2^14: [nmod][2][N/2][2] forward twiddles of the two half transforms
+    ichee::ModTables half_tab[2][kMaxModuli] = {};
     u64* d_dm = nullptr;         // [L][256]
     u64* d_ninv = nullptr;       // [nmod] N^{-1} mod modulus, then [nmod] N^{-1} 2^64 (d_ninv_r)
     u64* d_ninv_r = nullptr;     // inside d_ninv: not freed separately

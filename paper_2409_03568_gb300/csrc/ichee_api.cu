@@ -212,6 +212,27 @@ extern "C" ichee_status ichee_ctx_create(const ichee_params* p, int device, iche
         c->rns.tab[m].tw = reinterpret_cast<const ulonglong2*>(base);
         c->rns.tab[m].itw = reinterpret_cast<const ulonglong2*>(base + 2 * (size_t)c->n);
         ninv[m] = hm::invm((u64)c->n % qm, qm);
+        if (sqdiff_split(c->logn)) {   // twiddles of the two half transforms after the first stage
+            const size_t nh = (size_t)c->n / 2;
+            if (!c->d_half_tw && cudaMalloc(&c->d_half_tw, (size_t)c->nmod * 4 * nh * 8) != cudaSuccess)
+                return cleanup(fail(ICHEE_ENOMEM, "half tables"));
+            std::vector<u64> half(4 * nh, 0);
+            for (int h = 0; h < 2; ++h)
+                for (size_t k = 1; k < nh; ++k) {
+                    size_t s2 = 1;
+                    while (s2 * 2 <= k) s2 *= 2;
+                    const size_t src = (2 + h) * s2 + (k - s2);
+                    half[((size_t)h * nh + k) * 2] = t[src];
+                    half[((size_t)h * nh + k) * 2 + 1] = t[(size_t)c->n + src];
+                }
+            u64* hb = c->d_half_tw + (size_t)m * 4 * nh;
+            if (cudaMemcpy(hb, half.data(), half.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+                return cleanup(fail(ICHEE_ECUDA, "upload half tables"));
+            for (int h = 0; h < 2; ++h) {
+                c->half_tab[h][m].tw = reinterpret_cast<const ulonglong2*>(hb + (size_t)h * 2 * nh);
+                c->half_tab[h][m].itw = nullptr;
+            }
+        }
     }
     if (cudaMalloc(&c->d_ninv, 16 * (size_t)c->nmod) != cudaSuccess) return cleanup(fail(ICHEE_ENOMEM, "ninv"));
     for (int m = 0; m < c->nmod; ++m)   // N^{-1} 2^64: undoes a Montgomery product's 2^{-64} as well
@@ -267,7 +288,7 @@ extern "C" void ichee_ctx_destroy(ichee_ctx* c)
     if (!c) return;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
-    void* ptrs[] = {c->d_tables, c->d_dm, c->d_ninv, c->d_s, c->d_srev, c->d_pk, c->d_pk_hat, c->d_pk_hat_p, c->d_pk_pair,
+    void* ptrs[] = {c->d_tables, c->d_half_tw, c->d_dm, c->d_ninv, c->d_s, c->d_srev, c->d_pk, c->d_pk_hat, c->d_pk_hat_p, c->d_pk_pair,
                     c->d_evk, c->d_evk_hat, c->d_evk_hat_p, c->d_status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -1107,12 +1128,18 @@ extern "C" ichee_status ichee_meanfilter_rows(ichee_ctx* c, const uint64_t* d_in
 // entry point and the split form (ichee_sqdiff_accumulate / ichee_sqdiff_finish); they differ
 // only in where the working memory comes from.
 
-// Accumulating blocks of the first step: one per SM, rounded down to a multiple of the limbs.
+// Accumulating blocks of the first step: one per SM, rounded down to a multiple of the limbs
+// (of twice the limbs in the split form), and the scratch words of one block's slice.
+static int sqdiff_unit(const ichee_ctx* c, int limbs) { return sqdiff_split(c->logn) ? 2 * limbs : limbs; }
+
 static int sqdiff_blocks(const ichee_ctx* c, int limbs)
 {
-    const int nb = (c->num_sms / limbs) * limbs;
-    return nb < limbs ? limbs : nb;
+    const int u = sqdiff_unit(c, limbs);
+    const int nb = (c->num_sms / u) * u;
+    return nb < u ? u : nb;
 }
+
+static size_t sqdiff_slice_words(const ichee_ctx* c) { return (size_t)(sqdiff_split(c->logn) ? 2 : 4) * c->n; }
 
 // Words of the relinearisation working set: the tensor [3][limbs][N], the key-switching digits,
 // the accumulators over Q*P and the relinearised pair.
@@ -1139,6 +1166,8 @@ static ichee_status sqdiff_partial_sum(ichee_ctx* c, const uint64_t* d_a, const 
     sa.b = d_b;
     sa.partial = partial;
     sa.n_blocks = n_blocks;
+    for (int h = 0; h < 2; ++h)
+        for (int l = 0; l < limbs; ++l) sa.htab[h][l] = c->half_tab[h][l];
     CK(launch_sqdiff_accumulate(sa, st));
     CK(launch_sqdiff_reduce(sa.rns, limbs, partial, n_blocks, tensor, add, st));
     return ICHEE_OK;
@@ -1216,7 +1245,7 @@ static ichee_status op_sqdiff(ichee_ctx* c, const uint64_t* d_a, const ichee_cti
     if (ma->level == 0) return fail(ICHEE_ELEVEL, "matching needs a limb to drop");
     const int limbs = (int)ma->level + 1;
     const int n_blocks = sqdiff_blocks(c, limbs);
-    const size_t words = relin_words(c, limbs) + (size_t)n_blocks * 4 * c->n;
+    const size_t words = relin_words(c, limbs) + (size_t)n_blocks * sqdiff_slice_words(c);
     CK(c->scratch.ensure(words * 8, c->user_alloc, c->user_free, c->user_alloc_ctx, st));
     return sqdiff_in(c, d_a, ma, d_b, (u64*)c->scratch.p, n_blocks, d_out, mout, st);
 }
@@ -1261,7 +1290,8 @@ extern "C" ichee_status ichee_sqdiff_accumulate(ichee_ctx* c, const uint64_t* d_
     if (s != ICHEE_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     const int n_blocks = sqdiff_blocks(c, limbs);
-    CK(c->scratch.ensure((size_t)n_blocks * 4 * c->n * 8, c->user_alloc, c->user_free, c->user_alloc_ctx, st));
+    CK(c->scratch.ensure((size_t)n_blocks * sqdiff_slice_words(c) * 8, c->user_alloc, c->user_free, c->user_alloc_ctx,
+                         st));
     return sqdiff_partial_sum(c, d_a, ma, d_b, (u64*)c->scratch.p, n_blocks, d_acc, accumulate != 0, st);
 }
 
@@ -1499,17 +1529,18 @@ extern "C" ichee_status ichee_sqdiff_sum_noalloc(ichee_ctx* c, const uint64_t* d
     if (d_out == d_a || d_out == d_b) return fail(ICHEE_EINVAL, "this operation cannot run in place");
     const int limbs = (int)ma->level + 1;
     const size_t n = (size_t)c->n;
-    // fixed part (tensor and relinearisation working set), then one 4-row slice per
+    // fixed part (tensor and relinearisation working set), then one slice per
     // accumulating block, as many blocks as fit (a multiple of limbs)
     const size_t fixed_w = relin_words(c, limbs);
     const size_t cap_w = ICHEE_NOALLOC_SCRATCH_BYTES / 8;
-    const size_t slice_w = 4 * n;
+    const size_t slice_w = sqdiff_slice_words(c);
     const size_t fit = fixed_w < cap_w ? (cap_w - fixed_w) / slice_w : 0;
+    const int unit = sqdiff_unit(c, limbs);
     int n_blocks = sqdiff_blocks(c, limbs);
-    if ((size_t)n_blocks > fit) n_blocks = (int)((fit / limbs) * limbs);
-    if (n_blocks < limbs)
+    if ((size_t)n_blocks > fit) n_blocks = (int)((fit / unit) * unit);
+    if (n_blocks < unit)
         return fail(ICHEE_EINVAL, "matching at N=%zu with %d limbs needs %zu bytes of scratch; the allocation-free "
-                    "scratch holds %u bytes", n, limbs, (fixed_w + (size_t)limbs * slice_w) * 8,
+                    "scratch holds %u bytes", n, limbs, (fixed_w + (size_t)unit * slice_w) * 8,
                     (unsigned)ICHEE_NOALLOC_SCRATCH_BYTES);
     u64* base = nullptr;
     s = noalloc_scratch(c->device, &base);

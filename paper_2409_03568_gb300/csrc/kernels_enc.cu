@@ -248,10 +248,12 @@ cudaError_t launch_axpy_const(u64* out, const u64* x, const u64* y, u64 c, int n
 // ternary operand and needs no product.
 // ---------------------------------------------------------------------------------------
 
-// Shared memory of one encryption block: the transform buffer (N words), v, e0, e1 as int8
-// (3N bytes), then the search copy of the Gaussian table (32 words).
+// Shared memory of one encryption block: the transform buffers (N words each; two where both
+// inverse transforms of a limb run in lockstep: N = 2^13, 8 residues per thread), v, e0, e1 as
+// int8 (3N bytes),
+// then the search copy of the Gaussian table (32 words).
 template <int LOGN>
-static constexpr int kEncBufs = 1;
+static constexpr int kEncBufs = LOGN == 13 ? 2 : 1;
 
 template <int LOGN>
 __device__ __forceinline__ u64* enc_cdt_smem(u64* smem) { return smem + kEncBufs<LOGN> * (1 << LOGN) + (3 << LOGN) / 8; }
@@ -294,6 +296,44 @@ __device__ __forceinline__ void encrypt_ct(const EncArgs& a, int p, u64 seed, u6
 
     const int x0 = elem_index<LOGN, 0, E>(tid, 0);       // first-pass layout: x0 + elem_offset(e)
     const int xl = elem_index<LOGN, LAST, E>(tid, 0);    // last-pass layout
+    if constexpr (NB == 2 && KEEP_VHAT) {
+        // per limb: v^ = NTT(v), both products v^ . pk^_b at once, then the two inverse
+        // transforms in lockstep (one pass structure, barriers and twiddle loads shared)
+        for (int l = 0; l < L; ++l) {
+            const u64 q = a.rns.q[l];
+            const ModTables t = a.rns.tab[l];
+            u64 r[1][E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) r[0][e] = small_mod(sv[x0 + elem_offset<LOGN, 0, E>(e)], q);
+            __syncthreads();
+            ntt_fwd_regs<LOGN, 1, true, false, E>(smem, r, tid, t, q);
+            u64 rr[2][E];
+            const ulonglong2* pk0 = a.pk_pair + (size_t)l * N + xl;
+            const ulonglong2* pk1 = a.pk_pair + ((size_t)L + l) * N + xl;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const ulonglong2 w0 = __ldg(pk0 + elem_offset<LOGN, LAST, E>(e));
+                const ulonglong2 w1 = __ldg(pk1 + elem_offset<LOGN, LAST, E>(e));
+                rr[0][e] = shoup_lazy(r[0][e], w0.x, w0.y, q);
+                rr[1][e] = shoup_lazy(r[0][e], w1.x, w1.y, q);
+            }
+            __syncthreads();
+            ntt_inv_regs<LOGN, 2, false, E>(smem, rr, tid, t, q);
+#pragma unroll
+            for (int pb = 0; pb < 2; ++pb) {
+                const int8_t* noise = (pb == 0 ? se0 : se1) + x0;
+                u64* dst = ct + ((u64)pb * L + l) * N + x0;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int x = elem_offset<LOGN, 0, E>(e);
+                    u64 v = add_mod(csub(rr[pb][e], q), small_mod(noise[x], q), q);
+                    if (pb == 0 && x == 0 && x0 == 0) v = add_mod(v, a.dm[l * 256 + p], q);   // coefficient 0
+                    __stcs(dst + x, v);
+                }
+            }
+        }
+        return;
+    }
     for (int l = 0; l < L; ++l) {
         const u64 q = a.rns.q[l];
         const ModTables t = a.rns.tab[l];

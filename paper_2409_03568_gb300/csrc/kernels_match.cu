@@ -90,6 +90,88 @@ __global__ void __launch_bounds__(NttShape<LOGN, E>::T, 1) k_sqdiff_accumulate(c
     }
 }
 
+// N = 2^14, split: the first stage of the forward transform pairs x with x + N/2 and leaves two
+// independent 2^13-point transforms (outputs with the top index bit clear, and set). Block j
+// takes limb j % limbs and half h = (j / limbs) % 2: it loads both halves of d = a - b, applies
+// the first-stage butterfly for its half only (the product W d_hi is made by both halves'
+// blocks: 1/14 more products), and runs the other 13 stages with the 2^13-point code -- 8
+// residues per thread, 1024 threads, no spills -- and the half's twiddles:
+// tw_h[2^s + g] = tw[(2 + h) 2^s + g]. Its tensor terms go to a [4][N/2] slice. The two
+// blocks of a half pair read the same ciphertexts at about the same time (one HBM read, one
+// L2 hit).
+__global__ void __launch_bounds__(1024, 1) k_sqdiff_accumulate_split(const __grid_constant__ SqDiffArgs a)
+{
+    constexpr int LOGH = 13, NH = 1 << LOGH, N = 2 * NH, E = 8;
+    constexpr int LAST = NttShape<LOGH, E>::LAST;
+    extern __shared__ u64 buf[];
+    u64* d0buf = buf + NH;
+    const int tid = threadIdx.x;
+    const int limbs = a.limbs;
+    const int l = blockIdx.x % limbs;
+    const int h = (blockIdx.x / limbs) & 1;
+    const u64 stride = a.n_blocks / (2 * limbs);
+    const u64 start = blockIdx.x / (2 * limbs);
+    u64* acc = a.partial + (size_t)blockIdx.x * 4 * NH;
+    const u64 q = a.rns.q[l];
+    const u64 qinv = a.rns.qinv[l];
+    const ModTables t = a.htab[h][l];
+    const ulonglong2 w1 = a.rns.tab[l].tw[1];   // the first stage's twiddle and its companion
+#pragma unroll
+    for (int e = 0; e < E; e += 2) {
+        const int x = elem_index<LOGH, LAST, E>(tid, e);
+        *reinterpret_cast<ulonglong2*>(acc + x) = make_ulonglong2(0, 0);
+        *reinterpret_cast<ulonglong2*>(acc + NH + x) = make_ulonglong2(0, 0);
+        *reinterpret_cast<ulonglong2*>(acc + 2 * NH + x) = make_ulonglong2(0, 0);
+    }
+    for (u64 k = start; k < a.n_ct; k += stride) {
+        const u64* A = a.a + k * 2 * (u64)limbs * N;
+        const u64* B = a.b + k * 2 * (u64)limbs * N;
+#pragma unroll 1
+        for (int pb = 0; pb < 2; ++pb) {
+            const int x0 = elem_index<LOGH, 0, E>(tid, 0);
+            const u64* pa = A + ((u64)pb * limbs + l) * N + x0;
+            const u64* pbb = B + ((u64)pb * limbs + l) * N + x0;
+            u64 r[1][E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int x = elem_offset<LOGH, 0, E>(e);
+                const u64 lo = sub_mod(pa[x], pbb[x], q);
+                const u64 hi = sub_mod(pa[x + NH], pbb[x + NH], q);
+                const u64 tt = shoup_lazy(hi, w1.x, w1.y, q);   // [0, 2q)
+                r[0][e] = h ? lo + 2 * q - tt : lo + tt;         // [0, 3q)
+            }
+            __syncthreads();
+            ntt_fwd_regs<LOGH, 1, false, false, E>(buf, r, tid, t, q);
+            __syncthreads();
+            u64* dst = pb == 0 ? d0buf : buf;
+            const int sb = slot_base<LOGH, LAST, E>(tid);
+#pragma unroll
+            for (int e = 0; e < E; ++e) dst[slot_of<LOGH, LAST, E>(sb, e)] = csub(csub(r[0][e], 2 * q), q);
+        }
+#pragma unroll 1
+        for (int e = 0; e < E; e += 2) {
+            const int x = elem_index<LOGH, LAST, E>(tid, e);
+            ulonglong2* p0 = reinterpret_cast<ulonglong2*>(acc + x);
+            ulonglong2* p1 = reinterpret_cast<ulonglong2*>(acc + NH + x);
+            ulonglong2* p2 = reinterpret_cast<ulonglong2*>(acc + 2 * NH + x);
+            ulonglong2 s0 = *p0, s1 = *p1, s2 = *p2;
+            u64 tt[2][3];
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const u64 d1 = buf[swz<E>(x + hh)];
+                const u64 d0 = d0buf[swz<E>(x + hh)];
+                tt[hh][0] = mont_mul(d0, d0, q, qinv);   // every term carries 2^{-64}, undone after the INTT
+                const u64 c = mont_mul(d0, d1, q, qinv);
+                tt[hh][1] = add_mod(c, c, q);
+                tt[hh][2] = mont_mul(d1, d1, q, qinv);
+            }
+            *p0 = make_ulonglong2(add_mod(s0.x, tt[0][0], q), add_mod(s0.y, tt[1][0], q));
+            *p1 = make_ulonglong2(add_mod(s1.x, tt[0][1], q), add_mod(s1.y, tt[1][1], q));
+            *p2 = make_ulonglong2(add_mod(s2.x, tt[0][2], q), add_mod(s2.y, tt[1][2], q));
+        }
+    }
+}
+
 // Residues per thread: 8 at N = 2^13 (1024 threads), else 16.
 template <int LOGN>
 static constexpr int kSqE = LOGN == 13 ? 8 : 16;
@@ -110,6 +192,15 @@ static cudaError_t sqdiff_launch(const SqDiffArgs& a, cudaStream_t st)
 cudaError_t launch_sqdiff_accumulate(const SqDiffArgs& a, cudaStream_t st)
 {
     if (a.n_blocks <= 0 || a.n_blocks % a.limbs != 0) return cudaErrorInvalidValue;
+    if (sqdiff_split(a.rns.logn)) {
+        if (a.n_blocks % (2 * a.limbs) != 0) return cudaErrorInvalidValue;
+        const size_t smem = 2 * (sizeof(u64) << 13);
+        cudaError_t e = cudaFuncSetAttribute(k_sqdiff_accumulate_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        k_sqdiff_accumulate_split<<<a.n_blocks, NttShape<13, 8>::T, smem, st>>>(a);
+        return cudaGetLastError();
+    }
     switch (a.rns.logn) {
     case 10: return sqdiff_launch<10>(a, st);
     case 11: return sqdiff_launch<11>(a, st);
@@ -126,9 +217,13 @@ __global__ void k_sqdiff_reduce(RnsArgs rns, int limbs, const u64* partial, int 
     const int pl = blockIdx.y;                 // p * limbs + l
     const int p = pl / limbs, l = pl % limbs;
     const u64 q = rns.q[l];
+    const bool split = sqdiff_split(rns.logn);
+    const int row = split ? n / 2 : n;         // slice row length
+    const int step = split ? 2 * limbs : limbs;
     for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
         u64 s = add ? reduce64(tensor[(size_t)pl * n + x], q, rns.mu[l]) : 0;
-        for (int j = l; j < n_blocks; j += limbs) s = add_mod(s, partial[((size_t)j * 4 + p) * n + x], q);
+        const int h = split ? x / row : 0, xx = split ? x % row : x;
+        for (int j = l + h * limbs; j < n_blocks; j += step) s = add_mod(s, partial[((size_t)j * 4 + p) * row + xx], q);
         tensor[(size_t)pl * n + x] = s;
     }
 }

@@ -89,18 +89,23 @@ cudaError_t launch_radix_meanfilter3_batch(const RadixArgs& ra, const OpsArgs& a
                                            int num_sms, cudaStream_t st);
 
 // Matching: sum over ciphertexts of (a - b)^2 as a degree-2 ciphertext in the NTT domain.
+// At N = 2^14 the accumulation runs split: each polynomial as two 2^13-point halves after the
+// transform's first stage (sqdiff_split(logn)), block j taking limb j % limbs and half
+// (j / limbs) % 2, with twiddle tables per half (htab).
+__host__ __device__ inline bool sqdiff_split(int logn) { return logn == 14; }
 struct SqDiffArgs {
     RnsArgs rns;                   // moduli 0..limbs-1
     int limbs;
     u64 n_ct;
     const u64* a;
     const u64* b;
-    u64* partial;                  // [n_blocks][3][N] scratch: block j accumulates limb j % limbs
-    int n_blocks;
+    u64* partial;                  // [n_blocks][4][N] (split: [n_blocks][4][N/2]) scratch
+    int n_blocks;                  // a multiple of limbs (split: of 2 limbs)
+    ModTables htab[2][kMaxPrimes]; // split: twiddles of the two half transforms
 };
 cudaError_t launch_sqdiff_accumulate(const SqDiffArgs& a, cudaStream_t st);
-// tensor[p][l][x] = (add ? tensor[p][l][x] mod q_l : 0) + sum over blocks j = l (mod limbs) of
-// partial[j][p][x], mod q_l
+// tensor[p][l][x] = (add ? tensor[p][l][x] mod q_l : 0) + the sum over the blocks of limb l (and,
+// split, of the half holding x) of their partial terms, mod q_l
 cudaError_t launch_sqdiff_reduce(const RnsArgs& rns, int limbs, const u64* partial, int n_blocks, u64* tensor,
                                  bool add, cudaStream_t st);
 // out[r][x] = in[r][x] mod q_{r % limbs}, rows of N words, any 64-bit input
