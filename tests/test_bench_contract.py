@@ -55,3 +55,22 @@ def test_parity_on_sample_compares_word_for_word():
     flipped[int(idx[4]), 12345] ^= 1
     bad = bench.parity_on_sample(None, enc, ops, ref, n_check=9)
     assert not bad["bit_exact"] and bad["mismatched"] == ["radix10"]
+
+
+def test_serving_roofline_bytes():
+    """The serving record's algorithmic bytes: encryption written once, each operation's inputs
+    read and output written once (brightness in place), decryption reads half a ciphertext;
+    refused requests count nothing."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    wl = {"rings": ({"log_n": 10, "prime_bits": [60, 40, 60]},)}
+    n, L = 1024, 3
+    ct, ct1 = 2 * L * n * 8, 2 * (L - 1) * n * 8
+    reqs = [dict(kind=0, ring=0, h=2, w=3, c=1), dict(kind=1, ring=0, h=2, w=2, c=3),
+            dict(kind=2, ring=0, h=1, w=1, c=1), dict(kind=3, ring=0, h=2, w=2, c=3),
+            dict(kind=4, ring=0, h=1, w=2, c=1), dict(kind=0, ring=0, h=9, w=9, c=3)]
+    got = bench.serve_algorithmic_bytes(wl, reqs, [True] * 5 + [False])
+    want = (6 * ct + 6 * ct // 2) + (12 * ct + 12 * (ct + ct1) + 12 * ct1 // 2) + (ct + ct // 2) + \
+        ((12 + 4) * ct + 12 * (ct + ct1) + 4 * ct + 12 * ct1 // 2) + (4 * ct + 4 * ct)
+    assert got == want
