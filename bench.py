@@ -815,6 +815,8 @@ def run_ops128(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ms = {k: 0.0 for k in ev}
     total = 0.0
+    clocks = ClockSampler(0)
+    clocks.start()
     for i in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         e0.record()
@@ -831,6 +833,7 @@ def run_ops128(args):
             total += e0.elapsed_time(e1)
             for k in ev:
                 ms[k] += ev[k][0].elapsed_time(ev[k][1])
+    clk = clocks.stop()
     ms = {k: v / args.steps for k, v in ms.items()}
     step_ms = total / args.steps
     # correctness guard and quality against FP64 plaintext references of the operations
@@ -878,7 +881,7 @@ def run_ops128(args):
         "config": {"workload": wl["name"], "N": n, "primes_bits": wl["prime_bits"], "image": "%dx%dx%d" % (h, w, c),
                    "l2": "inputs (%.0f GB) far larger than L2" % ((2 * n_px + h * w) * ct_in / 1e9),
                    "peak_kind": peak_kind},
-        "ops": per_op}))
+        "ops": per_op, "clocks": clk}))
     ctx.close()
 
 

@@ -17,6 +17,8 @@ pytestmark = pytest.mark.gpu
 CASES = [
     dict(log_n=10, prime_bits=[60, 40, 40, 40], log2_scale=40, special_bits=61, shape=(5, 6, 3)),
     dict(log_n=13, prime_bits=[60, 40, 40, 40], log2_scale=40, special_bits=61, shape=(4, 4, 3)),
+    # N = 2^14: the accumulation runs as two half transforms per limb (its own scratch slices)
+    dict(log_n=14, prime_bits=[60, 40, 40, 40, 40], log2_scale=40, special_bits=61, shape=(3, 3, 1)),
 ]
 
 
