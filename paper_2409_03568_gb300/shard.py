@@ -44,11 +44,13 @@ def allreduce_accumulator(acc, group=None):
     """Add the ranks' matching accumulators in place (int64 words; at most 8 ranks)."""
     import torch
     import torch.distributed as dist
+    if acc.dtype != torch.int64:
+        raise TypeError("accumulators are int64 words")
+    if not (dist.is_available() and dist.is_initialized()):
+        return acc   # one process: nothing to add
     world = dist.get_world_size(group)
     if world > MAX_RANKS:
         raise ValueError("accumulator sums are exact for at most %d ranks, not %d" % (MAX_RANKS, world))
-    if acc.dtype != torch.int64:
-        raise TypeError("accumulators are int64 words")
     dist.all_reduce(acc, op=dist.ReduceOp.SUM, group=group)
     return acc
 

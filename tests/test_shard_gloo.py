@@ -94,3 +94,10 @@ def test_allreduce_of_partial_matching_sums_is_exact():
         assert equal is True, (rank, decodes)
         assert decodes is True
         assert rows >= 3
+
+
+def test_allreduce_without_a_process_group_is_the_identity():
+    acc = torch.arange(6, dtype=torch.int64)
+    assert torch.equal(shard.allreduce_accumulator(acc.clone()), acc)
+    with pytest.raises(TypeError):
+        shard.allreduce_accumulator(acc.to(torch.int32))
