@@ -1183,15 +1183,16 @@ def run_serve(args):
 
 
 SINGLE_OPS = ("fresh", "radix16", "full256_pool64", "meanfilter3", "brightness", "blend", "match", "sqdiff_image",
-              "decrypt", "radix16_meanfilter3_fused", "radix16_meanfilter3_two_kernels")
+              "decrypt", "radix16_meanfilter3_fused", "radix16_meanfilter3_two_kernels", "match_n16384")
 
 
 def run_single_op(args):
-    """One operation of the 64x64, N = 8192 workload, launched warmup + steps times (L2 flushed
+    """One operation of the 64x64, N = 8192 workload (match_n16384: matching on a 64x64 image at
+    N = 16384 with five primes, the serving ring), launched warmup + steps times (L2 flushed
     before each launch, CUDA events on the library's stream). Prints its mean time."""
     import torch
     from paper_2409_03568_gb300 import ichee
-    wl = W.ENC8192
+    wl = W.ENC8192 if args.op != "match_n16384" else dict(W.RING16384, h=64, w=64, c=1, image_seed=2)
     ctx = ichee.Context(**W.ctx_kwargs(wl))
     ctx.keygen(2024, with_evk=True)
     h, w, c = wl["h"], wl["w"], wl["c"]
@@ -1199,7 +1200,7 @@ def run_single_op(args):
     d_img = torch.from_numpy(img).cuda()
     a, ma = ctx.encrypt(d_img, h, w, c, 7)
     b = mb = wm = mw = None   # second operands only where the operation takes one
-    if args.op in ("match", "sqdiff_image"):
+    if args.op in ("match", "sqdiff_image", "match_n16384"):
         b, mb = ctx.encrypt(torch.from_numpy(inputs.noisy_copy(img, seed=6)).cuda(), h, w, c, 22)
     if args.op == "blend":
         wm, mw = ctx.encrypt(torch.from_numpy(inputs.binary_pattern(h, w, seed=5).reshape(-1)).cuda(), h, w, 1, 21)
@@ -1214,10 +1215,11 @@ def run_single_op(args):
         cache = ctx.build_cache(ichee.CACHE_FULL, 14, pool_size=64)
     enc = ctx.empty_cts(h * w * c, L - 1) if args.op in ("fresh", "radix16", "full256_pool64", "brightness") or pipeline \
         else None
-    out = ctx.empty_cts(h * w * c if args.op != "match" else 1, L - 2)
+    out = ctx.empty_cts(h * w * c if not args.op.startswith("match") else 1, L - 2)
     dec = torch.empty(h * w * c, dtype=torch.float64, device="cuda")
     ops = {"meanfilter3": (ichee.OP_MEANFILTER3, None, None, ()), "brightness": (ichee.OP_BRIGHTNESS, None, None, (7.5,)),
            "blend": (ichee.OP_BLEND, wm, mw, (0.9,)), "match": (ichee.OP_SQDIFF_SUM, b, mb, ()),
+           "match_n16384": (ichee.OP_SQDIFF_SUM, b, mb, ()),
            "sqdiff_image": (ichee.OP_SQDIFF, b, mb, ())}
 
     def once():
