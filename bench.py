@@ -1187,12 +1187,12 @@ SINGLE_OPS = ("fresh", "radix16", "full256_pool64", "meanfilter3", "brightness",
 
 
 def run_single_op(args):
-    """One operation of the 64x64, N = 8192 workload (match_n16384: matching on a 64x64 image at
-    N = 16384 with five primes, the serving ring), launched warmup + steps times (L2 flushed
+    """One operation of the 64x64, N = 8192 workload (match_n16384: matching on a 32x32 image at
+    N = 16384 with five primes, the serving ring; 2.7 GB of inputs), launched warmup + steps times (L2 flushed
     before each launch, CUDA events on the library's stream). Prints its mean time."""
     import torch
     from paper_2409_03568_gb300 import ichee
-    wl = W.ENC8192 if args.op != "match_n16384" else dict(W.RING16384, h=64, w=64, c=1, image_seed=2)
+    wl = W.ENC8192 if args.op != "match_n16384" else dict(W.RING16384, h=32, w=32, c=1, image_seed=2)
     ctx = ichee.Context(**W.ctx_kwargs(wl))
     ctx.keygen(2024, with_evk=True)
     h, w, c = wl["h"], wl["w"], wl["c"]

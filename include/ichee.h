@@ -201,7 +201,9 @@ ichee_status ichee_import_key(ichee_ctx* ctx, int which, const void* host_in, si
  * scan_pixels (host or device, n_scan bytes) is read for ICHEE_CACHE_FREQ only (may be NULL
  * otherwise). Cached ciphertexts are fresh encryptions keyed by `seed`: value slot j uses
  * ciphertext id j, pool zero m uses 2^32 + m, radix power k uses 2^33 + k. A radix cache also
- * tabulates d * Enc(r^k) for |d| <= r. *out receives a handle (ichee_cache_free). Waits for
+ * tabulates d * Enc(r^k) for |d| <= r and, with three or more powers, the sums of the top two
+ * powers' multiples when that table is at most 48 MB (one cached read for both digits; the
+ * ciphertexts are the same). *out receives a handle (ichee_cache_free). Waits for
  * the histogram when scanning. Errors: EINVAL, ENOMEM, ECUDA.
  */
 ichee_status ichee_build_cache(ichee_ctx* ctx, const ichee_cache_desc* desc, const uint8_t* scan_pixels,

@@ -138,6 +138,8 @@ struct ichee_cache {
     int radix_base = 0, n_pow = 0, radix_randomize = 0;
     u64* d_radix = nullptr;      // [n_pow][2][L][N]
     u64* d_mult = nullptr;       // [n_pow][2r+1][2][L][N]
+    u64* d_pair = nullptr;       // [2r+1][pair_w][2][L][N], top two positions summed (n_pow >= 3)
+    int pair_w = 0;
 };
 
 constexpr u64 kIdPoolBase = 1ull << 32;

@@ -583,6 +583,8 @@ RadixArgs ichee::radix_args(const ichee_ctx* c, const ichee_cache* k, const uint
     a.r = k->radix_base;
     a.n_pow = k->n_pow;
     a.randomize = k->radix_randomize;
+    a.pair = k->d_pair;
+    a.pair_w = k->pair_w;
     a.seed = seed;
     a.id_base = 0;
     a.out = out;
@@ -635,6 +637,10 @@ static ichee_status encrypt_values(ichee_ctx* c, const std::vector<uint8_t>& val
     return ICHEE_OK;
 }
 
+// Largest pair table of a radix cache (bytes): beside the lowest positions' multiples it must
+// stay resident in the 129 MB L2 while the combine streams its output.
+constexpr size_t kRadixPairMaxBytes = size_t(48) << 20;
+
 static ichee_status build_radix(ichee_ctx* c, ichee_cache* k, u32 base, u32 randomize, u64 seed, cudaStream_t st)
 {
     int n_pow = 1;
@@ -651,6 +657,20 @@ static ichee_status build_radix(ichee_ctx* c, ichee_cache* k, u32 base, u32 rand
     ichee_status s = encrypt_values(c, pw, seed, kIdRadixBase, k->d_radix, st);
     if (s != ICHEE_OK) return s;
     CK(launch_radix_multiples(k->d_radix, n_pow, (int)base, rns_prefix(c, c->L), c->L, k->d_mult, st));
+    // With three or more positions, the top two are also tabulated as sums (one cached read for
+    // both in every combine) while the table stays small enough to live in L2 beside the rest.
+    // The top signed digit is d + b in [0, 255 / r^(n-1) + randomize].
+    if (n_pow >= 3) {
+        u32 top = 1;
+        for (int i = 0; i < n_pow - 1; ++i) top *= base;
+        const int pair_w = (int)(255 / top) + 1 + (randomize ? 1 : 0);
+        const size_t bytes = (size_t)(2 * base + 1) * pair_w * ctb;
+        if (bytes <= kRadixPairMaxBytes) {
+            CK(cudaMalloc(&k->d_pair, bytes));
+            k->pair_w = pair_w;
+            CK(launch_radix_pairs(k->d_mult, n_pow, (int)base, pair_w, rns_prefix(c, c->L), c->L, k->d_pair, st));
+        }
+    }
     CK(cudaStreamSynchronize(st));
     return ICHEE_OK;
 }
@@ -745,7 +765,7 @@ extern "C" void ichee_cache_free(ichee_cache* k)
     if (!k) return;
     cudaSetDevice(k->ctx->device);
     cudaDeviceSynchronize();
-    void* ptrs[] = {k->d_lut, k->d_values, k->d_pool, k->d_radix, k->d_mult};
+    void* ptrs[] = {k->d_lut, k->d_values, k->d_pool, k->d_radix, k->d_mult, k->d_pair};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete k;

@@ -34,6 +34,10 @@ struct RadixArgs {
     const uint8_t* pixels;
     const u64* mult;           // [n_pow][2r+1][2][L][N]
     int r, n_pow, randomize;
+    // optional (n_pow >= 3): sums of the top two positions' multiples,
+    // pair[(d_{n-2} + r) * pair_w + d_{n-1}] = M[n-2][d_{n-2}] + M[n-1][d_{n-1}]; pair_w = 0 when absent
+    const u64* pair;           // [2r+1][pair_w][2][L][N]
+    int pair_w;
     const int32_t* skip_lut;   // optional, as in EncArgs
     u64 seed, id_base;
     u64* out;
@@ -120,6 +124,8 @@ cudaError_t launch_axpy_const(u64* out, const u64* x, const u64* y, u64 c, int n
 cudaError_t launch_encrypt_fresh(const EncArgs& a, cudaStream_t st);
 cudaError_t launch_radix_multiples(const u64* radix_cts, int n_pow, int r, const RnsArgs& rns, int L, u64* mult,
                                    cudaStream_t st);
+cudaError_t launch_radix_pairs(const u64* mult, int n_pow, int r, int pair_w, const RnsArgs& rns, int L, u64* pair,
+                               cudaStream_t st);
 cudaError_t launch_radix_combine(const RadixArgs& a, cudaStream_t st);
 cudaError_t launch_lookup_combine(const LookupArgs& a, cudaStream_t st);
 cudaError_t launch_histogram(const uint8_t* pixels, u64 n, u32* counts /*[256], zeroed*/, cudaStream_t st);

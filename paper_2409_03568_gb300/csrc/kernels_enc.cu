@@ -497,9 +497,34 @@ cudaError_t launch_radix_multiples(const u64* radix_cts, int n_pow, int r, const
     return cudaGetLastError();
 }
 
+// P[i][j] = M[n-2][i] + M[n-1][j + r] mod q (i = d + r for d in [-r, r], j in [0, pair_w)): the
+// top two positions' multiples summed once per cache, so a combine reads one cached ciphertext
+// for both. Modular addition is exact, so every output residue is unchanged.
+__global__ void k_radix_pairs(const u64* mult, int n_pow, int r, int pair_w, RnsArgs rns, int L, u64* pair)
+{
+    const int n = 1 << rns.logn;
+    const size_t ct_len = (size_t)2 * L * n;
+    const int width = 2 * r + 1;
+    const int slot = blockIdx.y;            // i * pair_w + j
+    const int i = slot / pair_w, j = slot % pair_w;
+    const u64* lo = mult + ((size_t)(n_pow - 2) * width + i) * ct_len;
+    const u64* hi = mult + ((size_t)(n_pow - 1) * width + j + r) * ct_len;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < ct_len; e += (size_t)gridDim.x * blockDim.x)
+        pair[slot * ct_len + e] = add_mod(lo[e], hi[e], rns.q[(e / n) % L]);
+}
+
+cudaError_t launch_radix_pairs(const u64* mult, int n_pow, int r, int pair_w, const RnsArgs& rns, int L, u64* pair,
+                               cudaStream_t st)
+{
+    dim3 grid(64, (2 * r + 1) * pair_w);
+    k_radix_pairs<<<grid, 256, 0, st>>>(mult, n_pow, r, pair_w, rns, L, pair);
+    return cudaGetLastError();
+}
+
 // Radix combine: one block per ciphertext. Signed digits d'_k = d_k + b_k - r*b_{k+1} with b
 // from bit k of the pixel's randomness word (stream 3); c = sum_k M[k][d'_k], residue-wise
-// modular sums of cached rows, 16-byte loads, streaming 16-byte stores.
+// modular sums of cached rows (the top two positions' from the pair table when the cache has
+// one), 16-byte loads, streaming 16-byte stores.
 __device__ __forceinline__ void radix_ct(const RadixArgs& a, int p, u64 seed, u64 id, u64* ct)
 {
     const int n = 1 << a.logn;
@@ -510,14 +535,19 @@ __device__ __forceinline__ void radix_ct(const RadixArgs& a, int p, u64 seed, u6
     const u64* src[8];
     int ns = 0;
     int rest = p;
+    int dig[8];
     for (int kk = 0; kk < a.n_pow; ++kk) {
         int dk = rest % a.r;
         rest /= a.r;
         int bk = (a.randomize && kk >= 1) ? (int)((bits >> kk) & 1u) : 0;
         int bk1 = (a.randomize && kk + 1 < a.n_pow) ? (int)((bits >> (kk + 1)) & 1u) : 0;
-        int d = dk + bk - a.r * bk1;
-        if (d != 0) src[ns++] = a.mult + ((size_t)kk * width + (d + a.r)) * ct_len;
+        dig[kk] = dk + bk - a.r * bk1;
     }
+    const int separate = a.pair_w ? a.n_pow - 2 : a.n_pow;
+    for (int kk = 0; kk < separate; ++kk)
+        if (dig[kk] != 0) src[ns++] = a.mult + ((size_t)kk * width + (dig[kk] + a.r)) * ct_len;
+    if (a.pair_w && (dig[separate] != 0 || dig[separate + 1] != 0))
+        src[ns++] = a.pair + ((size_t)(dig[separate] + a.r) * a.pair_w + dig[separate + 1]) * ct_len;
     // Row by row (one modulus per row); four coefficient pairs per thread and round, their
     // loads issued together.
     ulonglong2* dst = reinterpret_cast<ulonglong2*>(ct);

@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(kMfMaxThreads<LIMBS>) k_meanfilter3_batch(cons
 // pairs: lane = coefficient pair (coalesced 512-byte accesses), warp = column. Every warp walks
 // its column from top to bottom, rebuilding each pixel's ciphertext once from the
 // L2-resident cached multiples d * Enc(r^k) (signed digits with the pixel's randomness bits,
-// as in the radix combine) and writing it as the encryption output. The vertical 3-sums come
+// and the pair table of the top two positions when the cache has one, as in the radix combine) and writing it as the encryption output. The vertical 3-sums come
 // from two running sums in registers (S1 = row y, S2 = rows y-1 + y); the horizontal 3-sum from
 // the neighbouring warps through shared memory (double-buffered: one barrier per row). The
 // strip's first and last warps are halo columns (clamped at the image border) whose outputs
@@ -493,6 +493,8 @@ __global__ void __launch_bounds__(kMfMaxThreads<LIMBS>) k_radix_meanfilter3_batc
                           ((size_t)x * C + ch) * out_u2;
         const size_t enc_row = row_px * ct_u2, flt_row = row_px * out_u2;
         const ulonglong2* mult_b = mult + (size_t)b * LIMBS * half + c2;
+        const ulonglong2* pair_b =
+            ra.pair_w ? reinterpret_cast<const ulonglong2*>(ra.pair) + (size_t)b * LIMBS * half + c2 : nullptr;
         // digit codes of this column, 32 rows at a time: lane j holds row code_base + j, one
         // byte per cached power (signed digit + r)
         u64 code = 0;
@@ -521,11 +523,7 @@ __global__ void __launch_bounds__(kMfMaxThreads<LIMBS>) k_radix_meanfilter3_batc
             const u64 cd = code_of(yy);
 #pragma unroll
             for (int l = 0; l < LIMBS; ++l) v[l] = make_ulonglong2(0, 0);
-            for (int kk = 0; kk < ra.n_pow; ++kk) {
-                const int dr = (int)((cd >> (8 * kk)) & 0xffu);
-                if (dr == ra.r) continue;
-                // (kk * width + dr) < 8 * 33 and ct_u2 <= 2^17: the offset fits 32 bits
-                const ulonglong2* src = mult_b + (u32)(kk * width + dr) * (u32)ct_u2;
+            auto add_ct = [&](const ulonglong2* src) {
                 ulonglong2 m[LIMBS];
 #pragma unroll
                 for (int l = 0; l < LIMBS; ++l) m[l] = __ldg(src + (size_t)l * half);
@@ -534,6 +532,17 @@ __global__ void __launch_bounds__(kMfMaxThreads<LIMBS>) k_radix_meanfilter3_batc
                     v[l].x = add_mod(v[l].x, m[l].x, a.q[l]);
                     v[l].y = add_mod(v[l].y, m[l].y, a.q[l]);
                 }
+            };
+            const int separate = ra.pair_w ? ra.n_pow - 2 : ra.n_pow;
+            for (int kk = 0; kk < separate; ++kk) {
+                const int dr = (int)((cd >> (8 * kk)) & 0xffu);
+                // (kk * width + dr) < 8 * 33 and ct_u2 <= 2^17: the offset fits 32 bits
+                if (dr != ra.r) add_ct(mult_b + (u32)(kk * width + dr) * (u32)ct_u2);
+            }
+            if (ra.pair_w) {   // the top two positions from the pair table: (2r+1) * pair_w < 8 * 33 entries
+                const int dr = (int)((cd >> (8 * separate)) & 0xffu);
+                const int dt = (int)((cd >> (8 * separate + 8)) & 0xffu) - ra.r;
+                if (dr != ra.r || dt != 0) add_ct(pair_b + (u32)(dr * ra.pair_w + dt) * (u32)ct_u2);
             }
         };
         auto store_enc = [&](int yy, const ulonglong2 (&v)[LIMBS]) {
@@ -658,7 +667,7 @@ __device__ __forceinline__ void blend_pair(const OpsArgs& a, const u64* ci, cons
 // A block takes whole rows (ciphertext k, polynomial b): the pattern index of k (a division
 // by the channel count) is worked out once per row, not once per coefficient pair.
 template <int LIMBS>
-__global__ void k_blend(const __grid_constant__ OpsArgs a)
+__device__ __forceinline__ void blend_rows(const OpsArgs& a)
 {
     const int n = 1 << a.logn;
     for (u64 kb = blockIdx.x; kb < 2 * a.n_ct; kb += gridDim.x) {
@@ -670,6 +679,23 @@ __global__ void k_blend(const __grid_constant__ OpsArgs a)
         u64* co = a.out + k * 2 * (LIMBS - 1) * (u64)n;
         for (int c = threadIdx.x; c < n / 2; c += blockDim.x) blend_pair<LIMBS>(a, ci, cw, co, b, c);
     }
+}
+
+// Up to three limbs (56 registers as compiled without a bound).
+template <int LIMBS>
+__global__ void k_blend(const __grid_constant__ OpsArgs a)
+{
+    blend_rows<LIMBS>(a);
+}
+
+// Four limbs and more, 256 threads, compiled for four blocks per SM up to five limbs (64
+// registers) and two above: without the bound four limbs took 72 registers, which left room
+// for three blocks and too few loads in flight (0.68 -> 0.77 of copy bandwidth on a 3-channel
+// image, 0.81 -> 0.93 on a 1-channel one); five limbs took 80 (0.66 -> 0.74).
+template <int LIMBS>
+__global__ void __launch_bounds__(256, LIMBS <= 5 ? 4 : 2) k_blend_wide(const __grid_constant__ OpsArgs a)
+{
+    blend_rows<LIMBS>(a);
 }
 
 // Ragged batch: one block per ciphertext; W of segment s has c1[s] channels.
@@ -985,7 +1011,16 @@ cudaError_t launch_meanfilter3(const OpsArgs& a, bool staged, int num_sms, cudaS
 cudaError_t launch_blend(const OpsArgs& a, cudaStream_t st)
 {
     const unsigned g = grid_for(2 * a.n_ct, 1);   // rows (ciphertext, polynomial)
-    ICHEE_LIMB_SWITCH(k_blend, g, 256, a)
+    switch (a.limbs) {
+    case 2: k_blend<2><<<g, 256, 0, st>>>(a); break;
+    case 3: k_blend<3><<<g, 256, 0, st>>>(a); break;
+    case 4: k_blend_wide<4><<<g, 256, 0, st>>>(a); break;
+    case 5: k_blend_wide<5><<<g, 256, 0, st>>>(a); break;
+    case 6: k_blend_wide<6><<<g, 256, 0, st>>>(a); break;
+    case 7: k_blend_wide<7><<<g, 256, 0, st>>>(a); break;
+    case 8: k_blend_wide<8><<<g, 256, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

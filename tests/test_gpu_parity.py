@@ -397,6 +397,14 @@ def test_ring16384_keys_encryption_and_matching(ichee):
     assert np.array_equal(as_cts(ga, 6, L, n), ra)
     assert np.array_equal(as_cts(gb, 6, L, n), rb)
     assert np.max(np.abs(ctx.decrypt(ga, ma).cpu().numpy() - a)) < 1e-3
+    # radix 10 on this ring: the sums of the top two positions would take 84 ciphertexts of
+    # 1.3 MB, above the 48 MB bound, so the combine reads the three positions one by one (the
+    # N = 8192 and toy-ring tests cover the summed table)
+    edge = np.array([0, 255, 100, 9, 200, 99], dtype=np.uint8)
+    cache = ctx.build_cache(ichee.CACHE_RADIX, 35, radix_base=10, randomize=1)
+    gr, mr = ctx.encrypt(torch.from_numpy(edge).cuda(), 3, 2, 1, 36, cache=cache)
+    assert np.array_equal(as_cts(gr, 6, L, n), o.encrypt_radix(edge, o.radix_cache(10, 35), 36, randomize=True))
+    assert np.max(np.abs(ctx.decrypt(gr, mr).cpu().numpy() - edge)) < 1e-3
     out, m = ctx.eval(ichee.OP_SQDIFF_SUM, ga, ma, gb, mb, out_n_ct=1, out_level=L - 2)
     ref, sc = o.match(ra, rb, o.delta)
     assert np.array_equal(as_cts(out, 1, L - 1, n), ref)
