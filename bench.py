@@ -582,10 +582,12 @@ def extras_ours(args, ctx, ichee, a, ma, b, mb, flush, alu_peak):
         e1.record()
     torch.cuda.synchronize()
     ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / len(ev)
-    # transforms: 2L forward (d) + L inverse (t2) + (L+1) x (L forward digits + 2 inverse);
-    # pointwise: tensor 3LN, key-switch MAC 2L(L+1)N, P t folding 2LN, mod-down and rescale 4LN
-    n_tr = L * L + 6 * L + 2
-    modmul = n_tr * (n // 2) * logn + 3 * L * n + 2 * L * (L + 1) * n + 2 * L * n + 4 * L * n
+    # transforms: 2L forward (d) + L inverse (t2) + L^2 forward digits (each digit into the
+    # other L - 1 moduli and P; into its own modulus its transform is the tensor's d1^2) +
+    # 2(L+1) inverse accumulators; pointwise: tensor with N^{-1} and the d1^2 form 4LN,
+    # key-switch MAC 2L(L+1)N, P t folding 2LN, mod-down and rescale 4LN
+    n_tr = L * L + 5 * L + 2
+    modmul = n_tr * (n // 2) * logn + 4 * L * n + 2 * L * (L + 1) * n + 2 * L * n + 4 * L * n
     ach = n_px * modmul / (ms / 1e3) / 1e9
     return {"sqdiff_image": {"ms": round(ms, 4), "px_per_s": round(n_px / (ms / 1e3), 1), "transforms_per_px": n_tr,
                              "bound": "alu", "achieved": round(ach, 1), "peak": round(alu_peak, 1),

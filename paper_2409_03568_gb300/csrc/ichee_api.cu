@@ -1372,6 +1372,8 @@ static ichee_status op_sqdiff_image(ichee_ctx* c, const uint64_t* d_a, const ich
         a.ninv_p[j] = hm::shoup_of(a.ninv[j], qj);
         a.pn[j] = hm::mulm(c->P % qj, a.ninv[j], qj);
         a.pn_p[j] = hm::shoup_of(a.pn[j], qj);
+        a.r64[j] = r64;
+        a.r64_p[j] = hm::shoup_of(r64, qj);
         a.p_inv[j] = hm::invm(c->P % qj, qj);
         a.p_inv_p[j] = hm::shoup_of(a.p_inv[j], qj);
         const u64 r = c->P % qj;

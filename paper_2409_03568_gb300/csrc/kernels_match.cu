@@ -258,14 +258,16 @@ cudaError_t launch_reduce_rows(const RnsArgs& rns, int rows, int limbs, const u6
 // with centered rounding). A persistent block takes one pixel at a time and runs the whole chain on it:
 //   1. per limb l: d^ = NTT(a - b) for both polynomials; t0^ = d0^2, t1^ = 2 d0 d1 stay in the
 //      NTT domain; t2 = INTT(d1^2) (N^{-1} folded into the product). The squares are
-//      Montgomery products, so each carries 2^{-64}; the constants below carry 2^64;
-//   2. per modulus m (P first, then q_t, then q_0..q_{t-1}): acc_b = sum_j NTT([t2]_j lifted
-//      to m) * evk^_j[b][m]; for m != P the term P t_b is added as (P N^{-1} 2^64) t_b^ before the
-//      inverse transform, so INTT(acc_b) = P t_b + key-switched part and
-//      (INTT(acc_b) - [acc_b mod P]) P^{-1} is the relinearised limb m;
+//      Montgomery products, so each carries 2^{-64}; the constants below carry 2^64. Digit l
+//      of t2 lifted to its own modulus q_l is t2_l itself, whose transform d1^2 is at hand, so
+//      the accumulators of modulus q_l start here: acc_b = (P N^{-1} 2^64) t_b^ + d1^2 evk^_l[b][l];
+//   2. per modulus m (P first, then q_t, then q_0..q_{t-1}): acc_b += NTT([t2]_j lifted to m) *
+//      evk^_j[b][m] for every digit j != m (all j for P), so INTT(acc_b) = P t_b + key-switched
+//      part and (INTT(acc_b) - [acc_b mod P]) P^{-1} is the relinearised limb m;
 //   3. the relinearised limb q_t is kept; every other limb is rescaled against it and stored.
-// That is L^2 + 6L + 2 transforms per pixel (t2 is the only tensor limb inverse-transformed),
-// all in the compact pass form so the chain fits the instruction cache.
+// That is L^2 + 5L + 2 transforms per pixel (t2 is the only tensor limb inverse-transformed,
+// and no digit is transformed back into its own modulus), all in the compact pass form so the
+// chain fits the instruction cache.
 // Every intermediate word is produced and consumed by the same thread (the transforms move
 // data between threads only through their own shared buffer), so the block's scratch
 // ([3 limbs + 2][N] words: t0^, t1^, t2 per limb, then the two P accumulators) is stored
@@ -317,14 +319,23 @@ __global__ void __launch_bounds__(NttShape<LOGN, E>::T) k_sqdiff_image(const __g
 #pragma unroll
                 for (int e = 0; e < E; ++e) dst[e * T] = csub(csub(r[0][e], 2 * q), q);
             }
-            const u64 qinv = a.rns.qinv[l];   // Montgomery products: 2^64 is folded into ninv and pn
+            const u64 qinv = a.rns.qinv[l];   // Montgomery products: 2^64 is folded into ninv, pn and r64
+            const u64* e0 = a.evk_hat + (((size_t)l * 2 + 0) * (L + 1) + l) * N;
+            const u64* e0p = a.evk_hat_p + (((size_t)l * 2 + 0) * (L + 1) + l) * N;
+            const u64* e1 = a.evk_hat + (((size_t)l * 2 + 1) * (L + 1) + l) * N;
+            const u64* e1p = a.evk_hat_p + (((size_t)l * 2 + 1) * (L + 1) + l) * N;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
+                const int x = elem_index<LOGN, LAST, E>(tid, e);
                 const u64 d0 = t0[e * T], d1 = t2[e * T];
-                t0[e * T] = mont_mul(d0, d0, q, qinv);
+                const u64 m2 = mont_mul(d1, d1, q, qinv);
+                const u64 th = shoup(m2, a.r64[l], a.r64_p[l], q);   // d1^2, the transform of digit l
                 const u64 c = mont_mul(d0, d1, q, qinv);
-                t1[e * T] = add_mod(c, c, q);
-                r[0][e] = shoup(mont_mul(d1, d1, q, qinv), a.ninv[l], a.ninv_p[l], q);
+                t0[e * T] = add_mod(shoup(mont_mul(d0, d0, q, qinv), a.pn[l], a.pn_p[l], q),
+                                    shoup(th, __ldg(e0 + x), __ldg(e0p + x), q), q);
+                t1[e * T] = add_mod(shoup(add_mod(c, c, q), a.pn[l], a.pn_p[l], q),
+                                    shoup(th, __ldg(e1 + x), __ldg(e1p + x), q), q);
+                r[0][e] = shoup(m2, a.ninv[l], a.ninv_p[l], q);
             }
             __syncthreads();
             ntt_inv_regs<LOGN, 1, true, E>(sm, r, tid, a.rns.tab[l], q);
@@ -336,10 +347,11 @@ __global__ void __launch_bounds__(NttShape<LOGN, E>::T) k_sqdiff_image(const __g
             const int m = step == 0 ? -1 : (step == 1 ? t : step - 2);   // -1: the special prime
             const int mod = m < 0 ? L : m;
             const u64 q = a.rns.q[mod], mu = a.rns.mu[mod];
-            u64* acc0 = m < 0 ? AP : T0 + (size_t)m * N;    // t0^ on entry, then the accumulator
+            u64* acc0 = m < 0 ? AP : T0 + (size_t)m * N;    // started in step 1 (m != P)
             u64* acc1 = m < 0 ? AP + N : T1 + (size_t)m * N;
 #pragma unroll 1
             for (int j = 0; j < limbs; ++j) {
+                if (j == m) continue;   // digit m's term went in with t_b^ in step 1
                 const u64 qj = a.rns.q[j];
                 const u64 half = (qj - 1) / 2;
                 const u64* t2 = T2 + (size_t)j * N;
@@ -365,15 +377,10 @@ __global__ void __launch_bounds__(NttShape<LOGN, E>::T) k_sqdiff_image(const __g
                     const u64 d = csub(csub(r[0][e], 2 * q), q);
                     const u64 p0 = shoup(d, __ldg(e0 + x), __ldg(e0p + x), q);
                     const u64 p1 = shoup(d, __ldg(e1 + x), __ldg(e1p + x), q);
-                    u64 s0, s1;
-                    if (j > 0) {
+                    u64 s0 = 0, s1 = 0;   // the P accumulators start at digit 0
+                    if (m >= 0 || j > 0) {
                         s0 = acc0[e * T];
                         s1 = acc1[e * T];
-                    } else if (m >= 0) {
-                        s0 = shoup(acc0[e * T], a.pn[m], a.pn_p[m], q);
-                        s1 = shoup(acc1[e * T], a.pn[m], a.pn_p[m], q);
-                    } else {
-                        s0 = s1 = 0;
                     }
                     acc0[e * T] = add_mod(s0, p0, q);
                     acc1[e * T] = add_mod(s1, p1, q);

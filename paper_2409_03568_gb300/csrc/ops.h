@@ -138,6 +138,7 @@ struct SqImgArgs {
     const u64* evk_hat_p;
     u64 ninv[kMaxPrimes], ninv_p[kMaxPrimes];    // N^{-1} 2^64 mod q_j (Shoup; 2^64 undoes the tensor's Montgomery factor)
     u64 pn[kMaxPrimes], pn_p[kMaxPrimes];        // P N^{-1} 2^64 mod q_j (Shoup)
+    u64 r64[kMaxPrimes], r64_p[kMaxPrimes];      // 2^64 mod q_j (Shoup): d1^2 out of the Montgomery form
     u64 p_inv[kMaxPrimes], p_inv_p[kMaxPrimes];  // P^{-1} mod q_j (Shoup)
     u64 neg_p_mod[kMaxPrimes];                   // (-P) mod q_j
     u64 qt_inv[kMaxPrimes], qt_inv_p[kMaxPrimes], half_qt;  // rescale by q_t, t = limbs - 1
