@@ -615,6 +615,16 @@ __device__ __forceinline__ void blend_pair(const OpsArgs& a, const u64* ci, cons
     const ulonglong2* s1 = reinterpret_cast<const ulonglong2*>(cw + (u64)b * LIMBS * n) + c;
     const u64 qt = a.q[t];
     const ulonglong2 ut = __ldcs(s0 + t * (n / 2)), wt = __ldg(s1 + t * (n / 2));
+    // every limb's loads are issued before the first store: the compiler may not move a load
+    // past a store that could alias it, and loads issued limb by limb between the stores left
+    // too few bytes in flight (three limbs, 128x128x3: 0.77 -> 0.85 of copy bandwidth; four
+    // limbs 0.76 -> 0.83; five limbs 0.73 -> 0.84)
+    ulonglong2 uj[LIMBS - 1], vj[LIMBS - 1];
+#pragma unroll
+    for (int j = 0; j < LIMBS - 1; ++j) {
+        uj[j] = __ldcs(s0 + j * (n / 2));
+        vj[j] = __ldg(s1 + j * (n / 2));
+    }
     if (a.k01_same) {
         // With Ka, Kb one integer each below every modulus, Ka I_t + Kb W_t = u q_t + m (m
         // centered) and limb j of the result is Ka q_t^{-1}(I_j - I_t) + Kb q_t^{-1}(W_j - W_t) + u:
@@ -632,7 +642,7 @@ __device__ __forceinline__ void blend_pair(const OpsArgs& a, const u64* ci, cons
 #pragma unroll
         for (int j = 0; j < LIMBS - 1; ++j) {
             const u64 qj = a.q[j];
-            const ulonglong2 u = __ldcs(s0 + j * (n / 2)), v = __ldg(s1 + j * (n / 2));
+            const ulonglong2 u = uj[j], v = vj[j];
             auto limb = [&](u64 ij, u64 wj, u64 it, u64 wtt, u64 uu) -> u64 {
                 uu = uu >= qj ? uu - qj : uu;
                 u64 r = shoup_lazy(ij + a.mq[j] - it, a.k0r[j], a.k0rp[j], qj) +
@@ -654,7 +664,7 @@ __device__ __forceinline__ void blend_pair(const OpsArgs& a, const u64* ci, cons
 #pragma unroll
     for (int j = 0; j < LIMBS - 1; ++j) {
         const u64 qj = a.q[j];
-        const ulonglong2 u = __ldcs(s0 + j * (n / 2)), v = __ldg(s1 + j * (n / 2));
+        const ulonglong2 u = uj[j], v = vj[j];
         const u64 px = csub(shoup_lazy(u.x, a.k0r[j], a.k0rp[j], qj) + shoup_lazy(v.x, a.k1r[j], a.k1rp[j], qj), 2 * qj);
         const u64 py = csub(shoup_lazy(u.y, a.k0r[j], a.k0rp[j], qj) + shoup_lazy(v.y, a.k1r[j], a.k1rp[j], qj), 2 * qj);
         ulonglong2 o;
@@ -688,20 +698,21 @@ __global__ void k_blend(const __grid_constant__ OpsArgs a)
     blend_rows<LIMBS>(a);
 }
 
-// Four limbs and more, 256 threads, compiled for four blocks per SM up to five limbs (64
-// registers) and two above: without the bound four limbs took 72 registers, which left room
-// for three blocks and too few loads in flight (0.68 -> 0.77 of copy bandwidth on a 3-channel
-// image, 0.81 -> 0.93 on a 1-channel one); five limbs took 80 (0.66 -> 0.74).
+// Four limbs and more, 256 threads, compiled for three blocks per SM up to five limbs (80
+// registers: the loads of every limb held at once, no spills at four limbs) and two above.
 template <int LIMBS>
-__global__ void __launch_bounds__(256, LIMBS <= 5 ? 4 : 2) k_blend_wide(const __grid_constant__ OpsArgs a)
+__global__ void __launch_bounds__(256, LIMBS <= 5 ? 3 : 2) k_blend_wide(const __grid_constant__ OpsArgs a)
 {
     blend_rows<LIMBS>(a);
 }
 
-// Ragged batch: one block per ciphertext; W of segment s has c1[s] channels.
+// Ragged batch: one block of kBlendBatchThreads per ciphertext; W of segment s has c1[s]
+// channels. Compiled for three blocks per SM up to five limbs, as the single-image kernel.
+constexpr int kBlendBatchThreads = 256;
+
 template <int LIMBS>
-__global__ void __launch_bounds__(1024) k_blend_batch(const __grid_constant__ OpsArgs a,
-                                                      const __grid_constant__ SegTable t)
+__global__ void __launch_bounds__(kBlendBatchThreads, LIMBS <= 5 ? 3 : 2)
+    k_blend_batch(const __grid_constant__ OpsArgs a, const __grid_constant__ SegTable t)
 {
     const int n = 1 << a.logn;
     const u64 total = t.start[t.n];
@@ -1109,7 +1120,7 @@ cudaError_t launch_blend_batch(const OpsArgs& a, const SegTable& t, LaunchShape 
     const u64 total = t.n > 0 ? t.start[t.n] : 0;
     if (total == 0) return cudaSuccess;
     const unsigned g = persistent_grid(total, ls, num_sms);
-    ICHEE_LIMB_SWITCH_T(k_blend_batch, g, ls.threads, a, t)
+    ICHEE_LIMB_SWITCH_T(k_blend_batch, g, kBlendBatchThreads, a, t)
     return cudaGetLastError();
 }
 
