@@ -501,7 +501,7 @@ def test_torch_allocator_serves_working_memory(ichee):
 # ------------------------------------------------------------- degenerate pixel values
 def test_degenerate_pixel_values(ichee):
     """Pixels 0 and 255 and values with a single nonzero radix digit, through every cache kind
-    (radix 2 / 10 / 16 with and without randomness, full cache with the pool): bit for bit
+    (radix 2 / 7 / 10 / 15 / 16 with and without randomness, full cache with the pool): bit for bit
     against the oracle. Without randomness pixel 0 has no nonzero digit and encrypts to the
     all-zero ciphertext -- the paper's method as stated; its randomness removes that. A
     constant 255 image keeps its value through the mean filter."""
@@ -510,7 +510,7 @@ def test_degenerate_pixel_values(ichee):
     o = oracle_for(wl)
     pix = np.array([0, 255, 1, 16, 240, 128, 2, 100, 0, 255, 10, 15], dtype=np.uint8)
     dp = torch.from_numpy(pix).cuda()
-    for base in (2, 10, 16):
+    for base in (2, 7, 10, 15, 16):   # 8, 3, 3, 3 and 2 positions; 7 to 15 and 2 use the pair table
         for rnd in (0, 1):
             cache = ctx.build_cache(ichee.CACHE_RADIX, CACHE_SEED + base, radix_base=base, randomize=rnd)
             ct, meta = ctx.encrypt(dp, 3, 4, 1, IMG_SEED, cache=cache)
