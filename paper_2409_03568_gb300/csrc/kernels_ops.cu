@@ -447,7 +447,8 @@ __global__ void __launch_bounds__(kMfMaxThreads<LIMBS>) k_meanfilter3_batch(cons
 // pairs: lane = coefficient pair (coalesced 512-byte accesses), warp = column. Every warp walks
 // its column from top to bottom, rebuilding each pixel's ciphertext once from the
 // L2-resident cached multiples d * Enc(r^k) (signed digits with the pixel's randomness bits,
-// and the pair table of the top two positions when the cache has one, as in the radix combine) and writing it as the encryption output. The vertical 3-sums come
+// and the pair table of the top two positions when the cache has one, as in the radix
+// combine) and writing it as the encryption output. The vertical 3-sums come
 // from two running sums in registers (S1 = row y, S2 = rows y-1 + y); the horizontal 3-sum from
 // the neighbouring warps through shared memory (double-buffered: one barrier per row). The
 // strip's first and last warps are halo columns (clamped at the image border) whose outputs
@@ -691,7 +692,7 @@ __device__ __forceinline__ void blend_rows(const OpsArgs& a)
     }
 }
 
-// Up to three limbs (56 registers as compiled without a bound).
+// Up to three limbs: no register bound (62 registers at three limbs).
 template <int LIMBS>
 __global__ void k_blend(const __grid_constant__ OpsArgs a)
 {
