@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(NttShape<LOGN, E>::T) k_sqdiff_image(const __g
             const u64* e1p = a.evk_hat_p + (((size_t)l * 2 + 1) * (L + 1) + l) * N;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                const int x = elem_index<LOGN, LAST, E>(tid, e);
+                const int x = elem_index<LOGN, LAST, E, false>(tid, e);
                 const u64 d0 = t0[e * T], d1 = t2[e * T];
                 const u64 m2 = mont_mul(d1, d1, q, qinv);
                 const u64 th = shoup(m2, a.r64[l], a.r64_p[l], q);   // d1^2, the transform of digit l
@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(NttShape<LOGN, E>::T) k_sqdiff_image(const __g
                 const u64* e1p = a.evk_hat_p + (((size_t)j * 2 + 1) * (L + 1) + mod) * N;
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
-                    const int x = elem_index<LOGN, LAST, E>(tid, e);
+                    const int x = elem_index<LOGN, LAST, E, false>(tid, e);
                     const u64 d = csub(csub(r[0][e], 2 * q), q);
                     const u64 p0 = shoup(d, __ldg(e0 + x), __ldg(e0p + x), q);
                     const u64 p1 = shoup(d, __ldg(e1 + x), __ldg(e1p + x), q);

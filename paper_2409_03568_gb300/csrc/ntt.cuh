@@ -31,7 +31,7 @@ struct Radix {
 };
 
 template <int E = 16>
-__device__ __forceinline__ int swz(int x)
+__host__ __device__ constexpr int swz(int x)
 {
     if constexpr (E == 16) return x ^ ((x >> 4) & 15);
     else return x ^ ((x >> 2) & 7) ^ ((x >> 3) & 15);
@@ -55,66 +55,117 @@ struct NttShape {
     static constexpr int LAST = ((LOGN - 1) / LE) * LE;  // first stage of the last pass
 };
 
-// Natural index of register e of thread tid in the pass starting at stage S0.
-template <int LOGN, int S0, int E = 16>
-__device__ __forceinline__ int elem_index(int tid, int e)
+__host__ __device__ constexpr int ilog2(int x) { return x > 1 ? 1 + ilog2(x >> 1) : 0; }
+
+// Butterfly-group id of register group g of thread tid in a pass: a full pass has one group
+// per thread; a partial last pass (fewer than LE stages, G > 1 groups per thread) keeps a
+// warp's G x 32 groups adjacent (lane fastest, then g, then the warp), so that each warp holds
+// the same 2^(LE+5) consecutive indices as in the full pass before it -- the exchange into the
+// last pass stays inside the warp -- while a register's 32 lanes still touch consecutive
+// butterflies (the coalescing and the bank pattern of global and shared accesses unchanged).
+__host__ __device__ constexpr int pass_gid(int T, int G, int tid, int g, bool wt = true)
 {
-    using P = Pass<LOGN, S0, E>;
-    const int g = e >> P::S, j = e & ((1 << P::S) - 1);
-    const int gid = g * P::T + tid;
-    const int l = gid & ((1 << P::LO) - 1);
-    const int h = gid >> P::LO;
-    return (h << (P::LO + P::S)) | (j << P::LO) | l;
+    return G > 1 && wt ? (((tid >> 5) << (5 + ilog2(G))) | (g << 5) | (tid & 31)) : g * T + tid;
+}
+
+// Natural index of register e of thread tid in the pass starting at stage S0 (values of the
+// template parameters as arguments, for the compile-time checks below). WT = false keeps the
+// groups of a partial last pass strided by the thread count (g * T + tid): the layout of the
+// compact transform form.
+__host__ __device__ constexpr int elem_index_of(int logn, int s0, int E, int tid, int e, bool wt = true)
+{
+    const int le = E == 16 ? 4 : 3;
+    const int T = (1 << logn) / E;
+    const int S = (logn - s0) < le ? (logn - s0) : le;
+    const int G = E >> S, LO = logn - s0 - S;
+    const int g = e >> S, j = e & ((1 << S) - 1);
+    const int gid = pass_gid(T, G, tid, g, wt);
+    return ((gid >> LO) << (LO + S)) | (j << LO) | (gid & ((1 << LO) - 1));
+}
+
+template <int LOGN, int S0, int E = 16, bool WT = true>
+__device__ __forceinline__ int elem_index(int tid, int e) { return elem_index_of(LOGN, S0, E, tid, e, WT); }
+
+// Whether the exchange between the layouts of the passes starting at SA and SB stays inside
+// every warp: both layouts are bit permutations of (tid, e), so it does when the index bits
+// driven by a warp's lane bits and the register bits are the same set in both, and every
+// higher thread bit lands on the same index bit in both. Such an exchange needs only a warp
+// barrier: a thread stores to the slots it loaded in the exchange before (the same layout),
+// so no other warp's loads can be overtaken.
+__host__ __device__ constexpr bool exchange_in_warp(int logn, int sa, int sb, int E)
+{
+    const int T = (1 << logn) / E;
+    int va = 0, vb = 0;
+    for (int i = 0; i < 5; ++i) {
+        va |= elem_index_of(logn, sa, E, 1 << i, 0);
+        vb |= elem_index_of(logn, sb, E, 1 << i, 0);
+    }
+    for (int k = 1; k < E; k <<= 1) {
+        va |= elem_index_of(logn, sa, E, 0, k);
+        vb |= elem_index_of(logn, sb, E, 0, k);
+    }
+    if (va != vb) return false;
+    for (int i = 5; (1 << i) < T; ++i)
+        if (elem_index_of(logn, sa, E, 1 << i, 0) != elem_index_of(logn, sb, E, 1 << i, 0)) return false;
+    return true;
+}
+
+// The barrier of an exchange between two pass layouts.
+template <bool IN_WARP>
+__device__ __forceinline__ void exchange_barrier()
+{
+    if constexpr (IN_WARP) __syncwarp();
+    else __syncthreads();
 }
 
 // Without the swizzle the split is additive: elem_index(tid, e) = elem_index(tid, 0) +
 // elem_index(0, e) (disjoint bits), so global accesses take a per-thread base pointer and
 // compile-time offsets.
-template <int LOGN, int S0, int E = 16>
-__device__ __forceinline__ int elem_offset(int e) { return elem_index<LOGN, S0, E>(0, e); }
+template <int LOGN, int S0, int E = 16, bool WT = true>
+__device__ __forceinline__ int elem_offset(int e) { return elem_index<LOGN, S0, E, WT>(0, e); }
 
 // Shared-memory slot of register e of thread tid in the pass starting at S0. elem_index is a
 // permutation of the bits of (tid, e) and the swizzle is linear over GF(2), so the slot is
 // swz(elem_index(tid, 0)) ^ swz(elem_index(0, e)): a per-thread base XOR a compile-time
 // constant, one instruction per access (checked for every pass of N = 2^10 .. 2^14).
-template <int LOGN, int S0, int E = 16>
-__device__ __forceinline__ int slot_base(int tid) { return swz<E>(elem_index<LOGN, S0, E>(tid, 0)); }
+template <int LOGN, int S0, int E = 16, bool WT = true>
+__device__ __forceinline__ int slot_base(int tid) { return swz<E>(elem_index<LOGN, S0, E, WT>(tid, 0)); }
 
-template <int LOGN, int S0, int E = 16>
-__device__ __forceinline__ int slot_of(int base, int e) { return base ^ swz<E>(elem_index<LOGN, S0, E>(0, e)); }
+template <int LOGN, int S0, int E = 16, bool WT = true>
+__device__ __forceinline__ int slot_of(int base, int e) { return base ^ swz<E>(elem_index<LOGN, S0, E, WT>(0, e)); }
 
-template <int LOGN, int S0, int NP, int E = 16>
+template <int LOGN, int S0, int NP, int E = 16, bool WT = true>
 __device__ __forceinline__ void load_sm(const u64* sm, u64 (&r)[NP][E], int tid)
 {
-    const int base = slot_base<LOGN, S0, E>(tid);
+    const int base = slot_base<LOGN, S0, E, WT>(tid);
 #pragma unroll
     for (int p = 0; p < NP; ++p)
 #pragma unroll
-        for (int e = 0; e < E; ++e) r[p][e] = sm[p * (1 << LOGN) + slot_of<LOGN, S0, E>(base, e)];
+        for (int e = 0; e < E; ++e) r[p][e] = sm[p * (1 << LOGN) + slot_of<LOGN, S0, E, WT>(base, e)];
 }
 
-template <int LOGN, int S0, int NP, int E = 16>
+template <int LOGN, int S0, int NP, int E = 16, bool WT = true>
 __device__ __forceinline__ void store_sm(u64* sm, const u64 (&r)[NP][E], int tid)
 {
-    const int base = slot_base<LOGN, S0, E>(tid);
+    const int base = slot_base<LOGN, S0, E, WT>(tid);
 #pragma unroll
     for (int p = 0; p < NP; ++p)
 #pragma unroll
-        for (int e = 0; e < E; ++e) sm[p * (1 << LOGN) + slot_of<LOGN, S0, E>(base, e)] = r[p][e];
+        for (int e = 0; e < E; ++e) sm[p * (1 << LOGN) + slot_of<LOGN, S0, E, WT>(base, e)] = r[p][e];
 }
 
 // Forward stages S0 .. S0+S-1 on the registers. Stage s pairs x with x + N/2^{s+1} and uses
 // twiddle index 2^s + (x >> (LOGN - s)). With TERNARY0 the first stage of pass 0 takes the
 // odd operands as ternary residues {0, 1, q-1}, whose products with the twiddle are 0, W and
 // q - W: no multiplication.
-template <int LOGN, int S0, int NP, bool TERNARY0 = false, int E = 16>
+template <int LOGN, int S0, int NP, bool TERNARY0 = false, int E = 16, bool WT = true>
 __device__ __forceinline__ void fwd_regs(u64 (&r)[NP][E], int tid, const ulonglong2* __restrict__ tw, u64 q)
 {
     using P = Pass<LOGN, S0, E>;
     const u64 q2 = 2 * q;
 #pragma unroll
     for (int g = 0; g < P::G; ++g) {
-        const int h = (g * P::T + tid) >> P::LO;
+        const int h = pass_gid(P::T, P::G, tid, g, WT) >> P::LO;
 #pragma unroll
         for (int k = 0; k < P::S; ++k) {
             const int s = S0 + k;
@@ -148,14 +199,14 @@ __device__ __forceinline__ void fwd_regs(u64 (&r)[NP][E], int tid, const ulonglo
 }
 
 // Inverse stages S0+S-1 .. S0 (reverse order) on the registers.
-template <int LOGN, int S0, int NP, int E = 16>
+template <int LOGN, int S0, int NP, int E = 16, bool WT = true>
 __device__ __forceinline__ void inv_regs(u64 (&r)[NP][E], int tid, const ulonglong2* __restrict__ itw, u64 q)
 {
     using P = Pass<LOGN, S0, E>;
     const u64 q2 = 2 * q;
 #pragma unroll
     for (int g = 0; g < P::G; ++g) {
-        const int h = (g * P::T + tid) >> P::LO;
+        const int h = pass_gid(P::T, P::G, tid, g, WT) >> P::LO;
 #pragma unroll
         for (int k = P::S - 1; k >= 0; --k) {
             const int s = S0 + k;
@@ -190,7 +241,7 @@ __device__ __forceinline__ void fwd_rest(u64* sm, u64 (&r)[NP][E], int tid, cons
     constexpr int LE = Radix<E>::LE;
     if constexpr (S0 <= NttShape<LOGN, E>::LAST) {
         store_sm<LOGN, S0 - LE, NP, E>(sm, r, tid);
-        __syncthreads();
+        exchange_barrier<exchange_in_warp(LOGN, S0 - LE, S0, E)>();
         load_sm<LOGN, S0, NP, E>(sm, r, tid);
         fwd_regs<LOGN, S0, NP, false, E>(r, tid, tw, q);
         fwd_rest<LOGN, S0 + LE, NP, E>(sm, r, tid, tw, q);
@@ -206,7 +257,7 @@ __device__ __forceinline__ void inv_rest(u64* sm, u64 (&r)[NP][E], int tid, cons
     inv_regs<LOGN, S0, NP, E>(r, tid, itw, q);
     if constexpr (S0 > 0) {
         store_sm<LOGN, S0, NP, E>(sm, r, tid);
-        __syncthreads();
+        exchange_barrier<exchange_in_warp(LOGN, S0, S0 - LE, E)>();
         load_sm<LOGN, S0 - LE, NP, E>(sm, r, tid);
         inv_rest<LOGN, S0 - LE, NP, E>(sm, r, tid, itw, q);
     }
@@ -337,7 +388,11 @@ __device__ __forceinline__ void inv_regs_rt(u64 (&r)[NP][E], int tid, int S0, in
 // Passes: LOGN / LE full passes, then one pass of the remaining LOGN % LE stages.
 // COMPACT runs the full passes through one runtime loop (one copy of the pass code); otherwise
 // every pass is unrolled with its position known at compile time, which needs fewer address
-// instructions but about LOGN / LE times the code.
+// instructions but about LOGN / LE times the code. The unrolled form takes a warp barrier for
+// the exchanges that stay inside every warp (exchange_in_warp); the compact form, used by the
+// kernel that chains 26 transforms, keeps block barriers and the strided last-pass layout
+// (WT = false; its callers index the last pass with it): there the warp-adjacent layout and
+// warp barriers took more registers (spills 8 -> 76 bytes) and time (14.3 -> 14.7 ms).
 template <int LOGN, int NP, bool TERNARY0 = false, bool COMPACT = false, int E = 16>
 __device__ __forceinline__ void ntt_fwd_regs(u64* sm, u64 (&r)[NP][E], int tid, const ModTables& t, u64 q)
 {
@@ -366,8 +421,8 @@ __device__ __forceinline__ void ntt_fwd_regs(u64* sm, u64 (&r)[NP][E], int tid, 
     if constexpr (TAIL > 0) {
         store_sm_rt<LOGN, NP, E>(sm, r, tid, LOGN - LE * NFULL);
         __syncthreads();
-        load_sm<LOGN, LE * NFULL, NP, E>(sm, r, tid);
-        fwd_regs<LOGN, LE * NFULL, NP, false, E>(r, tid, t.tw, q);
+        load_sm<LOGN, LE * NFULL, NP, E, false>(sm, r, tid);
+        fwd_regs<LOGN, LE * NFULL, NP, false, E, false>(r, tid, t.tw, q);
     }
 }
 
@@ -384,8 +439,8 @@ __device__ __forceinline__ void ntt_inv_regs(u64* sm, u64 (&r)[NP][E], int tid, 
     }
     constexpr int NFULL = LOGN / LE, TAIL = LOGN % LE;
     if constexpr (TAIL > 0) {
-        inv_regs<LOGN, LE * NFULL, NP, E>(r, tid, t.itw, q);
-        store_sm<LOGN, LE * NFULL, NP, E>(sm, r, tid);
+        inv_regs<LOGN, LE * NFULL, NP, E, false>(r, tid, t.itw, q);
+        store_sm<LOGN, LE * NFULL, NP, E, false>(sm, r, tid);
         __syncthreads();
         load_sm_rt<LOGN, NP, E>(sm, r, tid, LOGN - LE * NFULL);
     }
