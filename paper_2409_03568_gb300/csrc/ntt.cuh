@@ -110,6 +110,18 @@ __host__ __device__ constexpr bool exchange_in_warp(int logn, int sa, int sb, in
     return true;
 }
 
+// Bit p set: the exchange between full passes p - 1 and p stays inside every warp (full passes
+// have the same layout in both forms of the transform; the exchange is the same in the inverse
+// direction).
+__host__ __device__ constexpr unsigned full_exchanges_in_warp(int logn, int E)
+{
+    const int le = E == 16 ? 4 : 3;
+    unsigned m = 0;
+    for (int p = 1; p < logn / le; ++p)
+        if (exchange_in_warp(logn, le * (p - 1), le * p, E)) m |= 1u << p;
+    return m;
+}
+
 // The barrier of an exchange between two pass layouts.
 template <bool IN_WARP>
 __device__ __forceinline__ void exchange_barrier()
@@ -388,11 +400,11 @@ __device__ __forceinline__ void inv_regs_rt(u64 (&r)[NP][E], int tid, int S0, in
 // Passes: LOGN / LE full passes, then one pass of the remaining LOGN % LE stages.
 // COMPACT runs the full passes through one runtime loop (one copy of the pass code); otherwise
 // every pass is unrolled with its position known at compile time, which needs fewer address
-// instructions but about LOGN / LE times the code. The unrolled form takes a warp barrier for
-// the exchanges that stay inside every warp (exchange_in_warp); the compact form, used by the
-// kernel that chains 26 transforms, keeps block barriers and the strided last-pass layout
-// (WT = false; its callers index the last pass with it): there the warp-adjacent layout and
-// warp barriers took more registers (spills 8 -> 76 bytes) and time (14.3 -> 14.7 ms).
+// instructions but about LOGN / LE times the code. Both take a warp barrier for the exchanges
+// that stay inside every warp (exchange_in_warp). The compact form, used by the kernel that
+// chains 26 transforms, keeps the strided last-pass layout (WT = false; its callers index the
+// last pass with it) and a block barrier into it: there the warp-adjacent layout took more
+// registers (spills 8 -> 76 bytes) and time (14.3 -> 14.7 ms).
 template <int LOGN, int NP, bool TERNARY0 = false, bool COMPACT = false, int E = 16>
 __device__ __forceinline__ void ntt_fwd_regs(u64* sm, u64 (&r)[NP][E], int tid, const ModTables& t, u64 q)
 {
@@ -408,12 +420,14 @@ __device__ __forceinline__ void ntt_fwd_regs(u64* sm, u64 (&r)[NP][E], int tid, 
         fwd_regs<LOGN, 0, NP, true, E>(r, tid, t.tw, q);
         p0 = 1;
     }
+    constexpr unsigned in_warp = full_exchanges_in_warp(LOGN, E);
 #pragma unroll 1
     for (int p = p0; p < NFULL; ++p) {
         const int lo = LOGN - LE * p - LE;
         if (p > 0) {
             store_sm_rt<LOGN, NP, E>(sm, r, tid, lo + LE);
-            __syncthreads();
+            if ((in_warp >> p) & 1u) __syncwarp();   // uniform across the block
+            else __syncthreads();
             load_sm_rt<LOGN, NP, E>(sm, r, tid, lo);
         }
         fwd_regs_rt<NP, E>(r, tid, LE * p, lo, t.tw, q);
@@ -444,13 +458,15 @@ __device__ __forceinline__ void ntt_inv_regs(u64* sm, u64 (&r)[NP][E], int tid, 
         __syncthreads();
         load_sm_rt<LOGN, NP, E>(sm, r, tid, LOGN - LE * NFULL);
     }
+    constexpr unsigned in_warp = full_exchanges_in_warp(LOGN, E);
 #pragma unroll 1
     for (int p = NFULL - 1; p >= 0; --p) {
         const int lo = LOGN - LE * p - LE;
         inv_regs_rt<NP, E>(r, tid, LE * p, lo, t.itw, q);
         if (p > 0) {
             store_sm_rt<LOGN, NP, E>(sm, r, tid, lo);
-            __syncthreads();
+            if ((in_warp >> p) & 1u) __syncwarp();
+            else __syncthreads();
             load_sm_rt<LOGN, NP, E>(sm, r, tid, lo + LE);
         }
     }
