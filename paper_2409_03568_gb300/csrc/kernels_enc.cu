@@ -298,14 +298,18 @@ __device__ __forceinline__ void encrypt_ct(const EncArgs& a, int p, u64 seed, u6
     const int xl = elem_index<LOGN, LAST, E>(tid, 0);    // last-pass layout
     if constexpr (NB == 2 && KEEP_VHAT) {
         // per limb: v^ = NTT(v), both products v^ . pk^_b at once, then the two inverse
-        // transforms in lockstep (one pass structure, barriers and twiddle loads shared)
+        // transforms in lockstep (one pass structure, barriers and twiddle loads shared). No
+        // block barrier separates the transforms: a transform's first exchange stores to the
+        // slots of the layout the previous one last loaded (pass 0 after an inverse, the last
+        // pass after a forward), so every thread overwrites only slots it has read itself, and
+        // the second buffer's last readers (the previous limb's inverse) are behind the forward
+        // transform's block-wide exchanges (3.19 -> 3.10 ms).
         for (int l = 0; l < L; ++l) {
             const u64 q = a.rns.q[l];
             const ModTables t = a.rns.tab[l];
             u64 r[1][E];
 #pragma unroll
             for (int e = 0; e < E; ++e) r[0][e] = small_mod(sv[x0 + elem_offset<LOGN, 0, E>(e)], q);
-            __syncthreads();
             ntt_fwd_regs<LOGN, 1, true, false, E>(smem, r, tid, t, q);
             u64 rr[2][E];
             const ulonglong2* pk0 = a.pk_pair + (size_t)l * N + xl;
@@ -317,7 +321,6 @@ __device__ __forceinline__ void encrypt_ct(const EncArgs& a, int p, u64 seed, u6
                 rr[0][e] = shoup_lazy(r[0][e], w0.x, w0.y, q);
                 rr[1][e] = shoup_lazy(r[0][e], w1.x, w1.y, q);
             }
-            __syncthreads();
             ntt_inv_regs<LOGN, 2, false, E>(smem, rr, tid, t, q);
 #pragma unroll
             for (int pb = 0; pb < 2; ++pb) {

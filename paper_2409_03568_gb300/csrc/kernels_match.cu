@@ -11,7 +11,10 @@ namespace ichee {
 // d0 and d1, and accumulates (d0^2, 2 d0 d1, d1^2) position by position into its own slice of
 // the scratch buffer (each position is owned by one thread, so no atomics are needed). The
 // transform of d0 waits in a second shared-memory buffer (SMEM_D0) or, for the 2^14 ring whose
-// buffers do not both fit, in the fourth scratch row; d1's waits in the transform buffer.
+// buffers do not both fit, in the fourth scratch row; d1's waits in the transform buffer. Every
+// thread parks and reads back only the slots of its own last-pass registers -- the slots it
+// loaded in the transform's last exchange -- so no barrier follows the transform (2.69 -> 2.67
+// ms); the barrier before each transform remains (its first exchange writes other slots).
 template <int LOGN, bool SMEM_D0, int E>
 __global__ void __launch_bounds__(NttShape<LOGN, E>::T, 1) k_sqdiff_accumulate(const __grid_constant__ SqDiffArgs a)
 {
@@ -53,7 +56,6 @@ __global__ void __launch_bounds__(NttShape<LOGN, E>::T, 1) k_sqdiff_accumulate(c
             }
             __syncthreads();
             ntt_fwd_regs<LOGN, 1, false, false, E>(buf, r, tid, t, q);
-            __syncthreads();
             u64* dst = pb == 0 ? d0buf : buf;
             const int sb = slot_base<LOGN, LAST, E>(tid);
             const int xl = elem_index<LOGN, LAST, E>(tid, 0);
@@ -142,7 +144,6 @@ __global__ void __launch_bounds__(1024, 1) k_sqdiff_accumulate_split(const __gri
             }
             __syncthreads();
             ntt_fwd_regs<LOGH, 1, false, false, E>(buf, r, tid, t, q);
-            __syncthreads();
             u64* dst = pb == 0 ? d0buf : buf;
             const int sb = slot_base<LOGH, LAST, E>(tid);
 #pragma unroll
