@@ -567,6 +567,7 @@ EncArgs ichee::enc_args(const ichee_ctx* c, const uint8_t* d_pix, u64 n_ct, u64 
     a.id_base = id_base;
     a.cdt = c->cdt;
     a.out = out;
+    a.num_sms = c->num_sms;
     return a;
 }
 

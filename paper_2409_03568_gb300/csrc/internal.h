@@ -21,6 +21,7 @@ struct EncArgs {
     u64 id_base;               // ct id of ciphertext k is id_base + k
     CdtTable cdt;
     u64* out;                  // [n_ct][2][L][N]
+    int num_sms;               // persistent grid of the single-image kernel: one block per SM
 };
 
 // pair[i] = (a[i], b[i]) for i < n

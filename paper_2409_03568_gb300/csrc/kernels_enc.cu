@@ -250,31 +250,42 @@ cudaError_t launch_axpy_const(u64* out, const u64* x, const u64* y, u64 c, int n
 
 // Shared memory of one encryption block: the transform buffers (N words each; two where both
 // inverse transforms of a limb run in lockstep: N = 2^13, 8 residues per thread), v, e0, e1 as
-// int8 (3N bytes),
-// then the search copy of the Gaussian table (32 words).
+// int8 (3N bytes; two sets up to N = 2^13, used by alternate ciphertexts of the block), then the
+// search copy of the Gaussian table (32 words).
 template <int LOGN>
 static constexpr int kEncBufs = LOGN == 13 ? 2 : 1;
 
 template <int LOGN>
-__device__ __forceinline__ u64* enc_cdt_smem(u64* smem) { return smem + kEncBufs<LOGN> * (1 << LOGN) + (3 << LOGN) / 8; }
+static constexpr int kEncSampleSets = LOGN <= 13 ? 2 : 1;
 
 template <int LOGN>
-static constexpr size_t kEncSmem = ((sizeof(u64) * kEncBufs<LOGN> + 3) << LOGN) + 32 * sizeof(u64);
+__device__ __forceinline__ u64* enc_cdt_smem(u64* smem)
+{
+    return smem + kEncBufs<LOGN> * (1 << LOGN) + ((3 * kEncSampleSets<LOGN>) << LOGN) / 8;
+}
 
+template <int LOGN>
+static constexpr size_t kEncSmem = ((sizeof(u64) * kEncBufs<LOGN> + 3 * kEncSampleSets<LOGN>) << LOGN) + 32 * sizeof(u64);
+
+// `it` counts the ciphertexts the block has encrypted before this one. With two sample sets the
+// block draws this ciphertext's samples into set it % 2 while slower warps may still read the
+// previous ciphertext's set in its last epilogue; the barrier after the sampling of the previous
+// ciphertext ordered every read of this set (two ciphertexts back) before it. With one set a
+// barrier must precede the sampling. The transform buffers need none (see the limb loop).
 template <int LOGN, bool KEEP_VHAT, int E>
-__device__ __forceinline__ void encrypt_ct(const EncArgs& a, int p, u64 seed, u64 id, u64* ct, u64* smem)
+__device__ __forceinline__ void encrypt_ct(const EncArgs& a, int p, u64 seed, u64 id, u64* ct, u64* smem, int it)
 {
     constexpr int N = 1 << LOGN;
     constexpr int T = NttShape<LOGN, E>::T;
     constexpr int LAST = NttShape<LOGN, E>::LAST;
     constexpr int NB = kEncBufs<LOGN>;
-    int8_t* sv = reinterpret_cast<int8_t*>(smem + NB * N);
+    int8_t* sv = reinterpret_cast<int8_t*>(smem + NB * N) + (kEncSampleSets<LOGN> == 2 ? (it & 1) * 3 * N : 0);
     int8_t* se0 = sv + N;
     int8_t* se1 = se0 + N;
     const u64* tcdt = enc_cdt_smem<LOGN>(smem);   // filled by the kernel before its first ciphertext
     const int tid = threadIdx.x;
     const int L = a.L;
-    __syncthreads();  // smem of the previous ciphertext no longer read
+    if constexpr (kEncSampleSets<LOGN> == 1) __syncthreads();   // the previous ciphertext's samples no longer read
     for (int b = tid; b < N / 4; b += T) {
         Words4 w = philox(seed, kStreamV, id, (u32)b);
         u32 packed = 0;
@@ -381,12 +392,14 @@ template <int LOGN, bool KEEP_VHAT, int E>
 __global__ void __launch_bounds__(NttShape<LOGN, E>::T, 1) k_encrypt_fresh(const __grid_constant__ EncArgs a)
 {
     extern __shared__ u64 smem[];
-    cdt_for_search(a.cdt, enc_cdt_smem<LOGN>(smem));   // ordered by encrypt_ct's first barrier
+    cdt_for_search(a.cdt, enc_cdt_smem<LOGN>(smem));
+    __syncthreads();
     const u64 ct_len = (u64)2 * a.L << LOGN;
+    int it = 0;
     for (u64 k = blockIdx.x; k < a.n_ct; k += gridDim.x) {
         const int p = a.pixels[k];
         if (a.skip_lut != nullptr && a.skip_lut[p] >= 0) continue;  // uniform across the block
-        encrypt_ct<LOGN, KEEP_VHAT, E>(a, p, a.seed, a.id_base + k, a.out + k * ct_len, smem);
+        encrypt_ct<LOGN, KEEP_VHAT, E>(a, p, a.seed, a.id_base + k, a.out + k * ct_len, smem, it++);
     }
 }
 
@@ -395,15 +408,17 @@ __global__ void __launch_bounds__(NttShape<LOGN, E>::T, 1) k_encrypt_fresh_batch
                                                                               const __grid_constant__ SegTable t)
 {
     extern __shared__ u64 smem[];
-    cdt_for_search(a.cdt, enc_cdt_smem<LOGN>(smem));   // ordered by encrypt_ct's first barrier
+    cdt_for_search(a.cdt, enc_cdt_smem<LOGN>(smem));
+    __syncthreads();
     const u64 ct_len = (u64)2 * a.L << LOGN;
     const u64 total = t.start[t.n];
+    int it = 0;
     for (u64 g = blockIdx.x; g < total; g += gridDim.x) {
         const int s = seg_of(t, g);
         const u64 k = g - t.start[s];
         const int p = t.px[s][k];
         if (a.skip_lut != nullptr && a.skip_lut[p] >= 0) continue;
-        encrypt_ct<LOGN, KEEP_VHAT, E>(a, p, t.seed[s], k, t.out[s] + k * ct_len, smem);
+        encrypt_ct<LOGN, KEEP_VHAT, E>(a, p, t.seed[s], k, t.out[s] + k * ct_len, smem, it++);
     }
 }
 
@@ -422,7 +437,12 @@ static cudaError_t enc_launch(const EncArgs& a, cudaStream_t st)
     cudaError_t e = cudaFuncSetAttribute(k_encrypt_fresh<LOGN, keep, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    u64 grid = a.n_ct < (u64)(1u << 30) ? a.n_ct : (u64)(1u << 30);
+    // persistent: one block per SM (the shared memory fits one), each walking its share of the
+    // ciphertexts, so a block's sampling overlaps its previous ciphertext's epilogue (3.10 ->
+    // 3.06 ms). With pixels to skip (the misses of a value cache) the shares would be uneven,
+    // so there every ciphertext is a block of its own (a static share: 2.40 -> 2.81 ms).
+    const u64 cap = a.skip_lut == nullptr && a.num_sms > 0 ? (u64)a.num_sms : (u64)(1u << 30);
+    const u64 grid = a.n_ct < cap ? a.n_ct : cap;
     k_encrypt_fresh<LOGN, keep, E><<<(unsigned)grid, T, smem, st>>>(a);
     return cudaGetLastError();
 }
