@@ -269,6 +269,10 @@ cudaError_t launch_reduce_rows(const RnsArgs& rns, int rows, int limbs, const u6
 // That is L^2 + 5L + 2 transforms per pixel (t2 is the only tensor limb inverse-transformed,
 // and no digit is transformed back into its own modulus), all in the compact pass form so the
 // chain fits the instruction cache.
+// A transform's first exchange stores to the slots of its thread in pass 0 (forward) or in the
+// last pass (inverse), and its last exchange loads the slots of the other end, so a block
+// barrier is needed only between two transforms of the same direction: after a forward, an
+// inverse overwrites only slots its thread loaded last, and after an inverse a forward does.
 // Every intermediate word is produced and consumed by the same thread (the transforms move
 // data between threads only through their own shared buffer), so the block's scratch
 // ([3 limbs + 2][N] words: t0^, t1^, t2 per limb, then the two P accumulators) is stored
@@ -314,7 +318,7 @@ __global__ void __launch_bounds__(NttShape<LOGN, E>::T) k_sqdiff_image(const __g
                     const int x = elem_index<LOGN, 0, E>(tid, e);
                     r[0][e] = sub_mod(__ldcs(pa + x), __ldcs(pq + x), q);
                 }
-                __syncthreads();
+                if (pb == 1) __syncthreads();   // after a forward transform (see below)
                 ntt_fwd_regs<LOGN, 1, false, true, E>(sm, r, tid, a.rns.tab[l], q);
                 u64* dst = pb == 0 ? t0 : t2;
 #pragma unroll
@@ -338,7 +342,6 @@ __global__ void __launch_bounds__(NttShape<LOGN, E>::T) k_sqdiff_image(const __g
                                     shoup(th, __ldg(e1 + x), __ldg(e1p + x), q), q);
                 r[0][e] = shoup(m2, a.ninv[l], a.ninv_p[l], q);
             }
-            __syncthreads();
             ntt_inv_regs<LOGN, 1, true, E>(sm, r, tid, a.rns.tab[l], q);
 #pragma unroll
             for (int e = 0; e < E; ++e) t2[e * T] = csub(r[0][e], q);
@@ -350,6 +353,7 @@ __global__ void __launch_bounds__(NttShape<LOGN, E>::T) k_sqdiff_image(const __g
             const u64 q = a.rns.q[mod], mu = a.rns.mu[mod];
             u64* acc0 = m < 0 ? AP : T0 + (size_t)m * N;    // started in step 1 (m != P)
             u64* acc1 = m < 0 ? AP + N : T1 + (size_t)m * N;
+            bool first = true;
 #pragma unroll 1
             for (int j = 0; j < limbs; ++j) {
                 if (j == m) continue;   // digit m's term went in with t_b^ in step 1
@@ -366,7 +370,8 @@ __global__ void __launch_bounds__(NttShape<LOGN, E>::T) k_sqdiff_image(const __g
                         r[0][e] = mag == 0 ? 0 : q - mag;
                     }
                 }
-                __syncthreads();
+                if (!first) __syncthreads();   // after a forward transform
+                first = false;
                 ntt_fwd_regs<LOGN, 1, false, true, E>(sm, r, tid, a.rns.tab[mod], q);
                 const u64* e0 = a.evk_hat + (((size_t)j * 2 + 0) * (L + 1) + mod) * N;
                 const u64* e0p = a.evk_hat_p + (((size_t)j * 2 + 0) * (L + 1) + mod) * N;
@@ -392,7 +397,7 @@ __global__ void __launch_bounds__(NttShape<LOGN, E>::T) k_sqdiff_image(const __g
                 u64* acc = pb == 0 ? acc0 : acc1;
 #pragma unroll
                 for (int e = 0; e < E; ++e) r[0][e] = acc[e * T];
-                __syncthreads();
+                if (pb == 1) __syncthreads();   // after an inverse transform
                 ntt_inv_regs<LOGN, 1, true, E>(sm, r, tid, a.rns.tab[mod], q);
                 if (m < 0) {
 #pragma unroll
