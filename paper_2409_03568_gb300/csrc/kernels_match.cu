@@ -54,8 +54,12 @@ __global__ void __launch_bounds__(NttShape<LOGN, E>::T, 1) k_sqdiff_accumulate(c
                 const int x = elem_offset<LOGN, 0, E>(e);
                 r[0][e] = sub_mod(__ldcs(pa + x), __ldcs(pbb + x), q);
             }
-            __syncthreads();
-            ntt_fwd_regs<LOGN, 1, false, false, E>(buf, r, tid, t, q);
+            // with both buffers in shared memory d0 is transformed in its parking buffer and d1 in
+            // the other one: d1's transform then starts after d0's block-wide exchanges, which
+            // every thread reaches only after its reads of the previous pixel, so it needs no
+            // barrier of its own
+            if (pb == 0 || !SMEM_D0) __syncthreads();
+            ntt_fwd_regs<LOGN, 1, false, false, E>(SMEM_D0 && pb == 0 ? d0buf : buf, r, tid, t, q);
             u64* dst = pb == 0 ? d0buf : buf;
             const int sb = slot_base<LOGN, LAST, E>(tid);
             const int xl = elem_index<LOGN, LAST, E>(tid, 0);
@@ -142,8 +146,8 @@ __global__ void __launch_bounds__(1024, 1) k_sqdiff_accumulate_split(const __gri
                 const u64 tt = shoup_lazy(hi, w1.x, w1.y, q);   // [0, 2q)
                 r[0][e] = h ? lo + 2 * q - tt : lo + tt;         // [0, 3q)
             }
-            __syncthreads();
-            ntt_fwd_regs<LOGH, 1, false, false, E>(buf, r, tid, t, q);
+            if (pb == 0) __syncthreads();   // d0 in its parking buffer, d1 in the other (as above)
+            ntt_fwd_regs<LOGH, 1, false, false, E>(pb == 0 ? d0buf : buf, r, tid, t, q);
             u64* dst = pb == 0 ? d0buf : buf;
             const int sb = slot_base<LOGH, LAST, E>(tid);
 #pragma unroll
