@@ -348,6 +348,8 @@ __device__ __forceinline__ void encrypt_ct(const EncArgs& a, int p, u64 seed, u6
         }
         return;
     }
+    // one transform at a time: a block barrier is needed only between two inverse transforms
+    // (with v^ kept, the second product's), as in the lockstep form above
     for (int l = 0; l < L; ++l) {
         const u64 q = a.rns.q[l];
         const ModTables t = a.rns.tab[l];
@@ -360,8 +362,7 @@ __device__ __forceinline__ void encrypt_ct(const EncArgs& a, int p, u64 seed, u6
             } else {
 #pragma unroll
                 for (int e = 0; e < E; ++e) r[0][e] = small_mod(sv[x0 + elem_offset<LOGN, 0, E>(e)], q);
-                __syncthreads();
-                ntt_fwd_regs<LOGN, 1, true, false, E>(smem, r, tid, t, q);
+                ntt_fwd_regs<LOGN, 1, true, false, E>(smem, r, tid, t, q);   // after an inverse: no barrier
                 if constexpr (KEEP_VHAT) {
 #pragma unroll
                     for (int e = 0; e < E; ++e) vh[e] = r[0][e];
@@ -373,7 +374,7 @@ __device__ __forceinline__ void encrypt_ct(const EncArgs& a, int p, u64 seed, u6
                 const ulonglong2 w = __ldg(pk + elem_offset<LOGN, LAST, E>(e));
                 r[0][e] = shoup_lazy(r[0][e], w.x, w.y, q);
             }
-            __syncthreads();
+            if (KEEP_VHAT && pb == 1) __syncthreads();   // an inverse right after an inverse
             ntt_inv_regs<LOGN, 1, false, E>(smem, r, tid, t, q);
             const int8_t* noise = (pb == 0 ? se0 : se1) + x0;
             u64* dst = ct + ((u64)pb * L + l) * N + x0;
