@@ -6,12 +6,20 @@
 // residues (E = 16 or 8) per polynomial in registers. The log2(N) butterfly stages run in
 // passes of up to log2(E) stages (a radix-E step entirely in registers); between passes the
 // block exchanges data through one shared-memory buffer of N words per polynomial,
-// XOR-swizzled so that every pass reads and writes without bank conflicts (checked by
-// simulating every pass of N = 2^10 .. 2^14): x ^ ((x >> 4) & 15) for E = 16,
+// XOR-swizzled so that every pass reads and writes without bank conflicts (the host-compiled
+// layout test checks every pass of N = 2^10 .. 2^14): x ^ ((x >> 4) & 15) for E = 16,
 // x ^ ((x >> 2) & 7) ^ ((x >> 3) & 15) for E = 8. E = 8 halves the registers a polynomial
 // takes, so twice the threads fit on an SM, at the price of one more exchange per transform.
-// NP polynomials over the same modulus can be transformed in lockstep: each twiddle pair is
-// loaded once for all of them and the block barriers are shared.
+// An exchange whose two layouts give every warp the same residues takes a warp barrier
+// instead of a block barrier (the later passes of a transform). NP polynomials over the same
+// modulus can be transformed in lockstep: each twiddle pair is loaded once for all of them and
+// the barriers are shared.
+//
+// Between transforms on the same buffer: a forward transform's first exchange stores to its
+// thread's pass-0 slots and its last exchange loads the thread's last-pass slots; an inverse
+// does the reverse. So a forward after an inverse (or an inverse after a forward) overwrites
+// only slots its own thread loaded last and needs no block barrier before it; two transforms
+// of the same direction in a row do.
 //
 // Forward: Cooley-Tukey with the negacyclic twist merged into the twiddles, natural-order
 // input, bit-reversed output; inputs in [0, q), outputs in [0, 4q) (Harvey's lazy bounds).
@@ -396,7 +404,8 @@ __device__ __forceinline__ void inv_regs_rt(u64 (&r)[NP][E], int tid, int S0, in
 // Whole forward transform of NP polynomials, input already in registers in the layout of
 // pass 0 (values in [0, 4q); with TERNARY0, residues of a ternary polynomial); output in
 // registers in the layout of the last pass. `sm` holds NP buffers of N words. The caller must
-// make sure no thread still reads `sm` from an earlier use (a __syncthreads before the call).
+// make sure no thread still reads `sm` from an earlier use other than an inverse transform's
+// (a __syncthreads before the call; see the header comment).
 // Passes: LOGN / LE full passes, then one pass of the remaining LOGN % LE stages.
 // COMPACT runs the full passes through one runtime loop (one copy of the pass code); otherwise
 // every pass is unrolled with its position known at compile time, which needs fewer address
