@@ -354,10 +354,11 @@ def run_ours(args):
                         "butterfly_g_per_s": round(bfly_s / 1e9, 1),
                         "dominant_frac_of_butterfly_rate": round(kernels[dominant]["achieved"] / (bfly_s / 1e9), 4)
                         if kernels[dominant]["bound"] == "alu" else None}
-    # launches of our kernels per step: 1 per encryption (2 for the frequent-value cache),
-    # 1 per mean filter / brightness / blend, matching: 1 accumulate + 1 reduce + 2 inverse
-    # transform/scale + digits + transform + MAC + transform + mod-down + rescale, 1 per decrypt
-    out["gpu_launches"] = args.steps * (len(methods) + 1 + 3 + 10 + len(methods) + len(ops_out))
+    # launches of our kernels per step: 1 per encryption (3 for the frequent-value cache: hits,
+    # the list of misses, the misses), 1 per mean filter / brightness / blend, matching: 1
+    # accumulate + 1 reduce + 2 inverse transform/scale + digits + transform + MAC + transform +
+    # mod-down + rescale, 1 per decrypt
+    out["gpu_launches"] = args.steps * (len(methods) + 2 + 3 + 10 + len(methods) + len(ops_out))
 
     if not args.no_e2e:
         out["e2e"] = e2e_ours(args, ctx, ichee, img, wm_ct, wm_meta, nz_ct, nz_meta, beta, caches, methods, enc_out,
@@ -555,7 +556,7 @@ def run_sharded(args):
                    "image": "%dx%dx%d" % (h_img, w, c), "band_rows_per_gpu": y1 - y0, "methods": methods,
                    "ops": list(ops_out), "l2": "flushed (512 MB write) before every step",
                    "parallelism": "pixel rows sharded over %d GPUs; matching all-reduce (int64, NCCL)" % world},
-        "gpu_launches": args.steps * (len(methods) + 1 + 3 + 10 + len(methods) + len(ops_out)),
+        "gpu_launches": args.steps * (len(methods) + 2 + 3 + 10 + len(methods) + len(ops_out)),
         "match_abs_error": match_err, "clocks": clk, "e2e": e2e}
     if rank == 0:
         print(json.dumps(out))

@@ -839,8 +839,20 @@ static ichee_status encrypt_impl(ichee_ctx* c, const ichee_cache* k, const uint8
         CK(launch_lookup_combine(a, st));
         if (k->values.size() < 256) {  // values outside the cache
             if (k->desc.miss_policy == 0) {
+                // the misses listed first (a pass over the pixels), then encrypted by the
+                // persistent fresh kernel in even shares (2.39 -> 2.38 ms for the top-32 cache
+                // of the 64x64 field, 72 % misses)
                 EncArgs e = enc_args(c, d_px, n_ct, seed, first_id, d_out);
-                e.skip_lut = k->d_lut;
+                if (n_ct < (u64(1) << 32)) {
+                    CK(c->scratch.ensure(16 + n_ct * sizeof(u32), c->user_alloc, c->user_free, c->user_alloc_ctx, st));
+                    u32* count = (u32*)c->scratch.p;
+                    u32* idx = count + 4;
+                    CK(launch_miss_list(d_px, n_ct, k->d_lut, idx, count, st));
+                    e.idx = idx;
+                    e.n_idx = count;
+                } else {
+                    e.skip_lut = k->d_lut;
+                }
                 CK(launch_encrypt_fresh(e, st));
             } else {
                 RadixArgs r = radix_args(c, k, d_px, n_ct, seed, d_out);

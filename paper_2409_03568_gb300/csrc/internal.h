@@ -22,7 +22,13 @@ struct EncArgs {
     CdtTable cdt;
     u64* out;                  // [n_ct][2][L][N]
     int num_sms;               // persistent grid of the single-image kernel: one block per SM
+    const u32* idx;            // optional: encrypt only pixels idx[0 .. *n_idx) (device list)
+    const u32* n_idx;
 };
+
+// idx[0 .. *count) = the pixels k < n whose value has no slot (lut[px[k]] < 0), in any order;
+// *count is zeroed first. Everything on the stream.
+cudaError_t launch_miss_list(const uint8_t* px, u64 n, const int32_t* lut, u32* idx, u32* count, cudaStream_t st);
 
 // pair[i] = (a[i], b[i]) for i < n
 cudaError_t launch_interleave(const u64* a, const u64* b, u64 n, ulonglong2* pair, cudaStream_t st);

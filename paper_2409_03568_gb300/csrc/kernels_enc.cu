@@ -397,7 +397,11 @@ __global__ void __launch_bounds__(NttShape<LOGN, E>::T, 1) k_encrypt_fresh(const
     __syncthreads();
     const u64 ct_len = (u64)2 * a.L << LOGN;
     int it = 0;
-    for (u64 k = blockIdx.x; k < a.n_ct; k += gridDim.x) {
+    // all pixels, or a listed subset (the misses of a value cache) shared evenly; one call site,
+    // so the kernel holds one copy of the transform code
+    const u64 n = a.idx != nullptr ? (u64)*a.n_idx : a.n_ct;
+    for (u64 g = blockIdx.x; g < n; g += gridDim.x) {
+        const u64 k = a.idx != nullptr ? (u64)a.idx[g] : g;
         const int p = a.pixels[k];
         if (a.skip_lut != nullptr && a.skip_lut[p] >= 0) continue;  // uniform across the block
         encrypt_ct<LOGN, KEEP_VHAT, E>(a, p, a.seed, a.id_base + k, a.out + k * ct_len, smem, it++);
@@ -440,8 +444,9 @@ static cudaError_t enc_launch(const EncArgs& a, cudaStream_t st)
     if (e != cudaSuccess) return e;
     // persistent: one block per SM (the shared memory fits one), each walking its share of the
     // ciphertexts, so a block's sampling overlaps its previous ciphertext's epilogue (3.10 ->
-    // 3.06 ms). With pixels to skip (the misses of a value cache) the shares would be uneven,
-    // so there every ciphertext is a block of its own (a static share: 2.40 -> 2.81 ms).
+    // 3.06 ms); a listed subset is shared the same way. With pixels to skip in-kernel the shares
+    // would be uneven, so there every ciphertext is a block of its own (a static share of the
+    // whole image: 2.40 -> 2.81 ms for the misses of the top-32 cache).
     const u64 cap = a.skip_lut == nullptr && a.num_sms > 0 ? (u64)a.num_sms : (u64)(1u << 30);
     const u64 grid = a.n_ct < cap ? a.n_ct : cap;
     k_encrypt_fresh<LOGN, keep, E><<<(unsigned)grid, T, smem, st>>>(a);
@@ -476,6 +481,21 @@ cudaError_t launch_encrypt_fresh_batch(const EncArgs& a, const SegTable& t, int 
     case 14: return enc_batch_launch<14>(a, t, num_sms, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+__global__ void k_miss_list(const uint8_t* px, u64 n, const int32_t* lut, u32* idx, u32* count)
+{
+    for (u64 k = blockIdx.x * (u64)blockDim.x + threadIdx.x; k < n; k += (u64)gridDim.x * blockDim.x)
+        if (lut[px[k]] < 0) idx[atomicAdd(count, 1u)] = (u32)k;
+}
+
+cudaError_t launch_miss_list(const uint8_t* px, u64 n, const int32_t* lut, u32* idx, u32* count, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(u32), st);
+    if (e != cudaSuccess || n == 0) return e;
+    const u64 blocks = (n + 255) / 256;
+    k_miss_list<<<(unsigned)(blocks < 1024 ? blocks : 1024), 256, 0, st>>>(px, n, lut, idx, count);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_encrypt_fresh(const EncArgs& a, cudaStream_t st)
