@@ -79,6 +79,9 @@ struct SegTable {
     double* dout[kMaxSegs];           // decoded output (decryption)
     u64 seed[kMaxSegs];
     uint32_t h[kMaxSegs], w[kMaxSegs], c[kMaxSegs], c1[kMaxSegs];
+    // mean filter of a band: output rows y0 .. y0 + rows - 1 (rows = 0: the whole image), the
+    // input holding the image's rows from row0 on
+    uint32_t y0[kMaxSegs], rows[kMaxSegs], row0[kMaxSegs];
     double scale[kMaxSegs];
     u64 kadd[kMaxSegs][kMaxPrimes];   // per-segment plaintext constant residues
 };
