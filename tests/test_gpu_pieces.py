@@ -74,7 +74,23 @@ def test_pixel_ranges_equal_whole_image(ichee, ring):
 
 
 def test_meanfilter_row_bands_equal_whole_image(ichee, ring):
-    ctx, o = ring
+    check_meanfilter_bands(ichee, *ring)
+
+
+def test_meanfilter_row_bands_five_limbs(ichee):
+    """Five limbs: whole images and bands run the batched filter kernel as one-image batches."""
+    ring5 = dict(RING, prime_bits=[60, 40, 40, 40, 40])
+    ctx = ichee.Context(**ring5)
+    ctx.keygen(KEY_SEED)
+    o = Oracle(Params(ring5["log_n"], ring5["prime_bits"], ring5["log2_scale"], ring5["special_bits"]))
+    o.keygen(KEY_SEED)
+    try:
+        check_meanfilter_bands(ichee, ctx, o)
+    finally:
+        ctx.close()
+
+
+def check_meanfilter_bands(ichee, ctx, o):
     h, w, c = 7, 5, 3
     img = inputs.random_field_image(h, w, seed=9, channels=c).reshape(-1)
     row = w * c
