@@ -31,6 +31,10 @@
  *    values), never on launch shape or batch composition. Random draws come from
  *    Philox4x32-10 keyed by the seed, countered by (block, stream, ciphertext id).
  *  - Threads: one context may be used from one host thread at a time.
+ *  - Streams: a context's working memory (below) is shared by its calls, so calls of one
+ *    context that use it -- matching, the per-pixel squared difference, frequent-value
+ *    encryption with fresh misses, host-buffer staging -- must be ordered on the device (one
+ *    stream per context, or events between streams).
  */
 #ifndef ICHEE_H
 #define ICHEE_H
@@ -162,8 +166,9 @@ ichee_status ichee_keygen(ichee_ctx* ctx, uint64_t seed, uint32_t flags, void* s
 
 /*
  * Working-memory allocator. By default the library takes the device memory it needs during a
- * call (scratch of matching and of the per-pixel squared difference, staging of host buffers,
- * per-ciphertext constant tables) from cudaMalloc and keeps it for later calls. After
+ * call (scratch of matching and of the per-pixel squared difference, the list of misses of a
+ * frequent-value cache, staging of host buffers, per-ciphertext constant tables) from
+ * cudaMalloc and keeps it for later calls. After
  * ichee_set_allocator those buffers come from alloc(bytes, stream, user), which must return
  * device memory of the context's device usable by work on `stream` (NULL: out of memory, the
  * call fails with ICHEE_ENOMEM), and go back through free_fn(ptr, stream, user), after which the
