@@ -224,11 +224,15 @@ def run_ours(args):
         return f
 
     def p_decrypt():
+        # one batched decryption per level: the encryptions and brightness keep every limb, the
+        # rescaled outputs (mean filter, blend, match) one fewer
         def f():
-            for k in methods:
-                ichee.ichee_decrypt_image(H, enc_out[k], metas[k], dec_out[k], st)
-            for k in ops_out:
-                ichee.ichee_decrypt_image(H, ops_out[k], metas[k], dec_out[k], st)
+            groups = {}
+            for k in methods + list(ops_out):
+                groups.setdefault(metas[k].level, []).append(k)
+            for ks in groups.values():
+                ichee.ichee_decrypt_batch(H, [enc_out[k] if k in enc_out else ops_out[k] for k in ks],
+                                          [metas[k] for k in ks], [dec_out[k] for k in ks], st)
         return f
 
     phases = [(m, p_encrypt(m)) for m in methods] + [
@@ -317,7 +321,7 @@ def run_ours(args):
     rl_hbm("brightness", n_px * 2 * ct_bytes)
     rl_hbm("blend", n_px * (2 * ct_bytes + 2 * (L - 1) * n * 8))
     rl_alu("match", n_px * L * (2 * (n // 2) * logn + 3 * n))
-    n_dec = len(methods) * n_px * L * n * 8 + n_px * ((L - 1) * n * 8) * 3
+    n_dec = sum(metas[k].n_ct * (metas[k].level + 1) * n * 8 for k in methods + list(ops_out))
     rl_hbm("decrypt", n_dec)
     dominant = max((k for k in kernels if "frac" in kernels[k]), key=lambda k: phase_ms[k])
     roof = dict(kernels[dominant])
@@ -357,8 +361,9 @@ def run_ours(args):
     # launches of our kernels per step: 1 per encryption (3 for the frequent-value cache: hits,
     # the list of misses, the misses), 1 per mean filter / brightness / blend, matching: 1
     # accumulate + 1 reduce + 2 inverse transform/scale + digits + transform + MAC + transform +
-    # mod-down + rescale, 1 per decrypt
-    out["gpu_launches"] = args.steps * (len(methods) + 2 + 3 + 10 + len(methods) + len(ops_out))
+    # mod-down + rescale, 1 batched decryption per level
+    n_levels = len({metas[k].level for k in methods + list(ops_out)})
+    out["gpu_launches"] = args.steps * (len(methods) + 2 + 3 + 10 + n_levels)
 
     if not args.no_e2e:
         out["e2e"] = e2e_ours(args, ctx, ichee, img, wm_ct, wm_meta, nz_ct, nz_meta, beta, caches, methods, enc_out,
@@ -467,11 +472,13 @@ def run_sharded(args):
         metas["match"] = shard.sharded_match(ichee, ctx, band_fresh, m_band, nz_ct, m_band, acc, ops_out["match"],
                                              stream=st)
 
-    def p_decrypt():
-        for k in methods:
-            ichee.ichee_decrypt_image(H, enc_out[k], metas[k], dec_out[k], st)
-        for k in ops_out:
-            ichee.ichee_decrypt_image(H, ops_out[k], metas[k], dec_out[k], st)
+    def p_decrypt():   # one batched decryption per level, as in the one-GPU step
+        groups = {}
+        for k in methods + list(ops_out):
+            groups.setdefault(metas[k].level, []).append(k)
+        for ks in groups.values():
+            ichee.ichee_decrypt_batch(H, [enc_out[k] if k in enc_out else ops_out[k] for k in ks],
+                                      [metas[k] for k in ks], [dec_out[k] for k in ks], st)
 
     phases = [(m, p_encrypt(m)) for m in methods] + [
         ("meanfilter3", p_meanfilter), ("brightness", p_op("brightness", ichee.OP_BRIGHTNESS, op_args=(beta,))),
@@ -556,7 +563,7 @@ def run_sharded(args):
                    "image": "%dx%dx%d" % (h_img, w, c), "band_rows_per_gpu": y1 - y0, "methods": methods,
                    "ops": list(ops_out), "l2": "flushed (512 MB write) before every step",
                    "parallelism": "pixel rows sharded over %d GPUs; matching all-reduce (int64, NCCL)" % world},
-        "gpu_launches": args.steps * (len(methods) + 2 + 3 + 10 + len(methods) + len(ops_out)),
+        "gpu_launches": args.steps * (len(methods) + 2 + 3 + 10 + len({metas[k].level for k in methods + list(ops_out)})),
         "match_abs_error": match_err, "clocks": clk, "e2e": e2e}
     if rank == 0:
         print(json.dumps(out))

@@ -832,7 +832,20 @@ static ichee_status encrypt_impl(ichee_ctx* c, const ichee_cache* k, const uint8
     } else if (k->desc.kind == ICHEE_CACHE_RADIX) {
         RadixArgs r = radix_args(c, k, d_px, n_ct, seed, d_out);
         r.id_base = first_id;
-        CK(launch_radix_combine(r, st));
+        if (first_id == 0) {
+            // a whole image runs the batched kernel as a one-image batch (same words; the 64x64
+            // image at N = 8192: radix 16 0.319 -> 0.290 ms, radix 10 0.325 -> 0.297 ms)
+            SegTable t;
+            std::memset(&t, 0, sizeof(t));
+            t.n = 1;
+            t.start[1] = n_ct;
+            t.px[0] = d_px;
+            t.out[0] = d_out;
+            t.seed[0] = seed;
+            CK(launch_radix_combine_batch(r, t, c->shape_radix, c->num_sms, st));
+        } else {
+            CK(launch_radix_combine(r, st));
+        }
     } else {
         LookupArgs a = lookup_args(c, k, d_px, n_ct, seed, d_out);
         a.id_base = first_id;
