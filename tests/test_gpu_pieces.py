@@ -184,11 +184,11 @@ def test_fused_rescale_general_constants(ichee):
     ctx.close()
 
 
-@pytest.mark.parametrize("shape", [(6, 5, 3), (1, 9, 1), (9, 1, 2)])
+@pytest.mark.parametrize("shape", [(6, 5, 3), (1, 9, 1), (9, 1, 2), (4, 64, 1), (3, 37, 3)])
 def test_meanfilter_forms_agree_with_the_oracle(ichee, ring, shape):
     """Both forms of the mean filter (register walk; input columns staged in shared memory by
     bulk copies), single-image and batched, give the oracle's ciphertexts; also one-row and
-    one-column images."""
+    one-column images, and wider rows (64 and 37 columns)."""
     ctx, o = ring
     h, w, c = shape
     img = inputs.random_field_image(h, w, seed=14, channels=c).reshape(-1)
