@@ -271,8 +271,11 @@ cudaError_t launch_reduce_rows(const RnsArgs& rns, int rows, int limbs, const u6
 //      part and (INTT(acc_b) - [acc_b mod P]) P^{-1} is the relinearised limb m;
 //   3. the relinearised limb q_t is kept; every other limb is rescaled against it and stored.
 // That is L^2 + 5L + 2 transforms per pixel (t2 is the only tensor limb inverse-transformed,
-// and no digit is transformed back into its own modulus), all in the compact pass form so the
-// chain fits the instruction cache.
+// and no digit is transformed back into its own modulus). They run in one loop over a per-pixel
+// schedule (one word per transform, in shared memory) with one call site per direction, so the
+// transform code with every pass unrolled appears twice and fits the instruction cache (four
+// unrolled call sites did not; the compact pass loop in this schedule took 15.0 ms for 4096
+// pixels at N = 2^13, the unrolled passes 12.6 ms, the compact loop at four call sites 13.9).
 // A transform's first exchange stores to the slots of its thread in pass 0 (forward) or in the
 // last pass (inverse), and its last exchange loads the slots of the other end, so a block
 // barrier is needed only between two transforms of the same direction: after a forward, an
@@ -286,13 +289,21 @@ cudaError_t launch_reduce_rows(const RnsArgs& rns, int rows, int limbs, const u6
 // them in shared memory instead was slower, because the larger carve-out leaves too little
 // L1 for the twiddle tables.
 // ---------------------------------------------------------------------------------------
+// Transform kinds of the per-pixel schedule.
+constexpr u32 kFwdDiff = 0, kInvT2 = 1, kFwdDigit = 2, kInvAcc = 3;
+
 template <int LOGN, int E>
 __global__ void __launch_bounds__(NttShape<LOGN, E>::T) k_sqdiff_image(const __grid_constant__ SqImgArgs a)
 {
     constexpr int N = 1 << LOGN;
     constexpr int T = NttShape<LOGN, E>::T;
     constexpr int LAST = NttShape<LOGN, E>::LAST;
+    // transforms with every pass unrolled up to N = 2^13 (one call site per direction, so the
+    // code fits the instruction cache), the compact pass loop at 2^14 (registers)
+    constexpr bool CMP = LOGN >= 14;
+    constexpr bool WT = !CMP;   // the last-pass layout of the unrolled form keeps a warp's groups adjacent
     extern __shared__ u64 sm[];
+    u32* sched = reinterpret_cast<u32*>(sm + N);
     const int tid = threadIdx.x;
     const int limbs = a.limbs, L = a.L;
     const int t = limbs - 1;
@@ -303,128 +314,157 @@ __global__ void __launch_bounds__(NttShape<LOGN, E>::T) k_sqdiff_image(const __g
     u64* AP = S + (size_t)3 * limbs * N;  // [2] accumulators modulo P, then their inverse transforms
     const u64 P = a.rns.q[L];
     const u64 halfP = (P - 1) / 2;
+    // The transforms of one pixel in order, one word each: kind (bits 0-1), polynomial (2), limb
+    // or digit (3-6), target modulus (7-10, 15 = P), barrier before the transform (11), first
+    // term of the P accumulators (12). A barrier is needed only between two transforms of the
+    // same direction (see above).
+    if (tid == 0) {
+        int n = 0;
+        auto push = [&](u32 kind, u32 pb, u32 x, u32 mm, u32 bar, u32 first) {
+            sched[n++] = kind | (pb << 2) | (x << 3) | (mm << 7) | (bar << 11) | (first << 12);
+        };
+        for (int l = 0; l < limbs; ++l) {
+            push(kFwdDiff, 0, l, 0, 0, 0);
+            push(kFwdDiff, 1, l, 0, 1, 0);
+            push(kInvT2, 0, l, 0, 0, 0);
+        }
+        for (int step = 0; step <= limbs; ++step) {
+            const int m = step == 0 ? -1 : (step == 1 ? t : step - 2);
+            const u32 mm = m < 0 ? 15u : (u32)m;
+            bool first = true;
+            for (int j = 0; j < limbs; ++j) {
+                if (j == m) continue;   // digit m's term went in with t_b^ in the first phase
+                push(kFwdDigit, 0, j, mm, first ? 0 : 1, m < 0 && j == 0 ? 1 : 0);
+                first = false;
+            }
+            push(kInvAcc, 0, 0, mm, 0, 0);
+            push(kInvAcc, 1, 0, mm, 1, 0);
+        }
+    }
+    __syncthreads();
+    const int n_ops = limbs * limbs + 5 * limbs + 2;
     for (u64 k = blockIdx.x; k < a.n_ct; k += gridDim.x) {
         const u64* A = a.a + k * 2 * (u64)limbs * N;
         const u64* B = a.b + k * 2 * (u64)limbs * N;
         u64 r[1][E];
 #pragma unroll 1
-        for (int l = 0; l < limbs; ++l) {
-            const u64 q = a.rns.q[l];
-            u64* t0 = T0 + (size_t)l * N;
-            u64* t1 = T1 + (size_t)l * N;
-            u64* t2 = T2 + (size_t)l * N;
-#pragma unroll 1
-            for (int pb = 0; pb < 2; ++pb) {
-                const u64* pa = A + ((u64)pb * limbs + l) * N;
-                const u64* pq = B + ((u64)pb * limbs + l) * N;
+        for (int op = 0; op < n_ops; ++op) {
+            const u32 code = sched[op];
+            const u32 kind = code & 3u;
+            const int pb = (int)((code >> 2) & 1u), x = (int)((code >> 3) & 15u);
+            const int m = ((code >> 7) & 15u) == 15u ? -1 : (int)((code >> 7) & 15u);
+            const int mod = kind == kFwdDiff || kind == kInvT2 ? x : (m < 0 ? L : m);
+            const u64 q = a.rns.q[mod];
+            if (kind == kFwdDiff || kind == kFwdDigit) {
+                if (kind == kFwdDiff) {   // d = a - b, polynomial pb of limb x
+                    const u64* pa = A + ((u64)pb * limbs + x) * N;
+                    const u64* pq = B + ((u64)pb * limbs + x) * N;
 #pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const int x = elem_index<LOGN, 0, E>(tid, e);
-                    r[0][e] = sub_mod(__ldcs(pa + x), __ldcs(pq + x), q);
-                }
-                if (pb == 1) __syncthreads();   // after a forward transform (see below)
-                ntt_fwd_regs<LOGN, 1, false, true, E>(sm, r, tid, a.rns.tab[l], q);
-                u64* dst = pb == 0 ? t0 : t2;
+                    for (int e = 0; e < E; ++e) {
+                        const int xi = elem_index<LOGN, 0, E>(tid, e);
+                        r[0][e] = sub_mod(__ldcs(pa + xi), __ldcs(pq + xi), q);
+                    }
+                } else {                  // digit x of t2, centered, lifted to the modulus
+                    const u64 mu = a.rns.mu[mod];
+                    const u64 qj = a.rns.q[x];
+                    const u64 half = (qj - 1) / 2;
+                    const u64* t2 = T2 + (size_t)x * N;
 #pragma unroll
-                for (int e = 0; e < E; ++e) dst[e * T] = csub(csub(r[0][e], 2 * q), q);
-            }
-            const u64 qinv = a.rns.qinv[l];   // Montgomery products: 2^64 is folded into ninv, pn and r64
-            const u64* e0 = a.evk_hat + (((size_t)l * 2 + 0) * (L + 1) + l) * N;
-            const u64* e0p = a.evk_hat_p + (((size_t)l * 2 + 0) * (L + 1) + l) * N;
-            const u64* e1 = a.evk_hat + (((size_t)l * 2 + 1) * (L + 1) + l) * N;
-            const u64* e1p = a.evk_hat_p + (((size_t)l * 2 + 1) * (L + 1) + l) * N;
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int x = elem_index<LOGN, LAST, E, false>(tid, e);
-                const u64 d0 = t0[e * T], d1 = t2[e * T];
-                const u64 m2 = mont_mul(d1, d1, q, qinv);
-                const u64 th = shoup(m2, a.r64[l], a.r64_p[l], q);   // d1^2, the transform of digit l
-                const u64 c = mont_mul(d0, d1, q, qinv);
-                t0[e * T] = add_mod(shoup(mont_mul(d0, d0, q, qinv), a.pn[l], a.pn_p[l], q),
-                                    shoup(th, __ldg(e0 + x), __ldg(e0p + x), q), q);
-                t1[e * T] = add_mod(shoup(add_mod(c, c, q), a.pn[l], a.pn_p[l], q),
-                                    shoup(th, __ldg(e1 + x), __ldg(e1p + x), q), q);
-                r[0][e] = shoup(m2, a.ninv[l], a.ninv_p[l], q);
-            }
-            ntt_inv_regs<LOGN, 1, true, E>(sm, r, tid, a.rns.tab[l], q);
-#pragma unroll
-            for (int e = 0; e < E; ++e) t2[e * T] = csub(r[0][e], q);
-        }
-#pragma unroll 1
-        for (int step = 0; step <= limbs; ++step) {
-            const int m = step == 0 ? -1 : (step == 1 ? t : step - 2);   // -1: the special prime
-            const int mod = m < 0 ? L : m;
-            const u64 q = a.rns.q[mod], mu = a.rns.mu[mod];
-            u64* acc0 = m < 0 ? AP : T0 + (size_t)m * N;    // started in step 1 (m != P)
-            u64* acc1 = m < 0 ? AP + N : T1 + (size_t)m * N;
-            bool first = true;
-#pragma unroll 1
-            for (int j = 0; j < limbs; ++j) {
-                if (j == m) continue;   // digit m's term went in with t_b^ in step 1
-                const u64 qj = a.rns.q[j];
-                const u64 half = (qj - 1) / 2;
-                const u64* t2 = T2 + (size_t)j * N;
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const u64 v = t2[e * T];
-                    if (v <= half) {
-                        r[0][e] = reduce64(v, q, mu);
-                    } else {
-                        const u64 mag = reduce64(qj - v, q, mu);
-                        r[0][e] = mag == 0 ? 0 : q - mag;
+                    for (int e = 0; e < E; ++e) {
+                        const u64 v = t2[e * T];
+                        if (v <= half) {
+                            r[0][e] = reduce64(v, q, mu);
+                        } else {
+                            const u64 mag = reduce64(qj - v, q, mu);
+                            r[0][e] = mag == 0 ? 0 : q - mag;
+                        }
                     }
                 }
-                if (!first) __syncthreads();   // after a forward transform
-                first = false;
-                ntt_fwd_regs<LOGN, 1, false, true, E>(sm, r, tid, a.rns.tab[mod], q);
-                const u64* e0 = a.evk_hat + (((size_t)j * 2 + 0) * (L + 1) + mod) * N;
-                const u64* e0p = a.evk_hat_p + (((size_t)j * 2 + 0) * (L + 1) + mod) * N;
-                const u64* e1 = a.evk_hat + (((size_t)j * 2 + 1) * (L + 1) + mod) * N;
-                const u64* e1p = a.evk_hat_p + (((size_t)j * 2 + 1) * (L + 1) + mod) * N;
+                if ((code >> 11) & 1u) __syncthreads();
+                ntt_fwd_regs<LOGN, 1, false, CMP, E>(sm, r, tid, a.rns.tab[mod], q);
+                if (kind == kFwdDiff) {
+                    u64* dst = (pb == 0 ? T0 : T2) + (size_t)x * N;
 #pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const int x = elem_index<LOGN, LAST, E, false>(tid, e);
-                    const u64 d = csub(csub(r[0][e], 2 * q), q);
-                    const u64 p0 = shoup(d, __ldg(e0 + x), __ldg(e0p + x), q);
-                    const u64 p1 = shoup(d, __ldg(e1 + x), __ldg(e1p + x), q);
-                    u64 s0 = 0, s1 = 0;   // the P accumulators start at digit 0
-                    if (m >= 0 || j > 0) {
-                        s0 = acc0[e * T];
-                        s1 = acc1[e * T];
+                    for (int e = 0; e < E; ++e) dst[e * T] = csub(csub(r[0][e], 2 * q), q);
+                } else {                  // acc_b(m) += NTT(digit) * evk^_x[b][m]
+                    u64* acc0 = m < 0 ? AP : T0 + (size_t)m * N;
+                    u64* acc1 = m < 0 ? AP + N : T1 + (size_t)m * N;
+                    const bool init = (code >> 12) & 1u;
+                    const u64* e0 = a.evk_hat + (((size_t)x * 2 + 0) * (L + 1) + mod) * N;
+                    const u64* e0p = a.evk_hat_p + (((size_t)x * 2 + 0) * (L + 1) + mod) * N;
+                    const u64* e1 = a.evk_hat + (((size_t)x * 2 + 1) * (L + 1) + mod) * N;
+                    const u64* e1p = a.evk_hat_p + (((size_t)x * 2 + 1) * (L + 1) + mod) * N;
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const int xi = elem_index<LOGN, LAST, E, WT>(tid, e);
+                        const u64 d = csub(csub(r[0][e], 2 * q), q);
+                        const u64 p0 = shoup(d, __ldg(e0 + xi), __ldg(e0p + xi), q);
+                        const u64 p1 = shoup(d, __ldg(e1 + xi), __ldg(e1p + xi), q);
+                        const u64 s0 = init ? 0 : acc0[e * T];
+                        const u64 s1 = init ? 0 : acc1[e * T];
+                        acc0[e * T] = add_mod(s0, p0, q);
+                        acc1[e * T] = add_mod(s1, p1, q);
                     }
-                    acc0[e * T] = add_mod(s0, p0, q);
-                    acc1[e * T] = add_mod(s1, p1, q);
                 }
-            }
-#pragma unroll 1
-            for (int pb = 0; pb < 2; ++pb) {
-                u64* acc = pb == 0 ? acc0 : acc1;
+            } else {
+                if (kind == kInvT2) {     // the tensor of limb x; t2 = INTT(d1^2) next
+                    u64* t0 = T0 + (size_t)x * N;
+                    u64* t1 = T1 + (size_t)x * N;
+                    const u64* t2 = T2 + (size_t)x * N;
+                    const u64 qinv = a.rns.qinv[x];   // Montgomery products: 2^64 is folded into ninv, pn and r64
+                    const u64* e0 = a.evk_hat + (((size_t)x * 2 + 0) * (L + 1) + x) * N;
+                    const u64* e0p = a.evk_hat_p + (((size_t)x * 2 + 0) * (L + 1) + x) * N;
+                    const u64* e1 = a.evk_hat + (((size_t)x * 2 + 1) * (L + 1) + x) * N;
+                    const u64* e1p = a.evk_hat_p + (((size_t)x * 2 + 1) * (L + 1) + x) * N;
 #pragma unroll
-                for (int e = 0; e < E; ++e) r[0][e] = acc[e * T];
-                if (pb == 1) __syncthreads();   // after an inverse transform
-                ntt_inv_regs<LOGN, 1, true, E>(sm, r, tid, a.rns.tab[mod], q);
-                if (m < 0) {
+                    for (int e = 0; e < E; ++e) {
+                        const int xi = elem_index<LOGN, LAST, E, WT>(tid, e);
+                        const u64 d0 = t0[e * T], d1 = t2[e * T];
+                        const u64 m2 = mont_mul(d1, d1, q, qinv);
+                        const u64 th = shoup(m2, a.r64[x], a.r64_p[x], q);   // d1^2, the transform of digit x
+                        const u64 c = mont_mul(d0, d1, q, qinv);
+                        t0[e * T] = add_mod(shoup(mont_mul(d0, d0, q, qinv), a.pn[x], a.pn_p[x], q),
+                                            shoup(th, __ldg(e0 + xi), __ldg(e0p + xi), q), q);
+                        t1[e * T] = add_mod(shoup(add_mod(c, c, q), a.pn[x], a.pn_p[x], q),
+                                            shoup(th, __ldg(e1 + xi), __ldg(e1p + xi), q), q);
+                        r[0][e] = shoup(m2, a.ninv[x], a.ninv_p[x], q);
+                    }
+                } else {
+                    const u64* acc = (m < 0 ? AP + (size_t)pb * N : (pb == 0 ? T0 : T1) + (size_t)m * N);
+#pragma unroll
+                    for (int e = 0; e < E; ++e) r[0][e] = acc[e * T];
+                }
+                if ((code >> 11) & 1u) __syncthreads();
+                ntt_inv_regs<LOGN, 1, CMP, E>(sm, r, tid, a.rns.tab[mod], q);
+                if (kind == kInvT2) {
+                    u64* t2 = T2 + (size_t)x * N;
+#pragma unroll
+                    for (int e = 0; e < E; ++e) t2[e * T] = csub(r[0][e], q);
+                } else if (m < 0) {
+                    u64* acc = AP + (size_t)pb * N;
 #pragma unroll
                     for (int e = 0; e < E; ++e) acc[e * T] = csub(r[0][e], q);
-                    continue;
-                }
-                const u64* last = (pb == 0 ? T0 : T1) + (size_t)t * N;
-                u64* o = a.out + ((k * 2 + pb) * (u64)t + m) * N;
+                } else {
+                    const u64 mu = a.rns.mu[mod];
+                    u64* acc = (pb == 0 ? T0 : T1) + (size_t)m * N;
+                    const u64* last = (pb == 0 ? T0 : T1) + (size_t)t * N;
+                    u64* o = a.out + ((k * 2 + pb) * (u64)t + m) * N;
 #pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const u64 ap = AP[(size_t)pb * N + e * T];
-                    u64 lp = reduce64(ap, q, mu);
-                    if (ap > halfP) lp = add_mod(lp, a.neg_p_mod[m], q);   // (ap - P) mod q_m
-                    const u64 md = shoup(sub_mod(csub(r[0][e], q), lp, q), a.p_inv[m], a.p_inv_p[m], q);
-                    if (m == t) {
-                        acc[e * T] = md;              // relinearised limb q_t, the rescale's divisor
-                    } else {
-                        const u64 ct = last[e * T];
-                        const u64 u = shoup_lazy(md, a.qt_inv[m], a.qt_inv_p[m], q);
-                        const u64 w = shoup_lazy(ct, a.qt_inv[m], a.qt_inv_p[m], q);
-                        u64 v = csub(csub(u + 2 * q - w, 2 * q), q);
-                        if (ct > a.half_qt) v = add_mod(v, 1, q);
-                        __stcs(o + elem_index<LOGN, 0, E>(tid, e), v);
+                    for (int e = 0; e < E; ++e) {
+                        const u64 ap = AP[(size_t)pb * N + e * T];
+                        u64 lp = reduce64(ap, q, mu);
+                        if (ap > halfP) lp = add_mod(lp, a.neg_p_mod[m], q);   // (ap - P) mod q_m
+                        const u64 md = shoup(sub_mod(csub(r[0][e], q), lp, q), a.p_inv[m], a.p_inv_p[m], q);
+                        if (m == t) {
+                            acc[e * T] = md;              // relinearised limb q_t, the rescale's divisor
+                        } else {
+                            const u64 ct = last[e * T];
+                            const u64 u = shoup_lazy(md, a.qt_inv[m], a.qt_inv_p[m], q);
+                            const u64 w = shoup_lazy(ct, a.qt_inv[m], a.qt_inv_p[m], q);
+                            u64 v = csub(csub(u + 2 * q - w, 2 * q), q);
+                            if (ct > a.half_qt) v = add_mod(v, 1, q);
+                            __stcs(o + elem_index<LOGN, 0, E>(tid, e), v);
+                        }
                     }
                 }
             }
@@ -440,7 +480,7 @@ template <int LOGN>
 static constexpr int kSqImgE = LOGN <= 13 ? 8 : 16;
 
 template <int LOGN>
-static size_t sqimg_smem() { return sizeof(u64) << LOGN; }
+static size_t sqimg_smem() { return (sizeof(u64) << LOGN) + 128 * sizeof(u32); }   // + the schedule
 
 template <int LOGN>
 static cudaError_t sqimg_prepare(int* blocks_per_sm)
