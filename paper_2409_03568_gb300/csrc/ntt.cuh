@@ -410,10 +410,10 @@ __device__ __forceinline__ void inv_regs_rt(u64 (&r)[NP][E], int tid, int S0, in
 // COMPACT runs the full passes through one runtime loop (one copy of the pass code); otherwise
 // every pass is unrolled with its position known at compile time, which needs fewer address
 // instructions but about LOGN / LE times the code. Both take a warp barrier for the exchanges
-// that stay inside every warp (exchange_in_warp). The compact form, used by the kernel that
-// chains 26 transforms, keeps the strided last-pass layout (WT = false; its callers index the
-// last pass with it) and a block barrier into it: there the warp-adjacent layout took more
-// registers (spills 8 -> 76 bytes) and time (14.3 -> 14.7 ms).
+// that stay inside every warp (exchange_in_warp). The compact form, used by the per-pixel
+// squared difference at N = 2^14 (where the unrolled passes spill), keeps the strided last-pass
+// layout (WT = false; its callers index the last pass with it) and a block barrier into it:
+// there the warp-adjacent layout took more registers (spills 8 -> 76 bytes) and time.
 template <int LOGN, int NP, bool TERNARY0 = false, bool COMPACT = false, int E = 16>
 __device__ __forceinline__ void ntt_fwd_regs(u64* sm, u64 (&r)[NP][E], int tid, const ModTables& t, u64 q)
 {
