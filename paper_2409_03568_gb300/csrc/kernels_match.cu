@@ -369,14 +369,22 @@ __global__ void __launch_bounds__(NttShape<LOGN, E>::T) k_sqdiff_image(const __g
                     const u64 qj = a.rns.q[x];
                     const u64 half = (qj - 1) / 2;
                     const u64* t2 = T2 + (size_t)x * N;
+                    if (qj <= q) {        // |digit| < q_j / 2 < q: no reduction
 #pragma unroll
-                    for (int e = 0; e < E; ++e) {
-                        const u64 v = t2[e * T];
-                        if (v <= half) {
-                            r[0][e] = reduce64(v, q, mu);
-                        } else {
-                            const u64 mag = reduce64(qj - v, q, mu);
-                            r[0][e] = mag == 0 ? 0 : q - mag;
+                        for (int e = 0; e < E; ++e) {
+                            const u64 v = t2[e * T];
+                            r[0][e] = v <= half ? v : q - (qj - v);
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < E; ++e) {
+                            const u64 v = t2[e * T];
+                            if (v <= half) {
+                                r[0][e] = reduce64(v, q, mu);
+                            } else {
+                                const u64 mag = reduce64(qj - v, q, mu);
+                                r[0][e] = mag == 0 ? 0 : q - mag;
+                            }
                         }
                     }
                 }
