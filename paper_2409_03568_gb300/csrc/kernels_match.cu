@@ -405,13 +405,14 @@ __global__ void __launch_bounds__(NttShape<LOGN, E>::T) k_sqdiff_image(const __g
 #pragma unroll
                     for (int e = 0; e < E; ++e) {
                         const int xi = elem_index<LOGN, LAST, E, WT>(tid, e);
+                        // the accumulators stay in [0, 2q): the inverse transform takes that range
                         const u64 d = csub(csub(r[0][e], 2 * q), q);
-                        const u64 p0 = shoup(d, __ldg(e0 + xi), __ldg(e0p + xi), q);
-                        const u64 p1 = shoup(d, __ldg(e1 + xi), __ldg(e1p + xi), q);
+                        const u64 p0 = shoup_lazy(d, __ldg(e0 + xi), __ldg(e0p + xi), q);
+                        const u64 p1 = shoup_lazy(d, __ldg(e1 + xi), __ldg(e1p + xi), q);
                         const u64 s0 = init ? 0 : acc0[e * T];
                         const u64 s1 = init ? 0 : acc1[e * T];
-                        acc0[e * T] = add_mod(s0, p0, q);
-                        acc1[e * T] = add_mod(s1, p1, q);
+                        acc0[e * T] = csub(s0 + p0, 2 * q);
+                        acc1[e * T] = csub(s1 + p1, 2 * q);
                     }
                 }
             } else {
@@ -431,10 +432,10 @@ __global__ void __launch_bounds__(NttShape<LOGN, E>::T) k_sqdiff_image(const __g
                         const u64 m2 = mont_mul(d1, d1, q, qinv);
                         const u64 th = shoup(m2, a.r64[x], a.r64_p[x], q);   // d1^2, the transform of digit x
                         const u64 c = mont_mul(d0, d1, q, qinv);
-                        t0[e * T] = add_mod(shoup(mont_mul(d0, d0, q, qinv), a.pn[x], a.pn_p[x], q),
-                                            shoup(th, __ldg(e0 + xi), __ldg(e0p + xi), q), q);
-                        t1[e * T] = add_mod(shoup(add_mod(c, c, q), a.pn[x], a.pn_p[x], q),
-                                            shoup(th, __ldg(e1 + xi), __ldg(e1p + xi), q), q);
+                        t0[e * T] = csub(shoup_lazy(mont_mul(d0, d0, q, qinv), a.pn[x], a.pn_p[x], q) +
+                                         shoup_lazy(th, __ldg(e0 + xi), __ldg(e0p + xi), q), 2 * q);
+                        t1[e * T] = csub(shoup_lazy(add_mod(c, c, q), a.pn[x], a.pn_p[x], q) +
+                                         shoup_lazy(th, __ldg(e1 + xi), __ldg(e1p + xi), q), 2 * q);
                         r[0][e] = shoup(m2, a.ninv[x], a.ninv_p[x], q);
                     }
                 } else {
