@@ -340,7 +340,8 @@ __device__ __forceinline__ void encrypt_ct(const EncArgs& a, int p, u64 seed, u6
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     const int x = elem_offset<LOGN, 0, E>(e);
-                    u64 v = add_mod(csub(rr[pb][e], q), small_mod(noise[x], q), q);
+                    u64 v = rr[pb][e] + (q + (u64)(i64)noise[x]);   // [q - 31, 3q + 31)
+                    v = csub(csub(v, 2 * q), q);
                     if (pb == 0 && x == 0 && x0 == 0) v = add_mod(v, a.dm[l * 256 + p], q);   // coefficient 0
                     __stcs(dst + x, v);
                 }
@@ -381,7 +382,8 @@ __device__ __forceinline__ void encrypt_ct(const EncArgs& a, int p, u64 seed, u6
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int x = elem_offset<LOGN, 0, E>(e);
-                u64 v = add_mod(csub(r[0][e], q), small_mod(noise[x], q), q);
+                u64 v = r[0][e] + (q + (u64)(i64)noise[x]);   // [q - 31, 3q + 31)
+                v = csub(csub(v, 2 * q), q);
                 if (pb == 0 && x == 0 && x0 == 0) v = add_mod(v, a.dm[l * 256 + p], q);   // coefficient 0
                 __stcs(dst + x, v);
             }
